@@ -1,0 +1,218 @@
+"""ctypes wrapper of the FP64 CPU oracle (test infrastructure only).
+
+Only the test suite, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` use this package.  It is independent of the CUDA library: it
+compiles ``irt_oracle.cpp`` with the host compiler and shares no code with
+``paper_2607_01338_b300``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "irt_oracle.cpp")
+_LIB = os.path.join(_HERE, "liboracle_irt.so")
+_lock = threading.Lock()
+_lib = None
+
+_dp = ctypes.POINTER(ctypes.c_double)
+_ip = ctypes.POINTER(ctypes.c_int)
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle (g++ -O2 -fopenmp, IEEE semantics, no fast-math)."""
+    if (not force and os.path.exists(_LIB)
+            and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)):
+        return _LIB
+    tmp = _LIB + f".tmp{os.getpid()}"
+    cmd = ["g++", "-O2", "-std=c++17", "-fopenmp", "-fPIC", "-shared",
+           "-fno-fast-math", "-ffp-contract=off", "-o", tmp, _SRC]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB)
+    return _LIB
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            L = ctypes.CDLL(build())
+            L.oracle_planck.restype = ctypes.c_double
+            L.oracle_planck.argtypes = [ctypes.c_double, ctypes.c_double]
+            L.oracle_partition.restype = ctypes.c_double
+            L.oracle_partition.argtypes = [_dp, ctypes.c_double]
+            L.oracle_profile.restype = ctypes.c_double
+            L.oracle_profile.argtypes = [_dp, ctypes.c_double, ctypes.c_double, ctypes.c_double]
+            L.oracle_sample_coeffs.restype = None
+            L.oracle_sample_coeffs.argtypes = [_dp, _dp, ctypes.c_double, ctypes.c_double,
+                                               ctypes.c_double, _dp]
+            L.oracle_ray.restype = None
+            L.oracle_ray.argtypes = ([_dp, _dp, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                      ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                      ctypes.c_int] + [_dp] * 5 + [ctypes.c_double] + [_dp] * 5)
+            L.oracle_ray_samples.restype = ctypes.c_int
+            L.oracle_ray_samples.argtypes = [ctypes.POINTER(_dp), ctypes.c_int, ctypes.c_int,
+                                             ctypes.c_int, ctypes.c_double, _dp, ctypes.c_int,
+                                             ctypes.c_int, ctypes.c_int, _dp, _dp]
+            L.oracle_render.restype = ctypes.c_int
+            L.oracle_render.argtypes = ([ctypes.POINTER(_dp), ctypes.c_int, ctypes.c_int,
+                                         ctypes.c_int, ctypes.c_double, _dp, _dp, _dp,
+                                         ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                         ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                         ctypes.c_double, ctypes.c_int, _ip] + [_dp] * 5)
+            L.oracle_loss_grad_zview.restype = ctypes.c_double
+            L.oracle_loss_grad_zview.argtypes = ([ctypes.POINTER(_dp), ctypes.c_int, ctypes.c_int,
+                                                  ctypes.c_int, ctypes.c_double, _dp, _dp,
+                                                  ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                                  ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                                  ctypes.c_double, _dp, ctypes.c_int, _ip,
+                                                  _dp, _dp, _dp])
+            L.oracle_num_threads.restype = ctypes.c_int
+            _lib = L
+    return _lib
+
+
+# --------------------------------------------------------------------------
+# argument packing
+# --------------------------------------------------------------------------
+LINE_KEYS = ("nu_ul_hz", "a_ul_s", "e_u_k", "b0_hz", "g_u", "g_l", "mass_amu", "t_inf_k",
+             "sigma_turb_kms")
+DUST_KEYS = ("kappa_cm2_per_g_gas", "mu_mass_per_h2_amu")
+FORMAL, SMOOTH = 0, 1
+TRJ, INTENSITY = 0, 1
+
+
+def _arr(vals):
+    a = np.ascontiguousarray(np.asarray(vals, dtype=np.float64))
+    return a, a.ctypes.data_as(_dp)
+
+
+def _line(line: dict):
+    return _arr([line[k] for k in LINE_KEYS])
+
+
+def _dust(dust: dict):
+    return _arr([dust[k] for k in DUST_KEYS])
+
+
+def _view(view):
+    return _arr([view.theta_rad, view.phi_rad, view.npx, view.npy, view.pixel_cm,
+                 view.trilinear])
+
+
+def _fields(fields):
+    arrs = [np.ascontiguousarray(np.asarray(a, dtype=np.float64)) for a in fields]
+    ptrs = (_dp * 5)(*[a.ctypes.data_as(_dp) for a in arrs])
+    return arrs, ptrs
+
+
+def num_threads() -> int:
+    return lib().oracle_num_threads()
+
+
+def planck(nu: float, T: float) -> float:
+    return lib().oracle_planck(nu, T)
+
+
+def partition(line: dict, T: float) -> float:
+    keep, p = _line(line)
+    return lib().oracle_partition(p, T)
+
+
+def profile_per_hz(line: dict, t_gas: float, v_los: float, u: float) -> float:
+    keep, p = _line(line)
+    return lib().oracle_profile(p, t_gas, v_los, u)
+
+
+def sample_coeffs(line: dict, dust: dict, n_h2: float, t_gas: float, x_tr: float) -> dict:
+    kl, pl = _line(line)
+    kd, pd = _dust(dust)
+    out = np.zeros(6)
+    lib().oracle_sample_coeffs(pl, pd, n_h2, t_gas, x_tr, out.ctypes.data_as(_dp))
+    return dict(n_u=out[0], n_l=out[1], jL=out[2], aL=out[3], aD=out[4], b_kms=out[5])
+
+
+def ray(line, dust, vaxis, samples, h, integration=SMOOTH, units=TRJ, t_bg=2.725):
+    """One ray from explicit samples: ``samples`` = dict of 1-D arrays
+    n_h2, t_gas, t_dust, v_los, x_tr in travel order.  Returns dict of
+    [nchan] arrays T, C, D, L, B."""
+    kl, pl = _line(line)
+    kd, pd = _dust(dust)
+    cols = [np.ascontiguousarray(np.asarray(samples[k], dtype=np.float64))
+            for k in ("n_h2", "t_gas", "t_dust", "v_los", "x_tr")]
+    K = len(cols[0])
+    nch = vaxis.nchan
+    outs = [np.zeros(nch) for _ in range(5)]
+    lib().oracle_ray(pl, pd, nch, vaxis.v_first_edge_kms, vaxis.dv_kms, vaxis.subsample_f,
+                     integration, units, t_bg, K, *[c.ctypes.data_as(_dp) for c in cols], h,
+                     *[o.ctypes.data_as(_dp) for o in outs])
+    return dict(zip("TCDLB", outs))
+
+
+def ray_samples(fields, cell_cm, view, px, py, kmax=100000):
+    shape = np.asarray(fields[0]).shape
+    nz, ny, nx = shape
+    arrs, ptrs = _fields(fields)
+    kv, pv = _view(view)
+    buf = np.zeros((min(kmax, 4 * (nx + ny + nz) + 8), 5))
+    h = np.zeros(1)
+    K = lib().oracle_ray_samples(ptrs, nx, ny, nz, cell_cm, pv, px, py, buf.shape[0],
+                                 h.ctypes.data_as(_dp), buf.ctypes.data_as(_dp))
+    return buf[:K].copy(), float(h[0])
+
+
+def render(fields, cell_cm, line, dust, view, vaxis, pixels, integration=SMOOTH, units=TRJ,
+           t_bg=2.725):
+    """Render the pixels ``pixels`` (int array [npix, 2] of (px, py)).
+    Returns dict of [npix, nchan] float64 arrays T, C, D, L, B."""
+    nz, ny, nx = np.asarray(fields[0]).shape
+    arrs, ptrs = _fields(fields)
+    kl, pl = _line(line)
+    kd, pd = _dust(dust)
+    kv, pv = _view(view)
+    pix = np.ascontiguousarray(np.asarray(pixels, dtype=np.int32).reshape(-1, 2))
+    npix = pix.shape[0]
+    nch = vaxis.nchan
+    outs = [np.zeros((npix, nch)) for _ in range(5)]
+    lib().oracle_render(ptrs, nx, ny, nz, cell_cm, pl, pd, pv, nch, vaxis.v_first_edge_kms,
+                        vaxis.dv_kms, vaxis.subsample_f, integration, units, t_bg, npix,
+                        pix.ctypes.data_as(_ip), *[o.ctypes.data_as(_dp) for o in outs])
+    return dict(zip("TCDLB", outs))
+
+
+def render_cube(fields, cell_cm, line, dust, view, vaxis, **kw):
+    """Whole cube, [nchan][npy][npx] per component."""
+    npx, npy = view.npx, view.npy
+    py, px = np.meshgrid(np.arange(npy), np.arange(npx), indexing="ij")
+    pix = np.stack([px.ravel(), py.ravel()], axis=1)
+    r = render(fields, cell_cm, line, dust, view, vaxis, pix, **kw)
+    return {k: v.reshape(npy, npx, -1).transpose(2, 0, 1).copy() for k, v in r.items()}
+
+
+def loss_grad_zview(fields, cell_cm, line, dust, vaxis, target_L, pixels=None,
+                    integration=SMOOTH, units=TRJ, t_bg=2.725):
+    """Loss = mean over all voxels of ([L] - target)^2 and its gradient with
+    respect to n_H2, T_gas, v_los (z view), by forward-mode dual numbers.
+    ``target_L`` is [nchan][ny][nx].  Returns (loss, g_n, g_t, g_v)."""
+    nz, ny, nx = np.asarray(fields[0]).shape
+    arrs, ptrs = _fields(fields)
+    kl, pl = _line(line)
+    kd, pd = _dust(dust)
+    tgt = np.ascontiguousarray(np.asarray(target_L, dtype=np.float64))
+    if pixels is None:
+        py, px = np.meshgrid(np.arange(ny), np.arange(nx), indexing="ij")
+        pixels = np.stack([px.ravel(), py.ravel()], axis=1)
+    pix = np.ascontiguousarray(np.asarray(pixels, dtype=np.int32).reshape(-1, 2))
+    gs = [np.zeros((nz, ny, nx)) for _ in range(3)]
+    loss = lib().oracle_loss_grad_zview(ptrs, nx, ny, nz, cell_cm, pl, pd, vaxis.nchan,
+                                        vaxis.v_first_edge_kms, vaxis.dv_kms,
+                                        vaxis.subsample_f, integration, units, t_bg,
+                                        tgt.ctypes.data_as(_dp), pix.shape[0],
+                                        pix.ctypes.data_as(_ip),
+                                        *[g.ctypes.data_as(_dp) for g in gs])
+    return loss, gs[0], gs[1], gs[2]

@@ -1,0 +1,646 @@
+// FP64 CPU oracle for the IRIS-SO synthetic-observation forward model.
+//
+// TEST INFRASTRUCTURE ONLY.  Only the test suite, the smoke check and the
+// bench's CPU-baseline leg may load this library.  It shares no code, header,
+// table or constant with the CUDA library; the two meet only in the seeded
+// input arrays.
+//
+// The code follows the paper's definitions in the paper's order, one plain
+// loop per definition, in double precision:
+//   Sec. 3.1  transfer equations for the total [T] and continuum [C] intensity
+//   Sec. 3.2  dust: alpha_D = kappa rho_gas, source function B_nu(T_dust)
+//   Sec. 3.3  line emission / absorption with a Gaussian Doppler profile
+//   Sec. 3.7  Einstein B relations
+//   Sec. 5.10 LTE (Boltzmann) level populations n_u = N g_u e^{-E_u/kT} / Z(T)
+//   Sec. 4.3  T_inf cut-off, Doppler-shifted line centre and dust Planck
+//   Sec. 4.4  channel averaging; background and continuum at channel value
+//   Sec. 4.5  fine velocity grid + Simpson rule for the total intensity
+//   Sec. 4.8  formal step and smooth (TR first step, BDF2, ReLU) integration
+//   Sec. 4.9  Rayleigh-Jeans temperature;  Sec. 4.10  continuum subtraction
+//
+// Readings taken where the paper is silent (each is listed with its reason
+// in the design notes):
+//   * LTE populations with E_l = E_u - h nu / k (so S_line = B_nu(T) exactly)
+//     and Z(T) = sum_J (2J+1) exp(-h B0 J(J+1) / kT) of a rigid rotor.
+//   * Velocity <-> frequency in the radio convention nu(u) = nu_ul (1 - u/c),
+//     positive = receding; the Doppler width uses nu_ul; the 1-D microturbulent
+//     dispersion adds 2 sigma^2 to the squared width.
+//   * Channel c spans [v0 + c dv, v0 + (c+1) dv]; fine points are spaced
+//     dv / (2f) with shared edges (Table 4: delta v = dv / (2f)); f = 0 samples
+//     the channel centre alone.
+//   * Smooth integration places the background at the first sample node, so
+//     it integrates (K-1) h; formal integration integrates K h.
+//   * [D] = [C] - [B] (continuum excess over the background), [L] = [T] - [C].
+//   * Geometry: z view = one ray per cell column, samples at the cells;
+//     oblique view = orthographic rays, chord split into K = ceil(chord/dx)
+//     equal steps, samples at step midpoints, trilinear field sampling with
+//     edge-clamped cell-centred values.
+//
+// Parity unpinned: the paper's own code (node placement, Planck at nu(u)) is
+// not available; the readings above are the definition this oracle encodes.
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <vector>
+
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+namespace {
+
+// CODATA 2018 (h, k, c exact by definition of the SI)
+const double H_PLANCK = 6.62607015e-27;   // erg s
+const double K_BOLTZ = 1.380649e-16;      // erg / K
+const double C_LIGHT = 2.99792458e10;     // cm / s
+const double C_KMS = 2.99792458e5;        // km / s
+const double AMU = 1.66053906660e-24;     // g
+const double PI = 3.14159265358979323846;
+
+// ---------------------------------------------------------------------------
+// Forward-mode dual numbers (value + ND directional derivatives), so that one
+// templated definition gives both the value and its exact gradient.
+// ---------------------------------------------------------------------------
+template <int ND>
+struct Dual {
+  double v;
+  double d[ND];
+  Dual() : v(0.0) { std::fill(d, d + ND, 0.0); }
+  Dual(double x) : v(x) { std::fill(d, d + ND, 0.0); }  // NOLINT
+};
+
+inline double val(double x) { return x; }
+template <int ND> inline double val(const Dual<ND>& x) { return x.v; }
+
+template <int ND> Dual<ND> operator+(const Dual<ND>& a, const Dual<ND>& b) {
+  Dual<ND> r; r.v = a.v + b.v; for (int i = 0; i < ND; ++i) r.d[i] = a.d[i] + b.d[i]; return r;
+}
+template <int ND> Dual<ND> operator-(const Dual<ND>& a, const Dual<ND>& b) {
+  Dual<ND> r; r.v = a.v - b.v; for (int i = 0; i < ND; ++i) r.d[i] = a.d[i] - b.d[i]; return r;
+}
+template <int ND> Dual<ND> operator-(const Dual<ND>& a) {
+  Dual<ND> r; r.v = -a.v; for (int i = 0; i < ND; ++i) r.d[i] = -a.d[i]; return r;
+}
+template <int ND> Dual<ND> operator*(const Dual<ND>& a, const Dual<ND>& b) {
+  Dual<ND> r; r.v = a.v * b.v;
+  for (int i = 0; i < ND; ++i) r.d[i] = a.d[i] * b.v + a.v * b.d[i];
+  return r;
+}
+template <int ND> Dual<ND> operator/(const Dual<ND>& a, const Dual<ND>& b) {
+  Dual<ND> r; r.v = a.v / b.v;
+  const double ib = 1.0 / b.v;
+  for (int i = 0; i < ND; ++i) r.d[i] = (a.d[i] - r.v * b.d[i]) * ib;
+  return r;
+}
+template <int ND> Dual<ND> operator+(const Dual<ND>& a, double b) { return a + Dual<ND>(b); }
+template <int ND> Dual<ND> operator+(double a, const Dual<ND>& b) { return Dual<ND>(a) + b; }
+template <int ND> Dual<ND> operator-(const Dual<ND>& a, double b) { return a - Dual<ND>(b); }
+template <int ND> Dual<ND> operator-(double a, const Dual<ND>& b) { return Dual<ND>(a) - b; }
+template <int ND> Dual<ND> operator*(const Dual<ND>& a, double b) {
+  Dual<ND> r; r.v = a.v * b; for (int i = 0; i < ND; ++i) r.d[i] = a.d[i] * b; return r;
+}
+template <int ND> Dual<ND> operator*(double a, const Dual<ND>& b) { return b * a; }
+template <int ND> Dual<ND> operator/(const Dual<ND>& a, double b) { return a * (1.0 / b); }
+template <int ND> Dual<ND> operator/(double a, const Dual<ND>& b) { return Dual<ND>(a) / b; }
+
+template <int ND> Dual<ND> exp(const Dual<ND>& a) {
+  Dual<ND> r; r.v = std::exp(a.v); for (int i = 0; i < ND; ++i) r.d[i] = r.v * a.d[i]; return r;
+}
+template <int ND> Dual<ND> expm1(const Dual<ND>& a) {
+  Dual<ND> r; r.v = std::expm1(a.v);
+  const double e = std::exp(a.v);
+  for (int i = 0; i < ND; ++i) r.d[i] = e * a.d[i];
+  return r;
+}
+template <int ND> Dual<ND> sqrt(const Dual<ND>& a) {
+  Dual<ND> r; r.v = std::sqrt(a.v);
+  const double g = (r.v > 0.0) ? 0.5 / r.v : 0.0;
+  for (int i = 0; i < ND; ++i) r.d[i] = g * a.d[i];
+  return r;
+}
+inline double exp(double a) { return std::exp(a); }
+inline double expm1(double a) { return std::expm1(a); }
+inline double sqrt(double a) { return std::sqrt(a); }
+
+// ReLU of Sec. 4.8; derivative 1 for x >= 0 and 0 otherwise.
+template <class S> S relu(const S& x) { return (val(x) >= 0.0) ? x : S(0.0); }
+
+// ---------------------------------------------------------------------------
+// Problem description (plain data, filled from the flat argument arrays).
+// ---------------------------------------------------------------------------
+struct Line {
+  double nu_ul, a_ul, e_u, b0, g_u, g_l, mass_amu, t_inf, sigma_turb;
+};
+struct DustP {
+  double kappa, mu_amu;
+};
+struct VAxis {
+  int nchan;
+  double v0, dv;
+  int f;
+};
+enum { FORMAL = 0, SMOOTH = 1 };
+enum { UNITS_TRJ = 0, UNITS_INTENSITY = 1 };
+
+// Sample values along one ray, in the order the ray travels (background side
+// first, observer side last).
+template <class S>
+struct Sample {
+  S n_h2, t_gas, t_dust, v_los, x_tr;
+};
+
+// ---------------------------------------------------------------------------
+// Physics definitions
+// ---------------------------------------------------------------------------
+
+// Frequency observed at line-of-sight velocity u [km/s] (radio convention).
+double nu_of_u(const Line& ln, double u) { return ln.nu_ul * (1.0 - u / C_KMS); }
+
+// Planck's law, Sec. 3.2 (dust source function) and Sec. 4.9.
+template <class S>
+S planck(double nu, const S& T) {
+  if (val(T) <= 0.0) return S(0.0);
+  const double a = 2.0 * H_PLANCK * nu * nu * nu / (C_LIGHT * C_LIGHT);
+  return a / expm1(H_PLANCK * nu / (K_BOLTZ * T));
+}
+
+// Rayleigh-Jeans temperature of an intensity at nu, Sec. 4.9.
+double rj_temperature(double nu, double I) {
+  return C_LIGHT * C_LIGHT * I / (2.0 * K_BOLTZ * nu * nu);
+}
+
+// Rigid-rotor partition function, summed until a term falls below 1e-17 of
+// the running sum.
+template <class S>
+S partition(const Line& ln, const S& T) {
+  S z(0.0);
+  for (int J = 0; J < 100000; ++J) {
+    const double eJ = H_PLANCK * ln.b0 * J * (J + 1.0) / K_BOLTZ;   // E_J / k  [K]
+    S term = (2.0 * J + 1.0) * exp(-eJ / T);
+    z = z + term;
+    if (J > 0 && val(term) < 1e-17 * val(z)) break;
+  }
+  return z;
+}
+
+// LTE level populations, Sec. 5.10:  n_i = N g_i exp(-E_i / kT) / Z(T).
+template <class S>
+void lte_populations(const Line& ln, const S& N, const S& T, S* n_u, S* n_l) {
+  const double e_l = ln.e_u - H_PLANCK * ln.nu_ul / K_BOLTZ;
+  const S z = partition(ln, T);
+  *n_u = N * ln.g_u * exp(-ln.e_u / T) / z;
+  *n_l = N * ln.g_l * exp(-e_l / T) / z;
+}
+
+// Frequency-integrated line coefficients j^L and alpha^L (Sec. 3.3) with the
+// Einstein B relations of Sec. 3.7.  Zero above T_inf (Sec. 4.3).
+template <class S>
+void line_coefficients(const Line& ln, const Sample<S>& s, S* jL, S* aL) {
+  if (val(s.t_gas) > ln.t_inf || val(s.t_gas) <= 0.0) {
+    *jL = S(0.0);
+    *aL = S(0.0);
+    return;
+  }
+  const S N = s.x_tr * s.n_h2;
+  S n_u, n_l;
+  lte_populations(ln, N, s.t_gas, &n_u, &n_l);
+  const double nu = ln.nu_ul;
+  const double B_ul = C_LIGHT * C_LIGHT * ln.a_ul / (2.0 * H_PLANCK * nu * nu * nu);
+  const double B_lu = (ln.g_u / ln.g_l) * B_ul;
+  *jL = (H_PLANCK * nu / (4.0 * PI)) * n_u * ln.a_ul;
+  *aL = (H_PLANCK * nu / (4.0 * PI)) * (n_l * B_lu - n_u * B_ul);
+}
+
+// Gaussian Doppler profile per unit frequency (Sec. 3.3), evaluated at the
+// observed velocity u for a cell moving at v_los.  The width adds the 1-D
+// microturbulent dispersion to the thermal one: b^2 = 2kT/m + 2 sigma^2.
+template <class S>
+S profile_per_hz(const Line& ln, const Sample<S>& s, double u) {
+  const double m = ln.mass_amu * AMU;
+  const S b2_cms = 2.0 * K_BOLTZ * s.t_gas / m
+                 + 2.0 * (ln.sigma_turb * 1e5) * (ln.sigma_turb * 1e5);
+  const S b_kms = sqrt(b2_cms) / 1e5;
+  const S dnu_D = (ln.nu_ul / C_KMS) * b_kms;            // Doppler width [Hz]
+  const S x = (u - s.v_los) / b_kms;                      // (nu - nu_0) / dnu_D
+  return exp(-(x * x)) / (dnu_D * std::sqrt(PI));
+}
+
+// Dust absorption coefficient alpha_D = kappa rho_gas (Sec. 3.2).
+template <class S>
+S dust_alpha(const DustP& du, const Sample<S>& s) {
+  return du.kappa * (s.n_h2 * (du.mu_amu * AMU));
+}
+
+// One formal step (Sec. 4.8): I <- I e^{-tau} + S (1 - e^{-tau}),
+// tau = h alpha, S = j / alpha.
+template <class S>
+S formal_step(const S& I, const S& j, const S& a, double h) {
+  if (val(a) == 0.0) return I + h * j;
+  const S tau = h * a;
+  const S src = j / a;
+  return I * exp(-tau) + src * (-expm1(-tau));
+}
+
+// Transfer of one frequency along the ray (Sec. 4.8).  j[k], a[k] are the
+// total coefficients at sample k; I0 is the background intensity.
+template <class S>
+S integrate(int mode, const std::vector<S>& j, const std::vector<S>& a, double h, const S& I0) {
+  const int K = (int)j.size();
+  if (mode == FORMAL) {
+    S I = I0;
+    for (int k = 0; k < K; ++k) I = formal_step(I, j[k], a[k], h);
+    return I;
+  }
+  // smooth: node 0 carries the background; TR to node 1, BDF2 afterwards,
+  // each step clamped at zero.
+  if (K <= 1) return I0;
+  S In = I0;
+  S In1 = relu((h * (j[0] + j[1]) + (2.0 - h * a[0]) * In) / (2.0 + h * a[1]));
+  for (int n = 0; n + 2 < K; ++n) {
+    S In2 = relu((2.0 * h * j[n + 2] + 4.0 * In1 - In) / (3.0 + 2.0 * h * a[n + 2]));
+    In = In1;
+    In1 = In2;
+  }
+  return In1;
+}
+
+// Outputs of one ray: the five components per channel, in T_RJ [K] or in
+// cgs intensity.  Order of the definition: coefficients per sample ->
+// fine-velocity transfer of [T] -> Simpson channel average -> continuum [C]
+// at channel centres -> background [B] -> [L] = [T] - [C], [D] = [C] - [B].
+template <class S>
+void ray_outputs(const Line& ln, const DustP& du, const VAxis& va, int mode, int units,
+                 double t_bg, const std::vector<Sample<S>>& smp, double h,
+                 S* oT, S* oC, S* oD, S* oL, S* oB) {
+  const int K = (int)smp.size();
+  const int nch = va.nchan;
+  const int f = va.f;
+  // per-sample frequency-independent coefficients
+  std::vector<S> jL(K), aL(K), aD(K);
+  for (int k = 0; k < K; ++k) {
+    line_coefficients(ln, smp[k], &jL[k], &aL[k]);
+    aD[k] = dust_alpha(du, smp[k]);
+  }
+  // fine velocity grid (Sec. 4.5, Table 4)
+  int nfine;
+  double dvf, ufirst;
+  if (f >= 1) {
+    nfine = 2 * f * nch + 1;
+    dvf = va.dv / (2.0 * f);
+    ufirst = va.v0;
+  } else {
+    nfine = nch;
+    dvf = va.dv;
+    ufirst = va.v0 + 0.5 * va.dv;
+  }
+  std::vector<S> Ifine(nfine);
+  std::vector<S> jt(K), at(K);
+  for (int g = 0; g < nfine; ++g) {
+    const double u = ufirst + g * dvf;
+    const double nu = nu_of_u(ln, u);
+    for (int k = 0; k < K; ++k) {
+      const S phi = profile_per_hz(ln, smp[k], u);
+      const S jD = aD[k] * planck(nu, smp[k].t_dust);
+      jt[k] = jL[k] * phi + jD;
+      at[k] = aL[k] * phi + aD[k];
+    }
+    Ifine[g] = integrate(mode, jt, at, h, S(planck(nu, t_bg)));
+  }
+  for (int c = 0; c < nch; ++c) {
+    const double uc = va.v0 + (c + 0.5) * va.dv;
+    const double nuc = nu_of_u(ln, uc);
+    // channel average of the total intensity (Simpson over f panels)
+    S Ibar(0.0);
+    if (f >= 1) {
+      for (int p = 0; p < f; ++p) {
+        const int g = 2 * f * c + 2 * p;
+        Ibar = Ibar + Ifine[g] + 4.0 * Ifine[g + 1] + Ifine[g + 2];
+      }
+      Ibar = Ibar / (6.0 * f);
+    } else {
+      Ibar = Ifine[c];
+    }
+    // continuum at the channel value (Sec. 4.4)
+    for (int k = 0; k < K; ++k) {
+      jt[k] = aD[k] * planck(nuc, smp[k].t_dust);
+      at[k] = aD[k];
+    }
+    const S IB(planck(nuc, t_bg));
+    const S IC = integrate(mode, jt, at, h, IB);
+    S vT = Ibar, vC = IC, vB = IB;
+    if (units == UNITS_TRJ) {
+      const double s = rj_temperature(nuc, 1.0);
+      vT = vT * s; vC = vC * s; vB = vB * s;
+    }
+    oT[c] = vT;
+    oC[c] = vC;
+    oB[c] = vB;
+    oL[c] = vT - vC;
+    oD[c] = vC - vB;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Geometry
+// ---------------------------------------------------------------------------
+struct Grid {
+  const double* f[5];  // n_h2, t_gas, t_dust, v_los, x_tr, each [z][y][x]
+  int nx, ny, nz;
+  double dx;
+  double at(int q, int x, int y, int z) const {
+    return f[q][((int64_t)z * ny + y) * nx + x];
+  }
+};
+
+struct ViewP {
+  double theta, phi;
+  int npx, npy;
+  double pixel;
+  int trilinear;
+};
+
+// Ray through the box for pixel (px, py): origin o, direction d, chord
+// [t_in, t_out].  Returns false if the ray misses the box.
+bool ray_chord(const Grid& g, const ViewP& v, int px, int py, double o[3], double d[3],
+               double* t_in, double* t_out) {
+  const double st = std::sin(v.theta), ct = std::cos(v.theta);
+  const double sp = std::sin(v.phi), cp = std::cos(v.phi);
+  d[0] = st * cp; d[1] = st * sp; d[2] = ct;
+  const double et[3] = {ct * cp, ct * sp, -st};
+  const double ep[3] = {-sp, cp, 0.0};
+  const double L[3] = {g.nx * g.dx, g.ny * g.dx, g.nz * g.dx};
+  const double a = (px - 0.5 * (v.npx - 1)) * v.pixel;
+  const double b = (py - 0.5 * (v.npy - 1)) * v.pixel;
+  for (int i = 0; i < 3; ++i) o[i] = 0.5 * L[i] + a * et[i] + b * ep[i];
+  double lo = -INFINITY, hi = INFINITY;
+  for (int i = 0; i < 3; ++i) {
+    if (d[i] == 0.0) {
+      if (o[i] < 0.0 || o[i] > L[i]) return false;
+      continue;
+    }
+    double t0 = (0.0 - o[i]) / d[i], t1 = (L[i] - o[i]) / d[i];
+    if (t0 > t1) std::swap(t0, t1);
+    lo = std::max(lo, t0);
+    hi = std::min(hi, t1);
+  }
+  if (!(hi > lo)) return false;
+  *t_in = lo;
+  *t_out = hi;
+  return true;
+}
+
+// Trilinear interpolation of the raw field q at position r [cm], cell-centred
+// values, indices clamped to the grid (edge extension).
+double trilinear(const Grid& g, int q, const double r[3]) {
+  const int n[3] = {g.nx, g.ny, g.nz};
+  int i0[3], i1[3];
+  double w[3];
+  for (int a = 0; a < 3; ++a) {
+    const double s = r[a] / g.dx - 0.5;
+    const double fl = std::floor(s);
+    w[a] = s - fl;
+    int lo = (int)fl;
+    i0[a] = std::min(std::max(lo, 0), n[a] - 1);
+    i1[a] = std::min(std::max(lo + 1, 0), n[a] - 1);
+  }
+  double acc = 0.0;
+  for (int c = 0; c < 8; ++c) {
+    const int ix = (c & 1) ? i1[0] : i0[0];
+    const int iy = (c & 2) ? i1[1] : i0[1];
+    const int iz = (c & 4) ? i1[2] : i0[2];
+    const double wx = (c & 1) ? w[0] : 1.0 - w[0];
+    const double wy = (c & 2) ? w[1] : 1.0 - w[1];
+    const double wz = (c & 4) ? w[2] : 1.0 - w[2];
+    acc += wx * wy * wz * g.at(q, ix, iy, iz);
+  }
+  return acc;
+}
+
+// Samples of one ray.  z view: the cells (px, py, k) for k = 0..nz-1 with
+// h = dx.  Oblique: K = ceil(chord/dx) midpoint samples of a uniform split.
+void ray_samples(const Grid& g, const ViewP& v, int px, int py,
+                 std::vector<Sample<double>>* smp, double* h) {
+  smp->clear();
+  if (!v.trilinear) {
+    *h = g.dx;
+    for (int k = 0; k < g.nz; ++k) {
+      Sample<double> s;
+      s.n_h2 = g.at(0, px, py, k);
+      s.t_gas = g.at(1, px, py, k);
+      s.t_dust = g.at(2, px, py, k);
+      s.v_los = g.at(3, px, py, k);
+      s.x_tr = g.at(4, px, py, k);
+      smp->push_back(s);
+    }
+    return;
+  }
+  double o[3], d[3], t0, t1;
+  if (!ray_chord(g, v, px, py, o, d, &t0, &t1)) {
+    *h = 0.0;
+    return;
+  }
+  const double chord = t1 - t0;
+  const int K = (int)std::ceil(chord / g.dx - 1e-9);
+  if (K <= 0) { *h = 0.0; return; }
+  *h = chord / K;
+  for (int k = 0; k < K; ++k) {
+    const double t = t0 + (k + 0.5) * (*h);
+    const double r[3] = {o[0] + t * d[0], o[1] + t * d[1], o[2] + t * d[2]};
+    Sample<double> s;
+    s.n_h2 = trilinear(g, 0, r);
+    s.t_gas = trilinear(g, 1, r);
+    s.t_dust = trilinear(g, 2, r);
+    s.v_los = trilinear(g, 3, r);
+    s.x_tr = trilinear(g, 4, r);
+    smp->push_back(s);
+  }
+}
+
+Line line_from(const double* p) {
+  Line l;
+  l.nu_ul = p[0]; l.a_ul = p[1]; l.e_u = p[2]; l.b0 = p[3]; l.g_u = p[4]; l.g_l = p[5];
+  l.mass_amu = p[6]; l.t_inf = p[7]; l.sigma_turb = p[8];
+  return l;
+}
+DustP dust_from(const double* p) { DustP d; d.kappa = p[0]; d.mu_amu = p[1]; return d; }
+VAxis vaxis_from(int nchan, double v0, double dv, int f) {
+  VAxis v; v.nchan = nchan; v.v0 = v0; v.dv = dv; v.f = f; return v;
+}
+
+}  // namespace
+
+// ===========================================================================
+// Flat C entry points (loaded with ctypes by the tests).
+//   line[9] = nu_ul_hz, a_ul_s, e_u_k, b0_hz, g_u, g_l, mass_amu, t_inf_k,
+//             sigma_turb_kms
+//   dust[2] = kappa_cm2_per_g_gas, mu_mass_per_h2_amu
+//   view[6] = theta_rad, phi_rad, npx, npy, pixel_cm, trilinear
+// ===========================================================================
+extern "C" {
+
+int oracle_num_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
+
+double oracle_planck(double nu, double T) { return planck(nu, T); }
+double oracle_partition(const double* line, double T) { return partition(line_from(line), T); }
+
+// Per-sample coefficients: out[0..5] = n_u, n_l, j^L, alpha^L, alpha^D, b [km/s]
+void oracle_sample_coeffs(const double* line, const double* dust, double n_h2, double t_gas,
+                          double x_tr, double* out) {
+  const Line ln = line_from(line);
+  const DustP du = dust_from(dust);
+  Sample<double> s{n_h2, t_gas, t_gas, 0.0, x_tr};
+  double nu_, nl_;
+  lte_populations(ln, x_tr * n_h2, t_gas, &nu_, &nl_);
+  double jL, aL;
+  line_coefficients(ln, s, &jL, &aL);
+  out[0] = nu_; out[1] = nl_; out[2] = jL; out[3] = aL; out[4] = dust_alpha(du, s);
+  const double m = ln.mass_amu * AMU;
+  out[5] = std::sqrt(2.0 * K_BOLTZ * t_gas / m + 2.0 * (ln.sigma_turb * 1e5) * (ln.sigma_turb * 1e5)) / 1e5;
+}
+
+// Profile per Hz at observed velocity u for a sample (t_gas, v_los).
+double oracle_profile(const double* line, double t_gas, double v_los, double u) {
+  Sample<double> s{1.0, t_gas, t_gas, v_los, 1.0};
+  return profile_per_hz(line_from(line), s, u);
+}
+
+// One ray given explicitly by its K samples (arrays in travel order) and the
+// step h [cm].  Outputs out_*[nchan].
+void oracle_ray(const double* line, const double* dust, int nchan, double v0, double dv, int f,
+                int integration, int units, double t_bg, int K, const double* n_h2,
+                const double* t_gas, const double* t_dust, const double* v_los,
+                const double* x_tr, double h, double* oT, double* oC, double* oD, double* oL,
+                double* oB) {
+  std::vector<Sample<double>> smp(K);
+  for (int k = 0; k < K; ++k) smp[k] = {n_h2[k], t_gas[k], t_dust[k], v_los[k], x_tr[k]};
+  ray_outputs(line_from(line), dust_from(dust), vaxis_from(nchan, v0, dv, f), integration, units,
+              t_bg, smp, h, oT, oC, oD, oL, oB);
+}
+
+// Sample list of a pixel: returns K (<= kmax), fills h and samples.
+int oracle_ray_samples(const double* const* fields, int nx, int ny, int nz, double cell_cm,
+                       const double* view, int px, int py, int kmax, double* h_out,
+                       double* samples /* [kmax][5] */) {
+  Grid g;
+  for (int q = 0; q < 5; ++q) g.f[q] = fields[q];
+  g.nx = nx; g.ny = ny; g.nz = nz; g.dx = cell_cm;
+  ViewP v{view[0], view[1], (int)view[2], (int)view[3], view[4], (int)view[5]};
+  std::vector<Sample<double>> smp;
+  double h = 0.0;
+  ray_samples(g, v, px, py, &smp, &h);
+  *h_out = h;
+  const int K = (int)smp.size();
+  for (int k = 0; k < K && k < kmax; ++k) {
+    samples[5 * k + 0] = smp[k].n_h2;
+    samples[5 * k + 1] = smp[k].t_gas;
+    samples[5 * k + 2] = smp[k].t_dust;
+    samples[5 * k + 3] = smp[k].v_los;
+    samples[5 * k + 4] = smp[k].x_tr;
+  }
+  return K;
+}
+
+// Render a list of pixels.  pix[2*i], pix[2*i+1] = (px, py); outputs are
+// [npix][nchan] per component (NULL = not wanted).
+int oracle_render(const double* const* fields, int nx, int ny, int nz, double cell_cm,
+                  const double* line, const double* dust, const double* view, int nchan,
+                  double v0, double dv, int f, int integration, int units, double t_bg,
+                  int npix, const int* pix, double* oT, double* oC, double* oD, double* oL,
+                  double* oB) {
+  Grid g;
+  for (int q = 0; q < 5; ++q) g.f[q] = fields[q];
+  g.nx = nx; g.ny = ny; g.nz = nz; g.dx = cell_cm;
+  const ViewP v{view[0], view[1], (int)view[2], (int)view[3], view[4], (int)view[5]};
+  const Line ln = line_from(line);
+  const DustP du = dust_from(dust);
+  const VAxis va = vaxis_from(nchan, v0, dv, f);
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int i = 0; i < npix; ++i) {
+    std::vector<Sample<double>> smp;
+    double h = 0.0;
+    ray_samples(g, v, pix[2 * i], pix[2 * i + 1], &smp, &h);
+    std::vector<double> T(nchan), C(nchan), D(nchan), L(nchan), B(nchan);
+    ray_outputs(ln, du, va, integration, units, t_bg, smp, h, T.data(), C.data(), D.data(),
+                L.data(), B.data());
+    const int64_t off = (int64_t)i * nchan;
+    for (int c = 0; c < nchan; ++c) {
+      if (oT) oT[off + c] = T[c];
+      if (oC) oC[off + c] = C[c];
+      if (oD) oD[off + c] = D[c];
+      if (oL) oL[off + c] = L[c];
+      if (oB) oB[off + c] = B[c];
+    }
+  }
+  return 0;
+}
+
+// Gradient of Loss = mean over all voxels of ([L] - target)^2 for the z view,
+// with respect to n_H2, T_gas and v_los of every cell, by forward-mode dual
+// numbers through the whole definition.  target is [nchan][ny][nx]; grads are
+// [nz][ny][nx].  Only pixels in pix[] contribute (the others are taken to
+// match their target exactly).  Returns the loss over those pixels.
+double oracle_loss_grad_zview(const double* const* fields, int nx, int ny, int nz,
+                              double cell_cm, const double* line, const double* dust, int nchan,
+                              double v0, double dv, int f, int integration, int units,
+                              double t_bg, const double* target, int npix, const int* pix,
+                              double* g_n, double* g_t, double* g_v) {
+  constexpr int CELLS = 8;
+  constexpr int ND = 3 * CELLS;
+  typedef Dual<ND> D;
+  Grid g;
+  for (int q = 0; q < 5; ++q) g.f[q] = fields[q];
+  g.nx = nx; g.ny = ny; g.nz = nz; g.dx = cell_cm;
+  const Line ln = line_from(line);
+  const DustP du = dust_from(dust);
+  const VAxis va = vaxis_from(nchan, v0, dv, f);
+  const double nvox = (double)nchan * nx * ny;
+  double loss = 0.0;
+#pragma omp parallel for schedule(dynamic, 1) reduction(+ : loss)
+  for (int i = 0; i < npix; ++i) {
+    const int px = pix[2 * i], py = pix[2 * i + 1];
+    std::vector<D> T(nchan), C(nchan), Dd(nchan), L(nchan), B(nchan);
+    double lray = 0.0;
+    for (int k0 = 0; k0 < nz; k0 += CELLS) {
+      std::vector<Sample<D>> smp(nz);
+      for (int k = 0; k < nz; ++k) {
+        smp[k].n_h2 = D(g.at(0, px, py, k));
+        smp[k].t_gas = D(g.at(1, px, py, k));
+        smp[k].t_dust = D(g.at(2, px, py, k));
+        smp[k].v_los = D(g.at(3, px, py, k));
+        smp[k].x_tr = D(g.at(4, px, py, k));
+        if (k >= k0 && k < k0 + CELLS) {
+          smp[k].n_h2.d[3 * (k - k0) + 0] = 1.0;
+          smp[k].t_gas.d[3 * (k - k0) + 1] = 1.0;
+          smp[k].v_los.d[3 * (k - k0) + 2] = 1.0;
+        }
+      }
+      ray_outputs(ln, du, va, integration, units, t_bg, smp, g.dx, T.data(), C.data(),
+                  Dd.data(), L.data(), B.data());
+      D l(0.0);
+      for (int c = 0; c < nchan; ++c) {
+        const D r = L[c] - target[((int64_t)c * ny + py) * nx + px];
+        l = l + r * r;
+      }
+      l = l / nvox;
+      if (k0 == 0) lray = l.v;
+      for (int k = k0; k < std::min(nz, k0 + CELLS); ++k) {
+        const int64_t idx = ((int64_t)k * ny + py) * nx + px;
+        g_n[idx] = l.d[3 * (k - k0) + 0];
+        g_t[idx] = l.d[3 * (k - k0) + 1];
+        g_v[idx] = l.d[3 * (k - k0) + 2];
+      }
+    }
+    loss += lray;
+  }
+  return loss;
+}
+
+}  // extern "C"
