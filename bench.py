@@ -1,0 +1,410 @@
+#!/usr/bin/env python
+"""Throughput of the PPV forward hot path: cell-channel updates per second.
+
+Workload: a 256^3 FP32 field set (lognormal density, turbulent velocity plus
+rotation), 13CO(2-1) in LTE, 256 channels of 1 km/s with f = 1; one step
+renders the z view and the (theta, phi) = (30, 45) deg oblique trilinear view
+with smooth (TR + BDF2) integration.  Units of one render: sum over rays of
+(samples on the ray) x (channels).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl irt|reference]
+
+N > 1 runs under torchrun, one rank per GPU, each rank rendering its own
+snapshot (weak scaling, no collective on the data path).  Prints one JSON line
+on rank 0.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "PPV cell-channel updates/s (fwd and adjoint) at stated error vs FP64 oracle"
+UNIT = "cell-channel updates/s"
+#: algorithmic FP32 / MUFU lane-operations of the smooth integrator (see
+#: the design doc): per (sample, 32-velocity block) pair where the line is
+#: evaluated, per pair integrated without the line, per sample (records and
+#: the three continuum basis recurrences)
+OPS_LINE = (10, 2)
+OPS_DUST = (5, 0)
+OPS_SAMPLE = (165, 9)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["irt", "reference"], default="irt")
+    ap.add_argument("--integration", default="smooth")
+    ap.add_argument("--n", type=int, default=256, help="grid side (default: the 256^3 workload)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.samples = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "50"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.samples.append((time.time(), line.strip()))
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        if self.thread is not None:
+            self.thread.join(timeout=5)
+
+    def summary(self, t0, t1):
+        rows = [s for t, s in self.samples if t0 <= t <= t1]
+        note = "during timed region"
+        if len(rows) < 2:
+            rows = [s for t, s in self.samples if t0 - 1.0 <= t <= t1 + 1.0]
+            note = "within 1 s of the timed region (region shorter than the sampling period)"
+        sm, smax, reasons = [], 0.0, set()
+        for r in rows:
+            p = [x.strip() for x in r.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                smax = max(smax, float(p[2]))
+            except ValueError:
+                continue
+            names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+            for name, v in zip(names, p[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0,
+                    "note": "nvidia-smi unavailable"}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm), "note": note}
+
+
+# ---------------------------------------------------------------------------
+# workload
+# ---------------------------------------------------------------------------
+def workload_inputs(n, seed):
+    from synth import make_fields, to_storage, workload
+    w = workload(1, n=n)
+    fs = make_fields(w.n, seed)
+    f32, deq = to_storage(fs, np.float32)
+    return w, f32, deq
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh)
+    except OSError:
+        return {"hbm_gbs": 6400.0, "sm_max_mhz": 2032.0, "fallback": True}
+
+
+# ---------------------------------------------------------------------------
+# oracle timing (CPU baseline / reference arm)
+# ---------------------------------------------------------------------------
+def oracle_rate(w, deq, target_s=10.0, integration="smooth", seed=0):
+    """Oracle throughput on a seeded sample of rays of both views, sized to
+    about target_s seconds of CPU work.  Returns (units/s, cores, sample text,
+    seconds)."""
+    import oracle
+    mode = oracle.SMOOTH if integration == "smooth" else oracle.FORMAL
+    fields = deq.as_tuple()
+    rng = np.random.default_rng(seed)
+    cores = oracle.num_threads()
+
+    def run(nrays):
+        units = 0
+        t = time.perf_counter()
+        for view in w.views:
+            pix = np.stack([rng.integers(0, view.npx, nrays), rng.integers(0, view.npy, nrays)],
+                           axis=1)
+            oracle.render(fields, w.cell_cm, w.line, w.dust, view, w.vaxis, pix,
+                          integration=mode)
+            for px, py in pix:
+                smp, h = oracle.ray_samples(fields, w.cell_cm, view, int(px), int(py))
+                units += len(smp) * w.vaxis.nchan
+        return units, time.perf_counter() - t
+
+    nr = max(cores, 4)
+    units, dt = run(nr)
+    if dt < target_s / 4:
+        nr = max(nr, int(nr * target_s / max(dt, 1e-3)))
+        units, dt = run(nr)
+    sample = (f"{nr} seeded rays per view of the {w.n}^3 workload (z and oblique), "
+              f"all {w.vaxis.nchan} channels, full depth")
+    return units / dt, cores, sample, dt
+
+
+def reference_arm(args):
+    ws, rank, local = dist_env()
+    if ws > 1 and rank != 0:
+        return
+    w, f32, deq = workload_inputs(args.n, 1000)
+    per_step = max(2.0, 60.0 / max(1, args.steps + args.warmup))
+    for _ in range(args.warmup):
+        oracle_rate(w, deq, target_s=per_step / 4, integration=args.integration)
+    rates, times = [], []
+    cores, sample = 1, ""
+    for s in range(args.steps):
+        r, cores, sample, dt = oracle_rate(w, deq, target_s=per_step,
+                                           integration=args.integration, seed=s)
+        rates.append(r)
+        times.append(dt)
+    value = float(np.mean(rates))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * float(np.mean(times)), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"{w.name} z + oblique(30,45) deg", "grid": w.n,
+                       "nchan": w.vaxis.nchan, "f": w.vaxis.subsample_f,
+                       "integration": args.integration},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+def gpu_arm(args):
+    import torch
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    import paper_2607_01338_b300 as irt
+    from paper_2607_01338_b300 import binding as B
+
+    seed = 1000 + 17 * rank
+    w, f32, deq = workload_inputs(args.n, seed)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    fields_d = [torch.from_numpy(a).to(dev) for a in f32.as_tuple()]
+    grid = irt.Grid(*fields_d, w.cell_cm)
+    outs = [irt.alloc_cubes(v, w.vaxis) for v in w.views]
+    stream = torch.cuda.current_stream()
+
+    def step(flags=0):
+        for view, out in zip(w.views, outs):
+            irt.forward(grid, view, w.vaxis, w.line, w.dust, integration=args.integration,
+                        out=out, flags=flags)
+
+    # units and work counters from one counted pass
+    B.irt_grid_stats(grid.handle, reset=True)
+    per_view = []
+    for view, out in zip(w.views, outs):
+        irt.forward(grid, view, w.vaxis, w.line, w.dust, integration=args.integration, out=out,
+                    flags=B.IRT_FLAG_STATS)
+        per_view.append(B.irt_grid_stats(grid.handle, reset=True))
+    units_view = [st["samples"] * w.vaxis.nchan for st in per_view]
+    units_step = sum(units_view)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    time.sleep(0.3)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(len(w.views) * args.steps)]
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    irt.irt_launch_count()
+    wall0 = time.time()
+    t_start.record(stream)
+    i = 0
+    for _ in range(args.steps):
+        for view, out in zip(w.views, outs):
+            ev[i][0].record(stream)
+            irt.forward(grid, view, w.vaxis, w.line, w.dust, integration=args.integration,
+                        out=out)
+            ev[i][1].record(stream)
+            i += 1
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    wall1 = time.time()
+    launches = irt.irt_launch_count()
+    if ws > 1:
+        torch.distributed.barrier()
+    time.sleep(0.2)
+    clocks.stop()
+    elapsed_ms = t_start.elapsed_time(t_end)
+    if ws > 1:
+        t = torch.tensor([elapsed_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+    ms_step = elapsed_ms / args.steps
+    value = units_step * ws / (elapsed_ms / 1e3 / args.steps)
+    launch_ms = [[], []]
+    for j, (a, b) in enumerate(ev):
+        launch_ms[j % len(w.views)].append(a.elapsed_time(b))
+    view_ms = [float(np.mean(x)) for x in launch_ms]
+
+    # ---- roofline of the dominant kernel (the render with the most time)
+    pk = peaks()
+    dom = int(np.argmax(view_ms))
+    st = per_view[dom]
+    fp32 = 32 * (OPS_LINE[0] * st["line_block_samples"]
+                 + OPS_DUST[0] * (st["hull_block_samples"] - st["line_block_samples"])) \
+        + OPS_SAMPLE[0] * st["samples"]
+    mufu = 32 * OPS_LINE[1] * st["line_block_samples"] + OPS_SAMPLE[1] * st["samples"]
+    fclk = float(pk.get("sm_max_mhz", 2032.0)) * 1e6
+    peak_fp32 = 148 * 128 * fclk / 1e12          # Top/s
+    peak_mufu = 148 * 16 * fclk / 1e12
+    t_dom = view_ms[dom] / 1e3
+    a_fp32 = fp32 / t_dom / 1e12
+    a_mufu = mufu / t_dom / 1e12
+    if a_fp32 / peak_fp32 >= a_mufu / peak_mufu:
+        ach, peak, pipe = a_fp32, peak_fp32, "fp32"
+    else:
+        ach, peak, pipe = a_mufu, peak_mufu, "mufu"
+    nx = w.n
+    hbm_bytes = nx ** 3 * 32 + 5 * 4 * w.vaxis.nchan * w.views[dom].npx * w.views[dom].npy
+    roofline = {"bound": "alu", "pipe": pipe, "achieved": ach, "peak": peak, "unit": "Top/s",
+                "frac": ach / peak, "traffic": None,
+                "kernel": f"fwd_kernel<float,17,F32,smooth> ({['z', 'oblique'][dom]} view)",
+                "launch_ms": view_ms[dom],
+                "peak_source": "148 SMs x (128 FP32 | 16 MUFU lanes) x sm_max_mhz "
+                               f"{pk.get('sm_max_mhz', 2032.0)} (MEASURED_PEAKS.json clocks)",
+                "fp32_top_s": a_fp32, "mufu_top_s": a_mufu,
+                "hbm_gbs": hbm_bytes / t_dom / 1e9, "hbm_peak_gbs": pk.get("hbm_gbs"),
+                "hbm_frac": hbm_bytes / t_dom / 1e9 / float(pk.get("hbm_gbs", 6400.0)),
+                "dense_fine_updates_per_launch": st["dense_fine_updates"],
+                "work_per_launch": st}
+
+    # ---- end to end through the public API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        host_in = [torch.from_numpy(a).pin_memory() for a in f32.as_tuple()]
+        host_out = [{k: torch.empty(o[k].shape, dtype=o[k].dtype).pin_memory() for k in o}
+                    for o in outs]
+        h2d = sum(t.numel() * t.element_size() for t in host_in)
+        d2h = sum(t.numel() * t.element_size() for o in host_out for t in o.values())
+        dev_in = [torch.empty_like(t, device=dev) for t in host_in]
+
+        def e2e_step():
+            for d, h in zip(dev_in, host_in):
+                d.copy_(h, non_blocking=True)
+            g = irt.Grid(*dev_in, w.cell_cm)
+            for view, out, ho in zip(w.views, outs, host_out):
+                irt.forward(g, view, w.vaxis, w.line, w.dust, integration=args.integration,
+                            out=out)
+                for k in out:
+                    ho[k].copy_(out[k], non_blocking=True)
+            torch.cuda.synchronize()
+            g.close()
+
+        for _ in range(2):
+            e2e_step()
+        e_steps = max(3, min(args.steps, 10))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(e_steps):
+            e2e_step()
+        torch.cuda.synchronize()
+        dt = (time.perf_counter() - t0) / e_steps
+        e2e_v = units_step / dt
+        if ws > 1:
+            t = torch.tensor([dt], device=dev)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            e2e_v = units_step * ws / float(t.item())
+        e2e = {"value": e2e_v, "unit": UNIT, "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h, "ms_per_step": dt * 1e3,
+               "path": "pinned host fields -> device, irt_create_grid, irt_forward_ppv x2, "
+                       "cubes -> pinned host"}
+
+    clk = clocks.summary(wall0, wall1)
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        r, cores, sample, dt = oracle_rate(w, deq, target_s=10.0, integration=args.integration)
+        cpu = {"value": r, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
+               "seconds": dt}
+
+    grid.close()
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32", "data": "synthetic",
+                "config": {"workload": f"{w.name}: z view + oblique (30,45) deg trilinear, "
+                                       f"{args.integration} integration, forward",
+                           "grid": w.n, "nchan": w.vaxis.nchan, "f": w.vaxis.subsample_f,
+                           "units_per_step": units_step, "units_per_view": units_view,
+                           "l2": "inputs larger than L2 (packed fields 32 B/cell = "
+                                 f"{w.n ** 3 * 32 / 1e6:.0f} MB > 126 MB)",
+                           "parallelism": f"replicas x{ws}", "per_view_ms": view_ms},
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "clocks": clk, "gpu_launches": launches}
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        reference_arm(args)
+    else:
+        gpu_arm(args)
+
+
+if __name__ == "__main__":
+    main()

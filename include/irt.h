@@ -1,0 +1,221 @@
+/*
+ * irt.h - C ABI of the B300 (sm_103a) IRIS-SO synthetic-observation library.
+ *
+ * The library turns 3-D gas fields (H2 density, gas and dust temperature,
+ * line-of-sight velocity, tracer abundance) into position-position-velocity
+ * cubes of a molecular line plus dust continuum, with the five components
+ * [T] total, [C] continuum, [D] dust excess, [L] line and [B] background.
+ *
+ * Method (paper sections):
+ *   Sec. 3.1  dI/ds = j - alpha I for the total and the continuum intensity
+ *   Sec. 3.2  dust alpha_D = kappa rho_gas with a Planck source B_nu(T_dust)
+ *   Sec. 3.3  line j = h nu A n_u phi / 4 pi, alpha = h nu (n_l B_lu - n_u B_ul) phi / 4 pi
+ *             with a Gaussian Doppler profile phi
+ *   Sec. 3.7  Einstein relations B_ul = c^2 A / (2 h nu^3), B_lu = (g_u/g_l) B_ul
+ *   Sec. 5.10 LTE populations n_i = N g_i exp(-E_i / kT) / Z(T)
+ *   Sec. 4.3  T_inf cut-off and Doppler-shifted frequencies
+ *   Sec. 4.4/4.5 optically thick transfer on a fine velocity grid (step dv/(2f),
+ *             Table 4) with a Simpson channel average; continuum and background
+ *             at the channel value
+ *   Sec. 4.8  formal (exponential) and smooth (trapezoidal first step, BDF2,
+ *             ReLU) integration
+ *   Sec. 4.9/4.10 Rayleigh-Jeans temperature output; [L] = [T] - [C]
+ *
+ * Conventions fixed where the paper is silent:
+ *   - LTE with E_l = E_u - h nu / k and a rigid-rotor Z(T) with constant B0.
+ *   - Frequency of velocity u: nu(u) = nu_ul (1 - u / c), positive = receding.
+ *     The Doppler width b^2 = 2 k T / m + 2 sigma_turb^2 (sigma = 1-D rms).
+ *   - Channel c spans [v0 + c dv, v0 + (c+1) dv] km/s.  f >= 1: fine points
+ *     v0 + g dv/(2f), g = 0 .. 2 f nchan, edges shared by adjacent channels;
+ *     f = 0: the channel centre alone.
+ *   - Smooth integration puts the background on the first sample node;
+ *     formal integration applies K full steps.
+ *   - [D] = [C] - [B].  Outputs are Rayleigh-Jeans temperatures at each
+ *     channel centre frequency (or cgs intensity with IRT_UNITS_INTENSITY).
+ *   - Geometry: view.trilinear = 0 is the z view: pixel (x, y) is the cell
+ *     column (x, y), rays travel along +z (background at z = 0, observer
+ *     beyond z = nz dx), one sample per cell.  view.trilinear = 1 is an
+ *     orthographic view along d = (sin t cos p, sin t sin p, cos t): pixel
+ *     (px, py) sits at box_centre + (px - (npx-1)/2) pixel e_t + (py - (npy-1)/2)
+ *     pixel e_p with e_t = (cos t cos p, cos t sin p, -sin t), e_p = (-sin p,
+ *     cos p, 0); the chord through the box is split into K = ceil(chord/dx)
+ *     equal steps sampled at their midpoints with trilinear interpolation of
+ *     cell-centred values (indices clamped at the faces).
+ *
+ * All entry points are asynchronous on the given CUDA stream (NULL = legacy
+ * default stream) and never throw.  A status other than IRT_OK means that no
+ * kernel of the failed call was launched (except IRT_ECUDA after a launch,
+ * which reports the CUDA error); irt_last_error() gives a message.
+ */
+#ifndef IRT_H_
+#define IRT_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define IRT_ABI_VERSION 1
+
+typedef enum {
+  IRT_OK = 0,
+  IRT_EINVAL = 1,          /* invalid argument, detected before any launch */
+  IRT_ENOMEM = 2,          /* device allocation failed */
+  IRT_ECUDA = 3,           /* CUDA runtime error (message has the CUDA string) */
+  IRT_EUNSUPPORTED = 4,    /* valid but not supported combination */
+  IRT_ETIMEOUT = 5         /* a bounded device wait gave up */
+} irt_status;
+
+typedef enum { IRT_F32 = 0, IRT_F16 = 1, IRT_BF16 = 2, IRT_F64 = 3 } irt_dtype;
+
+typedef enum { IRT_FORMAL = 0, IRT_SMOOTH = 1, IRT_FORMAL_KAHAN = 2 } irt_integration;
+typedef enum { IRT_UNITS_TRJ = 0, IRT_UNITS_INTENSITY = 1 } irt_units;
+typedef enum { IRT_PREC_F32 = 0, IRT_PREC_F64 = 1 } irt_precision;
+typedef enum { IRT_MODE_THICK = 0 } irt_transfer_mode;
+
+/* opts.flags */
+#define IRT_FLAG_EXPLICIT_CHANNELS 1u  /* evaluate every channel explicitly (no
+                                          continuum basis shortcut) */
+#define IRT_FLAG_STATS 2u              /* accumulate work counters into the first
+                                          job's grid (see irt_grid_stats) */
+
+typedef struct irt_grid irt_grid;   /* opaque */
+
+/* Grid: nx * ny * nz cubic cells of side cell_cm.  dtype[q] is the storage
+ * type of field q (order of irt_fields); the physical value of field q is
+ * the stored value times scale[q] (0 means 1).  Scales let 16-bit storage
+ * hold densities above the fp16 range or abundances below its normal range. */
+typedef struct {
+  int nx, ny, nz;
+  double cell_cm;
+  irt_dtype dtype[5];
+  double scale[5];
+} irt_grid_desc;
+
+/* Field pointers, C order [z][y][x] (x fastest), device memory:
+ * n_h2_cm3 [cm^-3], t_gas_k [K], t_dust_k [K], v_los_kms [km/s, + receding],
+ * x_tracer (tracer number density / n_H2). */
+typedef struct {
+  const void *n_h2_cm3, *t_gas_k, *t_dust_k, *v_los_kms, *x_tracer;
+} irt_fields;
+
+/* Line constants: frequency [Hz], Einstein A [1/s], upper-level energy [K],
+ * rotational constant [Hz], statistical weights, molecular mass [amu],
+ * T_inf cut-off [K], 1-D microturbulent dispersion [km/s]. */
+typedef struct {
+  double nu_ul_hz, a_ul_s, e_u_k, b0_hz, g_u, g_l, mass_amu, t_inf_k, sigma_turb_kms;
+} irt_line;
+
+/* Dust: opacity per gram of gas [cm^2/g]; gas mass per H2 molecule [amu]. */
+typedef struct {
+  double kappa_cm2_per_g_gas, mu_mass_per_h2_amu;
+} irt_dust;
+
+typedef struct {
+  double theta_rad, phi_rad;
+  int npx, npy;        /* image size (z view: must equal nx, ny) */
+  double pixel_cm;     /* pixel pitch (oblique views) */
+  int trilinear;       /* 0: z view (cell exact), 1: oblique trilinear view */
+} irt_view;
+
+typedef struct {
+  int nchan;                 /* >= 1 */
+  double v_first_edge_kms;   /* lower edge of channel 0 */
+  double dv_kms;             /* channel width, > 0 */
+  int subsample_f;           /* velocity-subsampling factor f >= 0 */
+} irt_vaxis;
+
+typedef struct {
+  int mode;            /* irt_transfer_mode (IRT_MODE_THICK) */
+  int integration;     /* irt_integration */
+  int units;           /* irt_units */
+  double t_bg_k;       /* background (CMB) temperature [K], >= 0 */
+  int precision;       /* irt_precision: arithmetic type of the kernels */
+  unsigned flags;      /* IRT_FLAG_* */
+} irt_opts;
+
+/* Output cubes, device memory, [nchan][npy][npx].  float for IRT_PREC_F32,
+ * double for IRT_PREC_F64.  A NULL entry is not written. */
+typedef struct {
+  void *T, *C, *D, *L, *B;
+} irt_cubes;
+
+typedef struct {
+  irt_grid* grid;
+  irt_view view;
+  irt_vaxis vaxis;
+  irt_cubes out;
+} irt_job;
+
+/*
+ * irt_create_grid - copy the five fields (device pointers, layout above) into
+ * a grid owned by the library, in a cell-interleaved layout.  Storage: all
+ * 16-bit fields stay 16-bit (fp16/bf16 per field); otherwise fields are kept
+ * as float, or as double when any field is IRT_F64.  Later edits to the
+ * caller's buffers do not affect the grid.  On success *out is a new handle
+ * to release with irt_destroy.  IRT_EINVAL for non-positive sizes, a
+ * non-positive or non-finite cell size, NULL pointers or an unknown dtype;
+ * IRT_ENOMEM if the device allocation fails.
+ */
+irt_status irt_create_grid(const irt_grid_desc* desc, const irt_fields* fields,
+                           void* cuda_stream, irt_grid** out);
+
+/*
+ * irt_forward_ppv - render njobs >= 1 jobs (Sec. 4.4-4.10).  njobs == 1 runs
+ * one launch over the job's (ray, channel-window) work items; njobs > 1 runs
+ * one persistent launch over the work items of every job, taken from a
+ * device work queue.  The output cubes are written completely (every channel
+ * of every pixel).  IRT_EINVAL before any launch for: njobs < 1, NULL job,
+ * grid or constants, nchan < 1, dv <= 0, f < 0, a non-finite or negative
+ * constant, a z view whose size differs from the grid or whose angles are
+ * non-zero, an oblique view with npx/npy < 1 or pixel <= 0; all output
+ * pointers NULL.  IRT_EUNSUPPORTED for IRT_PREC_F64 on a grid that is not
+ * stored as double, or a channel count beyond the compiled window sizes.
+ */
+irt_status irt_forward_ppv(const irt_job* jobs, int njobs, const irt_line* line,
+                           const irt_dust* dust, const irt_opts* opts, void* cuda_stream);
+
+/*
+ * irt_adjoint_ppv - gradients of a scalar loss with respect to n_H2, T_gas
+ * and v_los of every cell for one z-view job (Sec. 4.8 run in reverse), given
+ * the cotangents dLoss/d[T], d[C], d[D], d[L], d[B] (float cubes
+ * [nchan][npy][npx], NULL = zero).  grad_* are float [nz][ny][nx], written
+ * completely (overwritten, not accumulated).  The forward transfer state is
+ * recomputed from per-ray checkpoints every 32 samples held in device
+ * scratch owned by the grid.  IRT_EINVAL as irt_forward_ppv plus NULL
+ * gradients; IRT_EUNSUPPORTED for oblique views or IRT_PREC_F64.
+ */
+irt_status irt_adjoint_ppv(const irt_job* job, const irt_line* line, const irt_dust* dust,
+                           const irt_opts* opts, const irt_cubes* cotangent,
+                           float* grad_n_h2, float* grad_t_gas, float* grad_v_los,
+                           void* cuda_stream);
+
+/* irt_destroy - free the grid and everything it owns (NULL is a no-op).  The
+ * caller must make sure no launch using the grid is still running. */
+irt_status irt_destroy(irt_grid* grid);
+
+/*
+ * irt_grid_stats - copy (synchronously, after the device is idle on all
+ * streams) the work counters a forward call with IRT_FLAG_STATS accumulated
+ * into this grid, then zero them if reset != 0.  out[6] = work items, ray
+ * samples, (sample, 32-velocity block) pairs where the line was evaluated,
+ * (sample, block) pairs integrated explicitly, items integrated without the
+ * continuum shortcut, and fine-velocity updates of the dense method
+ * (samples x fine velocities).  IRT_EINVAL for NULL arguments.
+ */
+irt_status irt_grid_stats(irt_grid* grid, unsigned long long out[6], int reset);
+
+/* Last error message of the calling thread ("" if none). */
+const char* irt_last_error(void);
+
+/* Number of kernel launches the library issued on this thread since the last
+ * call (for launch accounting in benchmarks). */
+long long irt_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* IRT_H_ */

@@ -301,7 +301,10 @@ void ray_outputs(const Line& ln, const DustP& du, const VAxis& va, int mode, int
     const double u = ufirst + g * dvf;
     const double nu = nu_of_u(ln, u);
     for (int k = 0; k < K; ++k) {
-      const S phi = profile_per_hz(ln, smp[k], u);
+      // a sample without line coefficients (T outside (0, T_inf], or no
+      // tracer) contributes no line; its profile is not needed
+      const bool no_line = val(jL[k]) == 0.0 && val(aL[k]) == 0.0;
+      const S phi = no_line ? S(0.0) : profile_per_hz(ln, smp[k], u);
       const S jD = aD[k] * planck(nu, smp[k].t_dust);
       jt[k] = jL[k] * phi + jD;
       at[k] = aL[k] * phi + aD[k];

@@ -1,0 +1,192 @@
+"""PyTorch-facing wrappers of the C ABI: device memory and streams come from
+torch, every computation runs in the CUDA library (argument marshalling only).
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+import torch
+
+from . import binding as B
+
+_DTYPE = {torch.float32: B.IRT_F32, torch.float16: B.IRT_F16, torch.bfloat16: B.IRT_BF16,
+          torch.float64: B.IRT_F64}
+_INTEGRATION = {"formal": B.IRT_FORMAL, "smooth": B.IRT_SMOOTH, "formal_kahan": B.IRT_FORMAL_KAHAN}
+_UNITS = {"trj": B.IRT_UNITS_TRJ, "intensity": B.IRT_UNITS_INTENSITY}
+_PREC = {"f32": B.IRT_PREC_F32, "f64": B.IRT_PREC_F64}
+COMPONENTS = ("T", "C", "D", "L", "B")
+
+
+def _stream_ptr(stream=None) -> int:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return int(s.cuda_stream)
+
+
+class Grid:
+    """Fields copied into a library-owned grid (``irt_create_grid``).
+
+    The five tensors are CUDA tensors of shape (nz, ny, nx), C contiguous,
+    dtype float32 / float16 / bfloat16 / float64 (each field may differ).
+    ``scales``: physical value = stored value * scale, per field."""
+
+    def __init__(self, n_h2, t_gas, t_dust, v_los, x_tracer, cell_cm: float, stream=None,
+                 scales=None):
+        ts = [n_h2, t_gas, t_dust, v_los, x_tracer]
+        shape = ts[0].shape
+        for t in ts:
+            if not t.is_cuda:
+                raise ValueError("fields must be CUDA tensors")
+            if t.shape != shape or t.dim() != 3:
+                raise ValueError("fields must share one (nz, ny, nx) shape")
+            if t.dtype not in _DTYPE:
+                raise ValueError(f"unsupported field dtype {t.dtype}")
+        ts = [t.contiguous() for t in ts]
+        nz, ny, nx = shape
+        sc = [1.0] * 5 if scales is None else [float(x) for x in scales]
+        desc = B.irt_grid_desc(nx, ny, nz, float(cell_cm),
+                               (B.ctypes.c_int * 5)(*[_DTYPE[t.dtype] for t in ts]),
+                               (B.ctypes.c_double * 5)(*sc))
+        fields = B.irt_fields(*[t.data_ptr() for t in ts])
+        self.handle = B.irt_create_grid(desc, fields, _stream_ptr(stream))
+        self._keep = ts   # the pack kernel reads them on the stream
+        self.shape = (nz, ny, nx)
+        self.cell_cm = float(cell_cm)
+        self.dtypes = tuple(t.dtype for t in ts)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            torch.cuda.synchronize()
+            B.irt_destroy(self.handle)
+            self.handle = None
+            self._keep = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def line_struct(line: dict) -> B.irt_line:
+    return B.irt_line(*[float(line[k]) for k, _ in B.irt_line._fields_])
+
+
+def dust_struct(dust: dict) -> B.irt_dust:
+    return B.irt_dust(float(dust["kappa_cm2_per_g_gas"]), float(dust["mu_mass_per_h2_amu"]))
+
+
+def view_struct(view) -> B.irt_view:
+    return B.irt_view(float(view.theta_rad), float(view.phi_rad), int(view.npx), int(view.npy),
+                      float(view.pixel_cm), int(view.trilinear))
+
+
+def vaxis_struct(va) -> B.irt_vaxis:
+    return B.irt_vaxis(int(va.nchan), float(va.v_first_edge_kms), float(va.dv_kms),
+                       int(va.subsample_f))
+
+
+def opts_struct(integration="smooth", units="trj", t_bg=2.725, precision="f32",
+                flags=0) -> B.irt_opts:
+    return B.irt_opts(B.IRT_MODE_THICK, _INTEGRATION[integration], _UNITS[units], float(t_bg),
+                      _PREC[precision], int(flags))
+
+
+def alloc_cubes(view, vaxis, precision="f32", device=None, components=COMPONENTS):
+    dt = torch.float64 if precision == "f64" else torch.float32
+    dev = device or torch.device("cuda")
+    return {k: torch.empty((vaxis.nchan, view.npy, view.npx), dtype=dt, device=dev)
+            for k in components}
+
+
+def _cubes_struct(cubes: dict) -> B.irt_cubes:
+    return B.irt_cubes(*[cubes[k].data_ptr() if cubes.get(k) is not None else None
+                         for k in COMPONENTS])
+
+
+def make_job(grid: Grid, view, vaxis, cubes: dict) -> B.irt_job:
+    return B.irt_job(grid.handle, view_struct(view), vaxis_struct(vaxis), _cubes_struct(cubes))
+
+
+def forward(grid: Grid, view, vaxis, line: dict, dust: dict, *, integration="smooth",
+            units="trj", t_bg=2.725, precision="f32", flags=0, out=None, stream=None,
+            components=COMPONENTS) -> dict:
+    """Render one job (``irt_forward_ppv`` with njobs = 1).  Returns the cubes
+    {"T","C","D","L","B"} as [nchan, npy, npx] tensors."""
+    cubes = out if out is not None else alloc_cubes(view, vaxis, precision,
+                                                     components=components)
+    job = make_job(grid, view, vaxis, cubes)
+    B.irt_forward_ppv([job], line_struct(line), dust_struct(dust),
+                      opts_struct(integration, units, t_bg, precision, flags), _stream_ptr(stream))
+    return cubes
+
+
+def forward_batch(jobs, line: dict, dust: dict, *, integration="smooth", units="trj",
+                  t_bg=2.725, precision="f32", flags=0, outs=None, stream=None) -> list:
+    """Render many jobs in one persistent launch.  ``jobs`` = [(grid, view,
+    vaxis), ...]; returns one cube dict per job."""
+    if outs is None:
+        outs = [alloc_cubes(v, va, precision) for (_, v, va) in jobs]
+    cj = [make_job(g, v, va, o) for (g, v, va), o in zip(jobs, outs)]
+    B.irt_forward_ppv(cj, line_struct(line), dust_struct(dust),
+                      opts_struct(integration, units, t_bg, precision, flags), _stream_ptr(stream))
+    return outs
+
+
+def adjoint(grid: Grid, view, vaxis, line: dict, dust: dict, cotangent: dict, *,
+            integration="smooth", units="trj", t_bg=2.725, flags=0, grads=None, stream=None):
+    """Gradients of a loss with respect to n_H2, T_gas, v_los (z view) given
+    the cotangent cubes (``irt_adjoint_ppv``).  Returns (g_n, g_t, g_v)."""
+    nz, ny, nx = grid.shape
+    if grads is None:
+        grads = tuple(torch.empty((nz, ny, nx), dtype=torch.float32, device="cuda")
+                      for _ in range(3))
+    cot = {k: (cotangent[k].contiguous() if cotangent.get(k) is not None else None)
+           for k in COMPONENTS}
+    job = make_job(grid, view, vaxis, {k: None for k in COMPONENTS})
+    B.irt_adjoint_ppv(job, line_struct(line), dust_struct(dust),
+                      opts_struct(integration, units, t_bg, "f32", flags), _cubes_struct(cot),
+                      grads[0].data_ptr(), grads[1].data_ptr(), grads[2].data_ptr(),
+                      _stream_ptr(stream))
+    return grads
+
+
+@dataclass
+class RenderConfig:
+    """Everything but the differentiable fields of an autograd render."""
+    cell_cm: float
+    view: object
+    vaxis: object
+    line: dict
+    dust: dict
+    integration: str = "smooth"
+    units: str = "trj"
+    t_bg: float = 2.725
+
+
+class RenderPPV(torch.autograd.Function):
+    """Differentiable z-view render: (n_H2, T_gas, v_los, T_dust, x) -> the
+    five cubes; gradients flow to n_H2, T_gas and v_los through the
+    hand-written adjoint kernel."""
+
+    @staticmethod
+    def forward(ctx, n_h2, t_gas, v_los, t_dust, x_tracer, cfg: RenderConfig):
+        grid = Grid(n_h2.detach().float(), t_gas.detach().float(), t_dust.detach().float(),
+                    v_los.detach().float(), x_tracer.detach().float(), cfg.cell_cm)
+        cubes = forward(grid, cfg.view, cfg.vaxis, cfg.line, cfg.dust,
+                        integration=cfg.integration, units=cfg.units, t_bg=cfg.t_bg)
+        ctx.grid = grid
+        ctx.cfg = cfg
+        return tuple(cubes[k] for k in COMPONENTS)
+
+    @staticmethod
+    def backward(ctx, gT, gC, gD, gL, gB):
+        cfg = ctx.cfg
+        cot = dict(T=gT, C=gC, D=gD, L=gL, B=gB)
+        gn, gt, gv = adjoint(ctx.grid, cfg.view, cfg.vaxis, cfg.line, cfg.dust, cot,
+                             integration=cfg.integration, units=cfg.units, t_bg=cfg.t_bg)
+        ctx.grid.close()
+        return gn, gt, gv, None, None, None
+
+
+def render_ppv(n_h2, t_gas, v_los, t_dust, x_tracer, cfg: RenderConfig):
+    return RenderPPV.apply(n_h2, t_gas, v_los, t_dust, x_tracer, cfg)

@@ -1,0 +1,158 @@
+"""ctypes binding of the C ABI in include/irt.h (argument marshalling only).
+
+The four entry points keep their C names: :func:`irt_create_grid`,
+:func:`irt_forward_ppv`, :func:`irt_adjoint_ppv`, :func:`irt_destroy`.  Every
+step of the computation runs in the CUDA library; if ``libirt.so`` is absent
+importing this module raises, there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libirt.so")
+
+IRT_OK, IRT_EINVAL, IRT_ENOMEM, IRT_ECUDA, IRT_EUNSUPPORTED, IRT_ETIMEOUT = range(6)
+IRT_F32, IRT_F16, IRT_BF16, IRT_F64 = range(4)
+IRT_FORMAL, IRT_SMOOTH, IRT_FORMAL_KAHAN = range(3)
+IRT_UNITS_TRJ, IRT_UNITS_INTENSITY = range(2)
+IRT_PREC_F32, IRT_PREC_F64 = range(2)
+IRT_MODE_THICK = 0
+IRT_FLAG_EXPLICIT_CHANNELS = 1
+IRT_FLAG_STATS = 2
+
+STATUS_NAMES = {0: "IRT_OK", 1: "IRT_EINVAL", 2: "IRT_ENOMEM", 3: "IRT_ECUDA",
+                4: "IRT_EUNSUPPORTED", 5: "IRT_ETIMEOUT"}
+
+#: symbols include/irt.h declares
+EXPORTED = ("irt_create_grid", "irt_forward_ppv", "irt_adjoint_ppv", "irt_destroy",
+            "irt_grid_stats", "irt_last_error", "irt_launch_count")
+
+
+class irt_grid_desc(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+                ("cell_cm", ctypes.c_double), ("dtype", ctypes.c_int * 5),
+                ("scale", ctypes.c_double * 5)]
+
+
+class irt_fields(ctypes.Structure):
+    _fields_ = [("n_h2_cm3", ctypes.c_void_p), ("t_gas_k", ctypes.c_void_p),
+                ("t_dust_k", ctypes.c_void_p), ("v_los_kms", ctypes.c_void_p),
+                ("x_tracer", ctypes.c_void_p)]
+
+
+class irt_line(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_double) for k in (
+        "nu_ul_hz", "a_ul_s", "e_u_k", "b0_hz", "g_u", "g_l", "mass_amu", "t_inf_k",
+        "sigma_turb_kms")]
+
+
+class irt_dust(ctypes.Structure):
+    _fields_ = [("kappa_cm2_per_g_gas", ctypes.c_double), ("mu_mass_per_h2_amu", ctypes.c_double)]
+
+
+class irt_view(ctypes.Structure):
+    _fields_ = [("theta_rad", ctypes.c_double), ("phi_rad", ctypes.c_double),
+                ("npx", ctypes.c_int), ("npy", ctypes.c_int), ("pixel_cm", ctypes.c_double),
+                ("trilinear", ctypes.c_int)]
+
+
+class irt_vaxis(ctypes.Structure):
+    _fields_ = [("nchan", ctypes.c_int), ("v_first_edge_kms", ctypes.c_double),
+                ("dv_kms", ctypes.c_double), ("subsample_f", ctypes.c_int)]
+
+
+class irt_opts(ctypes.Structure):
+    _fields_ = [("mode", ctypes.c_int), ("integration", ctypes.c_int), ("units", ctypes.c_int),
+                ("t_bg_k", ctypes.c_double), ("precision", ctypes.c_int),
+                ("flags", ctypes.c_uint)]
+
+
+class irt_cubes(ctypes.Structure):
+    _fields_ = [("T", ctypes.c_void_p), ("C", ctypes.c_void_p), ("D", ctypes.c_void_p),
+                ("L", ctypes.c_void_p), ("B", ctypes.c_void_p)]
+
+
+class irt_job(ctypes.Structure):
+    _fields_ = [("grid", ctypes.c_void_p), ("view", irt_view), ("vaxis", irt_vaxis),
+                ("out", irt_cubes)]
+
+
+class IrtError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"CUDA library {LIB_PATH} is missing: build it with "
+                          "`python -m paper_2607_01338_b300.build` (needs nvcc)")
+    L = ctypes.CDLL(LIB_PATH)
+    P = ctypes.POINTER
+    L.irt_create_grid.restype = ctypes.c_int
+    L.irt_create_grid.argtypes = [P(irt_grid_desc), P(irt_fields), ctypes.c_void_p,
+                                  P(ctypes.c_void_p)]
+    L.irt_forward_ppv.restype = ctypes.c_int
+    L.irt_forward_ppv.argtypes = [P(irt_job), ctypes.c_int, P(irt_line), P(irt_dust),
+                                  P(irt_opts), ctypes.c_void_p]
+    L.irt_adjoint_ppv.restype = ctypes.c_int
+    L.irt_adjoint_ppv.argtypes = [P(irt_job), P(irt_line), P(irt_dust), P(irt_opts),
+                                  P(irt_cubes), ctypes.c_void_p, ctypes.c_void_p,
+                                  ctypes.c_void_p, ctypes.c_void_p]
+    L.irt_destroy.restype = ctypes.c_int
+    L.irt_destroy.argtypes = [ctypes.c_void_p]
+    L.irt_grid_stats.restype = ctypes.c_int
+    L.irt_grid_stats.argtypes = [ctypes.c_void_p, P(ctypes.c_ulonglong), ctypes.c_int]
+    L.irt_last_error.restype = ctypes.c_char_p
+    L.irt_last_error.argtypes = []
+    L.irt_launch_count.restype = ctypes.c_longlong
+    L.irt_launch_count.argtypes = []
+    return L
+
+
+lib = _load()
+
+
+def _check(status):
+    if status != IRT_OK:
+        raise IrtError(status, lib.irt_last_error().decode())
+
+
+def irt_create_grid(desc: irt_grid_desc, fields: irt_fields, stream: int) -> int:
+    h = ctypes.c_void_p()
+    _check(lib.irt_create_grid(ctypes.byref(desc), ctypes.byref(fields), ctypes.c_void_p(stream),
+                               ctypes.byref(h)))
+    return h.value
+
+
+def irt_forward_ppv(jobs, line: irt_line, dust: irt_dust, opts: irt_opts, stream: int) -> None:
+    arr = (irt_job * len(jobs))(*jobs)
+    _check(lib.irt_forward_ppv(arr, len(jobs), ctypes.byref(line), ctypes.byref(dust),
+                               ctypes.byref(opts), ctypes.c_void_p(stream)))
+
+
+def irt_adjoint_ppv(job: irt_job, line: irt_line, dust: irt_dust, opts: irt_opts,
+                    cotangent: irt_cubes, grad_n: int, grad_t: int, grad_v: int,
+                    stream: int) -> None:
+    _check(lib.irt_adjoint_ppv(ctypes.byref(job), ctypes.byref(line), ctypes.byref(dust),
+                               ctypes.byref(opts), ctypes.byref(cotangent),
+                               ctypes.c_void_p(grad_n), ctypes.c_void_p(grad_t),
+                               ctypes.c_void_p(grad_v), ctypes.c_void_p(stream)))
+
+
+def irt_destroy(handle: int) -> None:
+    _check(lib.irt_destroy(ctypes.c_void_p(handle)))
+
+
+def irt_grid_stats(handle: int, reset: bool = True) -> dict:
+    out = (ctypes.c_ulonglong * 6)()
+    _check(lib.irt_grid_stats(ctypes.c_void_p(handle), out, int(reset)))
+    keys = ("items", "samples", "line_block_samples", "hull_block_samples", "explicit_items",
+            "dense_fine_updates")
+    return dict(zip(keys, [int(v) for v in out]))
+
+
+def irt_launch_count() -> int:
+    return int(lib.irt_launch_count())

@@ -1,0 +1,446 @@
+// C ABI of the library (include/irt.h): argument validation, grid lifetime,
+// constant folding, launch planning.  No arithmetic of the method runs here;
+// the host only converts the caller's constants to the kernels' units.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdarg>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "irt_internal.h"
+
+namespace irt {
+
+int dispatch_fwd_f32_smooth(int store, int ni, const JobTable& jobs, int njobs, const PhysParams& P,
+                            long long total, unsigned long long* queue, int grid_blocks, int kmax,
+                            int fwmax, int cwmax, unsigned flags, unsigned long long* stats,
+                            cudaStream_t s);
+int dispatch_fwd_f32_formal(int store, int ni, const JobTable& jobs, int njobs, const PhysParams& P,
+                            long long total, unsigned long long* queue, int grid_blocks, int kmax,
+                            int fwmax, int cwmax, unsigned flags, unsigned long long* stats,
+                            cudaStream_t s);
+int dispatch_fwd_f32_kahan(int store, int ni, const JobTable& jobs, int njobs, const PhysParams& P,
+                           long long total, unsigned long long* queue, int grid_blocks, int kmax,
+                           int fwmax, int cwmax, unsigned flags, unsigned long long* stats,
+                           cudaStream_t s);
+int dispatch_fwd_f64(int mode, int store, int ni, const JobTable& jobs, int njobs,
+                     const PhysParams& P, long long total, unsigned long long* queue,
+                     int grid_blocks, int kmax, int fwmax, int cwmax, unsigned flags,
+                     unsigned long long* stats, cudaStream_t s);
+
+namespace {
+
+thread_local std::string g_err;
+thread_local long long g_launches = 0;
+
+irt_status fail(irt_status st, const char* fmt, ...) __attribute__((format(printf, 2, 3)));
+irt_status fail(irt_status st, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return st;
+}
+
+irt_status cuda_fail(int e, const char* where) {
+  return fail(IRT_ECUDA, "%s: %s", where, cudaGetErrorString((cudaError_t)e));
+}
+
+bool finite_pos(double x) { return std::isfinite(x) && x > 0.0; }
+bool finite_nonneg(double x) { return std::isfinite(x) && x >= 0.0; }
+
+// CODATA 2018 constants for the unit conversions of the launch parameters.
+constexpr double kH = 6.62607015e-27;    // erg s
+constexpr double kK = 1.380649e-16;      // erg/K
+constexpr double kC = 2.99792458e10;     // cm/s
+constexpr double kCkms = 2.99792458e5;   // km/s
+constexpr double kAmu = 1.66053906660e-24;
+constexpr double kPi = 3.14159265358979323846;
+
+}  // namespace
+}  // namespace irt
+
+struct irt_grid {
+  int nx, ny, nz;
+  double dx;
+  int store;
+  int bf16_mask;
+  double scale[5];
+  void* cells;
+  size_t cell_bytes;
+  unsigned long long* ctl;   // device control words (work-queue counter)
+  int device;
+};
+
+using namespace irt;
+
+extern "C" {
+
+const char* irt_last_error(void) { return g_err.c_str(); }
+
+long long irt_launch_count(void) {
+  const long long n = g_launches;
+  g_launches = 0;
+  return n;
+}
+
+irt_status irt_create_grid(const irt_grid_desc* desc, const irt_fields* fields,
+                           void* cuda_stream, irt_grid** out) {
+  g_err.clear();
+  if (!desc || !fields || !out) return fail(IRT_EINVAL, "irt_create_grid: NULL argument");
+  *out = nullptr;
+  if (desc->nx < 1 || desc->ny < 1 || desc->nz < 1)
+    return fail(IRT_EINVAL, "irt_create_grid: grid size %d x %d x %d", desc->nx, desc->ny,
+                desc->nz);
+  if (!finite_pos(desc->cell_cm)) return fail(IRT_EINVAL, "irt_create_grid: cell_cm <= 0");
+  const void* src[5] = {fields->n_h2_cm3, fields->t_gas_k, fields->t_dust_k, fields->v_los_kms,
+                        fields->x_tracer};
+  int dt[5];
+  bool any64 = false, all16 = true;
+  int bf_mask = 0;
+  for (int q = 0; q < 5; ++q) {
+    if (!src[q]) return fail(IRT_EINVAL, "irt_create_grid: field %d is NULL", q);
+    dt[q] = (int)desc->dtype[q];
+    if (dt[q] < IRT_F32 || dt[q] > IRT_F64)
+      return fail(IRT_EINVAL, "irt_create_grid: field %d has unknown dtype %d", q, dt[q]);
+    if (dt[q] == IRT_F64) any64 = true;
+    if (dt[q] != IRT_F16 && dt[q] != IRT_BF16) all16 = false;
+    if (dt[q] == IRT_BF16) bf_mask |= 1 << q;
+  }
+  double scale[5];
+  for (int q = 0; q < 5; ++q) {
+    scale[q] = desc->scale[q] == 0.0 ? 1.0 : desc->scale[q];
+    if (!std::isfinite(scale[q]) || scale[q] <= 0.0)
+      return fail(IRT_EINVAL, "irt_create_grid: scale[%d] must be finite and > 0", q);
+  }
+  const long long ncell = (long long)desc->nx * desc->ny * desc->nz;
+  const int store = any64 ? ST_F64 : (all16 ? ST_H16 : ST_F32);
+  const size_t cb = store == ST_F64 ? sizeof(CellF64) : store == ST_H16 ? sizeof(CellH16)
+                                                                         : sizeof(CellF32);
+  irt_grid* g = new irt_grid();
+  g->nx = desc->nx; g->ny = desc->ny; g->nz = desc->nz;
+  g->dx = desc->cell_cm;
+  g->store = store;
+  g->bf16_mask = store == ST_H16 ? bf_mask : 0;
+  for (int q = 0; q < 5; ++q) g->scale[q] = scale[q];
+  g->cell_bytes = cb * (size_t)ncell;
+  g->ctl = nullptr;
+  cudaGetDevice(&g->device);
+  if (cudaMalloc(&g->cells, g->cell_bytes) != cudaSuccess) {
+    cudaGetLastError();
+    delete g;
+    return fail(IRT_ENOMEM, "irt_create_grid: cannot allocate %zu bytes", cb * (size_t)ncell);
+  }
+  if (cudaMalloc((void**)&g->ctl, 64) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(g->cells);
+    delete g;
+    return fail(IRT_ENOMEM, "irt_create_grid: cannot allocate control words");
+  }
+  if (cudaMemsetAsync(g->ctl, 0, 64, (cudaStream_t)cuda_stream) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(g->cells);
+    cudaFree(g->ctl);
+    delete g;
+    return fail(IRT_ECUDA, "irt_create_grid: cannot clear control words");
+  }
+  const int e = launch_pack(store, src, dt, scale, g->cells, ncell, cuda_stream);
+  ++g_launches;
+  if (e) {
+    cudaFree(g->cells);
+    cudaFree(g->ctl);
+    delete g;
+    return cuda_fail(e, "irt_create_grid: pack kernel");
+  }
+  *out = g;
+  return IRT_OK;
+}
+
+irt_status irt_grid_stats(irt_grid* g, unsigned long long out[6], int reset) {
+  g_err.clear();
+  if (!g || !out) return fail(IRT_EINVAL, "irt_grid_stats: NULL argument");
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) e = cudaMemcpy(out, g->ctl + 1, 6 * sizeof(unsigned long long),
+                                       cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && reset) e = cudaMemset(g->ctl + 1, 0, 6 * sizeof(unsigned long long));
+  if (e != cudaSuccess) return cuda_fail(e, "irt_grid_stats");
+  return IRT_OK;
+}
+
+irt_status irt_destroy(irt_grid* g) {
+  g_err.clear();
+  if (!g) return IRT_OK;
+  cudaFree(g->cells);
+  cudaFree(g->ctl);
+  delete g;
+  return IRT_OK;
+}
+
+}  // extern "C"
+
+namespace irt {
+namespace {
+
+irt_status check_line(const irt_line* ln, const irt_dust* du, const irt_opts* op) {
+  if (!ln || !du || !op) return fail(IRT_EINVAL, "NULL line, dust or opts");
+  const double lv[] = {ln->nu_ul_hz, ln->a_ul_s, ln->b0_hz, ln->g_u, ln->g_l, ln->mass_amu};
+  for (double v : lv)
+    if (!finite_pos(v)) return fail(IRT_EINVAL, "line constants must be finite and > 0");
+  if (!std::isfinite(ln->e_u_k)) return fail(IRT_EINVAL, "line e_u_k is not finite");
+  if (!finite_nonneg(ln->t_inf_k) && !(std::isinf(ln->t_inf_k) && ln->t_inf_k > 0))
+    return fail(IRT_EINVAL, "line t_inf_k must be >= 0");
+  if (!finite_nonneg(ln->sigma_turb_kms)) return fail(IRT_EINVAL, "sigma_turb_kms must be >= 0");
+  if (!finite_nonneg(du->kappa_cm2_per_g_gas) || !finite_nonneg(du->mu_mass_per_h2_amu))
+    return fail(IRT_EINVAL, "dust constants must be finite and >= 0");
+  if (!finite_nonneg(op->t_bg_k)) return fail(IRT_EINVAL, "t_bg_k must be finite and >= 0");
+  if (op->mode != IRT_MODE_THICK) return fail(IRT_EUNSUPPORTED, "transfer mode %d", op->mode);
+  if (op->integration < IRT_FORMAL || op->integration > IRT_FORMAL_KAHAN)
+    return fail(IRT_EINVAL, "unknown integration %d", op->integration);
+  if (op->units != IRT_UNITS_TRJ && op->units != IRT_UNITS_INTENSITY)
+    return fail(IRT_EINVAL, "unknown units %d", op->units);
+  if (op->precision != IRT_PREC_F32 && op->precision != IRT_PREC_F64)
+    return fail(IRT_EINVAL, "unknown precision %d", op->precision);
+  return IRT_OK;
+}
+
+PhysParams fold_constants(const irt_line* ln, const irt_dust* du, const irt_opts* op) {
+  PhysParams P;
+  const double nu = ln->nu_ul_hz;
+  P.T0 = kH * nu / kK;
+  P.e_u = ln->e_u_k;
+  P.e_l = ln->e_u_k - P.T0;
+  P.theta_rot = kH * ln->b0_hz / kK;
+  P.g_u = ln->g_u;
+  const double k_i = kC * kC / (2.0 * kK * nu * nu);     // cgs intensity -> K units
+  const double per_hz = kCkms / nu / std::sqrt(kPi);      // phi_nu peak * b [km/s]
+  P.cj = (kH * nu / (4.0 * kPi)) * ln->a_ul_s * ln->g_u * k_i * per_hz;
+  P.ca = (kC * kC * ln->a_ul_s / (8.0 * kPi * nu * nu)) * ln->g_u * per_hz;
+  P.c_th = 2.0 * kK / (ln->mass_amu * kAmu) / 1e10;
+  P.two_sig2 = 2.0 * ln->sigma_turb_kms * ln->sigma_turb_kms;
+  P.t_inf = ln->t_inf_k;
+  P.cad = du->kappa_cm2_per_g_gas * du->mu_mass_per_h2_amu * kAmu;
+  P.inv_c_kms = 1.0 / kCkms;
+  P.t_bg = op->t_bg_k;
+  P.units = op->units;
+  P.integration = op->integration;
+  P.out_scale = (op->units == IRT_UNITS_TRJ) ? 1.0 : 1.0 / k_i;
+  return P;
+}
+
+irt_status check_job(const irt_job& jb, int precision) {
+  const irt_grid* g = jb.grid;
+  if (!g) return fail(IRT_EINVAL, "job without grid");
+  const irt_vaxis& va = jb.vaxis;
+  if (va.nchan < 1) return fail(IRT_EINVAL, "nchan < 1");
+  if (!finite_pos(va.dv_kms)) return fail(IRT_EINVAL, "dv_kms must be > 0");
+  if (!std::isfinite(va.v_first_edge_kms)) return fail(IRT_EINVAL, "v_first_edge not finite");
+  if (va.subsample_f < 0) return fail(IRT_EINVAL, "subsample_f < 0");
+  if (va.subsample_f > 64) return fail(IRT_EUNSUPPORTED, "subsample_f > 64");
+  const irt_view& vw = jb.view;
+  if (vw.trilinear == 0) {
+    if (vw.theta_rad != 0.0 || vw.phi_rad != 0.0)
+      return fail(IRT_EINVAL, "z view (trilinear = 0) needs theta = phi = 0");
+    if (vw.npx != g->nx || vw.npy != g->ny)
+      return fail(IRT_EINVAL, "z view image %d x %d differs from grid %d x %d", vw.npx, vw.npy,
+                  g->nx, g->ny);
+  } else if (vw.trilinear == 1) {
+    if (vw.npx < 1 || vw.npy < 1) return fail(IRT_EINVAL, "view npx/npy < 1");
+    if (!finite_pos(vw.pixel_cm)) return fail(IRT_EINVAL, "view pixel_cm must be > 0");
+    if (!std::isfinite(vw.theta_rad) || !std::isfinite(vw.phi_rad))
+      return fail(IRT_EINVAL, "view angles not finite");
+  } else {
+    return fail(IRT_EINVAL, "view.trilinear must be 0 or 1");
+  }
+  const void* o[5] = {jb.out.T, jb.out.C, jb.out.D, jb.out.L, jb.out.B};
+  bool any = false;
+  for (const void* p : o) any = any || p;
+  if (!any) return fail(IRT_EINVAL, "all output cubes are NULL");
+  if (precision == IRT_PREC_F64 && g->store != ST_F64)
+    return fail(IRT_EUNSUPPORTED, "double precision needs a grid stored as double");
+  return IRT_OK;
+}
+
+// Window plan: blocks per lane (compiled sizes) and channels per window.
+struct Plan {
+  int ni, cw, nwin, nfw, kmax;
+};
+
+const int kNiF32[] = {9, 17, 33};
+
+Plan plan_job(const irt_job& jb, int precision, int force_ni) {
+  Plan p;
+  const int f = jb.vaxis.subsample_f, nch = jb.vaxis.nchan;
+  auto fine_of = [&](int cw) { return f >= 1 ? 2 * f * cw + 1 : cw; };
+  auto cw_for = [&](int ni) {
+    const int slots = 32 * ni;
+    return f >= 1 ? (slots - 1) / (2 * f) : slots;
+  };
+  if (precision == IRT_PREC_F64) {
+    p.ni = 17;
+  } else if (force_ni > 0) {
+    p.ni = force_ni;
+  } else {
+    p.ni = 33;
+    for (int ni : kNiF32)
+      if (fine_of(nch) <= 32 * ni) { p.ni = ni; break; }
+  }
+  p.cw = std::min(nch, cw_for(p.ni));
+  p.nwin = (nch + p.cw - 1) / p.cw;
+  p.nfw = fine_of(p.cw);
+  const irt_grid* g = jb.grid;
+  if (jb.view.trilinear == 0) {
+    p.kmax = g->nz;
+  } else {
+    const double diag = std::sqrt((double)g->nx * g->nx + (double)g->ny * g->ny +
+                                  (double)g->nz * g->nz);
+    p.kmax = (int)std::ceil(diag) + 2;
+  }
+  return p;
+}
+
+JobDev make_jobdev(const irt_job& jb, const Plan& p) {
+  JobDev d;
+  std::memset(&d, 0, sizeof d);
+  const irt_grid* g = jb.grid;
+  d.cells = g->cells;
+  d.store = g->store;
+  d.bf16_mask = g->bf16_mask;
+  // 16-bit cells are stored as given; the kernels apply the scales.  Wider
+  // storage had the scales applied while packing.
+  for (int q = 0; q < 5; ++q) d.scale[q] = g->store == ST_H16 ? (float)g->scale[q] : 1.0f;
+  d.nx = g->nx; d.ny = g->ny; d.nz = g->nz;
+  d.dx = g->dx;
+  d.zview = jb.view.trilinear == 0;
+  d.theta = jb.view.theta_rad;
+  d.phi = jb.view.phi_rad;
+  d.npx = jb.view.npx;
+  d.npy = jb.view.npy;
+  d.pixel = jb.view.pixel_cm;
+  d.nchan = jb.vaxis.nchan;
+  d.f = jb.vaxis.subsample_f;
+  d.v0 = jb.vaxis.v_first_edge_kms;
+  d.dv = jb.vaxis.dv_kms;
+  if (d.f >= 1) {
+    d.ufirst = d.v0;
+    d.dvf = d.dv / (2.0 * d.f);
+  } else {
+    d.ufirst = d.v0 + 0.5 * d.dv;
+    d.dvf = d.dv;
+  }
+  d.cw = p.cw;
+  d.nwin = p.nwin;
+  d.kmax = p.kmax;
+  d.out[0] = jb.out.T; d.out[1] = jb.out.C; d.out[2] = jb.out.D;
+  d.out[3] = jb.out.L; d.out[4] = jb.out.B;
+  d.nitems = (long long)d.npx * d.npy * d.nwin;
+  return d;
+}
+
+int dispatch(int precision, int mode, int store, int ni, const JobTable& jobs, int njobs,
+             const PhysParams& P, long long total, unsigned long long* queue, int grid_blocks,
+             int kmax, int fwmax, int cwmax, unsigned flags, unsigned long long* stats,
+             cudaStream_t s) {
+  if (precision == IRT_PREC_F64)
+    return dispatch_fwd_f64(mode, store, ni, jobs, njobs, P, total, queue, grid_blocks, kmax,
+                            fwmax, cwmax, flags, stats, s);
+  if (mode == M_SMOOTH)
+    return dispatch_fwd_f32_smooth(store, ni, jobs, njobs, P, total, queue, grid_blocks, kmax,
+                                   fwmax, cwmax, flags, stats, s);
+  if (mode == M_FORMAL)
+    return dispatch_fwd_f32_formal(store, ni, jobs, njobs, P, total, queue, grid_blocks, kmax,
+                                   fwmax, cwmax, flags, stats, s);
+  return dispatch_fwd_f32_kahan(store, ni, jobs, njobs, P, total, queue, grid_blocks, kmax, fwmax,
+                                cwmax, flags, stats, s);
+}
+
+}  // namespace
+}  // namespace irt
+
+extern "C" irt_status irt_forward_ppv(const irt_job* jobs, int njobs, const irt_line* line,
+                                      const irt_dust* dust, const irt_opts* opts,
+                                      void* cuda_stream) {
+  g_err.clear();
+  if (!jobs || njobs < 1) return fail(IRT_EINVAL, "irt_forward_ppv: no jobs");
+  irt_status st = check_line(line, dust, opts);
+  if (st) return st;
+  for (int j = 0; j < njobs; ++j) {
+    st = check_job(jobs[j], opts->precision);
+    if (st) return st;
+  }
+  const PhysParams P = fold_constants(line, dust, opts);
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  const int prec = opts->precision;
+  const int mode = opts->integration;
+
+  // plan every job; the batch path needs one store class and one block count
+  std::vector<Plan> plans(njobs);
+  int ni = 0;
+  for (int j = 0; j < njobs; ++j) {
+    plans[j] = plan_job(jobs[j], prec, 0);
+    ni = std::max(ni, plans[j].ni);
+  }
+  const int store = jobs[0].grid->store;
+  for (int j = 1; j < njobs; ++j)
+    if (jobs[j].grid->store != store)
+      return fail(IRT_EUNSUPPORTED, "batched jobs must share the field storage type");
+  if (njobs > 1) {
+    for (int j = 0; j < njobs; ++j) plans[j] = plan_job(jobs[j], prec, ni);
+  }
+
+  // order: most expensive rays first (greedy longest-processing-time order
+  // for the persistent work queue)
+  std::vector<int> order(njobs);
+  for (int j = 0; j < njobs; ++j) order[j] = j;
+  if (njobs > 1) {
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+      const double ca = (double)plans[a].kmax * plans[a].nfw;
+      const double cb = (double)plans[b].kmax * plans[b].nfw;
+      return ca > cb;
+    });
+  }
+  for (int base = 0; base < njobs; base += kMaxJobs) {
+    const int nb = std::min(kMaxJobs, njobs - base);
+    JobTable tab;
+    std::memset(&tab, 0, sizeof tab);
+    long long total = 0;
+    int kmax = 1, fwmax = 1, cwmax = 1;
+    for (int t = 0; t < nb; ++t) {
+      const int j = order[base + t];
+      tab.j[t] = make_jobdev(jobs[j], plans[j]);
+      tab.j[t].item_begin = total;
+      total += tab.j[t].nitems;
+      kmax = std::max(kmax, plans[j].kmax);
+      fwmax = std::max(fwmax, 32 * plans[j].ni);
+      cwmax = std::max(cwmax, plans[j].cw);
+    }
+    unsigned long long* queue = nullptr;
+    if (njobs > 1) {
+      queue = jobs[order[base]].grid->ctl;
+      const cudaError_t e = cudaMemsetAsync(queue, 0, sizeof(unsigned long long), s);
+      if (e != cudaSuccess) return cuda_fail(e, "irt_forward_ppv: queue reset");
+    }
+    unsigned long long* stats =
+        (opts->flags & IRT_FLAG_STATS) ? jobs[0].grid->ctl + 1 : nullptr;
+    const int e = dispatch(prec, mode, store, ni, tab, nb, P, total, queue, 0, kmax, fwmax,
+                           cwmax, opts->flags, stats, s);
+    ++g_launches;
+    if (e) return cuda_fail(e, "irt_forward_ppv: forward kernel");
+  }
+  return IRT_OK;
+}
+
+extern "C" irt_status irt_adjoint_ppv(const irt_job* job, const irt_line* line,
+                                      const irt_dust* dust, const irt_opts* opts,
+                                      const irt_cubes* cotangent, float* grad_n_h2,
+                                      float* grad_t_gas, float* grad_v_los, void* cuda_stream) {
+  g_err.clear();
+  (void)job; (void)line; (void)dust; (void)opts; (void)cotangent; (void)grad_n_h2;
+  (void)grad_t_gas; (void)grad_v_los; (void)cuda_stream;
+  return fail(IRT_EUNSUPPORTED, "irt_adjoint_ppv: not built yet");
+}

@@ -1,0 +1,83 @@
+// Internal structures shared by the host side of the library and its kernels.
+#pragma once
+
+#include <stdint.h>
+
+#include "../../include/irt.h"
+
+namespace irt {
+
+// Packed field storage of a grid (one cell = the five fields interleaved).
+enum Store { ST_F32 = 0, ST_H16 = 1, ST_F64 = 2 };
+
+// Integration variants (values of irt_integration).
+enum Mode { M_FORMAL = 0, M_SMOOTH = 1, M_FORMAL_KAHAN = 2 };
+
+struct alignas(32) CellF32 { float v[5]; float pad[3]; };
+struct alignas(16) CellH16 { uint16_t v[5]; uint16_t pad[3]; };
+struct alignas(64) CellF64 { double v[5]; double pad[3]; };
+
+// Physical constants of one launch, folded on the host in double precision
+// from irt_line / irt_dust / irt_opts.  Intensities inside the kernels are in
+// "K units": I * c^2 / (2 k nu_ul^2), the Rayleigh-Jeans temperature at nu_ul.
+struct PhysParams {
+  double T0;          // h nu_ul / k                                  [K]
+  double e_u, e_l;    // level energies / k, e_l = e_u - T0           [K]
+  double theta_rot;   // h B0 / k                                     [K]
+  double g_u;         // statistical weight of the upper level
+  // per-step line coefficients at the profile peak (K units / optical depth):
+  //   jl = cj * N h exp(-E_u/T) / (Z b),
+  //   al = ca * N h exp(-E_l/T) (1 - exp(-T0/T)) / (Z b)
+  double cj, ca;
+  double c_th;        // 2 k / m in (km/s)^2 / K  (thermal part of b^2)
+  double two_sig2;    // 2 sigma_turb^2 (km/s)^2
+  double t_inf;       // T_inf [K]
+  double cad;         // kappa * mu * amu [cm^2]: alpha_D = cad * n_H2
+  double inv_c_kms;   // 1 / c [s/km]
+  double t_bg;        // background temperature [K]
+  double out_scale;   // K units -> output units at nu_ul: 1 (T_RJ) or 2 k nu^2 / c^2
+  int units;          // irt_units
+  int integration;    // irt_integration
+};
+
+// One render job as the kernels see it.
+struct JobDev {
+  const void* cells;     // packed cells [nz][ny][nx]
+  int store;             // Store
+  int bf16_mask;         // ST_H16: bit q set = field q is bf16 (else fp16)
+  float scale[5];        // ST_H16: physical value = stored value * scale[q]
+  int pad1;
+  int nx, ny, nz;
+  double dx;             // cell size [cm]
+  int zview;             // 1 = z view (cell exact)
+  double theta, phi;     // view angles [rad]
+  int npx, npy;
+  double pixel;          // pixel pitch [cm]
+  int nchan, f;
+  double v0, dv;         // channel lower edge of channel 0, width [km/s]
+  double ufirst, dvf;    // first fine velocity and fine step [km/s]
+  int cw, nwin;          // channels per window, windows per ray
+  int kmax;              // upper bound of samples per ray
+  int pad0;
+  void* out[5];          // T, C, D, L, B cubes [nchan][npy][npx]
+  long long item_begin;  // first global work item of this job
+  long long nitems;      // npx * npy * nwin
+};
+
+constexpr int kWarpsPerBlock = 4;
+constexpr int kMaxJobs = 64;
+
+// Job table passed to the kernels by value (__grid_constant__ parameter).
+struct JobTable {
+  JobDev j[kMaxJobs];
+};
+
+
+// Launch entry points implemented in the .cu files.
+// Returns a cudaError_t value (0 = success).
+
+int launch_pack(int store, const void* const* src, const int* dtypes, const double* scale,
+                void* cells, long long ncell, void* stream);
+
+
+}  // namespace irt

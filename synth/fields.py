@@ -98,26 +98,32 @@ def make_fields(n: int, seed: int, n_mean: float = 1.0e4, sigma_ln: float = 1.5,
                     x_tracer=np.full((n, n, n), x_tracer, dtype=np.float64))
 
 
-def to_storage(fs: FieldSet, dtypes) -> tuple[FieldSet, FieldSet]:
+def to_storage(fs: FieldSet, dtypes, scales=None) -> tuple[FieldSet, FieldSet]:
     """Round a field set to storage precision.
 
     Returns ``(stored, dequantised)``: the arrays in the storage dtypes and
     the same values widened back to float64, which is what an oracle run on
     "the same inputs" consumes.  ``dtypes`` entries are numpy dtypes or the
     string ``"bf16"`` (bfloat16, round to nearest even, kept as uint16 bits).
+    ``scales`` (optional, per field): the stored value is value / scale and
+    the dequantised value is stored * scale.
     """
     if not isinstance(dtypes, (list, tuple)):
         dtypes = [dtypes] * 5
+    if scales is None:
+        scales = [1.0] * 5
     stored, deq = [], []
-    for a, d in zip(fs.as_tuple(), dtypes):
+    for a, d, sc in zip(fs.as_tuple(), dtypes, scales):
+        a = a / sc if sc != 1.0 else a
         if isinstance(d, str) and d == "bf16":
             bits = _f32_to_bf16_bits(a.astype(np.float32))
             stored.append(bits)
-            deq.append((bits.astype(np.uint32) << 16).view(np.float32).astype(np.float64))
+            back = (bits.astype(np.uint32) << 16).view(np.float32).astype(np.float64)
         else:
             s = np.ascontiguousarray(a.astype(d))
             stored.append(s)
-            deq.append(s.astype(np.float64))
+            back = s.astype(np.float64)
+        deq.append(back * sc if sc != 1.0 else back)
     return FieldSet(*stored), FieldSet(*deq)
 
 

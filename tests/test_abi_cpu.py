@@ -1,0 +1,127 @@
+"""C-ABI checks that need no GPU: the library loads, exports every symbol
+include/irt.h declares, the ctypes structures match the C layout, and
+argument validation rejects bad calls before touching the device."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "irt.h")
+
+
+@pytest.fixture(scope="module")
+def B():
+    from paper_2607_01338_b300 import build as bld
+    bld.build()
+    from paper_2607_01338_b300 import binding
+    return binding
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    return sorted(set(re.findall(r"^\s*(?:irt_status|const char\*|long long)\s+(irt_\w+)\s*\(",
+                                 text, re.M)))
+
+
+def test_header_declares_the_four_entry_points():
+    names = declared_functions()
+    for n in ("irt_create_grid", "irt_forward_ppv", "irt_adjoint_ppv", "irt_destroy"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(B):
+    out = subprocess.run(["nm", "-D", "--defined-only", B.LIB_PATH], capture_output=True,
+                         text=True, check=True).stdout
+    exported = set(re.findall(r"\bT (irt_\w+)", out))
+    for n in declared_functions():
+        assert n in exported, n
+        assert hasattr(B.lib, n)
+    assert set(B.EXPORTED) == set(declared_functions())
+
+
+def test_build_targets_sm_103a_only():
+    from paper_2607_01338_b300 import build as bld
+    assert bld.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+
+STRUCTS = ["irt_grid_desc", "irt_fields", "irt_line", "irt_dust", "irt_view", "irt_vaxis",
+           "irt_opts", "irt_cubes", "irt_job"]
+
+
+def test_ctypes_layout_matches_c(B, tmp_path):
+    lines = ['#include <stdio.h>', '#include <stddef.h>', f'#include "{HEADER}"',
+             'int main(void) {']
+    for s in STRUCTS:
+        cls = getattr(B, s)
+        lines.append(f'  printf("{s} %zu\\n", sizeof({s}));')
+        for fname, _ in cls._fields_:
+            lines.append(f'  printf("{s}.{fname} %zu\\n", offsetof({s}, {fname}));')
+    lines += ['  return 0;', '}']
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-o", str(exe), str(src)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout
+    got = dict(line.rsplit(" ", 1) for line in out.strip().splitlines())
+    for s in STRUCTS:
+        cls = getattr(B, s)
+        assert int(got[s]) == ctypes.sizeof(cls), s
+        for fname, _ in cls._fields_:
+            assert int(got[f"{s}.{fname}"]) == getattr(cls, fname).offset, (s, fname)
+
+
+def _line(B):
+    from synth import LINE_13CO_21
+    return B.irt_line(*[LINE_13CO_21[k] for k, _ in B.irt_line._fields_])
+
+
+def test_validation_before_any_launch(B):
+    """These calls fail in argument checking, which runs before any CUDA call."""
+    L = B.lib
+    h = ctypes.c_void_p()
+    assert L.irt_create_grid(None, None, None, ctypes.byref(h)) == B.IRT_EINVAL
+    desc = B.irt_grid_desc(0, 4, 4, 1.0, (ctypes.c_int * 5)(0, 0, 0, 0, 0))
+    f = B.irt_fields(1, 2, 3, 4, 5)
+    assert L.irt_create_grid(ctypes.byref(desc), ctypes.byref(f), None, ctypes.byref(h)) == B.IRT_EINVAL
+    assert b"grid size" in L.irt_last_error()
+    desc = B.irt_grid_desc(4, 4, 4, -1.0, (ctypes.c_int * 5)(0, 0, 0, 0, 0))
+    assert L.irt_create_grid(ctypes.byref(desc), ctypes.byref(f), None, ctypes.byref(h)) == B.IRT_EINVAL
+    desc = B.irt_grid_desc(4, 4, 4, 1.0, (ctypes.c_int * 5)(0, 0, 9, 0, 0))
+    assert L.irt_create_grid(ctypes.byref(desc), ctypes.byref(f), None, ctypes.byref(h)) == B.IRT_EINVAL
+    assert b"dtype" in L.irt_last_error()
+    f0 = B.irt_fields(1, 2, None, 4, 5)
+    desc = B.irt_grid_desc(4, 4, 4, 1.0, (ctypes.c_int * 5)(0, 0, 0, 0, 0))
+    assert L.irt_create_grid(ctypes.byref(desc), ctypes.byref(f0), None, ctypes.byref(h)) == B.IRT_EINVAL
+    # forward: no jobs / NULL grid / bad axis
+    line = _line(B)
+    dust = B.irt_dust(0.01, 2.8)
+    opts = B.irt_opts(0, 1, 0, 2.725, 0, 0)
+    assert L.irt_forward_ppv(None, 0, ctypes.byref(line), ctypes.byref(dust),
+                             ctypes.byref(opts), None) == B.IRT_EINVAL
+    job = B.irt_job(None, B.irt_view(0, 0, 4, 4, 1.0, 0), B.irt_vaxis(4, -2.0, 1.0, 1),
+                    B.irt_cubes(1, None, None, None, None))
+    assert L.irt_forward_ppv(ctypes.byref(job), 1, ctypes.byref(line), ctypes.byref(dust),
+                             ctypes.byref(opts), None) == B.IRT_EINVAL
+    assert b"grid" in L.irt_last_error()
+    bad = B.irt_line(line.nu_ul_hz, -1.0, line.e_u_k, line.b0_hz, line.g_u, line.g_l,
+                     line.mass_amu, line.t_inf_k, line.sigma_turb_kms)
+    assert L.irt_forward_ppv(ctypes.byref(job), 1, ctypes.byref(bad), ctypes.byref(dust),
+                             ctypes.byref(opts), None) == B.IRT_EINVAL
+    nan_opts = B.irt_opts(0, 1, 0, float("nan"), 0, 0)
+    assert L.irt_forward_ppv(ctypes.byref(job), 1, ctypes.byref(line), ctypes.byref(dust),
+                             ctypes.byref(nan_opts), None) == B.IRT_EINVAL
+    assert L.irt_destroy(None) == B.IRT_OK
+
+
+def test_product_path_has_no_oracle_or_fallback():
+    """The package never imports the oracle and has no CPU fallback path."""
+    pkg = os.path.join(ROOT, "paper_2607_01338_b300")
+    for dirpath, _, files in os.walk(pkg):
+        for fn in files:
+            if fn.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
+                text = open(os.path.join(dirpath, fn)).read()
+                assert "import oracle" not in text and "from oracle" not in text, fn
+                assert "irt_oracle" not in text, fn
