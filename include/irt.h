@@ -192,6 +192,33 @@ irt_status irt_adjoint_ppv(const irt_job* job, const irt_line* line, const irt_d
                            float* grad_n_h2, float* grad_t_gas, float* grad_v_los,
                            void* cuda_stream);
 
+/*
+ * irt_forward_ppv_static - render one job without allocating device memory.
+ * The paper has no counterpart: this entry point exists for callers that may
+ * not call cudaMalloc, for example a plugin whose host application owns all
+ * device memory and hands it only finished buffers, or a real-time loop that
+ * must not block on the allocator or fail with out-of-memory after start-up.
+ * The caller passes the fields (device pointers, layout and dtypes as for
+ * irt_create_grid) and the output cubes; the packed copy of the fields and
+ * the work-queue counter go to one file-scope device array of
+ * 32 MiB + 256 bytes that every device loading the library holds until the
+ * process exits.  A grid needing more than 32 MiB of packed cells (32, 16 or
+ * 64 bytes per cell for float, 16-bit or double storage; e.g. 1,048,576 float
+ * cells) is rejected with IRT_EINVAL and a message giving both sizes.  The
+ * call issues no cudaMalloc/cudaFree.  The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress); make that first call before
+ * any stream capture.  All calls share the array and it keeps the last call's
+ * contents (the counter is cleared by each call): calls whose kernels overlap
+ * on the GPU, on different streams or host threads, race and must be
+ * serialised by the caller.  Other argument checks and errors as
+ * irt_forward_ppv.
+ */
+irt_status irt_forward_ppv_static(const irt_grid_desc* desc, const irt_fields* fields,
+                                  const irt_view* view, const irt_vaxis* vaxis,
+                                  const irt_cubes* out, const irt_line* line,
+                                  const irt_dust* dust, const irt_opts* opts,
+                                  void* cuda_stream);
+
 /* irt_destroy - free the grid and everything it owns (NULL is a no-op).  The
  * caller must make sure no launch using the grid is still running. */
 irt_status irt_destroy(irt_grid* grid);

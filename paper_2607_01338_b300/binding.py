@@ -27,7 +27,7 @@ STATUS_NAMES = {0: "IRT_OK", 1: "IRT_EINVAL", 2: "IRT_ENOMEM", 3: "IRT_ECUDA",
 
 #: symbols include/irt.h declares
 EXPORTED = ("irt_create_grid", "irt_forward_ppv", "irt_adjoint_ppv", "irt_destroy",
-            "irt_grid_stats", "irt_last_error", "irt_launch_count")
+            "irt_grid_stats", "irt_forward_ppv_static", "irt_last_error", "irt_launch_count")
 
 
 class irt_grid_desc(ctypes.Structure):
@@ -103,6 +103,10 @@ def _load():
                                   ctypes.c_void_p, ctypes.c_void_p]
     L.irt_destroy.restype = ctypes.c_int
     L.irt_destroy.argtypes = [ctypes.c_void_p]
+    L.irt_forward_ppv_static.restype = ctypes.c_int
+    L.irt_forward_ppv_static.argtypes = [P(irt_grid_desc), P(irt_fields), P(irt_view),
+                                         P(irt_vaxis), P(irt_cubes), P(irt_line), P(irt_dust),
+                                         P(irt_opts), ctypes.c_void_p]
     L.irt_grid_stats.restype = ctypes.c_int
     L.irt_grid_stats.argtypes = [ctypes.c_void_p, P(ctypes.c_ulonglong), ctypes.c_int]
     L.irt_last_error.restype = ctypes.c_char_p
@@ -140,6 +144,17 @@ def irt_adjoint_ppv(job: irt_job, line: irt_line, dust: irt_dust, opts: irt_opts
                                ctypes.byref(opts), ctypes.byref(cotangent),
                                ctypes.c_void_p(grad_n), ctypes.c_void_p(grad_t),
                                ctypes.c_void_p(grad_v), ctypes.c_void_p(stream)))
+
+
+def irt_forward_ppv_static(desc: irt_grid_desc, fields: irt_fields, view: irt_view,
+                           vaxis: irt_vaxis, out: irt_cubes, line: irt_line, dust: irt_dust,
+                           opts: irt_opts, stream: int) -> None:
+    """Render one job from the caller's field arrays without any device
+    allocation (the packed fields go to the library's static device array)."""
+    _check(lib.irt_forward_ppv_static(ctypes.byref(desc), ctypes.byref(fields), ctypes.byref(view),
+                                      ctypes.byref(vaxis), ctypes.byref(out), ctypes.byref(line),
+                                      ctypes.byref(dust), ctypes.byref(opts),
+                                      ctypes.c_void_p(stream)))
 
 
 def irt_destroy(handle: int) -> None:

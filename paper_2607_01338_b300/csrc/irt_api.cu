@@ -8,6 +8,7 @@
 #include <cstdio>
 #include <cstdarg>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -443,4 +444,140 @@ extern "C" irt_status irt_adjoint_ppv(const irt_job* job, const irt_line* line,
   (void)job; (void)line; (void)dust; (void)opts; (void)cotangent; (void)grad_n_h2;
   (void)grad_t_gas; (void)grad_v_los; (void)cuda_stream;
   return fail(IRT_EUNSUPPORTED, "irt_adjoint_ppv: not built yet");
+}
+
+// ---------------------------------------------------------------------------
+// Render without any device allocation (irt_forward_ppv_static).
+//
+// The packed cells of the grid and the work-queue counter of the persistent
+// launch live in one file-scope device array instead of memory allocated by
+// irt_create_grid.  Every device that loads the library holds this array
+// (kStaticCellBytes + kStaticCtlBytes) until the process exits.  All calls
+// share it: a call overwrites the cells and control words of the previous
+// call, and two calls whose kernels overlap on the GPU (different streams, or
+// different host threads) race on it.
+// ---------------------------------------------------------------------------
+namespace irt {
+namespace {
+
+constexpr size_t kStaticCellBytes = size_t(32) << 20;   // 32 MiB of packed cells
+constexpr size_t kStaticCtlBytes = 256;                   // work-queue and counters
+constexpr int kStaticMaxDevices = 64;
+
+static __device__ __align__(256) unsigned char g_static_scratch[kStaticCellBytes + kStaticCtlBytes];
+
+std::mutex g_static_mu;
+void* g_static_base[kStaticMaxDevices] = {};
+
+// Device address of the static array on the current device, looked up once per
+// device (the host-side name of the array is not a device address).
+irt_status static_scratch_base(void** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "irt_forward_ppv_static: cudaGetDevice");
+  if (dev < 0 || dev >= kStaticMaxDevices)
+    return fail(IRT_EUNSUPPORTED, "irt_forward_ppv_static: device index %d beyond %d", dev,
+                kStaticMaxDevices);
+  std::lock_guard<std::mutex> lock(g_static_mu);
+  if (!g_static_base[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_static_scratch);
+    if (e != cudaSuccess || !p)
+      return cuda_fail(e, "irt_forward_ppv_static: cudaGetSymbolAddress of the static scratch");
+    g_static_base[dev] = p;
+  }
+  *out = g_static_base[dev];
+  return IRT_OK;
+}
+
+}  // namespace
+}  // namespace irt
+
+extern "C" irt_status irt_forward_ppv_static(const irt_grid_desc* desc, const irt_fields* fields,
+                                             const irt_view* view, const irt_vaxis* vaxis,
+                                             const irt_cubes* out, const irt_line* line,
+                                             const irt_dust* dust, const irt_opts* opts,
+                                             void* cuda_stream) {
+  g_err.clear();
+  if (!desc || !fields || !view || !vaxis || !out)
+    return fail(IRT_EINVAL, "irt_forward_ppv_static: NULL argument");
+  if (desc->nx < 1 || desc->ny < 1 || desc->nz < 1)
+    return fail(IRT_EINVAL, "irt_forward_ppv_static: grid size %d x %d x %d", desc->nx, desc->ny,
+                desc->nz);
+  if (!finite_pos(desc->cell_cm)) return fail(IRT_EINVAL, "irt_forward_ppv_static: cell_cm <= 0");
+  const void* src[5] = {fields->n_h2_cm3, fields->t_gas_k, fields->t_dust_k, fields->v_los_kms,
+                        fields->x_tracer};
+  int dt[5];
+  bool any64 = false, all16 = true;
+  int bf_mask = 0;
+  double scale[5];
+  for (int q = 0; q < 5; ++q) {
+    if (!src[q]) return fail(IRT_EINVAL, "irt_forward_ppv_static: field %d is NULL", q);
+    dt[q] = (int)desc->dtype[q];
+    if (dt[q] < IRT_F32 || dt[q] > IRT_F64)
+      return fail(IRT_EINVAL, "irt_forward_ppv_static: field %d has unknown dtype %d", q, dt[q]);
+    if (dt[q] == IRT_F64) any64 = true;
+    if (dt[q] != IRT_F16 && dt[q] != IRT_BF16) all16 = false;
+    if (dt[q] == IRT_BF16) bf_mask |= 1 << q;
+    scale[q] = desc->scale[q] == 0.0 ? 1.0 : desc->scale[q];
+    if (!std::isfinite(scale[q]) || scale[q] <= 0.0)
+      return fail(IRT_EINVAL, "irt_forward_ppv_static: scale[%d] must be finite and > 0", q);
+  }
+  const int store = any64 ? ST_F64 : (all16 ? ST_H16 : ST_F32);
+  const size_t cb = store == ST_F64 ? sizeof(CellF64) : store == ST_H16 ? sizeof(CellH16)
+                                                                         : sizeof(CellF32);
+  const long long ncell = (long long)desc->nx * desc->ny * desc->nz;
+  const double need = (double)cb * (double)ncell;
+  if (need > (double)kStaticCellBytes)
+    return fail(IRT_EINVAL,
+                "irt_forward_ppv_static: the grid needs %.0f bytes of packed cells (%lld cells x "
+                "%zu B); the static scratch holds at most %zu bytes (%zu cells of this storage)",
+                need, ncell, cb, kStaticCellBytes, kStaticCellBytes / cb);
+  irt_status st = check_line(line, dust, opts);
+  if (st) return st;
+
+  // a grid descriptor on the host stack pointing into the static array
+  irt_grid g;
+  g.nx = desc->nx; g.ny = desc->ny; g.nz = desc->nz;
+  g.dx = desc->cell_cm;
+  g.store = store;
+  g.bf16_mask = store == ST_H16 ? bf_mask : 0;
+  for (int q = 0; q < 5; ++q) g.scale[q] = scale[q];
+  g.cell_bytes = (size_t)need;
+  g.device = 0;
+  irt_job job;
+  job.grid = &g;
+  job.view = *view;
+  job.vaxis = *vaxis;
+  job.out = *out;
+  st = check_job(job, opts->precision);
+  if (st) return st;
+
+  void* base = nullptr;
+  st = static_scratch_base(&base);
+  if (st) return st;
+  g.cells = base;
+  g.ctl = reinterpret_cast<unsigned long long*>(static_cast<unsigned char*>(base) +
+                                                kStaticCellBytes);
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  // the work-queue counter must start at zero; the array keeps the last call's values
+  cudaError_t ce = cudaMemsetAsync(g.ctl, 0, kStaticCtlBytes, s);
+  if (ce != cudaSuccess) return cuda_fail(ce, "irt_forward_ppv_static: clear control words");
+  int e = launch_pack(store, src, dt, scale, g.cells, ncell, cuda_stream);
+  ++g_launches;
+  if (e) return cuda_fail(e, "irt_forward_ppv_static: pack kernel");
+
+  const PhysParams P = fold_constants(line, dust, opts);
+  const Plan p = plan_job(job, opts->precision, 0);
+  JobTable tab;
+  std::memset(&tab, 0, sizeof tab);
+  tab.j[0] = make_jobdev(job, p);
+  tab.j[0].item_begin = 0;
+  const long long total = tab.j[0].nitems;
+  unsigned long long* stats = (opts->flags & IRT_FLAG_STATS) ? g.ctl + 1 : nullptr;
+  e = dispatch(opts->precision, opts->integration, store, p.ni, tab, 1, P, total, g.ctl, 0,
+               p.kmax, 32 * p.ni, p.cw, opts->flags, stats, s);
+  ++g_launches;
+  if (e) return cuda_fail(e, "irt_forward_ppv_static: forward kernel");
+  return IRT_OK;
 }
