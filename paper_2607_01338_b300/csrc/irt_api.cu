@@ -16,20 +16,20 @@
 
 namespace irt {
 
-int dispatch_fwd_f32_smooth(int store, int ni, const JobTable& jobs, int njobs, const PhysParams& P,
+int dispatch_fwd_f32_smooth(int store, int ni, const JobTable& jobs, int njobs, const PhysParams& P, const PhysF& PF,
                             long long total, unsigned long long* queue, int grid_blocks, int kmax,
                             int fwmax, int cwmax, unsigned flags, unsigned long long* stats,
                             cudaStream_t s);
-int dispatch_fwd_f32_formal(int store, int ni, const JobTable& jobs, int njobs, const PhysParams& P,
+int dispatch_fwd_f32_formal(int store, int ni, const JobTable& jobs, int njobs, const PhysParams& P, const PhysF& PF,
                             long long total, unsigned long long* queue, int grid_blocks, int kmax,
                             int fwmax, int cwmax, unsigned flags, unsigned long long* stats,
                             cudaStream_t s);
-int dispatch_fwd_f32_kahan(int store, int ni, const JobTable& jobs, int njobs, const PhysParams& P,
+int dispatch_fwd_f32_kahan(int store, int ni, const JobTable& jobs, int njobs, const PhysParams& P, const PhysF& PF,
                            long long total, unsigned long long* queue, int grid_blocks, int kmax,
                            int fwmax, int cwmax, unsigned flags, unsigned long long* stats,
                            cudaStream_t s);
 int dispatch_fwd_f64(int mode, int store, int ni, const JobTable& jobs, int njobs,
-                     const PhysParams& P, long long total, unsigned long long* queue,
+                     const PhysParams& P, const PhysF& PF, long long total, unsigned long long* queue,
                      int grid_blocks, int kmax, int fwmax, int cwmax, unsigned flags,
                      unsigned long long* stats, cudaStream_t s);
 
@@ -234,6 +234,25 @@ PhysParams fold_constants(const irt_line* ln, const irt_dust* du, const irt_opts
   return P;
 }
 
+PhysF to_float(const PhysParams& P) {
+  PhysF F;
+  F.T0 = (float)P.T0;
+  F.e_u = (float)P.e_u;
+  F.e_l = (float)P.e_l;
+  F.theta_rot = (float)P.theta_rot;
+  F.cj = (float)P.cj;
+  F.ca = (float)P.ca;
+  F.c_th = (float)P.c_th;
+  F.two_sig2 = (float)P.two_sig2;
+  F.t_inf = (float)std::min(P.t_inf, 3.0e38);
+  F.cad = (float)P.cad;
+  F.inv_c_kms = (float)P.inv_c_kms;
+  F.t_bg = (float)P.t_bg;
+  F.out_scale = (float)P.out_scale;
+  F.units = P.units;
+  return F;
+}
+
 irt_status check_job(const irt_job& jb, int precision) {
   const irt_grid* g = jb.grid;
   if (!g) return fail(IRT_EINVAL, "job without grid");
@@ -320,6 +339,22 @@ JobDev make_jobdev(const irt_job& jb, const Plan& p) {
   d.zview = jb.view.trilinear == 0;
   d.theta = jb.view.theta_rad;
   d.phi = jb.view.phi_rad;
+  {
+    // orthographic view basis: direction d = (st cp, st sp, ct), pixel axes
+    // e_theta = (ct cp, ct sp, -st), e_phi = (-sp, cp, 0)
+    const double st = std::sin(d.theta), ct = std::cos(d.theta);
+    const double sp = std::sin(d.phi), cp = std::cos(d.phi);
+    const double dd[3] = {st * cp, st * sp, ct};
+    const double et[3] = {ct * cp, ct * sp, -st};
+    const double ep[3] = {-sp, cp, 0.0};
+    for (int a = 0; a < 3; ++a) {
+      d.d[a] = dd[a];
+      d.et[a] = et[a];
+      d.ep[a] = ep[a];
+      d.inv_d[a] = dd[a] != 0.0 ? 1.0 / dd[a] : HUGE_VAL;
+    }
+    d.inv_dx = 1.0 / g->dx;
+  }
   d.npx = jb.view.npx;
   d.npy = jb.view.npy;
   d.pixel = jb.view.pixel_cm;
@@ -344,19 +379,19 @@ JobDev make_jobdev(const irt_job& jb, const Plan& p) {
 }
 
 int dispatch(int precision, int mode, int store, int ni, const JobTable& jobs, int njobs,
-             const PhysParams& P, long long total, unsigned long long* queue, int grid_blocks,
+             const PhysParams& P, const PhysF& PF, long long total, unsigned long long* queue, int grid_blocks,
              int kmax, int fwmax, int cwmax, unsigned flags, unsigned long long* stats,
              cudaStream_t s) {
   if (precision == IRT_PREC_F64)
-    return dispatch_fwd_f64(mode, store, ni, jobs, njobs, P, total, queue, grid_blocks, kmax,
+    return dispatch_fwd_f64(mode, store, ni, jobs, njobs, P, PF, total, queue, grid_blocks, kmax,
                             fwmax, cwmax, flags, stats, s);
   if (mode == M_SMOOTH)
-    return dispatch_fwd_f32_smooth(store, ni, jobs, njobs, P, total, queue, grid_blocks, kmax,
+    return dispatch_fwd_f32_smooth(store, ni, jobs, njobs, P, PF, total, queue, grid_blocks, kmax,
                                    fwmax, cwmax, flags, stats, s);
   if (mode == M_FORMAL)
-    return dispatch_fwd_f32_formal(store, ni, jobs, njobs, P, total, queue, grid_blocks, kmax,
+    return dispatch_fwd_f32_formal(store, ni, jobs, njobs, P, PF, total, queue, grid_blocks, kmax,
                                    fwmax, cwmax, flags, stats, s);
-  return dispatch_fwd_f32_kahan(store, ni, jobs, njobs, P, total, queue, grid_blocks, kmax, fwmax,
+  return dispatch_fwd_f32_kahan(store, ni, jobs, njobs, P, PF, total, queue, grid_blocks, kmax, fwmax,
                                 cwmax, flags, stats, s);
 }
 
@@ -375,6 +410,7 @@ extern "C" irt_status irt_forward_ppv(const irt_job* jobs, int njobs, const irt_
     if (st) return st;
   }
   const PhysParams P = fold_constants(line, dust, opts);
+  const PhysF PF = to_float(P);
   cudaStream_t s = (cudaStream_t)cuda_stream;
   const int prec = opts->precision;
   const int mode = opts->integration;
@@ -428,7 +464,7 @@ extern "C" irt_status irt_forward_ppv(const irt_job* jobs, int njobs, const irt_
     }
     unsigned long long* stats =
         (opts->flags & IRT_FLAG_STATS) ? jobs[0].grid->ctl + 1 : nullptr;
-    const int e = dispatch(prec, mode, store, ni, tab, nb, P, total, queue, 0, kmax, fwmax,
+    const int e = dispatch(prec, mode, store, ni, tab, nb, P, PF, total, queue, 0, kmax, fwmax,
                            cwmax, opts->flags, stats, s);
     ++g_launches;
     if (e) return cuda_fail(e, "irt_forward_ppv: forward kernel");
@@ -575,8 +611,8 @@ extern "C" irt_status irt_forward_ppv_static(const irt_grid_desc* desc, const ir
   tab.j[0].item_begin = 0;
   const long long total = tab.j[0].nitems;
   unsigned long long* stats = (opts->flags & IRT_FLAG_STATS) ? g.ctl + 1 : nullptr;
-  e = dispatch(opts->precision, opts->integration, store, p.ni, tab, 1, P, total, g.ctl, 0,
-               p.kmax, 32 * p.ni, p.cw, opts->flags, stats, s);
+  e = dispatch(opts->precision, opts->integration, store, p.ni, tab, 1, P, to_float(P), total,
+               g.ctl, 0, p.kmax, 32 * p.ni, p.cw, opts->flags, stats, s);
   ++g_launches;
   if (e) return cuda_fail(e, "irt_forward_ppv_static: forward kernel");
   return IRT_OK;

@@ -1,13 +1,13 @@
-// Forward PPV kernel of the IRIS-SO transfer (sm_103a).
+// Forward PPV kernel of the IRIS-SO transfer (sm_103a): device helpers.
 //
 // Work item = (ray, channel window).  One warp renders one item:
 //   1. sample pass: lane l evaluates samples k = l, l+32, ... of the ray (field
 //      load or trilinear interpolation, LTE populations, line and dust
 //      coefficients, Sec. 3.2-3.7, 5.10) into a per-warp shared-memory record;
 //   2. transfer pass: lane l owns the fine velocities g = l + 32 i of the
-//      window (register blocks i < NI) and integrates them sample by sample
-//      (Sec. 4.8, formal or smooth), evaluating the Gaussian profile only in
-//      the blocks the sample's line reaches;
+//      window (register blocks i) and integrates them sample by sample
+//      (Sec. 4.8, formal or smooth), evaluating the Gaussian profile only at
+//      the velocities the sample's line reaches;
 //   3. epilogue: Simpson channel average (Sec. 4.5), continuum and background
 //      at the channel centre (Sec. 4.4), [L] = [T] - [C] (Sec. 4.10), [D] =
 //      [C] - [B], Rayleigh-Jeans conversion (Sec. 4.9).
@@ -37,9 +37,9 @@ namespace irt {
 namespace dev {
 
 constexpr float kLog2e = 1.4426950408889634f;
-// Line tail cut: the profile is skipped where (u - v)^2 / b^2 > x2cut
-// (exp(-30) = 9e-14 of the peak).
-constexpr float kX2CutF32 = 30.0f;
+// Line tail cut: the profile is skipped where (u - v)^2 / b^2 > 30, i.e. below
+// exp(-30) = 9e-14 of its peak; sqrt(30) = 5.4772256.
+constexpr float kSqrtX2Cut = 5.4772256f;
 
 __device__ __forceinline__ float ex2_approx(float x) {
   float y;
@@ -84,7 +84,7 @@ __device__ __forceinline__ void load_cell(const void* cells, long long idx, int 
 }
 
 // ---------------------------------------------------------------------------
-// ray geometry (double precision, as the sample count must be exact)
+// ray geometry (double precision: the sample count must be exact)
 // ---------------------------------------------------------------------------
 struct RayGeom {
   int K;
@@ -104,24 +104,20 @@ __device__ inline RayGeom ray_geom(const JobDev& J, int px, int py) {
     g.d[2] = 1.0;
     return g;
   }
-  double st, ct, sp, cp;
-  sincos(J.theta, &st, &ct);
-  sincos(J.phi, &sp, &cp);
-  g.d[0] = st * cp; g.d[1] = st * sp; g.d[2] = ct;
-  const double et[3] = {ct * cp, ct * sp, -st};
-  const double ep[3] = {-sp, cp, 0.0};
   const double L[3] = {J.nx * J.dx, J.ny * J.dx, J.nz * J.dx};
   const double a = (px - 0.5 * (J.npx - 1)) * J.pixel;
   const double b = (py - 0.5 * (J.npy - 1)) * J.pixel;
   double lo = -CUDART_INF, hi = CUDART_INF;
   bool miss = false;
+#pragma unroll
   for (int i = 0; i < 3; ++i) {
-    g.o[i] = 0.5 * L[i] + a * et[i] + b * ep[i];
-    if (g.d[i] == 0.0) {
+    g.d[i] = J.d[i];
+    g.o[i] = 0.5 * L[i] + a * J.et[i] + b * J.ep[i];
+    if (J.d[i] == 0.0) {
       if (g.o[i] < 0.0 || g.o[i] > L[i]) miss = true;
       continue;
     }
-    double t0 = (0.0 - g.o[i]) / g.d[i], t1 = (L[i] - g.o[i]) / g.d[i];
+    double t0 = (0.0 - g.o[i]) * J.inv_d[i], t1 = (L[i] - g.o[i]) * J.inv_d[i];
     if (t0 > t1) { const double t = t0; t0 = t1; t1 = t; }
     lo = fmax(lo, t0);
     hi = fmin(hi, t1);
@@ -132,57 +128,110 @@ __device__ inline RayGeom ray_geom(const JobDev& J, int px, int py) {
     return g;
   }
   const double chord = hi - lo;
-  g.K = (int)ceil(chord / J.dx - 1e-9);
+  g.K = (int)ceil(chord * J.inv_dx - 1e-9);
   g.h = (g.K > 0) ? chord / g.K : 0.0;
   g.t0 = lo;
   return g;
 }
 
-// Raw sample values (n_H2, T_gas, T_dust, v_los, x) of sample k of a ray.
+// Trilinear blend of the eight cells around fractional cell coordinates
+// (i0 + w) per axis; indices clamped to the grid (edge extension).
 template <typename R, int ST>
-__device__ __forceinline__ void sample_raw(const JobDev& J, const RayGeom& g, int px, int py,
-                                           int k, R v[5]) {
-  if (J.zview) {
-    const long long idx = ((long long)k * J.ny + py) * J.nx + px;
-    load_cell<R, ST>(J.cells, idx, J.bf16_mask, J.scale, v);
-    return;
-  }
-  const double t = g.t0 + (k + 0.5) * g.h;
+__device__ __forceinline__ void trilinear(const JobDev& J, const int i0[3], const R w[3], R v[5]) {
   const int n[3] = {J.nx, J.ny, J.nz};
-  int i0[3], i1[3];
-  R w[3];
+  int lo[3], hi[3];
+#pragma unroll
   for (int a = 0; a < 3; ++a) {
-    const double s = (g.o[a] + t * g.d[a]) / J.dx - 0.5;
-    const double fl = floor(s);
-    w[a] = (R)(s - fl);
-    const int lo = (int)fl;
-    i0[a] = min(max(lo, 0), n[a] - 1);
-    i1[a] = min(max(lo + 1, 0), n[a] - 1);
+    lo[a] = min(max(i0[a], 0), n[a] - 1);
+    hi[a] = min(max(i0[a] + 1, 0), n[a] - 1);
   }
+#pragma unroll
   for (int q = 0; q < 5; ++q) v[q] = (R)0;
 #pragma unroll
   for (int c = 0; c < 8; ++c) {
-    const int ix = (c & 1) ? i1[0] : i0[0];
-    const int iy = (c & 2) ? i1[1] : i0[1];
-    const int iz = (c & 4) ? i1[2] : i0[2];
+    const int ix = (c & 1) ? hi[0] : lo[0];
+    const int iy = (c & 2) ? hi[1] : lo[1];
+    const int iz = (c & 4) ? hi[2] : lo[2];
     const R wx = (c & 1) ? w[0] : (R)1 - w[0];
     const R wy = (c & 2) ? w[1] : (R)1 - w[1];
     const R wz = (c & 4) ? w[2] : (R)1 - w[2];
     const R ww = wx * wy * wz;
     R cv[5];
-    load_cell<R, ST>(J.cells, ((long long)iz * J.ny + iy) * J.nx + ix, J.bf16_mask, J.scale,
-                     cv);
+    load_cell<R, ST>(J.cells, ((long long)iz * J.ny + iy) * J.nx + ix, J.bf16_mask, J.scale, cv);
 #pragma unroll
     for (int q = 0; q < 5; ++q) v[q] += ww * cv[q];
   }
+}
+
+// Raw sample values (n_H2, T_gas, T_dust, v_los, x) of sample k of a ray,
+// double arithmetic (double kernels).
+template <int ST>
+__device__ __forceinline__ void sample_raw(const JobDev& J, const RayGeom& g, int px, int py,
+                                           int k, double v[5]) {
+  if (J.zview) {
+    load_cell<double, ST>(J.cells, ((long long)k * J.ny + py) * J.nx + px, J.bf16_mask, J.scale,
+                          v);
+    return;
+  }
+  const double t = g.t0 + (k + 0.5) * g.h;
+  int i0[3];
+  double w[3];
+  for (int a = 0; a < 3; ++a) {
+    const double s = (g.o[a] + t * g.d[a]) * J.inv_dx - 0.5;
+    const double fl = floor(s);
+    w[a] = s - fl;
+    i0[a] = (int)fl;
+  }
+  trilinear<double, ST>(J, i0, w, v);
+}
+
+// Oblique sample positions in 32.32 fixed point (cell units, cell centres at
+// integers): sample k sits at base + k step.  Base and step are rounded from
+// double once per ray; the position of sample k is then exact to
+// k * 2^-33 cells (1e-7 cells after 900 samples).
+struct RayPos {
+  long long base[3], step[3];
+};
+
+__device__ __forceinline__ RayPos ray_pos(const JobDev& J, const RayGeom& g) {
+  RayPos c;
+  const double t = g.t0 + 0.5 * g.h;
+  const double sc = 4294967296.0;   // 2^32
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const double s = (g.o[a] + t * g.d[a]) * J.inv_dx - 0.5;
+    c.base[a] = __double2ll_rn(s * sc);
+    c.step[a] = __double2ll_rn(g.h * g.d[a] * J.inv_dx * sc);
+  }
+  return c;
+}
+
+// float kernels: sample k of the ray
+template <int ST>
+__device__ __forceinline__ void sample_raw(const JobDev& J, const RayPos& rp, int px, int py,
+                                           int k, float v[5]) {
+  if (J.zview) {
+    load_cell<float, ST>(J.cells, ((long long)k * J.ny + py) * J.nx + px, J.bf16_mask, J.scale,
+                         v);
+    return;
+  }
+  int i0[3];
+  float w[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const long long p = rp.base[a] + (long long)k * rp.step[a];
+    i0[a] = (int)(p >> 32);
+    w[a] = (float)(unsigned)(p & 0xFFFFFFFFll) * 2.3283064365386963e-10f;   // 2^-32
+  }
+  trilinear<float, ST>(J, i0, w, v);
 }
 
 // ---------------------------------------------------------------------------
 // per-sample physics
 // ---------------------------------------------------------------------------
 // Rigid-rotor partition function Z(T) = sum_J (2J+1) exp(-theta J(J+1)/T).
-__device__ inline float partition(const PhysParams& P, float T) {
-  const float r = (float)P.theta_rot / T;
+__device__ inline float partition(const PhysF& P, float T) {
+  const float r = P.theta_rot / T;
   if (r < 0.0132f) {
     // high-temperature expansion, truncation error O(r^4) < 1e-9 relative
     return 1.0f / r + (1.0f / 3.0f) + r * (1.0f / 15.0f + r * (4.0f / 315.0f + r * (1.0f / 315.0f)));
@@ -210,46 +259,52 @@ __device__ inline double partition(const PhysParams& P, double T) {
   return z;
 }
 
-__device__ __forceinline__ float expm1_(float x) { return expm1f(x); }
-__device__ __forceinline__ double expm1_(double x) { return expm1(x); }
-__device__ __forceinline__ float exp_(float x) { return expf(x); }
-__device__ __forceinline__ double exp_(double x) { return exp(x); }
-__device__ __forceinline__ float sqrt_(float x) { return sqrtf(x); }
-__device__ __forceinline__ double sqrt_(double x) { return sqrt(x); }
-
 // Frequency-independent per-step line coefficients at the profile peak (K
 // units / optical depth) and the Doppler parameter b [km/s].
-template <typename R>
-__device__ __forceinline__ void line_coeffs(const PhysParams& P, R n, R T, R x, R h, R* jl,
-                                            R* al, R* b) {
-  *b = sqrt_((R)P.c_th * T + (R)P.two_sig2);
-  if (!(T > (R)0) || T > (R)P.t_inf) {
-    *jl = (R)0;
-    *al = (R)0;
+__device__ __forceinline__ void line_coeffs(const PhysF& P, float n, float T, float x, float h,
+                                            float* jl, float* al, float* b) {
+  *b = sqrtf(P.c_th * T + P.two_sig2);
+  if (!(T > 0.0f) || T > P.t_inf) {
+    *jl = 0.0f;
+    *al = 0.0f;
     return;
   }
-  const R Z = partition(P, T);
-  const R c = (x * n) * h / (Z * *b);
-  *jl = (R)P.cj * c * exp_(-(R)P.e_u / T);
-  *al = (R)P.ca * c * exp_(-(R)P.e_l / T) * (-expm1_(-(R)P.T0 / T));
+  const float Z = partition(P, T);
+  const float c = (x * n) * h / (Z * *b);
+  *jl = P.cj * c * expf(-P.e_u / T);
+  *al = P.ca * c * expf(-P.e_l / T) * (-expm1f(-P.T0 / T));
+}
+
+__device__ __forceinline__ void line_coeffs(const PhysParams& P, double n, double T, double x,
+                                            double h, double* jl, double* al, double* b) {
+  *b = sqrt(P.c_th * T + P.two_sig2);
+  if (!(T > 0.0) || T > P.t_inf) {
+    *jl = 0.0;
+    *al = 0.0;
+    return;
+  }
+  const double Z = partition(P, T);
+  const double c = (x * n) * h / (Z * *b);
+  *jl = P.cj * c * exp(-P.e_u / T);
+  *al = P.ca * c * exp(-P.e_l / T) * (-expm1(-P.T0 / T));
 }
 
 // Dust Planck source in K units at the line frequency and its first-order
 // slope in u [per km/s]: B(u) = bk0 + bk1 u + O((u/c)^2).
-__device__ __forceinline__ void dust_source_lin(const PhysParams& P, float Td, float* bk0,
+__device__ __forceinline__ void dust_source_lin(const PhysF& P, float Td, float* bk0,
                                                 float* bk1) {
   if (!(Td > 0.0f)) {
     *bk0 = 0.0f;
     *bk1 = 0.0f;
     return;
   }
-  const float a = (float)P.T0 / Td;
+  const float a = P.T0 / Td;
   const float em1 = expm1f(a);
   const float inv = 1.0f / em1;
-  *bk0 = (float)P.T0 * inv;
+  *bk0 = P.T0 * inv;
   // d ln B / d ln nu at nu_ul is 3 - a e^a / (e^a - 1); nu = nu_ul (1 - u/c)
   const float slope = 3.0f - a * (1.0f + inv);
-  *bk1 = -(*bk0) * slope * (float)P.inv_c_kms;
+  *bk1 = -(*bk0) * slope * P.inv_c_kms;
 }
 
 // Exact Planck source in K units at velocity u: T0 y^3 / (exp(T0 y / T) - 1).
@@ -258,31 +313,69 @@ __device__ __forceinline__ double planck_k(const PhysParams& P, double T, double
   const double y = 1.0 - u * P.inv_c_kms;
   return P.T0 * y * y * y / expm1(P.T0 * y / T);
 }
-__device__ __forceinline__ float planck_k(const PhysParams& P, float T, float u) {
+__device__ __forceinline__ float planck_k(const PhysF& P, float T, float u) {
   if (!(T > 0.0f)) return 0.0f;
-  const float y = 1.0f - u * (float)P.inv_c_kms;
-  return (float)P.T0 * y * y * y / expm1f((float)P.T0 * y / T);
+  const float y = 1.0f - u * P.inv_c_kms;
+  return P.T0 * y * y * y / expm1f(P.T0 * y / T);
 }
 
 // ---------------------------------------------------------------------------
 // per-sample records in shared memory
 // ---------------------------------------------------------------------------
-// Window of fine blocks reached by the line: lo | hi << 16 (lo > hi = none).
+// Line window of a sample in local fine-velocity indices: lo | hi << 16
+// (lo > hi = the line reaches no velocity of the window).
 __device__ __forceinline__ int pack_win(int lo, int hi) { return (lo & 0xFFFF) | (hi << 16); }
 __device__ __forceinline__ int win_lo(int w) { return (int)(short)(w & 0xFFFF); }
 __device__ __forceinline__ int win_hi(int w) { return w >> 16; }
+constexpr int kNoWindow = 0xFFFF7FFF;   // lo = 32767, hi = -1
 
+// Float records keep the line centre as (gv, vr): gv = the local fine index
+// nearest to v_los and vr = u(gv) - v_los, so that u(g) - v_los =
+// (g - gv) dvf + vr is exact to ~1e-7 km/s even when the fine velocities are
+// not representable in float.
 // smooth, float: (2h j) and (2h alpha) scaled; d0 = 3 + 2 h alpha_D
 struct __align__(16) RecS32 {
-  float jl2, al2, v, nib2, d0, jd0, jd1;
+  float jl2, al2, vr, nib2, d0, jd0, jd1;
   int win;
+  int gv;
+  float pad[3];
 };
 // formal, float
 struct __align__(16) RecF32 {
-  float jl, al, v, nib2, ad, emD, bk0, bk1;
+  float jl, al, vr, nib2, ad, emD, bk0, bk1;
   int win;
-  float pad[3];
+  int gv;
+  float pad[2];
 };
+
+// Fine velocity grid of a window in float-float form: u(g) = (ufw_hi + ufw_lo)
+// + g (dvf_hi + dvf_lo).
+struct VGrid {
+  float ufw_hi, ufw_lo, dvf_hi, dvf_lo;
+};
+
+// Nearest fine index gv to v and vr = u(gv) - v, evaluated with error-free
+// product and sum steps (Dekker / Knuth) so that vr carries no rounding of
+// u(gv) itself.
+__device__ __forceinline__ void centre_offset(const VGrid& G, float v, int* gv_out,
+                                              float* vr_out) {
+  float q = rintf((v - G.ufw_hi) / G.dvf_hi);
+  q = fminf(fmaxf(q, -1048576.0f), 1048576.0f);
+  const float p_hi = q * G.dvf_hi;
+  const float p_lo = fmaf(q, G.dvf_hi, -p_hi);
+  const float s = G.ufw_hi + p_hi;
+  const float bb = s - G.ufw_hi;
+  const float s_lo = (G.ufw_hi - (s - bb)) + (p_hi - bb);
+  const float corr = p_lo + s_lo + fmaf(q, G.dvf_lo, G.ufw_lo);
+  *gv_out = (int)q;
+  *vr_out = (s - v) + corr;
+}
+
+// u(g) - v_los from a record's (gv, vr)
+__device__ __forceinline__ float vel_offset(const VGrid& G, int g, int gv, float vr) {
+  const float gd = (float)(g - gv);
+  return fmaf(gd, G.dvf_hi, fmaf(gd, G.dvf_lo, vr));
+}
 // double (both integrators, every channel explicit, exact Planck per channel)
 struct __align__(16) RecD {
   double jl, al, v, nib2, ad, emD, td;
@@ -298,17 +391,17 @@ template <> struct RecOf<double, M_SMOOTH> { using type = RecD; };
 template <> struct RecOf<double, M_FORMAL> { using type = RecD; };
 template <> struct RecOf<double, M_FORMAL_KAHAN> { using type = RecD; };
 
-// Fine-block window [lo, hi] (local block indices) reached by the line of a
-// sample with centre v and Doppler parameter b.
+// Local fine-velocity window [lo, hi] reached by the line of a sample with
+// centre v and Doppler parameter b.
 __device__ __forceinline__ int line_window(float v, float b, float ufirst, float dvf, int gw0,
                                            int nfw, bool has_line) {
-  if (!has_line) return pack_win(1, 0);
-  const float w = b * 5.4772256f;  // sqrt(x2cut)
+  if (!has_line) return kNoWindow;
+  const float w = b * kSqrtX2Cut;
   const int glo = (int)ceilf((v - w - ufirst) / dvf) - gw0;
   const int ghi = (int)floorf((v + w - ufirst) / dvf) - gw0;
   const int lo = max(glo, 0), hi = min(ghi, nfw - 1);
-  if (lo > hi) return pack_win(1, 0);
-  return pack_win(lo >> 5, hi >> 5);
+  if (lo > hi) return kNoWindow;
+  return pack_win(lo, hi);
 }
 
 }  // namespace dev

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <algorithm>
+#include <type_traits>
 
 #include "irt_forward.cuh"
 
@@ -9,64 +10,63 @@ namespace irt {
 namespace dev {
 
 // ---------------------------------------------------------------------------
-// sample pass: record of one sample
+// sample pass: record of one sample; returns h alpha_D of the sample
 // ---------------------------------------------------------------------------
-template <typename R, int MODE>
-struct SampleOut {
-  typename RecOf<R, MODE>::type rec;
-  int lo, hi;   // line window (local fine blocks)
-  R ad;         // h alpha_D of the sample
-};
-
 template <int MODE>
-__device__ __forceinline__ void make_record(const PhysParams& P, const float raw[5], float h,
-                                            float ufirst, float dvf, int gw0, int nfw,
-                                            SampleOut<float, MODE>* so) {
+__device__ __forceinline__ float make_record(const PhysF& P, const float raw[5], float h,
+                                             const VGrid& G, int nfw,
+                                             typename RecOf<float, MODE>::type* out) {
   const float n = raw[0], T = raw[1], Td = raw[2], v = raw[3], x = raw[4];
   float jl, al, b;
-  line_coeffs<float>(P, n, T, x, h, &jl, &al, &b);
-  const float ad = (float)P.cad * n * h;
+  line_coeffs(P, n, T, x, h, &jl, &al, &b);
+  const float ad = P.cad * n * h;
   float bk0, bk1;
   dust_source_lin(P, Td, &bk0, &bk1);
   const bool has_line = jl != 0.0f || al != 0.0f;
   // no line: any finite profile parameter (the coefficients are zero)
   const float nib2 = has_line ? -kLog2e / (b * b) : -kLog2e;
-  const int win = line_window(v, b, ufirst, dvf, gw0, nfw, has_line);
+  const int win = line_window(v, b, G.ufw_hi, G.dvf_hi, 0, nfw, has_line);
+  int gv;
+  float vr;
+  centre_offset(G, v, &gv, &vr);
   if constexpr (MODE == M_SMOOTH) {
-    RecS32& r = so->rec;
+    RecS32 r;
     r.jl2 = 2.0f * jl;
     r.al2 = 2.0f * al;
-    r.v = v;
+    r.vr = vr;
+    r.gv = gv;
+    r.pad[0] = r.pad[1] = r.pad[2] = 0.0f;
     r.nib2 = nib2;
     r.d0 = 3.0f + 2.0f * ad;
     r.jd0 = 2.0f * ad * bk0;
     r.jd1 = 2.0f * ad * bk1;
     r.win = win;
+    *out = r;
   } else {
-    RecF32& r = so->rec;
+    RecF32 r;
     r.jl = jl;
     r.al = al;
-    r.v = v;
+    r.vr = vr;
+    r.gv = gv;
     r.nib2 = nib2;
     r.ad = ad;
     r.emD = -expm1f(-ad);
     r.bk0 = bk0;
     r.bk1 = bk1;
     r.win = win;
+    r.pad[0] = r.pad[1] = 0.0f;
+    *out = r;
   }
-  so->lo = win_lo(win);
-  so->hi = win_hi(win);
-  so->ad = ad;
+  return ad;
 }
 
 template <int MODE>
-__device__ __forceinline__ void make_record(const PhysParams& P, const double raw[5], double h,
-                                            double, double, int, int nfw,
-                                            SampleOut<double, MODE>* so) {
+__device__ __forceinline__ double make_record(const PhysParams& P, const double raw[5], double h,
+                                              int nfw, RecD* out) {
   const double n = raw[0], T = raw[1], Td = raw[2], v = raw[3], x = raw[4];
   double jl, al, b;
-  line_coeffs<double>(P, n, T, x, h, &jl, &al, &b);
-  RecD& r = so->rec;
+  line_coeffs(P, n, T, x, h, &jl, &al, &b);
+  RecD r;
   r.jl = jl;
   r.al = al;
   r.v = v;
@@ -75,25 +75,28 @@ __device__ __forceinline__ void make_record(const PhysParams& P, const double ra
   r.emD = -expm1(-r.ad);
   r.td = Td;
   // the double path evaluates the line at every fine velocity
-  r.win = pack_win(0, (nfw - 1) >> 5);
-  so->lo = 0;
-  so->hi = (nfw - 1) >> 5;
-  so->ad = r.ad;
+  r.win = pack_win(0, nfw - 1);
+  r.pad = 0;
+  *out = r;
+  return r.ad;
 }
 
 // ---------------------------------------------------------------------------
 // per-(sample, fine velocity) coefficients of the total intensity
 // ---------------------------------------------------------------------------
-// smooth: jt = 2 h j_total, d = 3 + 2 h alpha_total
-__device__ __forceinline__ void coeff_line(const RecS32& r, float u, float* jt, float* d) {
-  const float dd = u - r.v;
+// smooth: jt = 2 h j_total, d = 3 + 2 h alpha_total at local fine index gi
+// (velocity u)
+__device__ __forceinline__ void coeff_line(const RecS32& r, const VGrid& G, int gi, float u,
+                                           float* jt, float* d) {
+  const float dd = vel_offset(G, gi, r.gv, r.vr);
   const float g = ex2_approx(dd * r.nib2 * dd);
   *jt = fmaf(r.jl2, g, fmaf(r.jd1, u, r.jd0));
   *d = fmaf(r.al2, g, r.d0);
 }
 // formal: per-step emission jt and optical depth tau
-__device__ __forceinline__ void coeff_line(const RecF32& r, float u, float* jt, float* tau) {
-  const float dd = u - r.v;
+__device__ __forceinline__ void coeff_line(const RecF32& r, const VGrid& G, int gi, float u,
+                                           float* jt, float* tau) {
+  const float dd = vel_offset(G, gi, r.gv, r.vr);
   const float g = ex2_approx(dd * r.nib2 * dd);
   *jt = fmaf(r.jl, g, r.ad * fmaf(r.bk1, u, r.bk0));
   *tau = fmaf(r.al, g, r.ad);
@@ -117,21 +120,29 @@ __device__ __forceinline__ double psi_d(double tau) {
   return (tau == 0.0) ? 1.0 : -expm1(-tau) / tau;
 }
 
+// Is block i inside the fine-index window w?
+__device__ __forceinline__ bool block_in_window(int i, int w) {
+  const int lo = win_lo(w), hi = win_hi(w);
+  return lo <= hi && i >= (lo >> 5) && i <= (hi >> 5);
+}
+
 // ---------------------------------------------------------------------------
-// the kernel
+// generic transfer (every precision and integrator): register blocks i < NI,
+// uniform branches on the hull and on the sample's line window
 // ---------------------------------------------------------------------------
-template <typename R, int NI, int ST, int MODE>
+template <typename R, int NI, int MODE>
 struct Fwd {
   using Rec = typename RecOf<R, MODE>::type;
   static constexpr bool kDouble = sizeof(R) == 8;
+  using PP = typename std::conditional<kDouble, PhysParams, PhysF>::type;
 
   // Total-intensity transfer of the hull blocks [hlo, hhi] (or, with
   // line == false, dust-only transfer of the blocks at velocities u[]).
   // On return s1[i] holds the final intensity of block i.
   template <bool LINE>
-  static __device__ __forceinline__ void transfer(const PhysParams& P, const Rec* rec, int K,
-                                                  const R* u, int hlo, int hhi, R* s0, R* s1,
-                                                  R* s2) {
+  static __device__ __forceinline__ void transfer(const PP& P, const VGrid& G, int lane,
+                                                  const Rec* rec, int K, const R* u, int hlo,
+                                                  int hhi, R* s0, R* s1, R* s2) {
     if constexpr (MODE == M_SMOOTH) {
       if (K <= 1) {
 #pragma unroll
@@ -145,7 +156,7 @@ struct Fwd {
         for (int i = 0; i < NI; ++i) {
           if (i < hlo || i > hhi) continue;
           R jt, d;
-          coeffs<LINE>(P, r, i, u[i], &jt, &d);
+          coeffs<LINE>(P, G, lane, r, i, u[i], &jt, &d);
           s1[i] = jt + ((R)7 - d) * s0[i];
         }
       }
@@ -156,18 +167,18 @@ struct Fwd {
         for (int i = 0; i < NI; ++i) {
           if (i < hlo || i > hhi) continue;
           R jt, d;
-          coeffs<LINE>(P, r, i, u[i], &jt, &d);
+          coeffs<LINE>(P, G, lane, r, i, u[i], &jt, &d);
           s1[i] = relu((s1[i] + jt) * recip((R)1 + d));
         }
       }
       // BDF2 steps, two per iteration with the state roles swapped
       int k = 2;
       for (; k + 1 < K; k += 2) {
-        bdf2_step<LINE>(P, rec[k], u, hlo, hhi, s0, s1);      // s0 <- I_k
-        bdf2_step<LINE>(P, rec[k + 1], u, hlo, hhi, s1, s0);  // s1 <- I_{k+1}
+        bdf2_step<LINE>(P, G, lane, rec[k], u, hlo, hhi, s0, s1);      // s0 <- I_k
+        bdf2_step<LINE>(P, G, lane, rec[k + 1], u, hlo, hhi, s1, s0);  // s1 <- I_{k+1}
       }
       if (k < K) {
-        bdf2_step<LINE>(P, rec[k], u, hlo, hhi, s0, s1);
+        bdf2_step<LINE>(P, G, lane, rec[k], u, hlo, hhi, s0, s1);
 #pragma unroll
         for (int i = 0; i < NI; ++i) s1[i] = s0[i];
       }
@@ -177,7 +188,7 @@ struct Fwd {
 #pragma unroll
         for (int i = 0; i < NI; ++i) {
           if (i < hlo || i > hhi) continue;
-          s0[i] = formal_step<LINE>(P, r, i, u[i], s0[i]);
+          s0[i] = formal_step<LINE>(P, G, lane, r, i, u[i], s0[i]);
         }
       }
 #pragma unroll
@@ -200,7 +211,7 @@ struct Fwd {
         for (int i = 0; i < NI; ++i) {
           if (i < hlo || i > hhi) continue;
           R jt, tau;
-          coeffs_formal<LINE>(P, r, i, u[i], &jt, &tau);
+          coeffs_formal<LINE>(P, G, lane, r, i, u[i], &jt, &tau);
           s0[i] += jt * psi(tau) * expneg(s1[i]);
           // Kahan summation of tau
           const R y = tau - s2[i];
@@ -227,8 +238,8 @@ struct Fwd {
 
   // smooth-mode coefficients (2h j, 3 + 2h alpha) of block i at velocity u
   template <bool LINE>
-  static __device__ __forceinline__ void coeffs(const PhysParams& P, const Rec& r, int i, R u,
-                                                R* jt, R* d) {
+  static __device__ __forceinline__ void coeffs(const PP& P, const VGrid& G, int lane,
+                                                const Rec& r, int i, R u, R* jt, R* d) {
     if constexpr (kDouble) {
       const double bk = planck_k(P, r.td, u);
       const double two_ad = 2.0 * r.ad;
@@ -242,8 +253,8 @@ struct Fwd {
         *d = 3.0 + two_ad;
       }
     } else {
-      if (LINE && i >= win_lo(r.win) && i <= win_hi(r.win)) {
-        coeff_line(r, u, jt, d);
+      if (LINE && block_in_window(i, r.win)) {
+        coeff_line(r, G, 32 * i + lane, u, jt, d);
       } else {
         *jt = fmaf(r.jd1, u, r.jd0);
         *d = r.d0;
@@ -252,8 +263,9 @@ struct Fwd {
   }
 
   template <bool LINE>
-  static __device__ __forceinline__ void bdf2_step(const PhysParams& P, const Rec& r, const R* u,
-                                                   int hlo, int hhi, R* sa, const R* sb) {
+  static __device__ __forceinline__ void bdf2_step(const PP& P, const VGrid& G, int lane,
+                                                   const Rec& r, const R* u, int hlo, int hhi,
+                                                   R* sa, const R* sb) {
     // sa holds I_{n}, sb holds I_{n+1}; sa <- I_{n+2}
     R rd0 = (R)0;
     if constexpr (!kDouble) rd0 = recip(r.d0);
@@ -262,11 +274,11 @@ struct Fwd {
       if (i < hlo || i > hhi) continue;
       R jt, d, rd;
       if constexpr (kDouble) {
-        coeffs<LINE>(P, r, i, u[i], &jt, &d);
+        coeffs<LINE>(P, G, lane, r, i, u[i], &jt, &d);
         rd = (R)1 / d;
       } else {
-        if (LINE && i >= win_lo(r.win) && i <= win_hi(r.win)) {
-          coeff_line(r, u[i], &jt, &d);
+        if (LINE && block_in_window(i, r.win)) {
+          coeff_line(r, G, 32 * i + lane, u[i], &jt, &d);
           rd = recip(d);
         } else {
           jt = fmaf(r.jd1, u[i], r.jd0);
@@ -279,8 +291,8 @@ struct Fwd {
 
   // formal-mode per-step emission and optical depth of block i
   template <bool LINE>
-  static __device__ __forceinline__ void coeffs_formal(const PhysParams& P, const Rec& r, int i,
-                                                       R u, R* jt, R* tau) {
+  static __device__ __forceinline__ void coeffs_formal(const PP& P, const VGrid& G, int lane,
+                                                       const Rec& r, int i, R u, R* jt, R* tau) {
     if constexpr (kDouble) {
       const double bk = planck_k(P, r.td, u);
       if (LINE) {
@@ -293,8 +305,8 @@ struct Fwd {
         *tau = r.ad;
       }
     } else {
-      if (LINE && i >= win_lo(r.win) && i <= win_hi(r.win)) {
-        coeff_line(r, u, jt, tau);
+      if (LINE && block_in_window(i, r.win)) {
+        coeff_line(r, G, 32 * i + lane, u, jt, tau);
       } else {
         *jt = r.ad * fmaf(r.bk1, u, r.bk0);
         *tau = r.ad;
@@ -303,16 +315,16 @@ struct Fwd {
   }
 
   template <bool LINE>
-  static __device__ __forceinline__ R formal_step(const PhysParams& P, const Rec& r, int i, R u,
-                                                  R I) {
+  static __device__ __forceinline__ R formal_step(const PP& P, const VGrid& G, int lane,
+                                                  const Rec& r, int i, R u, R I) {
     if constexpr (kDouble) {
       R jt, tau;
-      coeffs_formal<LINE>(P, r, i, u, &jt, &tau);
+      coeffs_formal<LINE>(P, G, lane, r, i, u, &jt, &tau);
       return I + (jt - tau * I) * psi_d(tau);
     } else {
-      if (LINE && i >= win_lo(r.win) && i <= win_hi(r.win)) {
+      if (LINE && block_in_window(i, r.win)) {
         float jt, tau;
-        coeff_line(r, u, &jt, &tau);
+        coeff_line(r, G, 32 * i + lane, u, &jt, &tau);
         return fmaf(fmaf(-tau, I, jt), psi_f(tau), I);
       }
       // dust only: I <- I + (S - I)(1 - e^{-tau_D})
@@ -370,18 +382,287 @@ struct Fwd {
   }
 };
 
-template <typename R>
-__device__ __forceinline__ R bg_intensity(const PhysParams& P, R u) {
-  return planck_k(P, (R)P.t_bg, u);
+// ---------------------------------------------------------------------------
+// branch-free transfer of NA consecutive fine blocks starting at block hb
+// (float path, smooth and formal integration).  With strided velocities a
+// line window of at most 32 fine velocities holds exactly one velocity of
+// each lane, so each lane evaluates its NS <= 2 line velocities once per
+// sample ("line slots") and applies them to the matching block with
+// predicated selects; the other blocks take the dust-only update.  The three
+// continuum basis recurrences ride along (lanes 0, 1, 2).
+// ---------------------------------------------------------------------------
+template <int NS>
+struct Slots {
+  int j[NS];      // block of the slot relative to hb, -1 = no line velocity
+  float a[NS];    // smooth: 2h j_line;     formal: per-step emission
+  float b[NS];    // smooth: 3 + 2h alpha;  formal: optical depth
+};
+
+template <int NS>
+__device__ __forceinline__ Slots<NS> slots_smooth(const RecS32& r, int hb, int lane,
+                                                  const VGrid& G) {
+  Slots<NS> s;
+  const int glo = win_lo(r.win), ghi = win_hi(r.win);
+  const int g0 = glo + ((lane - glo) & 31);
+#pragma unroll
+  for (int q = 0; q < NS; ++q) {
+    const int g = g0 + 32 * q;
+    const float dd = vel_offset(G, g, r.gv, r.vr);
+    const float e = ex2_approx(dd * r.nib2 * dd);
+    s.j[q] = (g <= ghi) ? (g >> 5) - hb : -1;
+    s.a[q] = r.jl2 * e;
+    s.b[q] = fmaf(r.al2, e, r.d0);
+  }
+  return s;
 }
 
-// One work item: ray (px, py) of job J, channel window `win`.
+template <int NS>
+__device__ __forceinline__ Slots<NS> slots_formal(const RecF32& r, int hb, int lane,
+                                                  const VGrid& G) {
+  Slots<NS> s;
+  const int glo = win_lo(r.win), ghi = win_hi(r.win);
+  const int g0 = glo + ((lane - glo) & 31);
+#pragma unroll
+  for (int q = 0; q < NS; ++q) {
+    const int g = g0 + 32 * q;
+    const float ug = fmaf((float)g, G.dvf_hi, G.ufw_hi);
+    const float dd = vel_offset(G, g, r.gv, r.vr);
+    const float e = ex2_approx(dd * r.nib2 * dd);
+    s.j[q] = (g <= ghi) ? (g >> 5) - hb : -1;
+    s.a[q] = fmaf(r.jl, e, r.ad * fmaf(r.bk1, ug, r.bk0));
+    s.b[q] = fmaf(r.al, e, r.ad);
+  }
+  return s;
+}
+
+template <int NA, int NS>
+struct FastSmooth {
+  // BDF2 step: sa <- I_{n+2} from sa = I_n, sb = I_{n+1}
+  static __device__ __forceinline__ void step(const RecS32& r, const float (&u)[NA],
+                                              float (&sa)[NA], const float (&sb)[NA], int hb,
+                                              int lane, const VGrid& G, float& xa, float xb,
+                                              float m1, float m2) {
+    const Slots<NS> sl = slots_smooth<NS>(r, hb, lane, G);
+    const float rd0 = rcp_approx(r.d0);
+    float rl[NS];
+#pragma unroll
+    for (int q = 0; q < NS; ++q) rl[q] = rcp_approx(sl.b[q]);
+#pragma unroll
+    for (int j = 0; j < NA; ++j) {
+      float t = fmaf(r.jd1, u[j], r.jd0) - sa[j];
+      float rr = rd0;
+#pragma unroll
+      for (int q = 0; q < NS; ++q) {
+        const bool p = sl.j[q] == j;
+        t = p ? t + sl.a[q] : t;
+        rr = p ? rl[q] : rr;
+      }
+      sa[j] = fmaxf(fmaf(4.0f, sb[j], t) * rr, 0.0f);
+    }
+    const float jb = fmaf(m2, r.jd1, m1 * r.jd0);
+    xa = fmaf(4.0f, xb, jb - xa) * rd0;
+  }
+
+  // Runs the whole ray; writes the fine intensities of its blocks to fbuf and
+  // returns this lane's basis value.
+  static __device__ __forceinline__ float run(const PhysF& P, const RecS32* rec, int K, int hb,
+                                              int lane, const VGrid& G, int nfw, float* fbuf) {
+    float u[NA], s0[NA], s1[NA];
+#pragma unroll
+    for (int j = 0; j < NA; ++j) {
+      const int g = min(32 * (hb + j) + lane, nfw - 1);
+      u[j] = fmaf((float)g, G.dvf_hi, G.ufw_hi);
+      s0[j] = planck_k(P, P.t_bg, u[j]);
+      s1[j] = s0[j];
+    }
+    const float m0 = (lane == 0) ? 1.0f : 0.0f;
+    const float m1 = (lane == 1) ? 1.0f : 0.0f;
+    const float m2 = (lane == 2) ? 1.0f : 0.0f;
+    float x0 = m0, x1 = m0;
+    if (K >= 2) {
+      // k = 0: s1 <- 2h j_0 + (7 - d_0) I_0
+      {
+        const RecS32 r = rec[0];
+        const Slots<NS> sl = slots_smooth<NS>(r, hb, lane, G);
+#pragma unroll
+        for (int j = 0; j < NA; ++j) {
+          float t = fmaf(r.jd1, u[j], r.jd0);
+          float d = r.d0;
+#pragma unroll
+          for (int q = 0; q < NS; ++q) {
+            const bool p = sl.j[q] == j;
+            t = p ? t + sl.a[q] : t;
+            d = p ? sl.b[q] : d;
+          }
+          s1[j] = t + (7.0f - d) * s0[j];
+        }
+        x1 = fmaf(m2, r.jd1, m1 * r.jd0) + (7.0f - r.d0) * x0;
+      }
+      // k = 1: trapezoidal step
+      {
+        const RecS32 r = rec[1];
+        const Slots<NS> sl = slots_smooth<NS>(r, hb, lane, G);
+        const float r1 = rcp_approx(1.0f + r.d0);
+        float rl[NS];
+#pragma unroll
+        for (int q = 0; q < NS; ++q) rl[q] = rcp_approx(1.0f + sl.b[q]);
+#pragma unroll
+        for (int j = 0; j < NA; ++j) {
+          float t = fmaf(r.jd1, u[j], r.jd0);
+          float rr = r1;
+#pragma unroll
+          for (int q = 0; q < NS; ++q) {
+            const bool p = sl.j[q] == j;
+            t = p ? t + sl.a[q] : t;
+            rr = p ? rl[q] : rr;
+          }
+          s1[j] = fmaxf((s1[j] + t) * rr, 0.0f);
+        }
+        x1 = (x1 + fmaf(m2, r.jd1, m1 * r.jd0)) * r1;
+      }
+      int k = 2;
+      for (; k + 1 < K; k += 2) {
+        step(rec[k], u, s0, s1, hb, lane, G, x0, x1, m1, m2);
+        step(rec[k + 1], u, s1, s0, hb, lane, G, x1, x0, m1, m2);
+      }
+      if (k < K) {
+        step(rec[k], u, s0, s1, hb, lane, G, x0, x1, m1, m2);
+#pragma unroll
+        for (int j = 0; j < NA; ++j) s1[j] = s0[j];
+        x1 = x0;
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < NA; ++j) {
+      const int g = 32 * (hb + j) + lane;
+      if (g < nfw) fbuf[g] = s1[j];
+    }
+    return x1;
+  }
+};
+
+template <int NA, int NS>
+struct FastFormal {
+  static __device__ __forceinline__ float run(const PhysF& P, const RecF32* rec, int K, int hb,
+                                              int lane, const VGrid& G, int nfw, float* fbuf) {
+    float u[NA], I[NA];
+#pragma unroll
+    for (int j = 0; j < NA; ++j) {
+      const int g = min(32 * (hb + j) + lane, nfw - 1);
+      u[j] = fmaf((float)g, G.dvf_hi, G.ufw_hi);
+      I[j] = planck_k(P, P.t_bg, u[j]);
+    }
+    const float m1 = (lane == 1) ? 1.0f : 0.0f;
+    const float m2 = (lane == 2) ? 1.0f : 0.0f;
+    float x = (lane == 0) ? 1.0f : 0.0f;
+    for (int k = 0; k < K; ++k) {
+      const RecF32 r = rec[k];
+      const Slots<NS> sl = slots_formal<NS>(r, hb, lane, G);
+      float ps[NS];
+#pragma unroll
+      for (int q = 0; q < NS; ++q) ps[q] = psi_f(sl.b[q]);
+#pragma unroll
+      for (int j = 0; j < NA; ++j) {
+        // dust: I + (S - I) emD;  line: I + (j - tau I) psi(tau)
+        float A = fmaf(r.bk1, u[j], r.bk0) - I[j];
+        float Bc = r.emD;
+#pragma unroll
+        for (int q = 0; q < NS; ++q) {
+          const bool p = sl.j[q] == j;
+          A = p ? fmaf(-sl.b[q], I[j], sl.a[q]) : A;
+          Bc = p ? ps[q] : Bc;
+        }
+        I[j] = fmaf(A, Bc, I[j]);
+      }
+      const float s = fmaf(m2, r.bk1, m1 * r.bk0);
+      x = fmaf(s - x, r.emD, x);
+    }
+#pragma unroll
+    for (int j = 0; j < NA; ++j) {
+      const int g = 32 * (hb + j) + lane;
+      if (g < nfw) fbuf[g] = I[j];
+    }
+    return x;
+  }
+};
+
+// Block-count buckets of the fast path (a hull of na blocks runs in the
+// smallest bucket >= na).
+__device__ __forceinline__ int fast_bucket(int na, int ns) {
+  if (ns == 1) {
+    if (na <= 8) return (na + 1) & ~1;   // 2, 4, 6, 8
+    if (na <= 10) return 10;
+    if (na <= 12) return 12;
+    if (na <= 14) return 14;
+    if (na <= 17) return 17;
+    if (na <= 20) return 20;
+    if (na <= 24) return 24;
+    if (na <= 28) return 28;
+    return 33;
+  }
+  if (na <= 4) return 4;
+  if (na <= 8) return 8;
+  if (na <= 12) return 12;
+  if (na <= 17) return 17;
+  if (na <= 24) return 24;
+  return 33;
+}
+
+// Runs the fast path for bucket `nb` (<= NI); returns false if nb is not
+// compiled for this NI.
+template <int NI, int MODE, int NS>
+__device__ __forceinline__ bool run_fast(int nb, const PhysF& P,
+                                         const typename RecOf<float, MODE>::type* rec, int K,
+                                         int hb, int lane, const VGrid& G, int nfw, float* fbuf,
+                                         float* xb) {
+#define IRT_FAST(NA_)                                                                        \
+  case NA_:                                                                                  \
+    if constexpr (NA_ <= NI) {                                                               \
+      if constexpr (MODE == M_SMOOTH)                                                        \
+        *xb = FastSmooth<NA_, NS>::run(P, rec, K, hb, lane, G, nfw, fbuf);                  \
+      else                                                                                   \
+        *xb = FastFormal<NA_, NS>::run(P, rec, K, hb, lane, G, nfw, fbuf);                  \
+      return true;                                                                           \
+    }                                                                                        \
+    return false;
+  if constexpr (NS == 1) {
+    switch (nb) {
+      IRT_FAST(2) IRT_FAST(4) IRT_FAST(6) IRT_FAST(8) IRT_FAST(10) IRT_FAST(12) IRT_FAST(14)
+      IRT_FAST(17) IRT_FAST(20) IRT_FAST(24) IRT_FAST(28) IRT_FAST(33)
+      default: return false;
+    }
+  } else {
+    switch (nb) {
+      IRT_FAST(4) IRT_FAST(8) IRT_FAST(12) IRT_FAST(17) IRT_FAST(24) IRT_FAST(33)
+      default: return false;
+    }
+  }
+#undef IRT_FAST
+}
+
+template <bool D> struct PSel;
+template <> struct PSel<true> {
+  static __device__ __forceinline__ const PhysParams& get(const PhysParams& a, const PhysF&) {
+    return a;
+  }
+};
+template <> struct PSel<false> {
+  static __device__ __forceinline__ const PhysF& get(const PhysParams&, const PhysF& b) {
+    return b;
+  }
+};
+
+// ---------------------------------------------------------------------------
+// one work item: ray (px, py) of job J, channel window `win`
+// ---------------------------------------------------------------------------
 template <typename R, int NI, int ST, int MODE>
-__device__ void render_item(const JobDev& J, const PhysParams& P, int px, int py, int win,
-                            unsigned char* wsm, int fw_off, int cw_off, int lane,
+__device__ void render_item(const JobDev& J, const PhysParams& PD, const PhysF& PF, int px,
+                            int py, int win, unsigned char* wsm, int fw_off, int cw_off, int lane,
                             unsigned flags, unsigned long long* stats) {
-  using F = Fwd<R, NI, ST, MODE>;
+  using F = Fwd<R, NI, MODE>;
   using Rec = typename F::Rec;
+  constexpr bool kDouble = F::kDouble;
+  const auto& P = PSel<kDouble>::get(PD, PF);
   Rec* rec = reinterpret_cast<Rec*>(wsm);
   R* fbuf = reinterpret_cast<R*>(wsm + fw_off);
   R* cbuf = reinterpret_cast<R*>(wsm + cw_off);
@@ -392,46 +673,63 @@ __device__ void render_item(const JobDev& J, const PhysParams& P, int px, int py
   const int f = J.f;
   const int gw0 = (f >= 1) ? 2 * f * c0 : c0;
   const int nfw = (f >= 1) ? 2 * f * cwn + 1 : cwn;
-  const R ufirst = (R)J.ufirst, dvf = (R)J.dvf;
-
-  R u[NI];
-#pragma unroll
-  for (int i = 0; i < NI; ++i) {
-    const int g = min(lane + 32 * i, nfw - 1);
-    u[i] = (R)(J.ufirst + (double)(gw0 + g) * J.dvf);
+  const int nblk = (nfw + 31) >> 5;
+  // fine velocities of the window: u(g) = J.ufirst + (gw0 + g) J.dvf
+  VGrid G;
+  {
+    const double ufw_d = J.ufirst + (double)gw0 * J.dvf;
+    G.ufw_hi = (float)ufw_d;
+    G.ufw_lo = (float)(ufw_d - (double)G.ufw_hi);
+    G.dvf_hi = (float)J.dvf;
+    G.dvf_lo = (float)(J.dvf - (double)G.dvf_hi);
   }
 
   // ---- sample pass
   const RayGeom geo = ray_geom(J, px, py);
   const int K = geo.K;
   const R h = (R)geo.h;
-  int hlo = 1 << 20, hhi = -1;
+  RayPos rp;
+  if constexpr (!kDouble) {
+    if (!J.zview && K > 0) rp = ray_pos(J, geo);
+  }
+  int hlo = 1 << 20, hhi = -1, wmax = 0;
   R admax = (R)0;
   for (int k0 = 0; k0 < K; k0 += 32) {
     const int k = k0 + lane;
-    if (k < K) {
-      R raw[5];
-      sample_raw<R, ST>(J, geo, px, py, k, raw);
-      SampleOut<R, MODE> so;
-      make_record<MODE>(P, raw, h, ufirst, dvf, gw0, nfw, &so);
-      rec[k] = so.rec;
-      if (so.lo <= so.hi) {
-        hlo = min(hlo, so.lo);
-        hhi = max(hhi, so.hi);
+    R raw[5];
+    R ad = (R)0;
+    if constexpr (kDouble) {
+      if (k < K) {
+        sample_raw<ST>(J, geo, px, py, k, raw);
+        ad = make_record<MODE>(PD, raw, h, nfw, &rec[k]);
       }
-      admax = fmax(admax, so.ad);
+    } else {
+      if (k < K) {
+        sample_raw<ST>(J, rp, px, py, k, raw);
+        ad = make_record<MODE>(PF, raw, h, G, nfw, &rec[k]);
+      }
+    }
+    if (k < K) {
+      const int w = rec[k].win;
+      const int lo = win_lo(w), hi = win_hi(w);
+      if (lo <= hi) {
+        hlo = min(hlo, lo >> 5);
+        hhi = max(hhi, hi >> 5);
+        wmax = max(wmax, hi - lo + 1);
+      }
+      admax = fmax(admax, ad);
     }
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     hlo = min(hlo, __shfl_xor_sync(0xffffffffu, hlo, o));
     hhi = max(hhi, __shfl_xor_sync(0xffffffffu, hhi, o));
+    wmax = max(wmax, __shfl_xor_sync(0xffffffffu, wmax, o));
     admax = fmax(admax, __shfl_xor_sync(0xffffffffu, admax, o));
   }
   __syncwarp();
 
-  const int nblk = (nfw + 31) >> 5;
-  const bool explicit_all = F::kDouble || (flags & IRT_FLAG_EXPLICIT_CHANNELS) ||
+  const bool explicit_all = kDouble || (flags & IRT_FLAG_EXPLICIT_CHANNELS) ||
                             (MODE == M_SMOOTH && admax > (R)0.5);
   if (explicit_all) {
     hlo = 0;
@@ -443,7 +741,7 @@ __device__ void render_item(const JobDev& J, const PhysParams& P, int px, int py
     for (int k = lane; k < K; k += 32) {
       const int w = rec[k].win;
       const int lo = win_lo(w), hi = win_hi(w);
-      if (lo <= hi) nline += (unsigned long long)(hi - lo + 1);
+      if (lo <= hi) nline += (unsigned long long)((hi >> 5) - (lo >> 5) + 1);
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) nline += __shfl_xor_sync(0xffffffffu, nline, o);
@@ -459,51 +757,82 @@ __device__ void render_item(const JobDev& J, const PhysParams& P, int px, int py
   }
 
   // ---- total intensity on the blocks the line reaches
-  R s0[NI], s1[NI], s2[NI];
-#pragma unroll
-  for (int i = 0; i < NI; ++i) {
-    s0[i] = (i >= hlo && i <= hhi) ? bg_intensity<R>(P, u[i]) : (R)0;
-    s1[i] = (R)0;
-    s2[i] = (R)0;
-  }
-  F::template transfer<true>(P, rec, K, u, hlo, hhi, s0, s1, s2);
-
-  // ---- continuum basis (float path, shortcut allowed)
   R X0 = (R)0, X1 = (R)0, X2 = (R)0;
-  if constexpr (!F::kDouble) {
-    if (!explicit_all) {
-      const float xb = F::basis(rec, K, lane);
-      X0 = __shfl_sync(0xffffffffu, xb, 0);
-      X1 = __shfl_sync(0xffffffffu, xb, 1);
-      X2 = __shfl_sync(0xffffffffu, xb, 2);
+  bool fast = false;
+  int hb = 0, nb = 0;
+  if constexpr (!kDouble && MODE != M_FORMAL_KAHAN) {
+    const int ns = (wmax <= 32) ? 1 : ((wmax <= 64) ? 2 : 3);
+    if (!explicit_all && ns <= 2) {
+      const bool none = hhi < hlo;
+      const int na = none ? 1 : hhi - hlo + 1;
+      nb = fast_bucket(na, ns);
+      if (nb <= NI) {
+        hb = none ? 0 : min(hlo, max(nblk - nb, 0));
+        float xb = 0.0f;
+        fast = (ns == 1) ? run_fast<NI, MODE, 1>(nb, PF, rec, K, hb, lane, G, nfw, fbuf, &xb)
+                         : run_fast<NI, MODE, 2>(nb, PF, rec, K, hb, lane, G, nfw, fbuf, &xb);
+        if (fast) {
+          X0 = __shfl_sync(0xffffffffu, xb, 0);
+          X1 = __shfl_sync(0xffffffffu, xb, 1);
+          X2 = __shfl_sync(0xffffffffu, xb, 2);
+        }
+      }
     }
   }
 
-  // fine intensities of the window -> shared memory
+  R u[NI];
+#pragma unroll
+  for (int i = 0; i < NI; ++i) {
+    const int g = min(lane + 32 * i, nfw - 1);
+    if constexpr (kDouble) u[i] = J.ufirst + (double)(gw0 + g) * J.dvf;
+    else u[i] = fmaf((float)g, G.dvf_hi, G.ufw_hi);
+  }
+  if (!fast) {
+    R s0[NI], s1[NI], s2[NI];
+#pragma unroll
+    for (int i = 0; i < NI; ++i) {
+      s0[i] = (i >= hlo && i <= hhi) ? planck_k(P, (R)P.t_bg, u[i]) : (R)0;
+      s1[i] = (R)0;
+      s2[i] = (R)0;
+    }
+    F::template transfer<true>(P, G, lane, rec, K, u, hlo, hhi, s0, s1, s2);
+    if constexpr (!kDouble) {
+      if (!explicit_all) {
+        const float xb = F::basis(rec, K, lane);
+        X0 = __shfl_sync(0xffffffffu, xb, 0);
+        X1 = __shfl_sync(0xffffffffu, xb, 1);
+        X2 = __shfl_sync(0xffffffffu, xb, 2);
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < NI; ++i) {
+      const int g = lane + 32 * i;
+      if (g < nfw && i >= hlo && i <= hhi) fbuf[g] = s1[i];
+    }
+    hb = hlo;
+    nb = (hhi >= hlo) ? hhi - hlo + 1 : 0;
+  }
+  // velocities outside the explicit blocks: continuum basis
 #pragma unroll
   for (int i = 0; i < NI; ++i) {
     const int g = lane + 32 * i;
-    if (g < nfw) {
-      R v;
-      if (i >= hlo && i <= hhi) v = s1[i];
-      else v = X0 * bg_intensity<R>(P, u[i]) + X1 + X2 * u[i];
-      fbuf[g] = v;
-    }
+    if (g < nfw && (i < hb || i >= hb + nb))
+      fbuf[g] = X0 * planck_k(P, (R)P.t_bg, u[i]) + X1 + X2 * u[i];
   }
 
   // ---- continuum at channel centres when every channel is explicit
   if (explicit_all) {
-    R uc[NI];
+    R uc[NI], s0[NI], s1[NI], s2[NI];
     const int cblk = (cwn + 31) >> 5;
 #pragma unroll
     for (int i = 0; i < NI; ++i) {
       const int c = min(lane + 32 * i, cwn - 1);
-      uc[i] = (R)(J.v0 + ((double)(c0 + c) + 0.5) * J.dv);
-      s0[i] = (i < cblk) ? bg_intensity<R>(P, uc[i]) : (R)0;
+      uc[i] = (R)J.v0 + ((R)(c0 + c) + (R)0.5) * (R)J.dv;
+      s0[i] = (i < cblk) ? planck_k(P, (R)P.t_bg, uc[i]) : (R)0;
       s1[i] = (R)0;
       s2[i] = (R)0;
     }
-    F::template transfer<false>(P, rec, K, uc, 0, cblk - 1, s0, s1, s2);
+    F::template transfer<false>(P, G, lane, rec, K, uc, 0, cblk - 1, s0, s1, s2);
 #pragma unroll
     for (int i = 0; i < NI; ++i) {
       const int c = lane + 32 * i;
@@ -517,8 +846,7 @@ __device__ void render_item(const JobDev& J, const PhysParams& P, int px, int py
   const long long pix = (long long)py * J.npx + px;
   for (int cl = lane; cl < cwn; cl += 32) {
     const int c = c0 + cl;
-    const double ucd = J.v0 + ((double)c + 0.5) * J.dv;
-    const R uc = (R)ucd;
+    const R uc = (R)J.v0 + ((R)c + (R)0.5) * (R)J.dv;
     R ibar;
     if (f >= 1) {
       const R* F6 = fbuf + 2 * f * cl;
@@ -529,7 +857,7 @@ __device__ void render_item(const JobDev& J, const PhysParams& P, int px, int py
     } else {
       ibar = fbuf[cl];
     }
-    const R ib = bg_intensity<R>(P, uc);
+    const R ib = planck_k(P, (R)P.t_bg, uc);
     const R ic = explicit_all ? cbuf[cl] : X0 * ib + X1 + X2 * uc;
     R s = (R)P.out_scale;
     if (P.units == IRT_UNITS_TRJ) {
@@ -549,8 +877,8 @@ __device__ void render_item(const JobDev& J, const PhysParams& P, int px, int py
 }
 
 template <typename R, int NI, int ST, int MODE>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32)
-fwd_kernel(const __grid_constant__ JobTable tab, int njobs, const PhysParams P,
+__global__ void __launch_bounds__(kWarpsPerBlock * 32, (sizeof(R) == 4 && NI <= 17) ? 4 : 1)
+fwd_kernel(const __grid_constant__ JobTable tab, int njobs, const PhysParams PD, const PhysF PF,
            long long total_items, unsigned long long* queue, int per_warp, int fw_off, int cw_off,
            unsigned flags, unsigned long long* stats) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -574,7 +902,8 @@ fwd_kernel(const __grid_constant__ JobTable tab, int njobs, const PhysParams P,
     const long long ray = local / J.nwin;
     const int px = (int)(ray % J.npx), py = (int)(ray / J.npx);
     if constexpr (ST == ST_F64 || sizeof(R) == 4) {
-      render_item<R, NI, ST, MODE>(J, P, px, py, win, wsm, fw_off, cw_off, lane, flags, stats);
+      render_item<R, NI, ST, MODE>(J, PD, PF, px, py, win, wsm, fw_off, cw_off, lane, flags,
+                                   stats);
     }
     if (queue) {
       unsigned long long t = 0;
@@ -590,9 +919,10 @@ fwd_kernel(const __grid_constant__ JobTable tab, int njobs, const PhysParams P,
 
 // Host-side launcher of one kernel instance.
 template <typename R, int NI, int ST, int MODE>
-int launch_fwd_inst(const JobTable& tab, int njobs, const PhysParams& P, long long total_items,
-                    unsigned long long* queue, int grid_blocks, int kmax, int fwmax, int cwmax,
-                    unsigned flags, unsigned long long* stats, cudaStream_t stream) {
+int launch_fwd_inst(const JobTable& tab, int njobs, const PhysParams& P, const PhysF& PF,
+                    long long total_items, unsigned long long* queue, int grid_blocks, int kmax,
+                    int fwmax, int cwmax, unsigned flags, unsigned long long* stats,
+                    cudaStream_t stream) {
   using Rec = typename dev::RecOf<R, MODE>::type;
   const int rec_bytes = (int)sizeof(Rec) * kmax;
   const int fw_off = (rec_bytes + 15) & ~15;
@@ -614,7 +944,7 @@ int launch_fwd_inst(const JobTable& tab, int njobs, const PhysParams& P, long lo
     blocks = (long long)std::max(per_sm, 1) * sms;
   }
   if (blocks < 1) return 0;
-  kern<<<(unsigned)blocks, kWarpsPerBlock * 32, smem, stream>>>(tab, njobs, P, total_items,
+  kern<<<(unsigned)blocks, kWarpsPerBlock * 32, smem, stream>>>(tab, njobs, P, PF, total_items,
                                                                  queue, per_warp, fw_off, cw_off,
                                                                  flags, stats);
   return (int)cudaGetLastError();

@@ -40,6 +40,13 @@ struct PhysParams {
   int integration;    // irt_integration
 };
 
+// The same constants rounded to float for the float kernels (no FP64 work
+// in their per-sample code).
+struct PhysF {
+  float T0, e_u, e_l, theta_rot, cj, ca, c_th, two_sig2, t_inf, cad, inv_c_kms, t_bg, out_scale;
+  int units;
+};
+
 // One render job as the kernels see it.
 struct JobDev {
   const void* cells;     // packed cells [nz][ny][nx]
@@ -51,6 +58,9 @@ struct JobDev {
   double dx;             // cell size [cm]
   int zview;             // 1 = z view (cell exact)
   double theta, phi;     // view angles [rad]
+  // oblique view basis (set up on the host from theta, phi): ray direction d,
+  // pixel axes et, ep, 1/d per axis (infinite where d = 0), 1/dx
+  double d[3], et[3], ep[3], inv_d[3], inv_dx;
   int npx, npy;
   double pixel;          // pixel pitch [cm]
   int nchan, f;

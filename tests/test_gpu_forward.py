@@ -259,3 +259,18 @@ def test_gpu_errors_are_reported():
     with pytest.raises(irt.IrtError, match="IRT_EINVAL"):
         irt.forward(g, View(0.0, 0.0, 8, 8, dx, 0), VelocityAxis(8, -8.0, -1.0, 1), LINE, DUST)
     g.close()
+
+
+@pytest.mark.parametrize("integration", ["smooth", "formal", "formal_kahan"])
+def test_non_dyadic_velocity_grid(integration):
+    """Fine velocities that float cannot represent (dv = 0.3 km/s, v0 = -37.7)."""
+    fs = small_fields((40, 10, 12), seed=71)
+    f32, deq = to_storage(fs, np.float32)
+    dx = 0.1 * PC
+    view = View(0.0, 0.0, 12, 10, dx, 0)
+    for va in (VelocityAxis(180, -37.7, 0.3, 1), VelocityAxis(70, -61.3, 1.7, 3)):
+        gpu = gpu_render(torch_fields(f32), dx, view, va, LINE, DUST, integration=integration)
+        pix = all_pixels(12, 10)
+        orc = oracle_pixels(deq.as_tuple(), dx, view, va, LINE, DUST, pix,
+                            integration=integration)
+        assert_parity(gpu, orc, pix)
