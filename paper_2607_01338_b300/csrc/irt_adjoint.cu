@@ -1,0 +1,665 @@
+// Reverse-mode adjoint of the smooth-integration forward render (z view).
+//
+// Gradients of a scalar loss with respect to n_H2, T_gas and v_los of every
+// cell, given the cotangents of the five output cubes.  One warp per ray
+// (one channel window).  The forward transfer of the ray is re-run exactly as
+// the forward kernel runs it (hull blocks with line slots, the three
+// continuum basis recurrences), saving its state pair every 32 samples in
+// per-warp device scratch.  The reverse sweep then walks the segments from
+// the observer back: each segment is recomputed from its checkpoint in
+// sub-segments of 16 samples whose pre-ReLU values go to scratch (L2
+// resident), and the TR / BDF2 steps are reversed sample by sample
+// (Sec. 4.8: I_{n+2} = max(0, (2h j + 4 I_{n+1} - I_n) / (3 + 2h alpha))).
+// Per-sample partial derivatives with respect to the record quantities
+// (h alpha_D, 2h j_line, 2h alpha_line, v_los, b) are reduced across the
+// lanes through shared memory and chained to the cell fields through the LTE
+// populations (Sec. 5.10), the partition function and the Doppler width.
+// The ReLU derivative is 1 for a non-negative argument, 0 otherwise.
+#include "irt_forward_impl.cuh"
+
+namespace irt {
+namespace dev {
+
+constexpr int kSeg = kAdjSeg;   // checkpoint spacing (samples)
+constexpr int kSub = kAdjSub;   // sub-segment whose pre-ReLU values are stored
+constexpr int kNP = 5;     // partials: h alpha_D, 2h j_L, 2h alpha_L, v, b
+constexpr int kPStride = 33;   // padded lane stride of the partial buffer
+
+// record quantities used by the adjoint only: 2 bk0, 2 bk1 (dust Planck
+// coefficients) ride in the pad words of the smooth record
+__device__ __forceinline__ float rec_bk0x2(const RecS32& r) { return r.pad[0]; }
+__device__ __forceinline__ float rec_bk1x2(const RecS32& r) { return r.pad[1]; }
+
+template <int NA, int NS>
+struct Adj {
+  static constexpr int NB = NA + 1;   // hull blocks + the basis slot
+
+  // pre-ReLU value of one BDF2 step (same arithmetic as FastSmooth::step)
+  static __device__ __forceinline__ void step(const RecS32& r, const float (&u)[NA],
+                                              float (&sa)[NA], const float (&sb)[NA], int hb,
+                                              int lane, const VGrid& G, float& xa, float xb,
+                                              float m1, float m2, float* pre_out, bool store) {
+    const Slots<NS> sl = slots_smooth<NS>(r, hb, lane, G);
+    const float rd0 = rcp_approx(r.d0);
+    float rl[NS];
+#pragma unroll
+    for (int q = 0; q < NS; ++q) rl[q] = rcp_approx(sl.b[q]);
+#pragma unroll
+    for (int j = 0; j < NA; ++j) {
+      float t = fmaf(r.jd1, u[j], r.jd0) - sa[j];
+      float rr = rd0;
+#pragma unroll
+      for (int q = 0; q < NS; ++q) {
+        const bool p = sl.j[q] == j;
+        t = p ? t + sl.a[q] : t;
+        rr = p ? rl[q] : rr;
+      }
+      const float pre = fmaf(4.0f, sb[j], t) * rr;
+      if (store) pre_out[j * 32] = pre;
+      sa[j] = fmaxf(pre, 0.0f);
+    }
+    const float jb = fmaf(m2, r.jd1, m1 * r.jd0);
+    xa = fmaf(4.0f, xb, jb - xa) * rd0;
+    if (store) pre_out[NA * 32] = xa;
+  }
+
+  // sample 0 and the trapezoidal step to sample 1 from the background
+  static __device__ __forceinline__ void start(const RecS32* rec, const float (&u)[NA],
+                                               const float (&bg)[NA], float (&s0)[NA],
+                                               float (&s1)[NA], int hb, int lane, const VGrid& G,
+                                               float& x0, float& x1, float m0, float m1, float m2,
+                                               float* pre1) {
+    const RecS32 r0 = rec[0];
+    const Slots<NS> sl0 = slots_smooth<NS>(r0, hb, lane, G);
+#pragma unroll
+    for (int j = 0; j < NA; ++j) {
+      float t = fmaf(r0.jd1, u[j], r0.jd0);
+      float d = r0.d0;
+#pragma unroll
+      for (int q = 0; q < NS; ++q) {
+        const bool p = sl0.j[q] == j;
+        t = p ? t + sl0.a[q] : t;
+        d = p ? sl0.b[q] : d;
+      }
+      s0[j] = bg[j];
+      s1[j] = t + (7.0f - d) * s0[j];
+    }
+    x0 = m0;
+    x1 = fmaf(m2, r0.jd1, m1 * r0.jd0) + (7.0f - r0.d0) * x0;
+    const RecS32 r1 = rec[1];
+    const Slots<NS> sl = slots_smooth<NS>(r1, hb, lane, G);
+    const float rr1 = rcp_approx(1.0f + r1.d0);
+    float rl[NS];
+#pragma unroll
+    for (int q = 0; q < NS; ++q) rl[q] = rcp_approx(1.0f + sl.b[q]);
+#pragma unroll
+    for (int j = 0; j < NA; ++j) {
+      float t = fmaf(r1.jd1, u[j], r1.jd0);
+      float rr = rr1;
+#pragma unroll
+      for (int q = 0; q < NS; ++q) {
+        const bool p = sl.j[q] == j;
+        t = p ? t + sl.a[q] : t;
+        rr = p ? rl[q] : rr;
+      }
+      const float pre = (s1[j] + t) * rr;
+      if (pre1) pre1[j * 32] = pre;
+      s1[j] = fmaxf(pre, 0.0f);
+    }
+    x1 = (x1 + fmaf(m2, r1.jd1, m1 * r1.jd0)) * rr1;
+    if (pre1) pre1[NA * 32] = x1;
+  }
+
+  // forward over samples [n0, n1) (n0 >= 2) with (sa, sb) = (I_{n0-2}, I_{n0-1});
+  // on return (sa, sb) = (I_{n1-2}, I_{n1-1}).  Stores the pre-values of
+  // samples n >= store_from at pre + n * NB * 32 (pre is indexed by absolute
+  // sample number; only stored samples are touched).
+  static __device__ __forceinline__ void run(const RecS32* rec, int n0, int n1,
+                                             const float (&u)[NA], float (&sa)[NA],
+                                             float (&sb)[NA], int hb, int lane, const VGrid& G,
+                                             float& xa, float& xb, float m1, float m2,
+                                             float* pre, int store_from) {
+    int n = n0;
+    for (; n + 1 < n1; n += 2) {
+      step(rec[n], u, sa, sb, hb, lane, G, xa, xb, m1, m2, pre + (long long)n * NB * 32,
+           n >= store_from);
+      step(rec[n + 1], u, sb, sa, hb, lane, G, xb, xa, m1, m2,
+           pre + (long long)(n + 1) * NB * 32, n + 1 >= store_from);
+    }
+    if (n < n1) {
+      step(rec[n], u, sa, sb, hb, lane, G, xa, xb, m1, m2, pre + (long long)n * NB * 32,
+           n >= store_from);
+      // roles: (sa, sb) = (I_n, I_{n-1}) -> swap to (I_{n-1}, I_n)
+#pragma unroll
+      for (int j = 0; j < NA; ++j) {
+        const float t = sa[j];
+        sa[j] = sb[j];
+        sb[j] = t;
+      }
+      const float t = xa;
+      xa = xb;
+      xb = t;
+    }
+  }
+
+  // Adjoint of one BDF2 step (sample n >= 2).  On entry lam_n = lambda_n
+  // (complete) and lam_m = the part of lambda_{n-1} from step n+1; on return
+  // lam_n = lambda_{n-1} (complete) and lam_m = -q, the part of lambda_{n-2}
+  // from step n.
+  static __device__ __forceinline__ void rstep(const RecS32& r, const float (&u)[NA],
+                                               float (&lam_n)[NA], float (&lam_m)[NA],
+                                               const float* pre, int hb, int lane, const VGrid& G,
+                                               float& xl_n, float& xl_m, float xpre, float m1,
+                                               float m2, float* part) {
+    const Slots<NS> sl = slots_smooth<NS>(r, hb, lane, G);
+    const float rd0 = rcp_approx(r.d0);
+    float rl[NS], qs[NS], ds[NS];
+#pragma unroll
+    for (int q = 0; q < NS; ++q) {
+      rl[q] = rcp_approx(sl.b[q]);
+      qs[q] = 0.0f;
+      ds[q] = 0.0f;
+    }
+    const float b0x2 = rec_bk0x2(r), b1x2 = rec_bk1x2(r);
+    float gad = 0.0f;
+#pragma unroll
+    for (int j = 0; j < NA; ++j) {
+      float rr = rd0;
+#pragma unroll
+      for (int q = 0; q < NS; ++q) rr = (sl.j[q] == j) ? rl[q] : rr;
+      const float p = pre[j * 32];
+      const float mu = (p >= 0.0f) ? lam_n[j] : 0.0f;
+      const float q = mu * rr;
+      const float dd = -q * p;                    // d loss / d (3 + 2h alpha)
+      gad = fmaf(q, fmaf(b1x2, u[j], b0x2), fmaf(2.0f, dd, gad));
+#pragma unroll
+      for (int s = 0; s < NS; ++s) {
+        const bool ps = sl.j[s] == j;
+        qs[s] = ps ? q : qs[s];
+        ds[s] = ps ? dd : ds[s];
+      }
+      lam_n[j] = fmaf(4.0f, q, lam_m[j]);
+      lam_m[j] = -q;
+    }
+    // basis recurrences (lanes 0..2): linear, sources m1 jd0 + m2 jd1
+    {
+      const float q = xl_n * rd0;
+      const float dd = -q * xpre;
+      gad = fmaf(q, fmaf(m2, b1x2, m1 * b0x2), fmaf(2.0f, dd, gad));
+      xl_n = fmaf(4.0f, q, xl_m);
+      xl_m = -q;
+    }
+    part[0] += gad;
+    line_partials(r, sl, qs, ds, lane, G, part);
+  }
+
+  // line partials of the NS slots: 2h j_L, 2h alpha_L, v_los, b
+  static __device__ __forceinline__ void line_partials(const RecS32& r, const Slots<NS>& sl,
+                                                       const float* qs, const float* ds, int lane,
+                                                       const VGrid& G, float* part) {
+    const int glo = win_lo(r.win);
+    const int g0 = glo + ((lane - glo) & 31);
+    const float ib2 = -r.nib2 * 0.69314718055994531f;   // 1 / b^2
+#pragma unroll
+    for (int q = 0; q < NS; ++q) {
+      if (sl.j[q] < 0) continue;
+      const float dv = vel_offset(G, g0 + 32 * q, r.gv, r.vr);   // u - v
+      const float e = ex2_approx(dv * r.nib2 * dv);
+      part[1] = fmaf(qs[q], e, part[1]);
+      part[2] = fmaf(ds[q], e, part[2]);
+      const float de = fmaf(r.jl2, qs[q], r.al2 * ds[q]) * e;
+      // de/dv = e 2 (u - v) / b^2 ; de/db = e 2 (u - v)^2 / b^3
+      const float t = 2.0f * dv * ib2 * de;
+      part[3] += t;
+      part[4] = fmaf(t * dv, sqrtf(ib2), part[4]);
+    }
+  }
+
+  // Adjoint of the trapezoidal step (sample 1) and of sample 0's coefficients.
+  static __device__ __forceinline__ void rstart(const RecS32* rec, const float (&u)[NA],
+                                                const float (&bg)[NA], const float (&lam1)[NA],
+                                                const float* pre1, int hb, int lane,
+                                                const VGrid& G, float xl1, float xpre1, float m0,
+                                                float m1, float m2, float* part0, float* part1) {
+    const RecS32 r0 = rec[0], r1 = rec[1];
+    const Slots<NS> sl0 = slots_smooth<NS>(r0, hb, lane, G);
+    const Slots<NS> sl1 = slots_smooth<NS>(r1, hb, lane, G);
+    const float rr1 = rcp_approx(1.0f + r1.d0);
+    float rl[NS], q0s[NS], d0s[NS], q1s[NS], d1s[NS];
+#pragma unroll
+    for (int q = 0; q < NS; ++q) {
+      rl[q] = rcp_approx(1.0f + sl1.b[q]);
+      q0s[q] = d0s[q] = q1s[q] = d1s[q] = 0.0f;
+    }
+    float gad0 = 0.0f, gad1 = 0.0f;
+    const float a0 = rec_bk0x2(r0), a1 = rec_bk1x2(r0);
+    const float c0 = rec_bk0x2(r1), c1 = rec_bk1x2(r1);
+#pragma unroll
+    for (int j = 0; j < NA; ++j) {
+      float rr = rr1;
+#pragma unroll
+      for (int q = 0; q < NS; ++q) rr = (sl1.j[q] == j) ? rl[q] : rr;
+      const float p = pre1[j * 32];
+      const float mu = (p >= 0.0f) ? lam1[j] : 0.0f;
+      const float q = mu * rr;
+      // pre_1 = (jt_0 + (7 - d_0) I_0 + jt_1) / (1 + d_1)
+      const float dd1 = -q * p;
+      const float dd0 = -q * bg[j];
+      gad1 = fmaf(q, fmaf(c1, u[j], c0), fmaf(2.0f, dd1, gad1));
+      gad0 = fmaf(q, fmaf(a1, u[j], a0), fmaf(2.0f, dd0, gad0));
+#pragma unroll
+      for (int s = 0; s < NS; ++s) {
+        q0s[s] = (sl0.j[s] == j) ? q : q0s[s];
+        d0s[s] = (sl0.j[s] == j) ? dd0 : d0s[s];
+        q1s[s] = (sl1.j[s] == j) ? q : q1s[s];
+        d1s[s] = (sl1.j[s] == j) ? dd1 : d1s[s];
+      }
+    }
+    {
+      const float q = xl1 * rr1;
+      gad1 = fmaf(q, fmaf(m2, c1, m1 * c0), fmaf(2.0f, -q * xpre1, gad1));
+      gad0 = fmaf(q, fmaf(m2, a1, m1 * a0), fmaf(2.0f, -q * m0, gad0));
+    }
+    part0[0] += gad0;
+    part1[0] += gad1;
+    line_partials(r0, sl0, q0s, d0s, lane, G, part0);
+    line_partials(r1, sl1, q1s, d1s, lane, G, part1);
+  }
+};
+
+// d Z / d T of the rigid rotor together with Z (float), same branches as
+// partition(): expansion above 200 K, ratio recurrence below.
+__device__ inline void partition_dz(const PhysF& P, float T, float* Z, float* dZ) {
+  const float r = P.theta_rot / T;
+  if (r < 0.0132f) {
+    const float z = 1.0f / r + (1.0f / 3.0f) + r * (1.0f / 15.0f + r * (4.0f / 315.0f + r * (1.0f / 315.0f)));
+    // dZ/dT = (dZ/dr) (-r/T)
+    const float dzdr = -1.0f / (r * r) + 1.0f / 15.0f + r * (8.0f / 315.0f + r * (3.0f / 315.0f));
+    *Z = z;
+    *dZ = dzdr * (-r / T);
+    return;
+  }
+  const float q2 = expf(-2.0f * r);
+  float t = 1.0f, m = q2, z = 1.0f, ze = 0.0f;
+  for (int J = 1; J < 400; ++J) {
+    t *= m;
+    m *= q2;
+    const float term = (2 * J + 1) * t;
+    z += term;
+    ze += term * (float)(J * (J + 1));
+    if (term < 3e-9f * z) break;
+  }
+  *Z = z;
+  *dZ = ze * r / T;   // sum (2J+1) (theta J(J+1) / T^2) t_J
+}
+
+// Chain rule from the record partials (h alpha_D, 2h j_L, 2h alpha_L, v, b)
+// to (n_H2, T_gas, v_los) of one sample.
+__device__ __forceinline__ void chain(const PhysF& P, const float raw[5], float h,
+                                      const float* G5, float* gn, float* gt, float* gv) {
+  const float n = raw[0], T = raw[1], x = raw[4];
+  const float b = sqrtf(P.c_th * T + P.two_sig2);
+  float g_n = G5[0] * P.cad * h;
+  float g_t = 0.0f;
+  if (T > 0.0f && T <= P.t_inf) {
+    float Z, dZ;
+    partition_dz(P, T, &Z, &dZ);
+    const float eu = expf(-P.e_u / T), el = expf(-P.e_l / T);
+    const float em = expf(-P.T0 / T);
+    const float st = -expm1f(-P.T0 / T);
+    const float base = x * h / (Z * b);              // per unit n
+    const float jl2_n = 2.0f * P.cj * base * eu;    // d(2h j_L)/dn
+    const float al2_n = 2.0f * P.ca * base * el * st;
+    g_n = fmaf(G5[1], jl2_n, fmaf(G5[2], al2_n, g_n));
+    const float jl2 = jl2_n * n, al2 = al2_n * n;
+    const float db = P.c_th / (2.0f * b);
+    const float common = -dZ / Z - db / b;
+    const float T2 = T * T;
+    const float dlnj = P.e_u / T2 + common;
+    const float dlna = P.e_l / T2 - (P.T0 / T2) * em / st + common;
+    g_t = fmaf(G5[1], jl2 * dlnj, fmaf(G5[2], al2 * dlna, G5[4] * db));
+  } else {
+    g_t = G5[4] * (T > 0.0f ? P.c_th / (2.0f * b) : 0.0f);
+  }
+  *gn = g_n;
+  *gt = g_t;
+  *gv = G5[3];
+}
+
+// Fine-channel cotangent: sum over the channels holding fine index g of the
+// Simpson weight times the channel cotangent.
+__device__ __forceinline__ float fine_cotangent(int g, int f, int cwn, const float* lamc) {
+  const int two_f = 2 * f;
+  float acc = 0.0f;
+  const int c = g / two_f;
+  const int m = g - c * two_f;
+  const float w = (m == 0) ? 1.0f : ((m & 1) ? 4.0f : 2.0f);
+  if (c < cwn) acc = w * lamc[c];
+  if (m == 0 && c > 0) acc += lamc[c - 1];     // upper edge (weight 1) of channel c - 1
+  return acc / (float)(6 * f);
+}
+
+// Reverse sweep of one ray with NA explicit hull blocks and NS line slots.
+template <int NA, int NS, int ST>
+__device__ __noinline__ void adj_ray(const JobDev& J, const PhysF& P, const AdjArgs& A,
+                                     const RecS32* rec, int K, int hb, int lane, const VGrid& G,
+                                     int nfw, const float* lamf, float lx, float* pbuf,
+                                     float* scr, int px, int py) {
+  using AD = Adj<NA, NS>;
+  constexpr int NB = NA + 1;
+  float u[NA], bg[NA];
+#pragma unroll
+  for (int j = 0; j < NA; ++j) {
+    const int g = min(32 * (hb + j) + lane, nfw - 1);
+    u[j] = fmaf((float)g, G.dvf_hi, G.ufw_hi);
+    bg[j] = planck_k(P, P.t_bg, u[j]);
+  }
+  const float m0 = (lane == 0) ? 1.0f : 0.0f;
+  const float m1 = (lane == 1) ? 1.0f : 0.0f;
+  const float m2 = (lane == 2) ? 1.0f : 0.0f;
+  const int nseg = (K + kSeg - 1) / kSeg;
+  float* ck = scr;                                        // [nseg][2][NB][32]
+  float* pre = scr + (long long)nseg * 2 * NB * 32;       // [kSub][NB][32]
+  float sa[NA], sb[NA], xa, xb;
+
+  // ---- forward with a checkpoint (I_{32s-2}, I_{32s-1}) at every segment s >= 1
+  AD::start(rec, u, bg, sa, sb, hb, lane, G, xa, xb, m0, m1, m2, nullptr);
+  {
+    int n = 2;
+    for (int s = 1; s < nseg; ++s) {
+      const int ne = s * kSeg;
+      if (n < ne) AD::run(rec, n, ne, u, sa, sb, hb, lane, G, xa, xb, m1, m2, pre, 1 << 30);
+      n = ne;
+      float* c = ck + (long long)s * 2 * NB * 32;
+#pragma unroll
+      for (int j = 0; j < NA; ++j) {
+        c[j * 32 + lane] = sa[j];
+        c[NB * 32 + j * 32 + lane] = sb[j];
+      }
+      c[NA * 32 + lane] = xa;
+      c[NB * 32 + NA * 32 + lane] = xb;
+    }
+  }
+
+  // ---- reverse sweep
+  float ln[NA], lm[NA];
+#pragma unroll
+  for (int j = 0; j < NA; ++j) {
+    const int g = 32 * (hb + j) + lane;
+    ln[j] = (g < nfw) ? lamf[g] : 0.0f;
+    lm[j] = 0.0f;
+  }
+  float xln = lx, xlm = 0.0f;
+  for (int s = nseg - 1; s >= 0; --s) {
+    const int seg_lo = s * kSeg;
+    const int seg_hi = min(seg_lo + kSeg, K);
+    for (int sub_hi = seg_hi; sub_hi > seg_lo;) {
+      const int sub_lo = max(seg_lo, sub_hi - kSub);
+      // recompute the forward of the segment up to sub_hi, keeping the
+      // pre-ReLU values of samples [sub_lo, sub_hi)
+      float* pre_base = pre - (long long)sub_lo * NB * 32;   // indexed by absolute n
+      if (s == 0) {
+        AD::start(rec, u, bg, sa, sb, hb, lane, G, xa, xb, m0, m1, m2,
+                  (sub_lo <= 1 && 1 < sub_hi) ? pre_base + 1 * NB * 32 + lane : nullptr);
+        if (sub_hi > 2)
+          AD::run(rec, 2, sub_hi, u, sa, sb, hb, lane, G, xa, xb, m1, m2, pre_base + lane,
+                  max(sub_lo, 2));
+      } else {
+        const float* c = ck + (long long)s * 2 * NB * 32;
+#pragma unroll
+        for (int j = 0; j < NA; ++j) {
+          sa[j] = c[j * 32 + lane];
+          sb[j] = c[NB * 32 + j * 32 + lane];
+        }
+        xa = c[NA * 32 + lane];
+        xb = c[NB * 32 + NA * 32 + lane];
+        AD::run(rec, seg_lo, sub_hi, u, sa, sb, hb, lane, G, xa, xb, m1, m2, pre_base + lane,
+                sub_lo);
+      }
+      // reverse steps of the sub-segment
+      for (int n = sub_hi - 1; n >= max(sub_lo, 2); --n) {
+        float part[kNP] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+        const float* pn = pre_base + (long long)n * NB * 32 + lane;
+        AD::rstep(rec[n], u, ln, lm, pn, hb, lane, G, xln, xlm, pn[NA * 32], m1, m2, part);
+        float* row = pbuf + (n - sub_lo) * kNP * kPStride + lane;
+#pragma unroll
+        for (int q = 0; q < kNP; ++q) row[q * kPStride] = part[q];
+      }
+      if (sub_lo == 0) {
+        float p0[kNP] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+        float p1[kNP] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+        const float* pn = pre_base + 1 * NB * 32 + lane;
+        AD::rstart(rec, u, bg, ln, pn, hb, lane, G, xln, pn[NA * 32], m0, m1, m2, p0, p1);
+#pragma unroll
+        for (int q = 0; q < kNP; ++q) {
+          pbuf[0 * kNP * kPStride + q * kPStride + lane] = p0[q];
+          pbuf[1 * kNP * kPStride + q * kPStride + lane] = p1[q];
+        }
+      }
+      __syncwarp();
+      // lane l reduces the partials of sample sub_lo + l and writes its gradients
+      const int nsub = sub_hi - sub_lo;
+      if (lane < nsub) {
+        float g5[kNP];
+#pragma unroll
+        for (int q = 0; q < kNP; ++q) {
+          const float* rowq = pbuf + lane * kNP * kPStride + q * kPStride;
+          float acc = 0.0f;
+#pragma unroll 8
+          for (int m = 0; m < 32; ++m) acc += rowq[m];
+          g5[q] = acc;
+        }
+        const int n = sub_lo + lane;
+        float raw[5];
+        RayPos rp;
+        sample_raw<ST>(J, rp, px, py, n, raw);
+        float gn, gt, gv;
+        chain(P, raw, (float)J.dx, g5, &gn, &gt, &gv);
+        const long long idx = ((long long)n * J.ny + py) * J.nx + px;
+        A.grad[0][idx] = gn;
+        A.grad[1][idx] = gt;
+        A.grad[2][idx] = gv;
+      }
+      __syncwarp();
+      sub_hi = sub_lo;
+    }
+  }
+}
+
+template <int NI, int ST>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32, 1)
+adj_kernel(const __grid_constant__ JobTable tab, const PhysF PF, const AdjArgs A,
+           long long total_items, unsigned long long* queue, int per_warp, int fw_off,
+           int cw_off, int pb_off) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  unsigned char* wsm = smem + (size_t)warp * per_warp;
+  RecS32* rec = reinterpret_cast<RecS32*>(wsm);
+  float* lamf = reinterpret_cast<float*>(wsm + fw_off);   // fine cotangents
+  float* lamc = reinterpret_cast<float*>(wsm + cw_off);   // channel cotangents (T total)
+  float* pbuf = reinterpret_cast<float*>(wsm + pb_off);   // [kSub][kNP][kPStride]
+  const long long gw = (long long)blockIdx.x * kWarpsPerBlock + warp;
+  float* scr = A.scratch + gw * A.scratch_per_warp;
+  const JobDev& J = tab.j[0];
+
+  for (;;) {
+    unsigned long long t = 0;
+    if (lane == 0) t = atomicAdd(queue, 1ull);
+    const long long item = (long long)__shfl_sync(0xffffffffu, t, 0);
+    if (item >= total_items) break;
+    const int px = (int)(item % J.npx), py = (int)(item / J.npx);
+    const int cwn = J.nchan;      // one window
+    const int f = J.f;
+    const int nfw = 2 * f * cwn + 1;
+    const int nblk = (nfw + 31) >> 5;
+    const int K = J.nz;
+    const float h = (float)J.dx;
+    VGrid G;
+    G.ufw_hi = (float)J.ufirst;
+    G.ufw_lo = (float)(J.ufirst - (double)G.ufw_hi);
+    G.dvf_hi = (float)J.dvf;
+    G.dvf_lo = (float)(J.dvf - (double)G.dvf_hi);
+
+    // ---- records
+    RayPos rp;
+    int hlo = 1 << 20, hhi = -1, wmax = 0;
+    float admax = 0.0f;
+    for (int k0 = 0; k0 < K; k0 += 32) {
+      const int k = k0 + lane;
+      if (k < K) {
+        float raw[5];
+        sample_raw<ST>(J, rp, px, py, k, raw);
+        const float ad = make_record<M_SMOOTH>(PF, raw, h, G, nfw, &rec[k]);
+        float bk0, bk1;
+        dust_source_lin(PF, raw[2], &bk0, &bk1);
+        rec[k].pad[0] = 2.0f * bk0;
+        rec[k].pad[1] = 2.0f * bk1;
+        const int w = rec[k].win;
+        const int lo = win_lo(w), hi = win_hi(w);
+        if (lo <= hi) {
+          hlo = min(hlo, lo >> 5);
+          hhi = max(hhi, hi >> 5);
+          wmax = max(wmax, hi - lo + 1);
+        }
+        admax = fmaxf(admax, ad);
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      hlo = min(hlo, __shfl_xor_sync(0xffffffffu, hlo, o));
+      hhi = max(hhi, __shfl_xor_sync(0xffffffffu, hhi, o));
+      wmax = max(wmax, __shfl_xor_sync(0xffffffffu, wmax, o));
+      admax = fmaxf(admax, __shfl_xor_sync(0xffffffffu, admax, o));
+    }
+    // ---- channel cotangents of [T] and [C] at the channel centres
+    const long long plane = (long long)J.npx * J.npy;
+    const long long pix = (long long)py * J.npx + px;
+    float lx0 = 0.0f, lx1 = 0.0f, lx2 = 0.0f;   // basis cotangents (lane partials)
+    for (int c = lane; c < cwn; c += 32) {
+      const long long o = (long long)c * plane + pix;
+      const float gT = A.cot[0] ? A.cot[0][o] : 0.0f;
+      const float gC = A.cot[1] ? A.cot[1][o] : 0.0f;
+      const float gD = A.cot[2] ? A.cot[2][o] : 0.0f;
+      const float gL = A.cot[3] ? A.cot[3][o] : 0.0f;
+      const float uc = (float)J.v0 + ((float)c + 0.5f) * (float)J.dv;
+      float s = PF.out_scale;
+      if (PF.units == IRT_UNITS_TRJ) {
+        const float y = 1.0f - uc * PF.inv_c_kms;
+        s = s / (y * y);
+      }
+      lamc[c] = s * (gT + gL);
+      const float lc = s * (gC - gL + gD);
+      const float ib = planck_k(PF, PF.t_bg, uc);
+      lx0 = fmaf(lc, ib, lx0);
+      lx1 += lc;
+      lx2 = fmaf(lc, uc, lx2);
+    }
+    __syncwarp();
+    const int ns = (wmax <= 32) ? 1 : ((wmax <= 64) ? 2 : 3);
+    const bool none = hhi < hlo;
+    int nb = fast_bucket(none ? 1 : hhi - hlo + 1, ns);
+    const int hb = none ? 0 : min(hlo, max(nblk - nb, 0));
+    bool ok = (ns <= 2) && admax <= 0.5f && nb <= NI && K >= 2;
+    // fine cotangents; velocities outside the explicit blocks go to the basis
+    for (int g = lane; g < nfw; g += 32) {
+      const float lf = fine_cotangent(g, f, cwn, lamc);
+      const int blk = g >> 5;
+      if (blk < hb || blk >= hb + nb) {
+        const float u = fmaf((float)g, G.dvf_hi, G.ufw_hi);
+        lx0 = fmaf(lf, planck_k(PF, PF.t_bg, u), lx0);
+        lx1 += lf;
+        lx2 = fmaf(lf, u, lx2);
+      }
+      lamf[g] = lf;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      lx0 += __shfl_xor_sync(0xffffffffu, lx0, o);
+      lx1 += __shfl_xor_sync(0xffffffffu, lx1, o);
+      lx2 += __shfl_xor_sync(0xffffffffu, lx2, o);
+    }
+    __syncwarp();
+
+    if (!ok) {
+      // K <= 1: the output is the background, no gradient; otherwise the ray
+      // is outside what this kernel integrates (NaN marks it)
+      const float val = (K <= 1) ? 0.0f : __int_as_float(0x7fc00000);
+      for (int k = lane; k < K; k += 32) {
+        const long long idx = ((long long)k * J.ny + py) * J.nx + px;
+        A.grad[0][idx] = val;
+        A.grad[1][idx] = val;
+        A.grad[2][idx] = val;
+      }
+      __syncwarp();
+      continue;
+    }
+    const float lx = (lane == 0) ? lx0 : ((lane == 1) ? lx1 : ((lane == 2) ? lx2 : 0.0f));
+
+#define IRT_ADJ(NA_)                                                                         \
+  case NA_:                                                                                  \
+    if constexpr (NA_ <= NI) {                                                               \
+      if (ns == 1)                                                                           \
+        adj_ray<NA_, 1, ST>(J, PF, A, rec, K, hb, lane, G, nfw, lamf, lx, pbuf, scr, px, py); \
+      else                                                                                   \
+        adj_ray<NA_, 2, ST>(J, PF, A, rec, K, hb, lane, G, nfw, lamf, lx, pbuf, scr, px, py); \
+    }                                                                                        \
+    break;
+    switch (nb) {
+      IRT_ADJ(2) IRT_ADJ(4) IRT_ADJ(6) IRT_ADJ(8) IRT_ADJ(10) IRT_ADJ(12) IRT_ADJ(14)
+      IRT_ADJ(17) IRT_ADJ(20) IRT_ADJ(24) IRT_ADJ(28) IRT_ADJ(33)
+      default: break;
+    }
+#undef IRT_ADJ
+    __syncwarp();
+  }
+}
+
+}  // namespace dev
+
+// Host launcher: smooth integration, float arithmetic, one window.
+int launch_adjoint(int store, int ni, const JobTable& tab, const PhysF& PF, const AdjArgs& A,
+                   long long total_items, unsigned long long* queue, int blocks, int kmax,
+                   int nfw, int nchan, cudaStream_t stream, int* per_warp_smem) {
+  const int rec_bytes = (int)sizeof(dev::RecS32) * kmax;
+  const int fw_off = (rec_bytes + 15) & ~15;
+  const int cw_off = (fw_off + 4 * nfw + 15) & ~15;
+  const int pb_off = (cw_off + 4 * nchan + 15) & ~15;
+  const int per_warp = (pb_off + 4 * dev::kSub * dev::kNP * dev::kPStride + 15) & ~15;
+  if (per_warp_smem) *per_warp_smem = per_warp;
+  const size_t smem = (size_t)per_warp * kWarpsPerBlock;
+#define IRT_LAUNCH(NI_, ST_)                                                                  \
+  if (ni == NI_ && store == ST_) {                                                            \
+    auto kern = dev::adj_kernel<NI_, ST_>;                                                    \
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,   \
+                                         (int)smem);                                          \
+    if (e != cudaSuccess) return (int)e;                                                      \
+    if (blocks <= 0) return 0;                                                                \
+    kern<<<blocks, kWarpsPerBlock * 32, smem, stream>>>(tab, PF, A, total_items, queue,       \
+                                                        per_warp, fw_off, cw_off, pb_off);    \
+    return (int)cudaGetLastError();                                                           \
+  }
+  IRT_LAUNCH(9, ST_F32) IRT_LAUNCH(17, ST_F32) IRT_LAUNCH(33, ST_F32)
+  IRT_LAUNCH(9, ST_H16) IRT_LAUNCH(17, ST_H16) IRT_LAUNCH(33, ST_H16)
+#undef IRT_LAUNCH
+  return (int)cudaErrorInvalidValue;
+}
+
+// Blocks per SM the adjoint kernel reaches with the given shared memory.
+int adjoint_blocks_per_sm(int store, int ni, size_t smem) {
+  int per_sm = 0;
+#define IRT_OCC(NI_, ST_)                                                                     \
+  if (ni == NI_ && store == ST_) {                                                            \
+    cudaFuncSetAttribute(dev::adj_kernel<NI_, ST_>,                                           \
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);             \
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dev::adj_kernel<NI_, ST_>,         \
+                                                  kWarpsPerBlock * 32, smem);                 \
+    return per_sm;                                                                            \
+  }
+  IRT_OCC(9, ST_F32) IRT_OCC(17, ST_F32) IRT_OCC(33, ST_F32)
+  IRT_OCC(9, ST_H16) IRT_OCC(17, ST_H16) IRT_OCC(33, ST_H16)
+#undef IRT_OCC
+  return 0;
+}
+
+}  // namespace irt

@@ -28,6 +28,10 @@ int dispatch_fwd_f32_kahan(int store, int ni, const JobTable& jobs, int njobs, c
                            long long total, unsigned long long* queue, int grid_blocks, int kmax,
                            int fwmax, int cwmax, unsigned flags, unsigned long long* stats,
                            cudaStream_t s);
+int launch_adjoint(int store, int ni, const JobTable& tab, const PhysF& PF, const AdjArgs& A,
+                   long long total_items, unsigned long long* queue, int blocks, int kmax,
+                   int nfw, int nchan, cudaStream_t stream, int* per_warp_smem);
+int adjoint_blocks_per_sm(int store, int ni, size_t smem);
 int dispatch_fwd_f64(int mode, int store, int ni, const JobTable& jobs, int njobs,
                      const PhysParams& P, const PhysF& PF, long long total, unsigned long long* queue,
                      int grid_blocks, int kmax, int fwmax, int cwmax, unsigned flags,
@@ -77,6 +81,8 @@ struct irt_grid {
   size_t cell_bytes;
   unsigned long long* ctl;   // device control words (work-queue counter)
   int device;
+  float* adj_scratch;        // adjoint checkpoints (grown on demand)
+  size_t adj_bytes;
 };
 
 using namespace irt;
@@ -132,6 +138,8 @@ irt_status irt_create_grid(const irt_grid_desc* desc, const irt_fields* fields,
   for (int q = 0; q < 5; ++q) g->scale[q] = scale[q];
   g->cell_bytes = cb * (size_t)ncell;
   g->ctl = nullptr;
+  g->adj_scratch = nullptr;
+  g->adj_bytes = 0;
   cudaGetDevice(&g->device);
   if (cudaMalloc(&g->cells, g->cell_bytes) != cudaSuccess) {
     cudaGetLastError();
@@ -179,6 +187,7 @@ irt_status irt_destroy(irt_grid* g) {
   if (!g) return IRT_OK;
   cudaFree(g->cells);
   cudaFree(g->ctl);
+  if (g->adj_scratch) cudaFree(g->adj_scratch);
   delete g;
   return IRT_OK;
 }
@@ -477,9 +486,87 @@ extern "C" irt_status irt_adjoint_ppv(const irt_job* job, const irt_line* line,
                                       const irt_cubes* cotangent, float* grad_n_h2,
                                       float* grad_t_gas, float* grad_v_los, void* cuda_stream) {
   g_err.clear();
-  (void)job; (void)line; (void)dust; (void)opts; (void)cotangent; (void)grad_n_h2;
-  (void)grad_t_gas; (void)grad_v_los; (void)cuda_stream;
-  return fail(IRT_EUNSUPPORTED, "irt_adjoint_ppv: not built yet");
+  if (!job) return fail(IRT_EINVAL, "irt_adjoint_ppv: NULL job");
+  if (!grad_n_h2 || !grad_t_gas || !grad_v_los)
+    return fail(IRT_EINVAL, "irt_adjoint_ppv: NULL gradient pointer");
+  irt_status st = check_line(line, dust, opts);
+  if (st) return st;
+  if (!job->grid) return fail(IRT_EINVAL, "irt_adjoint_ppv: job without grid");
+  // the cube pointers of the job are not written by the adjoint
+  irt_job jb = *job;
+  jb.out.T = grad_n_h2;   // satisfies the "some output" check; never written
+  st = check_job(jb, opts->precision);
+  if (st) return st;
+  if (opts->precision != IRT_PREC_F32)
+    return fail(IRT_EUNSUPPORTED, "irt_adjoint_ppv: float precision only");
+  if (opts->integration != IRT_SMOOTH)
+    return fail(IRT_EUNSUPPORTED, "irt_adjoint_ppv: smooth integration only");
+  if (jb.view.trilinear != 0) return fail(IRT_EUNSUPPORTED, "irt_adjoint_ppv: z view only");
+  if (jb.vaxis.subsample_f < 1) return fail(IRT_EUNSUPPORTED, "irt_adjoint_ppv: needs f >= 1");
+  irt_grid* g = jb.grid;
+  if (g->store == ST_F64)
+    return fail(IRT_EUNSUPPORTED, "irt_adjoint_ppv: float or 16-bit field storage only");
+  const Plan p = plan_job(jb, IRT_PREC_F32, 0);
+  if (p.nwin != 1)
+    return fail(IRT_EUNSUPPORTED,
+                "irt_adjoint_ppv: %d channels at f = %d need %d channel windows (one supported)",
+                jb.vaxis.nchan, jb.vaxis.subsample_f, p.nwin);
+  const PhysParams P = fold_constants(line, dust, opts);
+  const PhysF PF = to_float(P);
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+
+  // shared memory per warp and persistent grid size
+  int per_warp = 0;
+  JobTable tab;
+  std::memset(&tab, 0, sizeof tab);
+  tab.j[0] = make_jobdev(jb, p);
+  AdjArgs A;
+  std::memset(&A, 0, sizeof A);
+  if (cotangent) {
+    A.cot[0] = (const float*)cotangent->T;
+    A.cot[1] = (const float*)cotangent->C;
+    A.cot[2] = (const float*)cotangent->D;
+    A.cot[3] = (const float*)cotangent->L;
+    A.cot[4] = (const float*)cotangent->B;
+  }
+  A.grad[0] = grad_n_h2;
+  A.grad[1] = grad_t_gas;
+  A.grad[2] = grad_v_los;
+  int e = launch_adjoint(g->store, p.ni, tab, PF, A, 0, nullptr, 0, p.kmax, p.nfw,
+                         jb.vaxis.nchan, s, &per_warp);
+  if (e) return cuda_fail(e, "irt_adjoint_ppv: kernel attributes");
+  const size_t smem = (size_t)per_warp * kWarpsPerBlock;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int per_sm = std::max(1, adjoint_blocks_per_sm(g->store, p.ni, smem));
+  const int blocks = per_sm * sms;
+  const int nseg = (p.kmax + kAdjSeg - 1) / kAdjSeg;
+  const long long per_warp_floats = (long long)(2 * nseg + kAdjSub) * (p.ni + 1) * 32;
+  const size_t need = (size_t)blocks * kWarpsPerBlock * (size_t)per_warp_floats * sizeof(float);
+  if (g->adj_bytes < need) {
+    if (g->adj_scratch) {
+      cudaStreamSynchronize(s);
+      cudaFree(g->adj_scratch);
+      g->adj_scratch = nullptr;
+      g->adj_bytes = 0;
+    }
+    if (cudaMalloc((void**)&g->adj_scratch, need) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(IRT_ENOMEM, "irt_adjoint_ppv: cannot allocate %zu bytes of checkpoints", need);
+    }
+    g->adj_bytes = need;
+  }
+  A.scratch = g->adj_scratch;
+  A.scratch_per_warp = per_warp_floats;
+  cudaError_t ce = cudaMemsetAsync(g->ctl, 0, sizeof(unsigned long long), s);
+  if (ce != cudaSuccess) return cuda_fail(ce, "irt_adjoint_ppv: queue reset");
+  const long long total = (long long)jb.view.npx * jb.view.npy;
+  e = launch_adjoint(g->store, p.ni, tab, PF, A, total, g->ctl, blocks, p.kmax, p.nfw,
+                     jb.vaxis.nchan, s, nullptr);
+  ++g_launches;
+  if (e) return cuda_fail(e, "irt_adjoint_ppv: adjoint kernel");
+  return IRT_OK;
 }
 
 // ---------------------------------------------------------------------------

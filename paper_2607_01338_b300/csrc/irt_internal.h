@@ -77,6 +77,17 @@ struct JobDev {
 constexpr int kWarpsPerBlock = 4;
 constexpr int kMaxJobs = 64;
 
+// Adjoint: checkpoint spacing and stored sub-segment (samples).
+constexpr int kAdjSeg = 32;
+constexpr int kAdjSub = 16;
+
+struct AdjArgs {
+  const float* cot[5];          // cotangent cubes T, C, D, L, B (NULL = 0)
+  float* grad[3];               // n_H2, T_gas, v_los
+  float* scratch;               // per-warp scratch
+  long long scratch_per_warp;   // floats
+};
+
 // Job table passed to the kernels by value (__grid_constant__ parameter).
 struct JobTable {
   JobDev j[kMaxJobs];

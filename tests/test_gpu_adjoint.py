@@ -1,0 +1,158 @@
+"""Adjoint (reverse sweep) of the CUDA path against the FP64 oracle:
+dual-number gradients on a 16^3 grid and FP64 central differences on 200
+random cells of the 128^3 workload, tolerance 1e-3 relative."""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+import oracle  # noqa: E402
+from synth import (DUST, LINE_13CO_21, FieldSet, VelocityAxis, View, make_fields,  # noqa: E402
+                   to_storage, workload)
+
+LINE = dict(LINE_13CO_21)
+PC = 3.0856775814913673e18
+GRAD_RTOL = 1e-3
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2607_01338_b300  # noqa: F401
+
+
+def _gpu_loss_grads(f32, dx, view, va, target_L, integration="smooth"):
+    """GPU forward + adjoint of Loss = mean((L - target)^2)."""
+    import paper_2607_01338_b300 as irt
+    ts = [torch.from_numpy(a).cuda() for a in f32.as_tuple()]
+    g = irt.Grid(*ts, dx)
+    cubes = irt.forward(g, view, va, LINE, DUST, integration=integration)
+    tgt = torch.from_numpy(target_L.astype(np.float32)).cuda()
+    L = cubes["L"]
+    gL = 2.0 * (L - tgt) / L.numel()
+    grads = irt.adjoint(g, view, va, LINE, DUST, {"L": gL}, integration=integration)
+    torch.cuda.synchronize()
+    loss = float(torch.mean((L.double() - tgt.double()) ** 2).item())
+    out = [x.double().cpu().numpy() for x in grads]
+    g.close()
+    return loss, out
+
+
+def _cmp(got, ref, rtol=GRAD_RTOL, floor=1e-3):
+    """Elementwise |got - ref| <= rtol |ref| + floor * max|ref|."""
+    allow = rtol * np.abs(ref) + floor * np.abs(ref).max()
+    return float((np.abs(got - ref) / allow).max())
+
+
+def crop_fields(fs, n, seed=0):
+    rng = np.random.default_rng(seed)
+    N = fs.n_h2.shape[0]
+    o = rng.integers(0, N - n + 1, 3)
+    sl = (slice(o[0], o[0] + n), slice(o[1], o[1] + n), slice(o[2], o[2] + n))
+    return FieldSet(*[np.ascontiguousarray(a[sl]) for a in fs.as_tuple()])
+
+
+def test_adjoint_matches_oracle_gradient_16cube():
+    """16^3 crop of the 128^3 adjoint workload (128 channels, f = 2)."""
+    w = workload(3, n=48)
+    fs = crop_fields(make_fields(48, w.seed), 16, seed=3)
+    tfs = crop_fields(make_fields(48, w.seed + 7), 16, seed=3)
+    f32, deq = to_storage(fs, np.float32)
+    t32, tdeq = to_storage(tfs, np.float32)
+    view = View(0.0, 0.0, 16, 16, w.cell_cm, 0)
+    va = w.vaxis
+    target = oracle.render_cube(tdeq.as_tuple(), w.cell_cm, LINE, DUST, view, va)["L"]
+    loss, (gn, gt, gv) = _gpu_loss_grads(f32, w.cell_cm, view, va, target)
+    oloss, on, ot, ov = oracle.loss_grad_zview(deq.as_tuple(), w.cell_cm, LINE, DUST, va, target)
+    assert loss == pytest.approx(oloss, rel=1e-4)
+    r = {k: _cmp(a, b) for k, a, b in (("n", gn, on), ("T", gt, ot), ("v", gv, ov))}
+    assert all(v <= 1.0 for v in r.values()), r
+
+
+def test_adjoint_matches_fp64_finite_differences_128cube():
+    """200 random cells of the 128^3 / 128-channel / f = 2 workload: GPU
+    adjoint against FP64 central differences of the oracle (ray-local:
+    a cell only changes its own z-view ray)."""
+    w = workload(3)
+    fs = make_fields(w.n, w.seed)
+    tfs = make_fields(w.n, w.seed + 7)
+    f32, deq = to_storage(fs, np.float32)
+    t32, tdeq = to_storage(tfs, np.float32)
+    view, va = w.views[0], w.vaxis
+    import paper_2607_01338_b300 as irt
+    tg = irt.Grid(*[torch.from_numpy(a).cuda() for a in t32.as_tuple()], w.cell_cm)
+    target = irt.forward(tg, view, va, LINE, DUST)["L"].double().cpu().numpy()
+    tg.close()
+    loss, (gn, gt, gv) = _gpu_loss_grads(f32, w.cell_cm, view, va, target)
+    nvox = target.size
+    rng = np.random.default_rng(11)
+    cells = rng.integers(0, w.n, (200, 3))
+    fields = [a.copy() for a in deq.as_tuple()]
+    worst = {}
+    for q, g, name in ((0, gn, "n"), (1, gt, "T"), (3, gv, "v")):
+        fd, got = [], []
+        for (z, y, x) in cells:
+            v0 = fields[q][z, y, x]
+            eps = 1e-6 * max(abs(v0), 1.0)
+            vals = []
+            for sgn in (1, -1):
+                fields[q][z, y, x] = v0 + sgn * eps
+                Lr = oracle.render(fields, w.cell_cm, LINE, DUST, view, va, [(x, y)])["L"][0]
+                vals.append(np.sum((Lr - target[:, y, x]) ** 2))
+            fields[q][z, y, x] = v0
+            fd.append((vals[0] - vals[1]) / (2 * eps) / nvox)
+            got.append(g[z, y, x])
+        worst[name] = _cmp(np.array(got), np.array(fd))
+    assert all(v <= 1.0 for v in worst.values()), worst
+
+
+def test_autograd_function_matches_adjoint():
+    import paper_2607_01338_b300 as irt
+    n = 12
+    fs = make_fields(n, 5)
+    f32, _ = to_storage(fs, np.float32)
+    dx = 0.1 * PC
+    view = View(0.0, 0.0, n, n, dx, 0)
+    va = VelocityAxis(48, -72.0, 3.0, 1)
+    ts = [torch.from_numpy(a).cuda() for a in f32.as_tuple()]
+    n_h2 = ts[0].clone().requires_grad_(True)
+    t_gas = ts[1].clone().requires_grad_(True)
+    v_los = ts[3].clone().requires_grad_(True)
+    cfg = irt.RenderConfig(dx, view, va, LINE, DUST)
+    T, C, D, L, B = irt.render_ppv(n_h2, t_gas, v_los, ts[2], ts[4], cfg)
+    loss = (L ** 2).mean() + 0.5 * T.mean() - 0.25 * (D * C).sum() / D.numel()
+    loss.backward()
+    g = irt.Grid(*ts, dx)
+    with torch.no_grad():
+        cot = dict(L=2 * L / L.numel(), T=torch.full_like(T, 0.5 / T.numel()),
+                   D=-0.25 * C / D.numel(), C=-0.25 * D / D.numel())
+    gn, gt, gv = irt.adjoint(g, view, va, LINE, DUST, cot)
+    torch.cuda.synchronize()
+    for a, b in ((n_h2.grad, gn), (t_gas.grad, gt), (v_los.grad, gv)):
+        assert torch.allclose(a, b, rtol=1e-5, atol=1e-6 * b.abs().max().item())
+    g.close()
+
+
+def test_adjoint_edge_cases_and_errors():
+    import paper_2607_01338_b300 as irt
+    dx = 0.1 * PC
+    # one sample per ray: the output is the background, all gradients vanish
+    fs = make_fields(6, 8)
+    arrs = [np.ascontiguousarray(a[:1].astype(np.float32)) for a in fs.as_tuple()]
+    g = irt.Grid(*[torch.from_numpy(a).cuda() for a in arrs], dx)
+    view = View(0.0, 0.0, 6, 6, dx, 0)
+    va = VelocityAxis(16, -16.0, 2.0, 1)
+    cot = {"L": torch.ones(16, 6, 6, device="cuda")}
+    gn, gt, gv = irt.adjoint(g, view, va, LINE, DUST, cot)
+    torch.cuda.synchronize()
+    assert float(gn.abs().max()) == 0.0 and float(gt.abs().max()) == 0.0
+    with pytest.raises(irt.IrtError, match="IRT_EUNSUPPORTED"):
+        irt.adjoint(g, View(0.3, 0.2, 6, 6, dx, 1), va, LINE, DUST, cot)
+    with pytest.raises(irt.IrtError, match="IRT_EUNSUPPORTED"):
+        irt.adjoint(g, view, va, LINE, DUST, cot, integration="formal")
+    g.close()
