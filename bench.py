@@ -4,8 +4,9 @@
 Workload: a 256^3 FP32 field set (lognormal density, turbulent velocity plus
 rotation), 13CO(2-1) in LTE, 256 channels of 1 km/s with f = 1; one step
 renders the z view and the (theta, phi) = (30, 45) deg oblique trilinear view
-with smooth (TR + BDF2) integration.  Units of one render: sum over rays of
-(samples on the ray) x (channels).
+with smooth (TR + BDF2) integration and runs the adjoint of the z view (the
+gradient of a cube loss against a render of another snapshot).  Units of one
+render or adjoint: sum over rays of (samples on the ray) x (channels).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl irt|reference]
 
@@ -41,6 +42,13 @@ UNIT = "cell-channel updates/s"
 OPS_LINE = (10, 2)
 OPS_DUST = (5, 0)
 OPS_SAMPLE = (165, 9)
+#: adjoint: the forward is run 2.5 times (initial pass with checkpoints, then
+#: each 32-sample segment again in two 16-sample sub-segments) plus the reverse
+#: step (about 12 FP32 per block pair, 30 FP32 + 3 MUFU per line slot) and the
+#: per-sample chain rule
+OPS_ADJ_LINE = (2.5 * 10 + 12 + 30, 2.5 * 2 + 3)
+OPS_ADJ_DUST = (2.5 * 5 + 12, 0)
+OPS_ADJ_SAMPLE = (2.5 * 165 + 60, 2.5 * 9 + 6)
 
 
 def parse():
@@ -185,6 +193,35 @@ def oracle_rate(w, deq, target_s=10.0, integration="smooth", seed=0):
     return units / dt, cores, sample, dt
 
 
+def oracle_adjoint_rate(w, deq, target_s=4.0, seed=0):
+    """Oracle dual-number gradient throughput on seeded z-view rays (units of
+    the adjoint: samples x channels per ray).  Returns (units/s, nrays)."""
+    import oracle
+    fields = deq.as_tuple()
+    rng = np.random.default_rng(seed + 99)
+    view = w.views[0]
+    tgt = np.zeros((w.vaxis.nchan, view.npy, view.npx))
+
+    def run(nrays):
+        pix = np.stack([rng.integers(0, view.npx, nrays), rng.integers(0, view.npy, nrays)],
+                       axis=1)
+        t = time.perf_counter()
+        oracle.loss_grad_zview(fields, w.cell_cm, w.line, w.dust, w.vaxis, tgt, pixels=pix)
+        return nrays * w.n * w.vaxis.nchan, time.perf_counter() - t
+
+    nr = max(oracle.num_threads(), 2)
+    units, dt = run(nr)
+    if dt < target_s / 3:
+        nr = max(nr, int(nr * target_s / max(dt, 1e-3)))
+        units, dt = run(nr)
+    return units / dt, nr
+
+
+def combined_rate(r_fwd, r_adj, units_fwd, units_adj):
+    """Rate of a step made of units_fwd forward and units_adj adjoint units."""
+    return (units_fwd + units_adj) / (units_fwd / r_fwd + units_adj / r_adj)
+
+
 def reference_arm(args):
     ws, rank, local = dist_env()
     if ws > 1 and rank != 0:
@@ -195,11 +232,16 @@ def reference_arm(args):
         oracle_rate(w, deq, target_s=per_step / 4, integration=args.integration)
     rates, times = [], []
     cores, sample = 1, ""
+    n = w.n
+    units_fwd = n ** 3 * w.vaxis.nchan * 2      # z + oblique, about equal
+    units_adj = n ** 3 * w.vaxis.nchan
     for s in range(args.steps):
-        r, cores, sample, dt = oracle_rate(w, deq, target_s=per_step,
+        r, cores, sample, dt = oracle_rate(w, deq, target_s=per_step * 0.7,
                                            integration=args.integration, seed=s)
-        rates.append(r)
+        ra, na = oracle_adjoint_rate(w, deq, target_s=per_step * 0.3, seed=s)
+        rates.append(combined_rate(r, ra, units_fwd, units_adj))
         times.append(dt)
+        sample += f"; adjoint: dual-number gradient of {na} seeded z-view rays"
     value = float(np.mean(rates))
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
             "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
@@ -237,11 +279,26 @@ def gpu_arm(args):
     grid = irt.Grid(*fields_d, w.cell_cm)
     outs = [irt.alloc_cubes(v, w.vaxis) for v in w.views]
     stream = torch.cuda.current_stream()
+    # loss = mean over the z-view [L] cube of (L - L_target)^2, the target
+    # rendered from another snapshot; its cotangent feeds the adjoint
+    from synth import make_fields, to_storage
+    tfs, _ = to_storage(make_fields(w.n, seed + 7), np.float32)
+    tgrid = irt.Grid(*[torch.from_numpy(a).to(dev) for a in tfs.as_tuple()], w.cell_cm)
+    l_target = irt.forward(tgrid, w.views[0], w.vaxis, w.line, w.dust,
+                           integration=args.integration, components=("L",))["L"]
+    tgrid.close()
+    irt.forward(grid, w.views[0], w.vaxis, w.line, w.dust, integration=args.integration,
+                out=outs[0])
+    cot = {"L": 2.0 * (outs[0]["L"] - l_target) / outs[0]["L"].numel()}
+    grads = tuple(torch.empty((w.n, w.n, w.n), dtype=torch.float32, device=dev)
+                  for _ in range(3))
 
     def step(flags=0):
         for view, out in zip(w.views, outs):
             irt.forward(grid, view, w.vaxis, w.line, w.dust, integration=args.integration,
                         out=out, flags=flags)
+        irt.adjoint(grid, w.views[0], w.vaxis, w.line, w.dust, cot,
+                    integration=args.integration, grads=grads)
 
     # units and work counters from one counted pass
     B.irt_grid_stats(grid.handle, reset=True)
@@ -251,7 +308,8 @@ def gpu_arm(args):
                     flags=B.IRT_FLAG_STATS)
         per_view.append(B.irt_grid_stats(grid.handle, reset=True))
     units_view = [st["samples"] * w.vaxis.nchan for st in per_view]
-    units_step = sum(units_view)
+    units_adj = units_view[0]
+    units_step = sum(units_view) + units_adj
 
     for _ in range(args.warmup):
         step()
@@ -260,8 +318,9 @@ def gpu_arm(args):
     clocks = ClockSampler(torch.cuda.current_device())
     clocks.start()
     time.sleep(0.3)
+    nk = len(w.views) + 1
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-          for _ in range(len(w.views) * args.steps)]
+          for _ in range(nk * args.steps)]
     t_start = torch.cuda.Event(enable_timing=True)
     t_end = torch.cuda.Event(enable_timing=True)
     if ws > 1:
@@ -278,6 +337,11 @@ def gpu_arm(args):
                         out=out)
             ev[i][1].record(stream)
             i += 1
+        ev[i][0].record(stream)
+        irt.adjoint(grid, w.views[0], w.vaxis, w.line, w.dust, cot,
+                    integration=args.integration, grads=grads)
+        ev[i][1].record(stream)
+        i += 1
     t_end.record(stream)
     torch.cuda.synchronize()
     wall1 = time.time()
@@ -293,23 +357,28 @@ def gpu_arm(args):
         elapsed_ms = float(t.item())
     ms_step = elapsed_ms / args.steps
     value = units_step * ws / (elapsed_ms / 1e3 / args.steps)
-    launch_ms = [[], []]
+    launch_ms = [[] for _ in range(nk)]
     for j, (a, b) in enumerate(ev):
-        launch_ms[j % len(w.views)].append(a.elapsed_time(b))
-    view_ms = [float(np.mean(x)) for x in launch_ms]
+        launch_ms[j % nk].append(a.elapsed_time(b))
+    kern_ms = [float(np.mean(x)) for x in launch_ms]
+    view_ms = kern_ms[:len(w.views)]
+    adj_ms = kern_ms[-1]
 
-    # ---- roofline of the dominant kernel (the render with the most time)
+    # ---- roofline of the dominant kernel (the launch with the most time)
     pk = peaks()
-    dom = int(np.argmax(view_ms))
-    st = per_view[dom]
-    fp32 = 32 * (OPS_LINE[0] * st["line_block_samples"]
-                 + OPS_DUST[0] * (st["hull_block_samples"] - st["line_block_samples"])) \
-        + OPS_SAMPLE[0] * st["samples"]
-    mufu = 32 * OPS_LINE[1] * st["line_block_samples"] + OPS_SAMPLE[1] * st["samples"]
+    dom = int(np.argmax(kern_ms))
+    is_adj = dom == nk - 1
+    st = per_view[0] if is_adj else per_view[dom]
+    ol, od, os_ = (OPS_ADJ_LINE, OPS_ADJ_DUST, OPS_ADJ_SAMPLE) if is_adj else \
+        (OPS_LINE, OPS_DUST, OPS_SAMPLE)
+    fp32 = 32 * (ol[0] * st["line_block_samples"]
+                 + od[0] * (st["hull_block_samples"] - st["line_block_samples"])) \
+        + os_[0] * st["samples"]
+    mufu = 32 * ol[1] * st["line_block_samples"] + os_[1] * st["samples"]
     fclk = float(pk.get("sm_max_mhz", 2032.0)) * 1e6
     peak_fp32 = 148 * 128 * fclk / 1e12          # Top/s
     peak_mufu = 148 * 16 * fclk / 1e12
-    t_dom = view_ms[dom] / 1e3
+    t_dom = kern_ms[dom] / 1e3
     a_fp32 = fp32 / t_dom / 1e12
     a_mufu = mufu / t_dom / 1e12
     if a_fp32 / peak_fp32 >= a_mufu / peak_mufu:
@@ -317,11 +386,14 @@ def gpu_arm(args):
     else:
         ach, peak, pipe = a_mufu, peak_mufu, "mufu"
     nx = w.n
-    hbm_bytes = nx ** 3 * 32 + 5 * 4 * w.vaxis.nchan * w.views[dom].npx * w.views[dom].npy
+    vw = w.views[0 if is_adj else dom]
+    hbm_bytes = nx ** 3 * 32 + 5 * 4 * w.vaxis.nchan * vw.npx * vw.npy
+    kname = ("adj_kernel<17,F32> (z view)" if is_adj else
+             f"fwd_kernel<float,17,F32,smooth> ({['z', 'oblique'][dom]} view)")
     roofline = {"bound": "alu", "pipe": pipe, "achieved": ach, "peak": peak, "unit": "Top/s",
                 "frac": ach / peak, "traffic": None,
-                "kernel": f"fwd_kernel<float,17,F32,smooth> ({['z', 'oblique'][dom]} view)",
-                "launch_ms": view_ms[dom],
+                "kernel": kname,
+                "launch_ms": kern_ms[dom],
                 "peak_source": "148 SMs x (128 FP32 | 16 MUFU lanes) x sm_max_mhz "
                                f"{pk.get('sm_max_mhz', 2032.0)} (MEASURED_PEAKS.json clocks)",
                 "fp32_top_s": a_fp32, "mufu_top_s": a_mufu,
@@ -336,19 +408,33 @@ def gpu_arm(args):
         host_in = [torch.from_numpy(a).pin_memory() for a in f32.as_tuple()]
         host_out = [{k: torch.empty(o[k].shape, dtype=o[k].dtype).pin_memory() for k in o}
                     for o in outs]
-        h2d = sum(t.numel() * t.element_size() for t in host_in)
-        d2h = sum(t.numel() * t.element_size() for o in host_out for t in o.values())
+        host_tgt = l_target.cpu().pin_memory()
+        host_grads = [torch.empty(x.shape, dtype=x.dtype).pin_memory() for x in grads]
+        host_loss = torch.empty((), dtype=torch.float32).pin_memory()
+        h2d = sum(t.numel() * t.element_size() for t in host_in) + \
+            host_tgt.numel() * host_tgt.element_size()
+        d2h = sum(t.numel() * t.element_size() for o in host_out for t in o.values()) + \
+            sum(t.numel() * t.element_size() for t in host_grads) + 4
         dev_in = [torch.empty_like(t, device=dev) for t in host_in]
+        dev_tgt = torch.empty_like(host_tgt, device=dev)
 
         def e2e_step():
             for d, h in zip(dev_in, host_in):
                 d.copy_(h, non_blocking=True)
+            dev_tgt.copy_(host_tgt, non_blocking=True)
             g = irt.Grid(*dev_in, w.cell_cm)
             for view, out, ho in zip(w.views, outs, host_out):
                 irt.forward(g, view, w.vaxis, w.line, w.dust, integration=args.integration,
                             out=out)
                 for k in out:
                     ho[k].copy_(out[k], non_blocking=True)
+            resid = outs[0]["L"] - dev_tgt
+            host_loss.copy_(torch.mean(resid * resid), non_blocking=True)
+            irt.adjoint(g, w.views[0], w.vaxis, w.line, w.dust,
+                        {"L": 2.0 * resid / resid.numel()}, integration=args.integration,
+                        grads=grads)
+            for hg, dg in zip(host_grads, grads):
+                hg.copy_(dg, non_blocking=True)
             torch.cuda.synchronize()
             g.close()
 
@@ -368,15 +454,19 @@ def gpu_arm(args):
             e2e_v = units_step * ws / float(t.item())
         e2e = {"value": e2e_v, "unit": UNIT, "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "ms_per_step": dt * 1e3,
-               "path": "pinned host fields -> device, irt_create_grid, irt_forward_ppv x2, "
-                       "cubes -> pinned host"}
+               "path": "pinned host fields and target -> device, irt_create_grid, "
+                       "irt_forward_ppv x2, loss, irt_adjoint_ppv, cubes + gradients + loss -> "
+                       "pinned host"}
 
     clk = clocks.summary(wall0, wall1)
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         r, cores, sample, dt = oracle_rate(w, deq, target_s=10.0, integration=args.integration)
-        cpu = {"value": r, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
-               "seconds": dt}
+        ra, na = oracle_adjoint_rate(w, deq, target_s=6.0)
+        cpu = {"value": combined_rate(r, ra, sum(units_view), units_adj), "unit": UNIT,
+               "cores": cores, "kind": "oracle",
+               "sample": sample + f"; adjoint: dual-number gradient of {na} seeded z-view rays",
+               "forward_rate": r, "adjoint_rate": ra, "seconds": dt}
 
     grid.close()
     if rank == 0:
@@ -384,13 +474,14 @@ def gpu_arm(args):
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": "f32", "data": "synthetic",
-                "config": {"workload": f"{w.name}: z view + oblique (30,45) deg trilinear, "
-                                       f"{args.integration} integration, forward",
+                "config": {"workload": f"{w.name}: z view + oblique (30,45) deg trilinear "
+                                       f"forward, z-view adjoint, {args.integration} integration",
                            "grid": w.n, "nchan": w.vaxis.nchan, "f": w.vaxis.subsample_f,
                            "units_per_step": units_step, "units_per_view": units_view,
                            "l2": "inputs larger than L2 (packed fields 32 B/cell = "
                                  f"{w.n ** 3 * 32 / 1e6:.0f} MB > 126 MB)",
-                           "parallelism": f"replicas x{ws}", "per_view_ms": view_ms},
+                           "parallelism": f"replicas x{ws}", "per_view_ms": view_ms,
+                           "adjoint_ms": adj_ms, "units_adjoint": units_adj},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "clocks": clk, "gpu_launches": launches}
         print(json.dumps(line), flush=True)

@@ -23,7 +23,9 @@ namespace dev {
 constexpr int kSeg = kAdjSeg;   // checkpoint spacing (samples)
 constexpr int kSub = kAdjSub;   // sub-segment whose pre-ReLU values are stored
 constexpr int kNP = 5;     // partials: h alpha_D, 2h j_L, 2h alpha_L, v, b
-constexpr int kPStride = 33;   // padded lane stride of the partial buffer
+constexpr int kFlush = 8;   // reverse steps between partial reductions
+constexpr int kPStride = 36;   // row stride of the partial buffer (32 lanes + sum, float4 aligned)
+constexpr int kNC = kAdjChain;  // chain-rule factors per sample
 
 // record quantities used by the adjoint only: 2 bk0, 2 bk1 (dust Planck
 // coefficients) ride in the pad words of the smooth record
@@ -64,8 +66,8 @@ struct Adj {
   }
 
   // sample 0 and the trapezoidal step to sample 1 from the background
-  static __device__ __forceinline__ void start(const RecS32* rec, const float (&u)[NA],
-                                               const float (&bg)[NA], float (&s0)[NA],
+  static __device__ __forceinline__ void start(const PhysF& P, const RecS32* rec,
+                                               const float (&u)[NA], float (&s0)[NA],
                                                float (&s1)[NA], int hb, int lane, const VGrid& G,
                                                float& x0, float& x1, float m0, float m1, float m2,
                                                float* pre1) {
@@ -81,7 +83,7 @@ struct Adj {
         t = p ? t + sl0.a[q] : t;
         d = p ? sl0.b[q] : d;
       }
-      s0[j] = bg[j];
+      s0[j] = planck_k(P, P.t_bg, u[j]);
       s1[j] = t + (7.0f - d) * s0[j];
     }
     x0 = m0;
@@ -148,9 +150,10 @@ struct Adj {
   // from step n.
   static __device__ __forceinline__ void rstep(const RecS32& r, const float (&u)[NA],
                                                float (&lam_n)[NA], float (&lam_m)[NA],
-                                               const float* pre, int hb, int lane, const VGrid& G,
-                                               float& xl_n, float& xl_m, float xpre, float m1,
-                                               float m2, float* part) {
+                                               const float (&pre)[NB], int hb, int lane,
+                                               const VGrid& G, float& xl_n, float& xl_m,
+                                               float m1, float m2, float* part) {
+    const float xpre = pre[NA];
     const Slots<NS> sl = slots_smooth<NS>(r, hb, lane, G);
     const float rd0 = rcp_approx(r.d0);
     float rl[NS], qs[NS], ds[NS];
@@ -167,7 +170,7 @@ struct Adj {
       float rr = rd0;
 #pragma unroll
       for (int q = 0; q < NS; ++q) rr = (sl.j[q] == j) ? rl[q] : rr;
-      const float p = pre[j * 32];
+      const float p = pre[j];
       const float mu = (p >= 0.0f) ? lam_n[j] : 0.0f;
       const float q = mu * rr;
       const float dd = -q * p;                    // d loss / d (3 + 2h alpha)
@@ -197,14 +200,12 @@ struct Adj {
   static __device__ __forceinline__ void line_partials(const RecS32& r, const Slots<NS>& sl,
                                                        const float* qs, const float* ds, int lane,
                                                        const VGrid& G, float* part) {
-    const int glo = win_lo(r.win);
-    const int g0 = glo + ((lane - glo) & 31);
     const float ib2 = -r.nib2 * 0.69314718055994531f;   // 1 / b^2
 #pragma unroll
     for (int q = 0; q < NS; ++q) {
-      if (sl.j[q] < 0) continue;
-      const float dv = vel_offset(G, g0 + 32 * q, r.gv, r.vr);   // u - v
-      const float e = ex2_approx(dv * r.nib2 * dv);
+      // qs = ds = 0 for an empty slot: its terms vanish
+      const float dv = sl.dv[q];   // u - v
+      const float e = sl.e[q];
       part[1] = fmaf(qs[q], e, part[1]);
       part[2] = fmaf(ds[q], e, part[2]);
       const float de = fmaf(r.jl2, qs[q], r.al2 * ds[q]) * e;
@@ -216,8 +217,8 @@ struct Adj {
   }
 
   // Adjoint of the trapezoidal step (sample 1) and of sample 0's coefficients.
-  static __device__ __forceinline__ void rstart(const RecS32* rec, const float (&u)[NA],
-                                                const float (&bg)[NA], const float (&lam1)[NA],
+  static __device__ __forceinline__ void rstart(const PhysF& P, const RecS32* rec,
+                                                const float (&u)[NA], const float (&lam1)[NA],
                                                 const float* pre1, int hb, int lane,
                                                 const VGrid& G, float xl1, float xpre1, float m0,
                                                 float m1, float m2, float* part0, float* part1) {
@@ -244,7 +245,7 @@ struct Adj {
       const float q = mu * rr;
       // pre_1 = (jt_0 + (7 - d_0) I_0 + jt_1) / (1 + d_1)
       const float dd1 = -q * p;
-      const float dd0 = -q * bg[j];
+      const float dd0 = -q * planck_k(P, P.t_bg, u[j]);
       gad1 = fmaf(q, fmaf(c1, u[j], c0), fmaf(2.0f, dd1, gad1));
       gad0 = fmaf(q, fmaf(a1, u[j], a0), fmaf(2.0f, dd0, gad0));
 #pragma unroll
@@ -291,6 +292,32 @@ __device__ inline void partition_dz(const PhysF& P, float T, float* Z, float* dZ
   }
   *Z = z;
   *dZ = ze * r / T;   // sum (2J+1) (theta J(J+1) / T^2) t_J
+}
+
+// Chain-rule factors of one sample: d(2h j_L)/dn, d(2h alpha_L)/dn,
+// d(2h j_L)/dT, d(2h alpha_L)/dT, db/dT (LTE populations, Sec. 5.10).
+__device__ __forceinline__ void chain_factors(const PhysF& P, const float raw[5], float h,
+                                              float* cf) {
+  const float n = raw[0], T = raw[1], x = raw[4];
+  const float b = sqrtf(P.c_th * T + P.two_sig2);
+  cf[0] = cf[1] = cf[2] = cf[3] = 0.0f;
+  cf[4] = (T > 0.0f) ? P.c_th / (2.0f * b) : 0.0f;
+  if (T > 0.0f && T <= P.t_inf) {
+    float Z, dZ;
+    partition_dz(P, T, &Z, &dZ);
+    const float eu = expf(-P.e_u / T), el = expf(-P.e_l / T);
+    const float em = expf(-P.T0 / T);
+    const float st = -expm1f(-P.T0 / T);
+    const float base = x * h / (Z * b);              // per unit n
+    const float jl2_n = 2.0f * P.cj * base * eu;
+    const float al2_n = 2.0f * P.ca * base * el * st;
+    const float common = -dZ / Z - cf[4] / b;
+    const float T2 = T * T;
+    cf[0] = jl2_n;
+    cf[1] = al2_n;
+    cf[2] = jl2_n * n * (P.e_u / T2 + common);
+    cf[3] = al2_n * n * (P.e_l / T2 - (P.T0 / T2) * em / st + common);
+  }
 }
 
 // Chain rule from the record partials (h alpha_D, 2h j_L, 2h alpha_L, v, b)
@@ -342,17 +369,16 @@ __device__ __forceinline__ float fine_cotangent(int g, int f, int cwn, const flo
 // Reverse sweep of one ray with NA explicit hull blocks and NS line slots.
 template <int NA, int NS, int ST>
 __device__ __noinline__ void adj_ray(const JobDev& J, const PhysF& P, const AdjArgs& A,
-                                     const RecS32* rec, int K, int hb, int lane, const VGrid& G,
-                                     int nfw, const float* lamf, float lx, float* pbuf,
-                                     float* scr, int px, int py) {
+                                     const RecS32* rec, const float* chainf, int K, int hb,
+                                     int lane, const VGrid& G, int nfw, const float* lamf,
+                                     float lx, float* pbuf, float* scr, int px, int py) {
   using AD = Adj<NA, NS>;
   constexpr int NB = NA + 1;
-  float u[NA], bg[NA];
+  float u[NA];
 #pragma unroll
   for (int j = 0; j < NA; ++j) {
     const int g = min(32 * (hb + j) + lane, nfw - 1);
     u[j] = fmaf((float)g, G.dvf_hi, G.ufw_hi);
-    bg[j] = planck_k(P, P.t_bg, u[j]);
   }
   const float m0 = (lane == 0) ? 1.0f : 0.0f;
   const float m1 = (lane == 1) ? 1.0f : 0.0f;
@@ -363,7 +389,7 @@ __device__ __noinline__ void adj_ray(const JobDev& J, const PhysF& P, const AdjA
   float sa[NA], sb[NA], xa, xb;
 
   // ---- forward with a checkpoint (I_{32s-2}, I_{32s-1}) at every segment s >= 1
-  AD::start(rec, u, bg, sa, sb, hb, lane, G, xa, xb, m0, m1, m2, nullptr);
+  AD::start(P, rec, u, sa, sb, hb, lane, G, xa, xb, m0, m1, m2, nullptr);
   {
     int n = 2;
     for (int s = 1; s < nseg; ++s) {
@@ -399,7 +425,7 @@ __device__ __noinline__ void adj_ray(const JobDev& J, const PhysF& P, const AdjA
       // pre-ReLU values of samples [sub_lo, sub_hi)
       float* pre_base = pre - (long long)sub_lo * NB * 32;   // indexed by absolute n
       if (s == 0) {
-        AD::start(rec, u, bg, sa, sb, hb, lane, G, xa, xb, m0, m1, m2,
+        AD::start(P, rec, u, sa, sb, hb, lane, G, xa, xb, m0, m1, m2,
                   (sub_lo <= 1 && 1 < sub_hi) ? pre_base + 1 * NB * 32 + lane : nullptr);
         if (sub_hi > 2)
           AD::run(rec, 2, sub_hi, u, sa, sb, hb, lane, G, xa, xb, m1, m2, pre_base + lane,
@@ -416,58 +442,75 @@ __device__ __noinline__ void adj_ray(const JobDev& J, const PhysF& P, const AdjA
         AD::run(rec, seg_lo, sub_hi, u, sa, sb, hb, lane, G, xa, xb, m1, m2, pre_base + lane,
                 sub_lo);
       }
-      // reverse steps of the sub-segment
-      for (int n = sub_hi - 1; n >= max(sub_lo, 2); --n) {
-        float part[kNP] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
-        const float* pn = pre_base + (long long)n * NB * 32 + lane;
-        AD::rstep(rec[n], u, ln, lm, pn, hb, lane, G, xln, xlm, pn[NA * 32], m1, m2, part);
-        float* row = pbuf + (n - sub_lo) * kNP * kPStride + lane;
+      // reverse steps of the sub-segment, flushing the partials of every 16
+      // samples (lane l reduces sample bot + l and writes its gradients)
+      for (int top = sub_hi; top > sub_lo;) {
+        const int bot = max(sub_lo, top - kFlush);
+        const int nlo = max(bot, 2);
+        for (int n = top - 1; n >= nlo; --n) {
+          float pc[NB];
+          const float* src = pre_base + (long long)n * NB * 32 + lane;
 #pragma unroll
-        for (int q = 0; q < kNP; ++q) row[q * kPStride] = part[q];
-      }
-      if (sub_lo == 0) {
-        float p0[kNP] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
-        float p1[kNP] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
-        const float* pn = pre_base + 1 * NB * 32 + lane;
-        AD::rstart(rec, u, bg, ln, pn, hb, lane, G, xln, pn[NA * 32], m0, m1, m2, p0, p1);
+          for (int j = 0; j < NB; ++j) pc[j] = src[j * 32];
+          float part[kNP] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+          AD::rstep(rec[n], u, ln, lm, pc, hb, lane, G, xln, xlm, m1, m2, part);
+          float* row = pbuf + (n - bot) * kNP * kPStride + lane;
 #pragma unroll
-        for (int q = 0; q < kNP; ++q) {
-          pbuf[0 * kNP * kPStride + q * kPStride + lane] = p0[q];
-          pbuf[1 * kNP * kPStride + q * kPStride + lane] = p1[q];
+          for (int q = 0; q < kNP; ++q) row[q * kPStride] = part[q];
         }
-      }
-      __syncwarp();
-      // lane l reduces the partials of sample sub_lo + l and writes its gradients
-      const int nsub = sub_hi - sub_lo;
-      if (lane < nsub) {
-        float g5[kNP];
+        if (bot == 0) {
+          float p0[kNP] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+          float p1[kNP] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+          const float* pn = pre_base + 1 * NB * 32 + lane;
+          AD::rstart(P, rec, u, ln, pn, hb, lane, G, xln, pn[NA * 32], m0, m1, m2, p0, p1);
 #pragma unroll
-        for (int q = 0; q < kNP; ++q) {
-          const float* rowq = pbuf + lane * kNP * kPStride + q * kPStride;
+          for (int q = 0; q < kNP; ++q) {
+            pbuf[0 * kNP * kPStride + q * kPStride + lane] = p0[q];
+            pbuf[1 * kNP * kPStride + q * kPStride + lane] = p1[q];
+          }
+        }
+        __syncwarp();
+        // each lane sums whole 32-lane rows (row = sample x partial), results
+        // go back to the first column of the row
+        const int nrows = (top - bot) * kNP;
+        for (int row = lane; row < nrows; row += 32) {
+          const float4* v4 = reinterpret_cast<const float4*>(pbuf + row * kPStride);
           float acc = 0.0f;
-#pragma unroll 8
-          for (int m = 0; m < 32; ++m) acc += rowq[m];
-          g5[q] = acc;
+#pragma unroll
+          for (int m = 0; m < 8; ++m) {
+            const float4 v = v4[m];
+            acc += (v.x + v.y) + (v.z + v.w);
+          }
+          pbuf[row * kPStride + 32] = acc;
         }
-        const int n = sub_lo + lane;
-        float raw[5];
-        RayPos rp;
-        sample_raw<ST>(J, rp, px, py, n, raw);
-        float gn, gt, gv;
-        chain(P, raw, (float)J.dx, g5, &gn, &gt, &gv);
-        const long long idx = ((long long)n * J.ny + py) * J.nx + px;
-        A.grad[0][idx] = gn;
-        A.grad[1][idx] = gt;
-        A.grad[2][idx] = gv;
+        __syncwarp();
+        if (lane < top - bot) {
+          const float* g5 = pbuf + lane * kNP * kPStride + 32;
+          const int n = bot + lane;
+          const float* cf = chainf + n * kNC;
+          // d/dn = G_ad cad h + G_jl d(2h j_L)/dn + G_al d(2h alpha_L)/dn;
+          // d/dT = G_jl d(2h j_L)/dT + G_al d(2h alpha_L)/dT + G_b db/dT; d/dv = G_v
+          const float gad = g5[0 * kPStride], gjl = g5[1 * kPStride], gal = g5[2 * kPStride];
+          const float gvv = g5[3 * kPStride], gb = g5[4 * kPStride];
+          const float gn = fmaf(gjl, cf[0], fmaf(gal, cf[1], gad * P.cad * (float)J.dx));
+          const float gt = fmaf(gjl, cf[2], fmaf(gal, cf[3], gb * cf[4]));
+          const long long idx = ((long long)n * J.ny + py) * J.nx + px;
+          A.grad[0][idx] = gn;
+          A.grad[1][idx] = gt;
+          A.grad[2][idx] = gvv;
+        }
+        __syncwarp();
+        top = bot;
       }
-      __syncwarp();
       sub_hi = sub_lo;
     }
   }
 }
 
+__device__ __forceinline__ int J0kmax(const JobTable& t) { return t.j[0].kmax; }
+
 template <int NI, int ST>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32, 1)
+__global__ void __launch_bounds__(kAdjWarps * 32, 1)
 adj_kernel(const __grid_constant__ JobTable tab, const PhysF PF, const AdjArgs A,
            long long total_items, unsigned long long* queue, int per_warp, int fw_off,
            int cw_off, int pb_off) {
@@ -478,9 +521,11 @@ adj_kernel(const __grid_constant__ JobTable tab, const PhysF PF, const AdjArgs A
   RecS32* rec = reinterpret_cast<RecS32*>(wsm);
   float* lamf = reinterpret_cast<float*>(wsm + fw_off);   // fine cotangents
   float* lamc = reinterpret_cast<float*>(wsm + cw_off);   // channel cotangents (T total)
-  float* pbuf = reinterpret_cast<float*>(wsm + pb_off);   // [kSub][kNP][kPStride]
-  const long long gw = (long long)blockIdx.x * kWarpsPerBlock + warp;
+  float* pbuf = reinterpret_cast<float*>(wsm + pb_off);   // [kFlush][kNP][kPStride]
+  const long long gw = (long long)blockIdx.x * kAdjWarps + warp;
   float* scr = A.scratch + gw * A.scratch_per_warp;
+  // chain-rule factors [K][kNC] at the end of the warp's scratch
+  float* chainf = scr + A.scratch_per_warp - (long long)kNC * J0kmax(tab);
   const JobDev& J = tab.j[0];
 
   for (;;) {
@@ -515,6 +560,7 @@ adj_kernel(const __grid_constant__ JobTable tab, const PhysF PF, const AdjArgs A
         dust_source_lin(PF, raw[2], &bk0, &bk1);
         rec[k].pad[0] = 2.0f * bk0;
         rec[k].pad[1] = 2.0f * bk1;
+        chain_factors(PF, raw, h, chainf + k * kNC);
         const int w = rec[k].win;
         const int lo = win_lo(w), hi = win_hi(w);
         if (lo <= hi) {
@@ -600,9 +646,11 @@ adj_kernel(const __grid_constant__ JobTable tab, const PhysF PF, const AdjArgs A
   case NA_:                                                                                  \
     if constexpr (NA_ <= NI) {                                                               \
       if (ns == 1)                                                                           \
-        adj_ray<NA_, 1, ST>(J, PF, A, rec, K, hb, lane, G, nfw, lamf, lx, pbuf, scr, px, py); \
+        adj_ray<NA_, 1, ST>(J, PF, A, rec, chainf, K, hb, lane, G, nfw, lamf, lx, pbuf, scr, px, \
+                            py);                                                              \
       else                                                                                   \
-        adj_ray<NA_, 2, ST>(J, PF, A, rec, K, hb, lane, G, nfw, lamf, lx, pbuf, scr, px, py); \
+        adj_ray<NA_, 2, ST>(J, PF, A, rec, chainf, K, hb, lane, G, nfw, lamf, lx, pbuf, scr, px, \
+                            py);                                                              \
     }                                                                                        \
     break;
     switch (nb) {
@@ -625,9 +673,9 @@ int launch_adjoint(int store, int ni, const JobTable& tab, const PhysF& PF, cons
   const int fw_off = (rec_bytes + 15) & ~15;
   const int cw_off = (fw_off + 4 * nfw + 15) & ~15;
   const int pb_off = (cw_off + 4 * nchan + 15) & ~15;
-  const int per_warp = (pb_off + 4 * dev::kSub * dev::kNP * dev::kPStride + 15) & ~15;
+  const int per_warp = (pb_off + 4 * dev::kFlush * dev::kNP * dev::kPStride + 15) & ~15;
   if (per_warp_smem) *per_warp_smem = per_warp;
-  const size_t smem = (size_t)per_warp * kWarpsPerBlock;
+  const size_t smem = (size_t)per_warp * kAdjWarps;
 #define IRT_LAUNCH(NI_, ST_)                                                                  \
   if (ni == NI_ && store == ST_) {                                                            \
     auto kern = dev::adj_kernel<NI_, ST_>;                                                    \
@@ -635,8 +683,8 @@ int launch_adjoint(int store, int ni, const JobTable& tab, const PhysF& PF, cons
                                          (int)smem);                                          \
     if (e != cudaSuccess) return (int)e;                                                      \
     if (blocks <= 0) return 0;                                                                \
-    kern<<<blocks, kWarpsPerBlock * 32, smem, stream>>>(tab, PF, A, total_items, queue,       \
-                                                        per_warp, fw_off, cw_off, pb_off);    \
+    kern<<<blocks, kAdjWarps * 32, smem, stream>>>(tab, PF, A, total_items, queue,            \
+                                                   per_warp, fw_off, cw_off, pb_off);         \
     return (int)cudaGetLastError();                                                           \
   }
   IRT_LAUNCH(9, ST_F32) IRT_LAUNCH(17, ST_F32) IRT_LAUNCH(33, ST_F32)
@@ -653,7 +701,7 @@ int adjoint_blocks_per_sm(int store, int ni, size_t smem) {
     cudaFuncSetAttribute(dev::adj_kernel<NI_, ST_>,                                           \
                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);             \
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dev::adj_kernel<NI_, ST_>,         \
-                                                  kWarpsPerBlock * 32, smem);                 \
+                                                  kAdjWarps * 32, smem);                      \
     return per_sm;                                                                            \
   }
   IRT_OCC(9, ST_F32) IRT_OCC(17, ST_F32) IRT_OCC(33, ST_F32)

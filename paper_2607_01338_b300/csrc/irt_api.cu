@@ -535,15 +535,17 @@ extern "C" irt_status irt_adjoint_ppv(const irt_job* job, const irt_line* line,
   int e = launch_adjoint(g->store, p.ni, tab, PF, A, 0, nullptr, 0, p.kmax, p.nfw,
                          jb.vaxis.nchan, s, &per_warp);
   if (e) return cuda_fail(e, "irt_adjoint_ppv: kernel attributes");
-  const size_t smem = (size_t)per_warp * kWarpsPerBlock;
+  const size_t smem = (size_t)per_warp * kAdjWarps;
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int per_sm = std::max(1, adjoint_blocks_per_sm(g->store, p.ni, smem));
   const int blocks = per_sm * sms;
   const int nseg = (p.kmax + kAdjSeg - 1) / kAdjSeg;
-  const long long per_warp_floats = (long long)(2 * nseg + kAdjSub) * (p.ni + 1) * 32;
-  const size_t need = (size_t)blocks * kWarpsPerBlock * (size_t)per_warp_floats * sizeof(float);
+  // checkpoints, one stored sub-segment, the per-sample chain-rule factors
+  const long long per_warp_floats =
+      (long long)(2 * nseg + kAdjSub) * (p.ni + 1) * 32 + (long long)kAdjChain * p.kmax;
+  const size_t need = (size_t)blocks * kAdjWarps * (size_t)per_warp_floats * sizeof(float);
   if (g->adj_bytes < need) {
     if (g->adj_scratch) {
       cudaStreamSynchronize(s);

@@ -396,6 +396,8 @@ struct Slots {
   int j[NS];      // block of the slot relative to hb, -1 = no line velocity
   float a[NS];    // smooth: 2h j_line;     formal: per-step emission
   float b[NS];    // smooth: 3 + 2h alpha;  formal: optical depth
+  float e[NS];    // profile factor exp(-(u - v)^2 / b^2)
+  float dv[NS];   // u - v_los
 };
 
 template <int NS>
@@ -412,6 +414,8 @@ __device__ __forceinline__ Slots<NS> slots_smooth(const RecS32& r, int hb, int l
     s.j[q] = (g <= ghi) ? (g >> 5) - hb : -1;
     s.a[q] = r.jl2 * e;
     s.b[q] = fmaf(r.al2, e, r.d0);
+    s.e[q] = e;
+    s.dv[q] = dd;
   }
   return s;
 }
@@ -431,6 +435,8 @@ __device__ __forceinline__ Slots<NS> slots_formal(const RecF32& r, int hb, int l
     s.j[q] = (g <= ghi) ? (g >> 5) - hb : -1;
     s.a[q] = fmaf(r.jl, e, r.ad * fmaf(r.bk1, ug, r.bk0));
     s.b[q] = fmaf(r.al, e, r.ad);
+    s.e[q] = e;
+    s.dv[q] = dd;
   }
   return s;
 }

@@ -77,9 +77,12 @@ struct JobDev {
 constexpr int kWarpsPerBlock = 4;
 constexpr int kMaxJobs = 64;
 
-// Adjoint: checkpoint spacing and stored sub-segment (samples).
+// Adjoint: checkpoint spacing and stored sub-segment (samples), warps per
+// block, chain-rule factors per sample.
 constexpr int kAdjSeg = 32;
-constexpr int kAdjSub = 16;
+constexpr int kAdjSub = 32;
+constexpr int kAdjWarps = 2;
+constexpr int kAdjChain = 5;
 
 struct AdjArgs {
   const float* cot[5];          // cotangent cubes T, C, D, L, B (NULL = 0)
