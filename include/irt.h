@@ -80,6 +80,9 @@ typedef enum { IRT_MODE_THICK = 0 } irt_transfer_mode;
                                           continuum basis shortcut) */
 #define IRT_FLAG_STATS 2u              /* accumulate work counters into the first
                                           job's grid (see irt_grid_stats) */
+#define IRT_FLAG_AUTOTUNE 4u           /* time the launch plans for this job mix
+                                          (synchronous; not during stream capture)
+                                          and cache the fastest */
 
 typedef struct irt_grid irt_grid;   /* opaque */
 
@@ -178,6 +181,29 @@ irt_status irt_forward_ppv(const irt_job* jobs, int njobs, const irt_line* line,
                            const irt_dust* dust, const irt_opts* opts, void* cuda_stream);
 
 /*
+ * CUDA graph of one irt_forward_ppv call (usually a batch): the queue reset and
+ * the persistent kernel with the job table and launch plan baked in.  The
+ * grids and output cubes named by the jobs must outlive the graph; launching
+ * it re-renders them from the grids' current contents.  With
+ * IRT_FLAG_AUTOTUNE the plan is tuned first (synchronously) if the job mix
+ * has no cached plan.  Errors as irt_forward_ppv; IRT_ECUDA if capture or
+ * instantiation fails.
+ */
+typedef struct irt_graph irt_graph;
+irt_status irt_forward_graph_create(const irt_job* jobs, int njobs, const irt_line* line,
+                                    const irt_dust* dust, const irt_opts* opts,
+                                    irt_graph** out);
+irt_status irt_forward_graph_launch(irt_graph* graph, void* cuda_stream);
+irt_status irt_forward_graph_destroy(irt_graph* graph);
+
+/*
+ * irt_tuned_plan - the cached plan of a job mix: out = {fine blocks per lane
+ * NI (32 NI velocities per channel window), tile width, tile height} in rays,
+ * or {0, 0, 0} if the mix was never tuned (the default plan is used).
+ */
+irt_status irt_tuned_plan(const irt_job* jobs, int njobs, const irt_opts* opts, int out[3]);
+
+/*
  * irt_adjoint_ppv - gradients of a scalar loss with respect to n_H2, T_gas
  * and v_los of every cell for one z-view job (Sec. 4.8 run in reverse), given
  * the cotangents dLoss/d[T], d[C], d[D], d[L], d[B] (float cubes
@@ -227,7 +253,8 @@ irt_status irt_destroy(irt_grid* grid);
  * irt_grid_stats - copy (synchronously, after the device is idle on all
  * streams) the work counters a forward call with IRT_FLAG_STATS accumulated
  * into this grid, then zero them if reset != 0.  out[6] = work items, ray
- * samples, (sample, 32-velocity block) pairs where the line was evaluated,
+ * samples (summed over rays once, whatever the number of channel windows),
+ * (sample, 32-velocity block) pairs where the line was evaluated,
  * (sample, block) pairs integrated explicitly, items integrated without the
  * continuum shortcut, and fine-velocity updates of the dense method
  * (samples x fine velocities).  IRT_EINVAL for NULL arguments.

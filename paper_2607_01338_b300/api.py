@@ -121,15 +121,58 @@ def forward(grid: Grid, view, vaxis, line: dict, dust: dict, *, integration="smo
 
 
 def forward_batch(jobs, line: dict, dust: dict, *, integration="smooth", units="trj",
-                  t_bg=2.725, precision="f32", flags=0, outs=None, stream=None) -> list:
+                  t_bg=2.725, precision="f32", flags=0, outs=None, stream=None,
+                  autotune=False) -> list:
     """Render many jobs in one persistent launch.  ``jobs`` = [(grid, view,
-    vaxis), ...]; returns one cube dict per job."""
+    vaxis), ...]; returns one cube dict per job.  ``autotune`` times the
+    launch plans for this job mix first (synchronous) and caches the best."""
     if outs is None:
         outs = [alloc_cubes(v, va, precision) for (_, v, va) in jobs]
     cj = [make_job(g, v, va, o) for (g, v, va), o in zip(jobs, outs)]
+    if autotune:
+        flags |= B.IRT_FLAG_AUTOTUNE
     B.irt_forward_ppv(cj, line_struct(line), dust_struct(dust),
                       opts_struct(integration, units, t_bg, precision, flags), _stream_ptr(stream))
     return outs
+
+
+class ForwardGraph:
+    """A CUDA graph of one batched render (``irt_forward_graph_create``).
+    The grids and output cubes must outlive it; ``launch`` re-renders them."""
+
+    def __init__(self, jobs, line: dict, dust: dict, *, integration="smooth", units="trj",
+                 t_bg=2.725, precision="f32", flags=0, outs=None, autotune=False):
+        if outs is None:
+            outs = [alloc_cubes(v, va, precision) for (_, v, va) in jobs]
+        self.outs = outs
+        self._keep = list(jobs)
+        cj = [make_job(g, v, va, o) for (g, v, va), o in zip(jobs, outs)]
+        if autotune:
+            flags |= B.IRT_FLAG_AUTOTUNE
+        self.opts = opts_struct(integration, units, t_bg, precision, flags)
+        self._jobs = cj
+        self.handle = B.irt_forward_graph_create(cj, line_struct(line), dust_struct(dust),
+                                                 self.opts)
+
+    def plan(self):
+        """(NI, tile width, tile height) used by the graph's launch plan."""
+        return B.irt_tuned_plan(self._jobs, self.opts)
+
+    def launch(self, stream=None):
+        B.irt_forward_graph_launch(self.handle, _stream_ptr(stream))
+        return self.outs
+
+    def close(self):
+        if getattr(self, "handle", None):
+            torch.cuda.synchronize()
+            B.irt_forward_graph_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def adjoint(grid: Grid, view, vaxis, line: dict, dust: dict, cotangent: dict, *,

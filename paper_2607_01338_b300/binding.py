@@ -21,13 +21,16 @@ IRT_PREC_F32, IRT_PREC_F64 = range(2)
 IRT_MODE_THICK = 0
 IRT_FLAG_EXPLICIT_CHANNELS = 1
 IRT_FLAG_STATS = 2
+IRT_FLAG_AUTOTUNE = 4
 
 STATUS_NAMES = {0: "IRT_OK", 1: "IRT_EINVAL", 2: "IRT_ENOMEM", 3: "IRT_ECUDA",
                 4: "IRT_EUNSUPPORTED", 5: "IRT_ETIMEOUT"}
 
 #: symbols include/irt.h declares
 EXPORTED = ("irt_create_grid", "irt_forward_ppv", "irt_adjoint_ppv", "irt_destroy",
-            "irt_grid_stats", "irt_forward_ppv_static", "irt_last_error", "irt_launch_count")
+            "irt_grid_stats", "irt_forward_ppv_static", "irt_forward_graph_create",
+            "irt_forward_graph_launch", "irt_forward_graph_destroy", "irt_tuned_plan",
+            "irt_last_error", "irt_launch_count")
 
 
 class irt_grid_desc(ctypes.Structure):
@@ -107,6 +110,15 @@ def _load():
     L.irt_forward_ppv_static.argtypes = [P(irt_grid_desc), P(irt_fields), P(irt_view),
                                          P(irt_vaxis), P(irt_cubes), P(irt_line), P(irt_dust),
                                          P(irt_opts), ctypes.c_void_p]
+    L.irt_forward_graph_create.restype = ctypes.c_int
+    L.irt_forward_graph_create.argtypes = [P(irt_job), ctypes.c_int, P(irt_line), P(irt_dust),
+                                           P(irt_opts), P(ctypes.c_void_p)]
+    L.irt_forward_graph_launch.restype = ctypes.c_int
+    L.irt_forward_graph_launch.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
+    L.irt_forward_graph_destroy.restype = ctypes.c_int
+    L.irt_forward_graph_destroy.argtypes = [ctypes.c_void_p]
+    L.irt_tuned_plan.restype = ctypes.c_int
+    L.irt_tuned_plan.argtypes = [P(irt_job), ctypes.c_int, P(irt_opts), P(ctypes.c_int)]
     L.irt_grid_stats.restype = ctypes.c_int
     L.irt_grid_stats.argtypes = [ctypes.c_void_p, P(ctypes.c_ulonglong), ctypes.c_int]
     L.irt_last_error.restype = ctypes.c_char_p
@@ -155,6 +167,29 @@ def irt_forward_ppv_static(desc: irt_grid_desc, fields: irt_fields, view: irt_vi
                                       ctypes.byref(vaxis), ctypes.byref(out), ctypes.byref(line),
                                       ctypes.byref(dust), ctypes.byref(opts),
                                       ctypes.c_void_p(stream)))
+
+
+def irt_forward_graph_create(jobs, line: irt_line, dust: irt_dust, opts: irt_opts) -> int:
+    arr = (irt_job * len(jobs))(*jobs)
+    h = ctypes.c_void_p()
+    _check(lib.irt_forward_graph_create(arr, len(jobs), ctypes.byref(line), ctypes.byref(dust),
+                                        ctypes.byref(opts), ctypes.byref(h)))
+    return h.value
+
+
+def irt_forward_graph_launch(handle: int, stream: int) -> None:
+    _check(lib.irt_forward_graph_launch(ctypes.c_void_p(handle), ctypes.c_void_p(stream)))
+
+
+def irt_forward_graph_destroy(handle: int) -> None:
+    _check(lib.irt_forward_graph_destroy(ctypes.c_void_p(handle)))
+
+
+def irt_tuned_plan(jobs, opts: irt_opts):
+    arr = (irt_job * len(jobs))(*jobs)
+    out = (ctypes.c_int * 3)()
+    _check(lib.irt_tuned_plan(arr, len(jobs), ctypes.byref(opts), out))
+    return tuple(int(v) for v in out)
 
 
 def irt_destroy(handle: int) -> None:

@@ -6,6 +6,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstdarg>
 #include <cstring>
 #include <mutex>
@@ -298,6 +299,7 @@ irt_status check_job(const irt_job& jb, int precision) {
 // Window plan: blocks per lane (compiled sizes) and channels per window.
 struct Plan {
   int ni, cw, nwin, nfw, kmax;
+  int tw = 1, th = 1;
 };
 
 const int kNiF32[] = {9, 17, 33};
@@ -383,7 +385,11 @@ JobDev make_jobdev(const irt_job& jb, const Plan& p) {
   d.kmax = p.kmax;
   d.out[0] = jb.out.T; d.out[1] = jb.out.C; d.out[2] = jb.out.D;
   d.out[3] = jb.out.L; d.out[4] = jb.out.B;
-  d.nitems = (long long)d.npx * d.npy * d.nwin;
+  d.tw = std::max(1, p.tw);
+  d.th = std::max(1, p.th);
+  d.ntx = (d.npx + d.tw - 1) / d.tw;
+  const long long nty = (d.npy + d.th - 1) / d.th;
+  d.nitems = (long long)d.ntx * d.tw * nty * d.th * d.nwin;
   return d;
 }
 
@@ -407,38 +413,100 @@ int dispatch(int precision, int mode, int store, int ni, const JobTable& jobs, i
 }  // namespace
 }  // namespace irt
 
-extern "C" irt_status irt_forward_ppv(const irt_job* jobs, int njobs, const irt_line* line,
-                                      const irt_dust* dust, const irt_opts* opts,
-                                      void* cuda_stream) {
-  g_err.clear();
-  if (!jobs || njobs < 1) return fail(IRT_EINVAL, "irt_forward_ppv: no jobs");
-  irt_status st = check_line(line, dust, opts);
-  if (st) return st;
+namespace irt {
+namespace {
+
+// Launch plan of a forward call (channel window and ray tile), tuned or default.
+struct Tuned {
+  int ni = 0;      // 0 = smallest window size holding all channels
+  int tw = 1, th = 1;
+};
+
+std::mutex g_tune_mu;
+std::vector<std::pair<unsigned long long, Tuned>> g_tuned;   // signature -> plan
+
+// Signature of a job mix for the tuning cache (sizes, axes, views, storage,
+// integration, precision; not the field values).
+unsigned long long job_signature(const irt_job* jobs, int njobs, const irt_opts* op) {
+  unsigned long long h = 1469598103934665603ull;
+  auto mix = [&](unsigned long long v) {
+    h ^= v;
+    h *= 1099511628211ull;
+  };
+  mix((unsigned long long)njobs);
+  mix((unsigned long long)op->integration);
+  mix((unsigned long long)op->precision);
+  mix((unsigned long long)(op->flags & IRT_FLAG_EXPLICIT_CHANNELS));
   for (int j = 0; j < njobs; ++j) {
-    st = check_job(jobs[j], opts->precision);
-    if (st) return st;
+    const irt_job& b = jobs[j];
+    mix((unsigned long long)b.grid->nx);
+    mix((unsigned long long)b.grid->ny);
+    mix((unsigned long long)b.grid->nz);
+    mix((unsigned long long)b.grid->store);
+    mix((unsigned long long)b.view.npx);
+    mix((unsigned long long)b.view.npy);
+    mix((unsigned long long)b.view.trilinear);
+    mix((unsigned long long)b.vaxis.nchan);
+    mix((unsigned long long)b.vaxis.subsample_f);
   }
-  const PhysParams P = fold_constants(line, dust, opts);
-  const PhysF PF = to_float(P);
-  cudaStream_t s = (cudaStream_t)cuda_stream;
+  return h;
+}
+
+bool lookup_tuned(unsigned long long sig, Tuned* t) {
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  for (const auto& e : g_tuned)
+    if (e.first == sig) {
+      *t = e.second;
+      return true;
+    }
+  return false;
+}
+
+void store_tuned(unsigned long long sig, const Tuned& t) {
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  for (auto& e : g_tuned)
+    if (e.first == sig) {
+      e.second = t;
+      return;
+    }
+  g_tuned.emplace_back(sig, t);
+}
+
+// Launch-plan override for tests and manual tuning: IRT_PLAN="NI,tw,th"
+// (NI one of 9, 17, 33; tiles >= 1).  Read on every call.
+void forced_plan(Tuned* t) {
+  const char* e = std::getenv("IRT_PLAN");
+  if (!e || !*e) return;
+  int ni = 0, tw = 0, th = 0;
+  if (std::sscanf(e, "%d,%d,%d", &ni, &tw, &th) != 3) return;
+  if ((ni == 9 || ni == 17 || ni == 33) && tw >= 1 && th >= 1 && tw <= 64 && th <= 64) {
+    t->ni = ni;
+    t->tw = tw;
+    t->th = th;
+  }
+}
+
+// Validated forward launch with a given plan (no tuning, no cache).
+irt_status run_forward(const irt_job* jobs, int njobs, const PhysParams& P, const PhysF& PF,
+                       const irt_opts* opts, const Tuned& tp, cudaStream_t s) {
   const int prec = opts->precision;
   const int mode = opts->integration;
-
-  // plan every job; the batch path needs one store class and one block count
   std::vector<Plan> plans(njobs);
   int ni = 0;
   for (int j = 0; j < njobs; ++j) {
     plans[j] = plan_job(jobs[j], prec, 0);
     ni = std::max(ni, plans[j].ni);
   }
+  if (prec != IRT_PREC_F64 && tp.ni > 0) ni = tp.ni;
   const int store = jobs[0].grid->store;
   for (int j = 1; j < njobs; ++j)
     if (jobs[j].grid->store != store)
       return fail(IRT_EUNSUPPORTED, "batched jobs must share the field storage type");
-  if (njobs > 1) {
-    for (int j = 0; j < njobs; ++j) plans[j] = plan_job(jobs[j], prec, ni);
+  for (int j = 0; j < njobs; ++j) {
+    if (njobs > 1 || tp.ni > 0) plans[j] = plan_job(jobs[j], prec, ni);
+    plans[j].tw = tp.tw;
+    plans[j].th = tp.th;
   }
-
   // order: most expensive rays first (greedy longest-processing-time order
   // for the persistent work queue)
   std::vector<int> order(njobs);
@@ -478,6 +546,195 @@ extern "C" irt_status irt_forward_ppv(const irt_job* jobs, int njobs, const irt_
     ++g_launches;
     if (e) return cuda_fail(e, "irt_forward_ppv: forward kernel");
   }
+  return IRT_OK;
+}
+
+// Times the candidate plans on the given stream (synchronous) and returns the
+// fastest.  Candidates: window sizes NI = 9, 17, 33 (where they hold the
+// channel count of some job in few windows) x ray tiles 1x1, 2x2, 4x1, 4x4.
+irt_status autotune(const irt_job* jobs, int njobs, const PhysParams& P, const PhysF& PF,
+                    const irt_opts* opts, cudaStream_t s, Tuned* best) {
+  int ni_min = 9;
+  {
+    // smallest NI that still needs at most 4 windows for every job
+    for (int ni : {9, 17, 33}) {
+      bool ok = true;
+      for (int j = 0; j < njobs && ok; ++j) {
+        const Plan p = plan_job(jobs[j], opts->precision, ni);
+        ok = p.nwin <= 4;
+      }
+      if (ok) { ni_min = ni; break; }
+      ni_min = 33;
+    }
+  }
+  std::vector<Tuned> cands;
+  const int tiles[4][2] = {{1, 1}, {2, 2}, {4, 1}, {4, 4}};
+  for (int ni : {9, 17, 33}) {
+    if (ni < ni_min) continue;
+    for (const auto& t : tiles) {
+      Tuned c;
+      c.ni = ni;
+      c.tw = t[0];
+      c.th = t[1];
+      cands.push_back(c);
+    }
+  }
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+    return fail(IRT_ECUDA, "autotune: cannot create events");
+  float best_ms = 1e30f;
+  irt_status st = IRT_OK;
+  irt_opts o = *opts;
+  o.flags &= ~(unsigned)IRT_FLAG_STATS;
+  for (const Tuned& c : cands) {
+    st = run_forward(jobs, njobs, P, PF, &o, c, s);   // warm-up
+    if (st) break;
+    cudaEventRecord(e0, s);
+    for (int r = 0; r < 2 && !st; ++r) st = run_forward(jobs, njobs, P, PF, &o, c, s);
+    cudaEventRecord(e1, s);
+    if (st) break;
+    cudaError_t ce = cudaEventSynchronize(e1);
+    if (ce != cudaSuccess) {
+      st = cuda_fail(ce, "autotune: timing");
+      break;
+    }
+    float ms = 0.0f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms < best_ms) {
+      best_ms = ms;
+      *best = c;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return st;
+}
+
+}  // namespace
+}  // namespace irt
+
+extern "C" irt_status irt_forward_ppv(const irt_job* jobs, int njobs, const irt_line* line,
+                                      const irt_dust* dust, const irt_opts* opts,
+                                      void* cuda_stream) {
+  g_err.clear();
+  if (!jobs || njobs < 1) return fail(IRT_EINVAL, "irt_forward_ppv: no jobs");
+  irt_status st = check_line(line, dust, opts);
+  if (st) return st;
+  for (int j = 0; j < njobs; ++j) {
+    st = check_job(jobs[j], opts->precision);
+    if (st) return st;
+  }
+  const PhysParams P = fold_constants(line, dust, opts);
+  const PhysF PF = to_float(P);
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  Tuned tp;
+  if (opts->precision != IRT_PREC_F64) {
+    const unsigned long long sig = job_signature(jobs, njobs, opts);
+    if (!lookup_tuned(sig, &tp) && (opts->flags & IRT_FLAG_AUTOTUNE)) {
+      st = autotune(jobs, njobs, P, PF, opts, s, &tp);
+      if (st) return st;
+      store_tuned(sig, tp);
+    }
+    forced_plan(&tp);
+  }
+  return run_forward(jobs, njobs, P, PF, opts, tp, s);
+}
+
+// ---------------------------------------------------------------------------
+// CUDA graph of one forward call (typically a batch)
+// ---------------------------------------------------------------------------
+struct irt_graph {
+  cudaGraph_t graph;
+  cudaGraphExec_t exec;
+};
+
+extern "C" irt_status irt_forward_graph_create(const irt_job* jobs, int njobs,
+                                               const irt_line* line, const irt_dust* dust,
+                                               const irt_opts* opts, irt_graph** out) {
+  g_err.clear();
+  if (!out) return fail(IRT_EINVAL, "irt_forward_graph_create: NULL out");
+  *out = nullptr;
+  if (!jobs || njobs < 1) return fail(IRT_EINVAL, "irt_forward_graph_create: no jobs");
+  irt_status st = check_line(line, dust, opts);
+  if (st) return st;
+  for (int j = 0; j < njobs; ++j) {
+    st = check_job(jobs[j], opts->precision);
+    if (st) return st;
+  }
+  cudaStream_t cs;
+  if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess)
+    return fail(IRT_ECUDA, "irt_forward_graph_create: cannot create a capture stream");
+  const PhysParams P = fold_constants(line, dust, opts);
+  const PhysF PF = to_float(P);
+  Tuned tp;
+  if (opts->precision != IRT_PREC_F64) {
+    const unsigned long long sig = job_signature(jobs, njobs, opts);
+    if (!lookup_tuned(sig, &tp) && (opts->flags & IRT_FLAG_AUTOTUNE)) {
+      st = autotune(jobs, njobs, P, PF, opts, cs, &tp);
+      if (st) {
+        cudaStreamDestroy(cs);
+        return st;
+      }
+      store_tuned(sig, tp);
+    }
+  }
+  irt_graph* g = new irt_graph();
+  cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed);
+  if (e == cudaSuccess) {
+    st = run_forward(jobs, njobs, P, PF, opts, tp, cs);
+    const cudaError_t e2 = cudaStreamEndCapture(cs, &g->graph);
+    if (!st && e2 != cudaSuccess) st = cuda_fail(e2, "irt_forward_graph_create: end capture");
+  } else {
+    st = cuda_fail(e, "irt_forward_graph_create: begin capture");
+  }
+  if (!st) {
+    e = cudaGraphInstantiate(&g->exec, g->graph, 0);
+    if (e != cudaSuccess) {
+      cudaGraphDestroy(g->graph);
+      st = cuda_fail(e, "irt_forward_graph_create: instantiate");
+    }
+  }
+  cudaStreamDestroy(cs);
+  if (st) {
+    delete g;
+    return st;
+  }
+  *out = g;
+  return IRT_OK;
+}
+
+extern "C" irt_status irt_forward_graph_launch(irt_graph* g, void* cuda_stream) {
+  g_err.clear();
+  if (!g) return fail(IRT_EINVAL, "irt_forward_graph_launch: NULL graph");
+  const cudaError_t e = cudaGraphLaunch(g->exec, (cudaStream_t)cuda_stream);
+  ++g_launches;
+  if (e != cudaSuccess) return cuda_fail(e, "irt_forward_graph_launch");
+  return IRT_OK;
+}
+
+extern "C" irt_status irt_forward_graph_destroy(irt_graph* g) {
+  g_err.clear();
+  if (!g) return IRT_OK;
+  cudaGraphExecDestroy(g->exec);
+  cudaGraphDestroy(g->graph);
+  delete g;
+  return IRT_OK;
+}
+
+extern "C" irt_status irt_tuned_plan(const irt_job* jobs, int njobs, const irt_opts* opts,
+                                     int out[3]) {
+  g_err.clear();
+  if (!jobs || njobs < 1 || !opts || !out) return fail(IRT_EINVAL, "irt_tuned_plan: argument");
+  for (int j = 0; j < njobs; ++j)
+    if (!jobs[j].grid) return fail(IRT_EINVAL, "irt_tuned_plan: job without grid");
+  Tuned t;
+  if (!lookup_tuned(job_signature(jobs, njobs, opts), &t)) {
+    out[0] = out[1] = out[2] = 0;
+    return IRT_OK;
+  }
+  out[0] = t.ni;
+  out[1] = t.tw;
+  out[2] = t.th;
   return IRT_OK;
 }
 

@@ -754,7 +754,7 @@ __device__ void render_item(const JobDev& J, const PhysParams& PD, const PhysF& 
     if (lane == 0) {
       const unsigned long long nh = (hhi >= hlo) ? (unsigned long long)(hhi - hlo + 1) : 0ull;
       atomicAdd(stats + 0, 1ull);
-      atomicAdd(stats + 1, (unsigned long long)K);
+      if (win == 0) atomicAdd(stats + 1, (unsigned long long)K);   // once per ray
       atomicAdd(stats + 2, nline);
       atomicAdd(stats + 3, nh * (unsigned long long)K);
       atomicAdd(stats + 4, explicit_all ? 1ull : 0ull);
@@ -906,10 +906,17 @@ fwd_kernel(const __grid_constant__ JobTable tab, int njobs, const PhysParams PD,
     const long long local = item - J.item_begin;
     const int win = (int)(local % J.nwin);
     const long long ray = local / J.nwin;
-    const int px = (int)(ray % J.npx), py = (int)(ray / J.npx);
+    // rays come in tiles of tw x th pixels (row-major inside the tile and
+    // over the tiles); pixels past the image edge are padding
+    const int tsz = J.tw * J.th;
+    const long long tile = ray / tsz;
+    const int within = (int)(ray - tile * tsz);
+    const int px = (int)(tile % J.ntx) * J.tw + within % J.tw;
+    const int py = (int)(tile / J.ntx) * J.th + within / J.tw;
     if constexpr (ST == ST_F64 || sizeof(R) == 4) {
-      render_item<R, NI, ST, MODE>(J, PD, PF, px, py, win, wsm, fw_off, cw_off, lane, flags,
-                                   stats);
+      if (px < J.npx && py < J.npy)
+        render_item<R, NI, ST, MODE>(J, PD, PF, px, py, win, wsm, fw_off, cw_off, lane, flags,
+                                     stats);
     }
     if (queue) {
       unsigned long long t = 0;

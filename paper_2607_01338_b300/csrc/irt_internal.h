@@ -67,6 +67,8 @@ struct JobDev {
   double v0, dv;         // channel lower edge of channel 0, width [km/s]
   double ufirst, dvf;    // first fine velocity and fine step [km/s]
   int cw, nwin;          // channels per window, windows per ray
+  int tw, th;            // rays are handed out in tiles of tw x th pixels
+  int ntx;               // tiles per image row
   int kmax;              // upper bound of samples per ray
   int pad0;
   void* out[5];          // T, C, D, L, B cubes [nchan][npy][npx]

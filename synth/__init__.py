@@ -8,6 +8,12 @@ from .fields import grf, make_fields, FieldSet, to_storage
 from .configs import (LINE_13CO_21, DUST, VelocityAxis, View, Workload,
                       workload, batch_jobs, BatchJob)
 
-__all__ = ["grf", "make_fields", "FieldSet", "to_storage", "LINE_13CO_21",
+def make_fields_torch(*a, **k):
+    """GPU generator (torch); see synth.gpu_fields."""
+    from .gpu_fields import make_fields_torch as f
+    return f(*a, **k)
+
+
+__all__ = ["grf", "make_fields", "make_fields_torch", "FieldSet", "to_storage", "LINE_13CO_21",
            "DUST", "VelocityAxis", "View", "Workload", "workload",
            "batch_jobs", "BatchJob"]

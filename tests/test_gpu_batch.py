@@ -1,0 +1,124 @@
+"""Batched persistent rendering (many snapshots of uneven size and view in one
+launch, BF16/FP16 storage, Kahan-compensated formal transfer), its CUDA
+graph, the autotuner and forced launch plans, against the FP64 oracle."""
+import math
+import os
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+import oracle  # noqa: E402
+from synth import DUST, LINE_13CO_21, View, batch_jobs, make_fields, to_storage  # noqa: E402
+from tests.gpu_helpers import COMP, assert_parity, oracle_pixels, torch_fields  # noqa: E402
+
+LINE = dict(LINE_13CO_21)
+BF16_V16 = ["bf16", "bf16", "bf16", np.float16, "bf16"]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2607_01338_b300  # noqa: F401
+
+
+@pytest.fixture(scope="module")
+def batch():
+    """12 uneven jobs with the recipe of the 64-job workload, scaled down:
+    N in 16..40, 32..140 channels of 1 km/s, random directions, BF16 fields
+    with an FP16 velocity."""
+    import paper_2607_01338_b300 as irt
+    jobs = batch_jobs(12, seed=2100, n_lo=16, n_hi=40, ch_lo=32, ch_hi=140)
+    out = []
+    for bj in jobs:
+        fs = make_fields(bj.n, bj.seed, n_mean=bj.n_mean)
+        st, deq = to_storage(fs, BF16_V16)
+        g = irt.Grid(*torch_fields(st), bj.cell_cm)
+        out.append((bj, g, deq))
+    yield out
+    for _, g, _ in out:
+        g.close()
+
+
+def _render(batch, integration, **kw):
+    import paper_2607_01338_b300 as irt
+    jobs = [(g, bj.view(), bj.vaxis) for bj, g, _ in batch]
+    outs = irt.forward_batch(jobs, LINE, DUST, integration=integration, **kw)
+    torch.cuda.synchronize()
+    return outs
+
+
+def _close(a, b, rtol=1e-5, atol_frac=1e-6):
+    for k in COMP:
+        peak = float(b["T"].abs().max())
+        allow = torch.clamp(rtol * b[k].abs(), min=atol_frac * peak)
+        assert float(((a[k] - b[k]).abs() / allow).max()) <= 1.0, k
+
+
+@pytest.mark.parametrize("integration", ["formal_kahan", "smooth"])
+def test_batch_parity_on_four_random_jobs(batch, integration):
+    outs = _render(batch, integration)
+    rng = np.random.default_rng(5)
+    for ji in rng.choice(len(batch), 4, replace=False):
+        bj, g, deq = batch[ji]
+        view = bj.view()
+        pix = np.stack([rng.integers(0, view.npx, 40), rng.integers(0, view.npy, 40)], axis=1)
+        orc = oracle_pixels(deq.as_tuple(), bj.cell_cm, view, bj.vaxis, LINE, DUST, pix,
+                            integration=integration)
+        gpu = {k: outs[ji][k].double().cpu().numpy() for k in COMP}
+        assert_parity(gpu, orc, pix)
+
+
+def test_graph_launch_equals_direct_batch(batch):
+    import paper_2607_01338_b300 as irt
+    direct = _render(batch, "formal_kahan")
+    jobs = [(g, bj.view(), bj.vaxis) for bj, g, _ in batch]
+    graph = irt.ForwardGraph(jobs, LINE, DUST, integration="formal_kahan")
+    for _ in range(2):
+        outs = graph.launch()
+        torch.cuda.synchronize()
+        for a, b in zip(outs, direct):
+            for k in COMP:
+                assert torch.equal(a[k], b[k]), k
+    graph.close()
+
+
+def test_autotune_caches_a_plan_and_keeps_the_results(batch):
+    import paper_2607_01338_b300 as irt
+    base = _render(batch, "smooth")
+    tuned = _render(batch, "smooth", autotune=True)
+    jobs = [(g, bj.view(), bj.vaxis) for bj, g, _ in batch]
+    graph = irt.ForwardGraph(jobs, LINE, DUST, integration="smooth")
+    ni, tw, th = graph.plan()
+    assert ni in (9, 17, 33) and tw >= 1 and th >= 1
+    graph.close()
+    for a, b in zip(tuned, base):
+        _close(a, b)
+
+
+@pytest.mark.parametrize("plan", ["9,2,2", "17,4,4", "33,4,1", "9,3,5"])
+def test_forced_plans_render_the_same_cubes(batch, plan):
+    base = _render(batch, "formal_kahan")
+    os.environ["IRT_PLAN"] = plan
+    try:
+        got = _render(batch, "formal_kahan")
+    finally:
+        del os.environ["IRT_PLAN"]
+    for a, b in zip(got, base):
+        _close(a, b)
+
+
+def test_torch_generator_matches_recipe():
+    from synth import make_fields_torch
+    n_h2, t_gas, t_dust, v_los, x = make_fields_torch(24, 7, n_mean=3e3)
+    assert n_h2.shape == (24, 24, 24) and n_h2.dtype == torch.float64
+    ln = torch.log(n_h2 / 3e3)
+    g = (ln + 1.5 ** 2 / 2) / 1.5
+    assert abs(float(g.mean())) < 1e-9 and abs(float(g.std(unbiased=False)) - 1.0) < 1e-9
+    assert float(t_gas.min()) >= 20.0 and float(t_gas.max()) <= 100.0
+    assert torch.equal(t_gas, t_dust)
+    assert float(x.min()) == float(x.max()) == 2e-6
