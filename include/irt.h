@@ -225,10 +225,12 @@ irt_status irt_adjoint_ppv(const irt_job* job, const irt_line* line, const irt_d
  * device memory and hands it only finished buffers, or a real-time loop that
  * must not block on the allocator or fail with out-of-memory after start-up.
  * The caller passes the fields (device pointers, layout and dtypes as for
- * irt_create_grid) and the output cubes; the packed copy of the fields and
- * the work-queue counter go to one file-scope device array of
- * 32 MiB + 256 bytes that every device loading the library holds until the
- * process exits.  A grid needing more than 32 MiB of packed cells (32, 16 or
+ * irt_create_grid) and the output cubes; the packed copy of the fields, the
+ * per-warp sample records and the work-queue counter go to one file-scope
+ * device array of 32 MiB + 16 MiB + 256 bytes that every device loading the
+ * library holds until the process exits (the 16 MiB of records bound the
+ * warps the launch keeps resident: each holds the records of its longest
+ * ray).  A grid needing more than 32 MiB of packed cells (32, 16 or
  * 64 bytes per cell for float, 16-bit or double storage; e.g. 1,048,576 float
  * cells) is rejected with IRT_EINVAL and a message giving both sizes.  The
  * call issues no cudaMalloc/cudaFree.  The first call on a device looks up the

@@ -17,26 +17,21 @@
 
 namespace irt {
 
-int dispatch_fwd_f32_smooth(int store, int ni, const JobTable& jobs, int njobs, const PhysParams& P, const PhysF& PF,
-                            long long total, unsigned long long* queue, int grid_blocks, int kmax,
-                            int fwmax, int cwmax, unsigned flags, unsigned long long* stats,
+int dispatch_fwd_f32_smooth(int store, int ni, const JobTable& jobs, int njobs,
+                            const PhysParams& P, const PhysF& PF, const FwdLaunch& L,
                             cudaStream_t s);
-int dispatch_fwd_f32_formal(int store, int ni, const JobTable& jobs, int njobs, const PhysParams& P, const PhysF& PF,
-                            long long total, unsigned long long* queue, int grid_blocks, int kmax,
-                            int fwmax, int cwmax, unsigned flags, unsigned long long* stats,
+int dispatch_fwd_f32_formal(int store, int ni, const JobTable& jobs, int njobs,
+                            const PhysParams& P, const PhysF& PF, const FwdLaunch& L,
                             cudaStream_t s);
-int dispatch_fwd_f32_kahan(int store, int ni, const JobTable& jobs, int njobs, const PhysParams& P, const PhysF& PF,
-                           long long total, unsigned long long* queue, int grid_blocks, int kmax,
-                           int fwmax, int cwmax, unsigned flags, unsigned long long* stats,
+int dispatch_fwd_f32_kahan(int store, int ni, const JobTable& jobs, int njobs,
+                           const PhysParams& P, const PhysF& PF, const FwdLaunch& L,
                            cudaStream_t s);
 int launch_adjoint(int store, int ni, const JobTable& tab, const PhysF& PF, const AdjArgs& A,
                    long long total_items, unsigned long long* queue, int blocks, int kmax,
                    int nfw, int nchan, cudaStream_t stream, int* per_warp_smem);
 int adjoint_blocks_per_sm(int store, int ni, size_t smem);
 int dispatch_fwd_f64(int mode, int store, int ni, const JobTable& jobs, int njobs,
-                     const PhysParams& P, const PhysF& PF, long long total, unsigned long long* queue,
-                     int grid_blocks, int kmax, int fwmax, int cwmax, unsigned flags,
-                     unsigned long long* stats, cudaStream_t s);
+                     const PhysParams& P, const PhysF& PF, const FwdLaunch& L, cudaStream_t s);
 
 namespace {
 
@@ -84,6 +79,8 @@ struct irt_grid {
   int device;
   float* adj_scratch;        // adjoint checkpoints (grown on demand)
   size_t adj_bytes;
+  unsigned char* fwd_scratch;   // forward sample records of launches led by this grid
+  size_t fwd_bytes;
 };
 
 using namespace irt;
@@ -141,6 +138,8 @@ irt_status irt_create_grid(const irt_grid_desc* desc, const irt_fields* fields,
   g->ctl = nullptr;
   g->adj_scratch = nullptr;
   g->adj_bytes = 0;
+  g->fwd_scratch = nullptr;
+  g->fwd_bytes = 0;
   cudaGetDevice(&g->device);
   if (cudaMalloc(&g->cells, g->cell_bytes) != cudaSuccess) {
     cudaGetLastError();
@@ -189,6 +188,7 @@ irt_status irt_destroy(irt_grid* g) {
   cudaFree(g->cells);
   cudaFree(g->ctl);
   if (g->adj_scratch) cudaFree(g->adj_scratch);
+  if (g->fwd_scratch) cudaFree(g->fwd_scratch);
   delete g;
   return IRT_OK;
 }
@@ -394,20 +394,24 @@ JobDev make_jobdev(const irt_job& jb, const Plan& p) {
 }
 
 int dispatch(int precision, int mode, int store, int ni, const JobTable& jobs, int njobs,
-             const PhysParams& P, const PhysF& PF, long long total, unsigned long long* queue, int grid_blocks,
-             int kmax, int fwmax, int cwmax, unsigned flags, unsigned long long* stats,
-             cudaStream_t s) {
-  if (precision == IRT_PREC_F64)
-    return dispatch_fwd_f64(mode, store, ni, jobs, njobs, P, PF, total, queue, grid_blocks, kmax,
-                            fwmax, cwmax, flags, stats, s);
-  if (mode == M_SMOOTH)
-    return dispatch_fwd_f32_smooth(store, ni, jobs, njobs, P, PF, total, queue, grid_blocks, kmax,
-                                   fwmax, cwmax, flags, stats, s);
-  if (mode == M_FORMAL)
-    return dispatch_fwd_f32_formal(store, ni, jobs, njobs, P, PF, total, queue, grid_blocks, kmax,
-                                   fwmax, cwmax, flags, stats, s);
-  return dispatch_fwd_f32_kahan(store, ni, jobs, njobs, P, PF, total, queue, grid_blocks, kmax, fwmax,
-                                cwmax, flags, stats, s);
+             const PhysParams& P, const PhysF& PF, const FwdLaunch& L, cudaStream_t s) {
+  if (precision == IRT_PREC_F64) return dispatch_fwd_f64(mode, store, ni, jobs, njobs, P, PF, L, s);
+  if (mode == M_SMOOTH) return dispatch_fwd_f32_smooth(store, ni, jobs, njobs, P, PF, L, s);
+  if (mode == M_FORMAL) return dispatch_fwd_f32_formal(store, ni, jobs, njobs, P, PF, L, s);
+  return dispatch_fwd_f32_kahan(store, ni, jobs, njobs, P, PF, L, s);
+}
+
+// Record scratch a forward launch over these plans wants: every warp that can
+// be resident on the device holds the records of its longest ray.
+size_t fwd_scratch_need(const std::vector<Plan>& plans, int precision) {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  int kmax = 1;
+  for (const Plan& p : plans) kmax = std::max(kmax, p.kmax);
+  const size_t rec = precision == IRT_PREC_F64 ? kRecBytesF64 : kRecBytesF32;
+  const size_t stride = ((size_t)kmax * rec + 255) & ~(size_t)255;
+  return (size_t)std::max(sms, 1) * kFwdWarpsPerSm * stride;
 }
 
 }  // namespace
@@ -487,8 +491,42 @@ void forced_plan(Tuned* t) {
 }
 
 // Validated forward launch with a given plan (no tuning, no cache).
+// Device buffer handed to a launch from outside the grids (graphs own one so
+// that a later call cannot free it under them; the static entry uses its array).
+struct Scratch {
+  unsigned char* p = nullptr;
+  size_t bytes = 0;
+};
+
+// The first job's grid holds the record scratch of a direct call; it grows on
+// demand (cudaFree waits for the launches that used the old buffer).
+irt_status grid_fwd_scratch(irt_grid* g, size_t need, cudaStream_t s, Scratch* out) {
+  if (g->fwd_bytes < need) {
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    cudaStreamIsCapturing(s, &cap);
+    if (cap != cudaStreamCaptureStatusNone)
+      return fail(IRT_EUNSUPPORTED,
+                  "irt_forward_ppv: the record scratch of the grid must grow (%zu bytes), which "
+                  "cannot happen during stream capture; run the call once before capturing it",
+                  need);
+    if (g->fwd_scratch) cudaFree(g->fwd_scratch);
+    g->fwd_scratch = nullptr;
+    g->fwd_bytes = 0;
+    if (cudaMalloc((void**)&g->fwd_scratch, need) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(IRT_ENOMEM, "irt_forward_ppv: cannot allocate %zu bytes of record scratch",
+                  need);
+    }
+    g->fwd_bytes = need;
+  }
+  out->p = g->fwd_scratch;
+  out->bytes = g->fwd_bytes;
+  return IRT_OK;
+}
+
 irt_status run_forward(const irt_job* jobs, int njobs, const PhysParams& P, const PhysF& PF,
-                       const irt_opts* opts, const Tuned& tp, cudaStream_t s) {
+                       const irt_opts* opts, const Tuned& tp, cudaStream_t s,
+                       const Scratch* ext = nullptr) {
   const int prec = opts->precision;
   const int mode = opts->integration;
   std::vector<Plan> plans(njobs);
@@ -518,6 +556,13 @@ irt_status run_forward(const irt_job* jobs, int njobs, const PhysParams& P, cons
       return ca > cb;
     });
   }
+  Scratch sc;
+  if (ext) {
+    sc = *ext;
+  } else {
+    const irt_status st = grid_fwd_scratch(jobs[0].grid, fwd_scratch_need(plans, prec), s, &sc);
+    if (st) return st;
+  }
   for (int base = 0; base < njobs; base += kMaxJobs) {
     const int nb = std::min(kMaxJobs, njobs - base);
     JobTable tab;
@@ -533,16 +578,24 @@ irt_status run_forward(const irt_job* jobs, int njobs, const PhysParams& P, cons
       fwmax = std::max(fwmax, 32 * plans[j].ni);
       cwmax = std::max(cwmax, plans[j].cw);
     }
-    unsigned long long* queue = nullptr;
-    if (njobs > 1) {
-      queue = jobs[order[base]].grid->ctl;
-      const cudaError_t e = cudaMemsetAsync(queue, 0, sizeof(unsigned long long), s);
-      if (e != cudaSuccess) return cuda_fail(e, "irt_forward_ppv: queue reset");
+    FwdLaunch L;
+    L.total = total;
+    // a batch balances its uneven items through the queue; one job's items
+    // go round-robin
+    L.queue = nb > 1 ? jobs[order[base]].grid->ctl : nullptr;
+    L.grid_blocks = 0;
+    L.kmax = kmax;
+    L.fwmax = fwmax;
+    L.cwmax = cwmax;
+    L.flags = opts->flags;
+    L.stats = (opts->flags & IRT_FLAG_STATS) ? jobs[0].grid->ctl + 1 : nullptr;
+    L.rscr = sc.p;
+    L.rbytes = sc.bytes;
+    if (L.queue) {
+      const cudaError_t ce = cudaMemsetAsync(L.queue, 0, sizeof(unsigned long long), s);
+      if (ce != cudaSuccess) return cuda_fail(ce, "irt_forward_ppv: queue reset");
     }
-    unsigned long long* stats =
-        (opts->flags & IRT_FLAG_STATS) ? jobs[0].grid->ctl + 1 : nullptr;
-    const int e = dispatch(prec, mode, store, ni, tab, nb, P, PF, total, queue, 0, kmax, fwmax,
-                           cwmax, opts->flags, stats, s);
+    const int e = dispatch(prec, mode, store, ni, tab, nb, P, PF, L, s);
     ++g_launches;
     if (e) return cuda_fail(e, "irt_forward_ppv: forward kernel");
   }
@@ -646,6 +699,7 @@ extern "C" irt_status irt_forward_ppv(const irt_job* jobs, int njobs, const irt_
 struct irt_graph {
   cudaGraph_t graph;
   cudaGraphExec_t exec;
+  unsigned char* scratch;   // record scratch owned by the graph
 };
 
 extern "C" irt_status irt_forward_graph_create(const irt_job* jobs, int njobs,
@@ -678,10 +732,24 @@ extern "C" irt_status irt_forward_graph_create(const irt_job* jobs, int njobs,
       store_tuned(sig, tp);
     }
   }
+  // the graph's own record scratch, sized like a direct call's
+  Scratch sc;
+  {
+    std::vector<Plan> plans(njobs);
+    for (int j = 0; j < njobs; ++j) plans[j] = plan_job(jobs[j], opts->precision, 0);
+    sc.bytes = fwd_scratch_need(plans, opts->precision);
+  }
+  if (cudaMalloc((void**)&sc.p, sc.bytes) != cudaSuccess) {
+    cudaGetLastError();
+    cudaStreamDestroy(cs);
+    return fail(IRT_ENOMEM, "irt_forward_graph_create: cannot allocate %zu bytes of scratch",
+                sc.bytes);
+  }
   irt_graph* g = new irt_graph();
+  g->scratch = sc.p;
   cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed);
   if (e == cudaSuccess) {
-    st = run_forward(jobs, njobs, P, PF, opts, tp, cs);
+    st = run_forward(jobs, njobs, P, PF, opts, tp, cs, &sc);
     const cudaError_t e2 = cudaStreamEndCapture(cs, &g->graph);
     if (!st && e2 != cudaSuccess) st = cuda_fail(e2, "irt_forward_graph_create: end capture");
   } else {
@@ -696,6 +764,7 @@ extern "C" irt_status irt_forward_graph_create(const irt_job* jobs, int njobs,
   }
   cudaStreamDestroy(cs);
   if (st) {
+    cudaFree(g->scratch);
     delete g;
     return st;
   }
@@ -717,6 +786,7 @@ extern "C" irt_status irt_forward_graph_destroy(irt_graph* g) {
   if (!g) return IRT_OK;
   cudaGraphExecDestroy(g->exec);
   cudaGraphDestroy(g->graph);
+  cudaFree(g->scratch);   // waits for launches of the graph still running
   delete g;
   return IRT_OK;
 }
@@ -831,10 +901,12 @@ extern "C" irt_status irt_adjoint_ppv(const irt_job* job, const irt_line* line,
 // ---------------------------------------------------------------------------
 // Render without any device allocation (irt_forward_ppv_static).
 //
-// The packed cells of the grid and the work-queue counter of the persistent
-// launch live in one file-scope device array instead of memory allocated by
-// irt_create_grid.  Every device that loads the library holds this array
-// (kStaticCellBytes + kStaticCtlBytes) until the process exits.  All calls
+// The packed cells of the grid, the per-warp sample records and the
+// work-queue counter of the persistent launch live in one file-scope device
+// array instead of memory allocated by irt_create_grid.  Every device that
+// loads the library holds this array (kStaticCellBytes + kStaticRecBytes +
+// kStaticCtlBytes) until the process exits.  The record part bounds the
+// number of resident warps (each holds the records of its longest ray).  All calls
 // share it: a call overwrites the cells and control words of the previous
 // call, and two calls whose kernels overlap on the GPU (different streams, or
 // different host threads) race on it.
@@ -843,10 +915,12 @@ namespace irt {
 namespace {
 
 constexpr size_t kStaticCellBytes = size_t(32) << 20;   // 32 MiB of packed cells
+constexpr size_t kStaticRecBytes = size_t(16) << 20;    // 16 MiB of sample records
 constexpr size_t kStaticCtlBytes = 256;                   // work-queue and counters
 constexpr int kStaticMaxDevices = 64;
 
-static __device__ __align__(256) unsigned char g_static_scratch[kStaticCellBytes + kStaticCtlBytes];
+static __device__ __align__(256) unsigned char
+    g_static_scratch[kStaticCellBytes + kStaticRecBytes + kStaticCtlBytes];
 
 std::mutex g_static_mu;
 void* g_static_base[kStaticMaxDevices] = {};
@@ -939,8 +1013,8 @@ extern "C" irt_status irt_forward_ppv_static(const irt_grid_desc* desc, const ir
   st = static_scratch_base(&base);
   if (st) return st;
   g.cells = base;
-  g.ctl = reinterpret_cast<unsigned long long*>(static_cast<unsigned char*>(base) +
-                                                kStaticCellBytes);
+  unsigned char* recs = static_cast<unsigned char*>(base) + kStaticCellBytes;
+  g.ctl = reinterpret_cast<unsigned long long*>(recs + kStaticRecBytes);
   cudaStream_t s = (cudaStream_t)cuda_stream;
   // the work-queue counter must start at zero; the array keeps the last call's values
   cudaError_t ce = cudaMemsetAsync(g.ctl, 0, kStaticCtlBytes, s);
@@ -956,9 +1030,18 @@ extern "C" irt_status irt_forward_ppv_static(const irt_grid_desc* desc, const ir
   tab.j[0] = make_jobdev(job, p);
   tab.j[0].item_begin = 0;
   const long long total = tab.j[0].nitems;
-  unsigned long long* stats = (opts->flags & IRT_FLAG_STATS) ? g.ctl + 1 : nullptr;
-  e = dispatch(opts->precision, opts->integration, store, p.ni, tab, 1, P, to_float(P), total,
-               g.ctl, 0, p.kmax, 32 * p.ni, p.cw, opts->flags, stats, s);
+  FwdLaunch L;
+  L.total = total;
+  L.queue = nullptr;   // one job: round-robin items
+  L.grid_blocks = 0;
+  L.kmax = p.kmax;
+  L.fwmax = 32 * p.ni;
+  L.cwmax = p.cw;
+  L.flags = opts->flags;
+  L.stats = (opts->flags & IRT_FLAG_STATS) ? g.ctl + 1 : nullptr;
+  L.rscr = recs;
+  L.rbytes = kStaticRecBytes;
+  e = dispatch(opts->precision, opts->integration, store, p.ni, tab, 1, P, to_float(P), L, s);
   ++g_launches;
   if (e) return cuda_fail(e, "irt_forward_ppv_static: forward kernel");
   return IRT_OK;

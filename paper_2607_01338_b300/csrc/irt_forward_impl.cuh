@@ -81,6 +81,60 @@ __device__ __forceinline__ double make_record(const PhysParams& P, const double 
   return r.ad;
 }
 
+// Per-sample records of one ray.  The sample pass writes them to this warp's
+// slot of a global scratch buffer (it stays in L2); the transfer passes stream
+// them back 32 at a time into a two-chunk ring in shared memory with cp.async,
+// the next chunk in flight while the current one is integrated.  Lane l copies
+// record k0 + l, the record it wrote itself in the sample pass.
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.wait_all;" ::: "memory");
+}
+
+template <typename Rec>
+struct RecStream {
+  const Rec* grec;   // records 0..K-1 of this ray (global)
+  Rec* ring;         // 2 x 32 records (shared)
+  int K, lane;
+
+  __device__ __forceinline__ void request(int k0) const {
+    const int k = k0 + lane;
+    if (k < K) {
+      const unsigned char* src = reinterpret_cast<const unsigned char*>(grec + k);
+      unsigned char* dst = reinterpret_cast<unsigned char*>(ring + ((k0 >> 5) & 1) * 32 + lane);
+#pragma unroll
+      for (int q = 0; q < (int)(sizeof(Rec) / 16); ++q) cp_async16(dst + 16 * q, src + 16 * q);
+    }
+    cp_async_commit();
+  }
+  // First chunk of a sweep (forward from 0, or backward from the last chunk).
+  __device__ __forceinline__ void begin(int k0) const { request(k0); }
+  // Waits for chunk k0 (requested by begin() or the previous call), requests
+  // chunk kn (kn < 0: none) into the other half of the ring and returns the
+  // half that holds chunk k0.
+  __device__ __forceinline__ const Rec* take(int k0, int kn) const {
+    cp_async_wait_all();
+    __syncwarp();   // chunk k0 visible to every lane; the other half is free
+    if (kn >= 0) request(kn);
+    return ring + ((k0 >> 5) & 1) * 32;
+  }
+  __device__ __forceinline__ const Rec* take_fwd(int k0) const {
+    return take(k0, (k0 + 32 < K) ? k0 + 32 : -1);
+  }
+  __device__ __forceinline__ const Rec* take_bwd(int k0) const {
+    return take(k0, (k0 >= 32) ? k0 - 32 : -1);
+  }
+  static __device__ __forceinline__ int last_chunk(int K) { return ((K - 1) >> 5) << 5; }
+};
+static_assert(sizeof(RecS32) == kRecBytesF32 && sizeof(RecF32) == kRecBytesF32 &&
+              sizeof(RecD) == kRecBytesF64, "record sizes");
+
 // ---------------------------------------------------------------------------
 // per-(sample, fine velocity) coefficients of the total intensity
 // ---------------------------------------------------------------------------
@@ -138,10 +192,11 @@ struct Fwd {
 
   // Total-intensity transfer of the hull blocks [hlo, hhi] (or, with
   // line == false, dust-only transfer of the blocks at velocities u[]).
-  // On return s1[i] holds the final intensity of block i.
-  template <bool LINE>
+  // Records come from `gen` in chunks of 32 samples.  On return s1[i] holds
+  // the final intensity of block i.
+  template <bool LINE, class Gen>
   static __device__ __forceinline__ void transfer(const PP& P, const VGrid& G, int lane,
-                                                  const Rec* rec, int K, const R* u, int hlo,
+                                                  const Gen& gen, int K, const R* u, int hlo,
                                                   int hhi, R* s0, R* s1, R* s2) {
     if constexpr (MODE == M_SMOOTH) {
       if (K <= 1) {
@@ -149,9 +204,11 @@ struct Fwd {
         for (int i = 0; i < NI; ++i) s1[i] = s0[i];
         return;
       }
+      gen.begin(0);
+      const Rec* ring = gen.take_fwd(0);
       // k = 0: s1 <- 2h j_0 + (7 - d_0) I_0   (numerator of the trapezoidal step)
       {
-        const Rec r = rec[0];
+        const Rec r = ring[0];
 #pragma unroll
         for (int i = 0; i < NI; ++i) {
           if (i < hlo || i > hhi) continue;
@@ -162,7 +219,7 @@ struct Fwd {
       }
       // k = 1: trapezoidal step I_1 = (2h (j_0 + j_1) + (4 - 2h a_0) I_0) / (1 + d_1)
       {
-        const Rec r = rec[1];
+        const Rec r = ring[1];
 #pragma unroll
         for (int i = 0; i < NI; ++i) {
           if (i < hlo || i > hhi) continue;
@@ -171,24 +228,39 @@ struct Fwd {
           s1[i] = relu((s1[i] + jt) * recip((R)1 + d));
         }
       }
-      // BDF2 steps, two per iteration with the state roles swapped
-      int k = 2;
-      for (; k + 1 < K; k += 2) {
-        bdf2_step<LINE>(P, G, lane, rec[k], u, hlo, hhi, s0, s1);      // s0 <- I_k
-        bdf2_step<LINE>(P, G, lane, rec[k + 1], u, hlo, hhi, s1, s0);  // s1 <- I_{k+1}
+      // BDF2 steps, two per iteration with the state roles swapped (chunks
+      // hold 32 samples, so every chunk but the last ends on an even step)
+      int kk = 2, n = min(32, K);
+      for (int k0 = 0;;) {
+#pragma unroll 1
+        for (; kk + 1 < n; kk += 2) {
+          bdf2_step<LINE>(P, G, lane, ring[kk], u, hlo, hhi, s0, s1);      // s0 <- I_k
+          bdf2_step<LINE>(P, G, lane, ring[kk + 1], u, hlo, hhi, s1, s0);  // s1 <- I_{k+1}
+        }
+        if (k0 + 32 >= K) break;
+        k0 += 32;
+        ring = gen.take_fwd(k0);
+        kk = 0;
+        n = min(32, K - k0);
       }
-      if (k < K) {
-        bdf2_step<LINE>(P, G, lane, rec[k], u, hlo, hhi, s0, s1);
+      if (kk < n) {
+        bdf2_step<LINE>(P, G, lane, ring[kk], u, hlo, hhi, s0, s1);
 #pragma unroll
         for (int i = 0; i < NI; ++i) s1[i] = s0[i];
       }
     } else if constexpr (MODE == M_FORMAL) {
-      for (int k = 0; k < K; ++k) {
-        const Rec r = rec[k];
+      if (K > 0) gen.begin(0);
+      for (int k0 = 0; k0 < K; k0 += 32) {
+        const Rec* ring = gen.take_fwd(k0);
+        const int n = min(32, K - k0);
+#pragma unroll 1
+        for (int kk = 0; kk < n; ++kk) {
+          const Rec r = ring[kk];
 #pragma unroll
-        for (int i = 0; i < NI; ++i) {
-          if (i < hlo || i > hhi) continue;
-          s0[i] = formal_step<LINE>(P, G, lane, r, i, u[i], s0[i]);
+          for (int i = 0; i < NI; ++i) {
+            if (i < hlo || i > hhi) continue;
+            s0[i] = formal_step<LINE>(P, G, lane, r, i, u[i], s0[i]);
+          }
         }
       }
 #pragma unroll
@@ -196,32 +268,39 @@ struct Fwd {
     } else {
       // front-to-back formal integration with Kahan-compensated optical depth:
       // s0 = accumulated intensity, s1 = tau to the observer, s2 = compensation;
-      // on entry s0 holds the background, which is added last.
-      R bg[NI];
+      // the background (s0 on entry) is re-evaluated and added last.
 #pragma unroll
       for (int i = 0; i < NI; ++i) {
-        bg[i] = s0[i];
         s0[i] = (R)0;
         s1[i] = (R)0;
         s2[i] = (R)0;
       }
-      for (int k = K - 1; k >= 0; --k) {
-        const Rec r = rec[k];
+      if (K > 0) gen.begin(Gen::last_chunk(K));
+      for (int k0 = Gen::last_chunk(K); k0 >= 0; k0 -= 32) {
+        const Rec* ring = gen.take_bwd(k0);
+        const int n = min(32, K - k0);
+#pragma unroll 1
+        for (int kk = n - 1; kk >= 0; --kk) {
+          const Rec r = ring[kk];
 #pragma unroll
-        for (int i = 0; i < NI; ++i) {
-          if (i < hlo || i > hhi) continue;
-          R jt, tau;
-          coeffs_formal<LINE>(P, G, lane, r, i, u[i], &jt, &tau);
-          s0[i] += jt * psi(tau) * expneg(s1[i]);
-          // Kahan summation of tau
-          const R y = tau - s2[i];
-          const R t = s1[i] + y;
-          s2[i] = (t - s1[i]) - y;
-          s1[i] = t;
+          for (int i = 0; i < NI; ++i) {
+            if (i < hlo || i > hhi) continue;
+            R jt, tau;
+            coeffs_formal<LINE>(P, G, lane, r, i, u[i], &jt, &tau);
+            s0[i] += jt * psi(tau) * expneg(s1[i]);
+            // Kahan summation of tau
+            const R y = tau - s2[i];
+            const R t = s1[i] + y;
+            s2[i] = (t - s1[i]) - y;
+            s1[i] = t;
+          }
         }
       }
 #pragma unroll
-      for (int i = 0; i < NI; ++i) s1[i] = s0[i] + bg[i] * expneg(s1[i]);
+      for (int i = 0; i < NI; ++i) {
+        const R bg = (i >= hlo && i <= hhi) ? planck_k(P, (R)P.t_bg, u[i]) : (R)0;
+        s1[i] = s0[i] + bg * expneg(s1[i]);
+      }
     }
   }
 
@@ -335,7 +414,8 @@ struct Fwd {
   // Continuum basis recurrences (float path): lane 0 -> X0 (unit background,
   // no source), lane 1 -> X1 (source coefficient 0), lane 2 -> X2 (source
   // coefficient 1); other lanes run a zero recurrence.  Returns the final X.
-  static __device__ __forceinline__ float basis(const Rec* rec, int K, int lane) {
+  template <class Gen>
+  static __device__ __forceinline__ float basis(const Gen& gen, int K, int lane) {
     const float m0 = (lane == 0) ? 1.0f : 0.0f;
     const float m1 = (lane == 1) ? 1.0f : 0.0f;
     const float m2 = (lane == 2) ? 1.0f : 0.0f;
@@ -344,40 +424,62 @@ struct Fwd {
       // combination (see the header), so they are not clamped
       float x0 = m0;  // I_0
       if (K <= 1) return x0;
-      const RecS32& r0 = rec[0];
-      const RecS32& r1 = rec[1];
-      const float j0 = fmaf(m2, r0.jd1, m1 * r0.jd0);
-      const float j1 = fmaf(m2, r1.jd1, m1 * r1.jd0);
-      float x1 = (j0 + (7.0f - r0.d0) * x0 + j1) * rcp_approx(1.0f + r1.d0);
-      for (int k = 2; k < K; ++k) {
-        const RecS32& r = rec[k];
-        const float jt = fmaf(m2, r.jd1, m1 * r.jd0);
-        const float x2 = fmaf(4.0f, x1, jt - x0) * rcp_approx(r.d0);
-        x0 = x1;
-        x1 = x2;
+      gen.begin(0);
+      const RecS32* ring = gen.take_fwd(0);
+      float x1;
+      {
+        const RecS32 r0 = ring[0];
+        const RecS32 r1 = ring[1];
+        const float j0 = fmaf(m2, r0.jd1, m1 * r0.jd0);
+        const float j1 = fmaf(m2, r1.jd1, m1 * r1.jd0);
+        x1 = (j0 + (7.0f - r0.d0) * x0 + j1) * rcp_approx(1.0f + r1.d0);
+      }
+      for (int k0 = 0; k0 < K; k0 += 32) {
+        if (k0 > 0) ring = gen.take_fwd(k0);
+        const int n = min(32, K - k0);
+#pragma unroll 1
+        for (int kk = (k0 == 0) ? 2 : 0; kk < n; ++kk) {
+          const RecS32 r = ring[kk];
+          const float jt = fmaf(m2, r.jd1, m1 * r.jd0);
+          const float x2 = fmaf(4.0f, x1, jt - x0) * rcp_approx(r.d0);
+          x0 = x1;
+          x1 = x2;
+        }
       }
       return x1;
     } else if constexpr (MODE == M_FORMAL) {
       float x = m0;
-      for (int k = 0; k < K; ++k) {
-        const RecF32& r = rec[k];
-        const float s = fmaf(m2, r.bk1, m1 * r.bk0);
-        x = fmaf(s - x, r.emD, x);
+      if (K > 0) gen.begin(0);
+      for (int k0 = 0; k0 < K; k0 += 32) {
+        const RecF32* ring = gen.take_fwd(k0);
+        const int n = min(32, K - k0);
+#pragma unroll 1
+        for (int kk = 0; kk < n; ++kk) {
+          const RecF32 r = ring[kk];
+          const float s = fmaf(m2, r.bk1, m1 * r.bk0);
+          x = fmaf(s - x, r.emD, x);
+        }
       }
       return x;
     } else {
       // front-to-back with Kahan-compensated dust optical depth
       float acc = 0.0f, T = 0.0f, c = 0.0f;
-      for (int k = K - 1; k >= 0; --k) {
-        const RecF32& r = rec[k];
-        const float s = fmaf(m2, r.bk1, m1 * r.bk0);
-        acc = fmaf(s * r.emD, ex2_approx(-T * kLog2e), acc);
-        const float y = r.ad - c;
-        const float t = T + y;
-        c = (t - T) - y;
-        T = t;
+      if (K > 0) gen.begin(Gen::last_chunk(K));
+      for (int k0 = Gen::last_chunk(K); k0 >= 0; k0 -= 32) {
+        const RecF32* ring = gen.take_bwd(k0);
+        const int n = min(32, K - k0);
+#pragma unroll 1
+        for (int kk = n - 1; kk >= 0; --kk) {
+          const RecF32 r = ring[kk];
+          const float s = fmaf(m2, r.bk1, m1 * r.bk0);
+          acc = fmaf(s * r.emD, ex2_approx(-T * kLog2e), acc);
+          const float y = r.ad - c;
+          const float t = T + y;
+          c = (t - T) - y;
+          T = t;
+        }
       }
-      return acc + m0 * ex2_approx(-T * kLog2e);
+      return (lane == 0) ? ex2_approx(-T * kLog2e) : acc;
     }
   }
 };
@@ -471,7 +573,8 @@ struct FastSmooth {
 
   // Runs the whole ray; writes the fine intensities of its blocks to fbuf and
   // returns this lane's basis value.
-  static __device__ __forceinline__ float run(const PhysF& P, const RecS32* rec, int K, int hb,
+  template <class Gen>
+  static __device__ __forceinline__ float run(const PhysF& P, const Gen& gen, int K, int hb,
                                               int lane, const VGrid& G, int nfw, float* fbuf) {
     float u[NA], s0[NA], s1[NA];
 #pragma unroll
@@ -486,9 +589,11 @@ struct FastSmooth {
     const float m2 = (lane == 2) ? 1.0f : 0.0f;
     float x0 = m0, x1 = m0;
     if (K >= 2) {
+      gen.begin(0);
+      const RecS32* ring = gen.take_fwd(0);
       // k = 0: s1 <- 2h j_0 + (7 - d_0) I_0
       {
-        const RecS32 r = rec[0];
+        const RecS32 r = ring[0];
         const Slots<NS> sl = slots_smooth<NS>(r, hb, lane, G);
 #pragma unroll
         for (int j = 0; j < NA; ++j) {
@@ -506,7 +611,7 @@ struct FastSmooth {
       }
       // k = 1: trapezoidal step
       {
-        const RecS32 r = rec[1];
+        const RecS32 r = ring[1];
         const Slots<NS> sl = slots_smooth<NS>(r, hb, lane, G);
         const float r1 = rcp_approx(1.0f + r.d0);
         float rl[NS];
@@ -526,13 +631,22 @@ struct FastSmooth {
         }
         x1 = (x1 + fmaf(m2, r.jd1, m1 * r.jd0)) * r1;
       }
-      int k = 2;
-      for (; k + 1 < K; k += 2) {
-        step(rec[k], u, s0, s1, hb, lane, G, x0, x1, m1, m2);
-        step(rec[k + 1], u, s1, s0, hb, lane, G, x1, x0, m1, m2);
+      // BDF2 pairs; every chunk but the last holds an even number of steps
+      int kk = 2, n = min(32, K);
+      for (int k0 = 0;;) {
+#pragma unroll 1
+        for (; kk + 1 < n; kk += 2) {
+          step(ring[kk], u, s0, s1, hb, lane, G, x0, x1, m1, m2);
+          step(ring[kk + 1], u, s1, s0, hb, lane, G, x1, x0, m1, m2);
+        }
+        if (k0 + 32 >= K) break;
+        k0 += 32;
+        ring = gen.take_fwd(k0);
+        kk = 0;
+        n = min(32, K - k0);
       }
-      if (k < K) {
-        step(rec[k], u, s0, s1, hb, lane, G, x0, x1, m1, m2);
+      if (kk < n) {
+        step(ring[kk], u, s0, s1, hb, lane, G, x0, x1, m1, m2);
 #pragma unroll
         for (int j = 0; j < NA; ++j) s1[j] = s0[j];
         x1 = x0;
@@ -549,7 +663,8 @@ struct FastSmooth {
 
 template <int NA, int NS>
 struct FastFormal {
-  static __device__ __forceinline__ float run(const PhysF& P, const RecF32* rec, int K, int hb,
+  template <class Gen>
+  static __device__ __forceinline__ float run(const PhysF& P, const Gen& gen, int K, int hb,
                                               int lane, const VGrid& G, int nfw, float* fbuf) {
     float u[NA], I[NA];
 #pragma unroll
@@ -561,8 +676,12 @@ struct FastFormal {
     const float m1 = (lane == 1) ? 1.0f : 0.0f;
     const float m2 = (lane == 2) ? 1.0f : 0.0f;
     float x = (lane == 0) ? 1.0f : 0.0f;
+    const RecF32* ring = nullptr;
+    if (K > 0) gen.begin(0);
+#pragma unroll 1
     for (int k = 0; k < K; ++k) {
-      const RecF32 r = rec[k];
+      if ((k & 31) == 0) ring = gen.take_fwd(k);
+      const RecF32 r = ring[k & 31];
       const Slots<NS> sl = slots_formal<NS>(r, hb, lane, G);
       float ps[NS];
 #pragma unroll
@@ -592,6 +711,106 @@ struct FastFormal {
   }
 };
 
+// Front-to-back formal transfer with Kahan-compensated optical depth.  The
+// depth to the observer splits into the dust part T_D (frequency independent
+// in the band: one compensated sum per ray, shared by every velocity) and the
+// line part T_L(u) (one compensated sum per fine velocity, kept in shared
+// memory `kb` and touched only on the samples whose line window reaches u).
+// Registers hold the accumulated intensity and EL = exp(-T_L) per block, so a
+// dust-only (sample, block) costs two FMAs; the line slots override the
+// block's emission factor and its EL with predicated selects.
+template <int NA, int NS>
+struct FastKahan {
+  static __device__ __forceinline__ void kahan_add(float& T, float& c, float x) {
+    const float y = x - c;
+    const float t = T + y;
+    c = (t - T) - y;
+    T = t;
+  }
+
+  template <class Gen>
+  static __device__ __forceinline__ float run(const PhysF& P, const Gen& gen, int K, int hb,
+                                              int lane, const VGrid& G, int nfw, float* fbuf,
+                                              float* kb) {
+    float acc[NA], EL[NA];
+    float* TL = kb;             // [32 NA]: compensated line depth, index g - 32 hb
+    float* CL = kb + 32 * NA;   // [32 NA]: its compensation
+#pragma unroll
+    for (int j = 0; j < NA; ++j) {
+      acc[j] = 0.0f;
+      EL[j] = 1.0f;
+      TL[32 * j + lane] = 0.0f;
+      CL[32 * j + lane] = 0.0f;
+    }
+    const float u0 = fmaf((float)(32 * hb + lane), G.dvf_hi, G.ufw_hi);
+    const float du = 32.0f * G.dvf_hi;   // velocity step between a lane's blocks
+    const float m1 = (lane == 1) ? 1.0f : 0.0f;
+    const float m2 = (lane == 2) ? 1.0f : 0.0f;
+    float TD = 0.0f, cD = 0.0f, ED = 1.0f, xb = 0.0f;
+    const RecF32* ring = nullptr;
+    if (K > 0) gen.begin(Gen::last_chunk(K));
+#pragma unroll 1
+    for (int k = K - 1; k >= 0; --k) {
+      if (k == K - 1 || (k & 31) == 31) ring = gen.take_bwd(k & ~31);
+      const RecF32 r = ring[k & 31];
+      // line slots: emission factor and the updated EL of the slot's velocity
+      const int glo = win_lo(r.win), ghi = win_hi(r.win);
+      const int g0 = glo + ((lane - glo) & 31);
+      int sj[NS];
+      float sA[NS], sE[NS];
+#pragma unroll
+      for (int q = 0; q < NS; ++q) {
+        const int g = g0 + 32 * q;
+        const float ug = fmaf((float)g, G.dvf_hi, G.ufw_hi);
+        const float dd = vel_offset(G, g, r.gv, r.vr);
+        const float e = ex2_approx(dd * r.nib2 * dd);
+        const float tl = r.al * e;
+        const float a = fmaf(r.jl, e, r.ad * fmaf(r.bk1, ug, r.bk0));
+        sA[q] = a * psi_f(tl + r.ad) * ED;
+        sj[q] = -1;
+        sE[q] = 1.0f;
+        if (g <= ghi) {
+          const int idx = g - 32 * hb;
+          float T = TL[idx], c = CL[idx];
+          kahan_add(T, c, tl);
+          TL[idx] = T;
+          CL[idx] = c;
+          sj[q] = (g >> 5) - hb;
+          sE[q] = ex2_approx(-T * kLog2e);
+        }
+      }
+      // dust-only emission factor of block j: emD ED (bk0 + bk1 u_j)
+      const float w = r.emD * ED;
+      const float c0 = w * fmaf(r.bk1, u0, r.bk0);
+      const float c1 = w * r.bk1 * du;
+#pragma unroll
+      for (int j = 0; j < NA; ++j) {
+        float A = fmaf((float)j, c1, c0);
+        float En = EL[j];
+#pragma unroll
+        for (int q = 0; q < NS; ++q) {
+          const bool p = sj[q] == j;
+          A = p ? sA[q] : A;
+          En = p ? sE[q] : En;
+        }
+        acc[j] = fmaf(A, EL[j], acc[j]);
+        EL[j] = En;
+      }
+      // continuum basis: lane 1 sums bk0 w, lane 2 sums bk1 w
+      xb = fmaf(fmaf(m2, r.bk1, m1 * r.bk0), w, xb);
+      kahan_add(TD, cD, r.ad);
+      ED = ex2_approx(-TD * kLog2e);
+    }
+#pragma unroll
+    for (int j = 0; j < NA; ++j) {
+      const int g = 32 * (hb + j) + lane;
+      const float u = fmaf((float)g, G.dvf_hi, G.ufw_hi);
+      if (g < nfw) fbuf[g] = fmaf(planck_k(P, P.t_bg, u) * ED, EL[j], acc[j]);
+    }
+    return (lane == 0) ? ED : xb;
+  }
+};
+
 // Block-count buckets of the fast path (a hull of na blocks runs in the
 // smallest bucket >= na).
 __device__ __forceinline__ int fast_bucket(int na, int ns) {
@@ -616,18 +835,19 @@ __device__ __forceinline__ int fast_bucket(int na, int ns) {
 
 // Runs the fast path for bucket `nb` (<= NI); returns false if nb is not
 // compiled for this NI.
-template <int NI, int MODE, int NS>
-__device__ __forceinline__ bool run_fast(int nb, const PhysF& P,
-                                         const typename RecOf<float, MODE>::type* rec, int K,
-                                         int hb, int lane, const VGrid& G, int nfw, float* fbuf,
-                                         float* xb) {
+template <int NI, int MODE, int NS, class Gen>
+__device__ __forceinline__ bool run_fast(int nb, const PhysF& P, const Gen& gen, int K, int hb,
+                                         int lane, const VGrid& G, int nfw, float* fbuf,
+                                         float* kb, float* xb) {
 #define IRT_FAST(NA_)                                                                        \
   case NA_:                                                                                  \
     if constexpr (NA_ <= NI) {                                                               \
       if constexpr (MODE == M_SMOOTH)                                                        \
-        *xb = FastSmooth<NA_, NS>::run(P, rec, K, hb, lane, G, nfw, fbuf);                  \
+        *xb = FastSmooth<NA_, NS>::run(P, gen, K, hb, lane, G, nfw, fbuf);                  \
+      else if constexpr (MODE == M_FORMAL)                                                   \
+        *xb = FastFormal<NA_, NS>::run(P, gen, K, hb, lane, G, nfw, fbuf);                  \
       else                                                                                   \
-        *xb = FastFormal<NA_, NS>::run(P, rec, K, hb, lane, G, nfw, fbuf);                  \
+        *xb = FastKahan<NA_, NS>::run(P, gen, K, hb, lane, G, nfw, fbuf, kb);               \
       return true;                                                                           \
     }                                                                                        \
     return false;
@@ -663,13 +883,14 @@ template <> struct PSel<false> {
 // ---------------------------------------------------------------------------
 template <typename R, int NI, int ST, int MODE>
 __device__ void render_item(const JobDev& J, const PhysParams& PD, const PhysF& PF, int px,
-                            int py, int win, unsigned char* wsm, int fw_off, int cw_off, int lane,
+                            int py, int win, unsigned char* wsm, int fw_off, int cw_off,
+                            int kb_off, typename RecOf<R, MODE>::type* grec, int lane,
                             unsigned flags, unsigned long long* stats) {
   using F = Fwd<R, NI, MODE>;
   using Rec = typename F::Rec;
+  using Gen = RecStream<Rec>;
   constexpr bool kDouble = F::kDouble;
   const auto& P = PSel<kDouble>::get(PD, PF);
-  Rec* rec = reinterpret_cast<Rec*>(wsm);
   R* fbuf = reinterpret_cast<R*>(wsm + fw_off);
   R* cbuf = reinterpret_cast<R*>(wsm + cw_off);
 
@@ -690,7 +911,9 @@ __device__ void render_item(const JobDev& J, const PhysParams& PD, const PhysF& 
     G.dvf_lo = (float)(J.dvf - (double)G.dvf_hi);
   }
 
-  // ---- sample pass
+  // ---- sample pass: lane l evaluates samples l, l + 32, ... into this warp's
+  // record slot; the hull of the line windows, the widest window and the
+  // largest dust step depth come along
   const RayGeom geo = ray_geom(J, px, py);
   const int K = geo.K;
   const R h = (R)geo.h;
@@ -700,28 +923,27 @@ __device__ void render_item(const JobDev& J, const PhysParams& PD, const PhysF& 
   }
   int hlo = 1 << 20, hhi = -1, wmax = 0;
   R admax = (R)0;
+  unsigned long long nline = 0;
   for (int k0 = 0; k0 < K; k0 += 32) {
     const int k = k0 + lane;
-    R raw[5];
-    R ad = (R)0;
-    if constexpr (kDouble) {
-      if (k < K) {
-        sample_raw<ST>(J, geo, px, py, k, raw);
-        ad = make_record<MODE>(PD, raw, h, nfw, &rec[k]);
-      }
-    } else {
-      if (k < K) {
-        sample_raw<ST>(J, rp, px, py, k, raw);
-        ad = make_record<MODE>(PF, raw, h, G, nfw, &rec[k]);
-      }
-    }
     if (k < K) {
-      const int w = rec[k].win;
-      const int lo = win_lo(w), hi = win_hi(w);
+      R raw[5];
+      Rec r;
+      R ad;
+      if constexpr (kDouble) {
+        sample_raw<ST>(J, geo, px, py, k, raw);
+        ad = make_record<MODE>(PD, raw, h, nfw, &r);
+      } else {
+        sample_raw<ST>(J, rp, px, py, k, raw);
+        ad = make_record<MODE>(PF, raw, h, G, nfw, &r);
+      }
+      grec[k] = r;
+      const int lo = win_lo(r.win), hi = win_hi(r.win);
       if (lo <= hi) {
         hlo = min(hlo, lo >> 5);
         hhi = max(hhi, hi >> 5);
         wmax = max(wmax, hi - lo + 1);
+        nline += (unsigned long long)((hi >> 5) - (lo >> 5) + 1);
       }
       admax = fmax(admax, ad);
     }
@@ -733,7 +955,9 @@ __device__ void render_item(const JobDev& J, const PhysParams& PD, const PhysF& 
     wmax = max(wmax, __shfl_xor_sync(0xffffffffu, wmax, o));
     admax = fmax(admax, __shfl_xor_sync(0xffffffffu, admax, o));
   }
-  __syncwarp();
+  // the records are read back by the lane that wrote them (cp.async)
+  __threadfence_block();
+  const Gen gen{grec, reinterpret_cast<Rec*>(wsm), K, lane};
 
   const bool explicit_all = kDouble || (flags & IRT_FLAG_EXPLICIT_CHANNELS) ||
                             (MODE == M_SMOOTH && admax > (R)0.5);
@@ -742,13 +966,6 @@ __device__ void render_item(const JobDev& J, const PhysParams& PD, const PhysF& 
     hhi = nblk - 1;
   }
   if (stats) {
-    // work counters: line-reached (sample, block) pairs from the records
-    unsigned long long nline = 0;
-    for (int k = lane; k < K; k += 32) {
-      const int w = rec[k].win;
-      const int lo = win_lo(w), hi = win_hi(w);
-      if (lo <= hi) nline += (unsigned long long)((hi >> 5) - (lo >> 5) + 1);
-    }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) nline += __shfl_xor_sync(0xffffffffu, nline, o);
     if (lane == 0) {
@@ -766,7 +983,7 @@ __device__ void render_item(const JobDev& J, const PhysParams& PD, const PhysF& 
   R X0 = (R)0, X1 = (R)0, X2 = (R)0;
   bool fast = false;
   int hb = 0, nb = 0;
-  if constexpr (!kDouble && MODE != M_FORMAL_KAHAN) {
+  if constexpr (!kDouble) {
     const int ns = (wmax <= 32) ? 1 : ((wmax <= 64) ? 2 : 3);
     if (!explicit_all && ns <= 2) {
       const bool none = hhi < hlo;
@@ -775,8 +992,10 @@ __device__ void render_item(const JobDev& J, const PhysParams& PD, const PhysF& 
       if (nb <= NI) {
         hb = none ? 0 : min(hlo, max(nblk - nb, 0));
         float xb = 0.0f;
-        fast = (ns == 1) ? run_fast<NI, MODE, 1>(nb, PF, rec, K, hb, lane, G, nfw, fbuf, &xb)
-                         : run_fast<NI, MODE, 2>(nb, PF, rec, K, hb, lane, G, nfw, fbuf, &xb);
+        float* kb = reinterpret_cast<float*>(wsm + kb_off);
+        fast = (ns == 1)
+                   ? run_fast<NI, MODE, 1>(nb, PF, gen, K, hb, lane, G, nfw, fbuf, kb, &xb)
+                   : run_fast<NI, MODE, 2>(nb, PF, gen, K, hb, lane, G, nfw, fbuf, kb, &xb);
         if (fast) {
           X0 = __shfl_sync(0xffffffffu, xb, 0);
           X1 = __shfl_sync(0xffffffffu, xb, 1);
@@ -801,10 +1020,10 @@ __device__ void render_item(const JobDev& J, const PhysParams& PD, const PhysF& 
       s1[i] = (R)0;
       s2[i] = (R)0;
     }
-    F::template transfer<true>(P, G, lane, rec, K, u, hlo, hhi, s0, s1, s2);
+    F::template transfer<true>(P, G, lane, gen, K, u, hlo, hhi, s0, s1, s2);
     if constexpr (!kDouble) {
       if (!explicit_all) {
-        const float xb = F::basis(rec, K, lane);
+        const float xb = F::basis(gen, K, lane);
         X0 = __shfl_sync(0xffffffffu, xb, 0);
         X1 = __shfl_sync(0xffffffffu, xb, 1);
         X2 = __shfl_sync(0xffffffffu, xb, 2);
@@ -838,7 +1057,7 @@ __device__ void render_item(const JobDev& J, const PhysParams& PD, const PhysF& 
       s1[i] = (R)0;
       s2[i] = (R)0;
     }
-    F::template transfer<false>(P, G, lane, rec, K, uc, 0, cblk - 1, s0, s1, s2);
+    F::template transfer<false>(P, G, lane, gen, K, uc, 0, cblk - 1, s0, s1, s2);
 #pragma unroll
     for (int i = 0; i < NI; ++i) {
       const int c = lane + 32 * i;
@@ -886,18 +1105,25 @@ template <typename R, int NI, int ST, int MODE>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32, (sizeof(R) == 4 && NI <= 17) ? 4 : 1)
 fwd_kernel(const __grid_constant__ JobTable tab, int njobs, const PhysParams PD, const PhysF PF,
            long long total_items, unsigned long long* queue, int per_warp, int fw_off, int cw_off,
-           unsigned flags, unsigned long long* stats) {
+           int kb_off, unsigned flags, unsigned long long* stats, unsigned char* rscr,
+           long long rstride) {
+  using Rec = typename RecOf<R, MODE>::type;
   extern __shared__ __align__(16) unsigned char smem[];
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
   unsigned char* wsm = smem + (size_t)warp * per_warp;
-  long long item;
+  // persistent: every warp owns one global record slot.  With a queue, warps
+  // pull work items until it runs dry (uneven batches); without one they take
+  // items round-robin, so that the warps of a block render neighbouring rays
+  // at the same time (one job: measured faster than the queue).
+  const long long gw = (long long)blockIdx.x * kWarpsPerBlock + warp;
+  const long long nw = (long long)gridDim.x * kWarpsPerBlock;
+  Rec* grec = reinterpret_cast<Rec*>(rscr + gw * rstride);
+  long long item = gw;
   if (queue) {
     unsigned long long t = 0;
     if (lane == 0) t = atomicAdd(queue, 1ull);
     item = (long long)__shfl_sync(0xffffffffu, t, 0);
-  } else {
-    item = (long long)blockIdx.x * kWarpsPerBlock + warp;
   }
   while (item < total_items) {
     int j = 0;
@@ -915,51 +1141,58 @@ fwd_kernel(const __grid_constant__ JobTable tab, int njobs, const PhysParams PD,
     const int py = (int)(tile / J.ntx) * J.th + within / J.tw;
     if constexpr (ST == ST_F64 || sizeof(R) == 4) {
       if (px < J.npx && py < J.npy)
-        render_item<R, NI, ST, MODE>(J, PD, PF, px, py, win, wsm, fw_off, cw_off, lane, flags,
-                                     stats);
+        render_item<R, NI, ST, MODE>(J, PD, PF, px, py, win, wsm, fw_off, cw_off, kb_off, grec,
+                                     lane, flags, stats);
     }
     if (queue) {
       unsigned long long t = 0;
       if (lane == 0) t = atomicAdd(queue, 1ull);
       item = (long long)__shfl_sync(0xffffffffu, t, 0);
     } else {
-      break;
+      item += nw;
     }
   }
 }
 
 }  // namespace dev
 
-// Host-side launcher of one kernel instance.
+// Host-side launcher of one kernel instance (persistent).  The block count
+// is the resident maximum, capped by the record scratch: each warp needs kmax
+// records.  L.queue (zero at launch) selects the dynamic schedule, nullptr the
+// round-robin one.
 template <typename R, int NI, int ST, int MODE>
 int launch_fwd_inst(const JobTable& tab, int njobs, const PhysParams& P, const PhysF& PF,
-                    long long total_items, unsigned long long* queue, int grid_blocks, int kmax,
-                    int fwmax, int cwmax, unsigned flags, unsigned long long* stats,
-                    cudaStream_t stream) {
+                    const FwdLaunch& L, cudaStream_t stream) {
   using Rec = typename dev::RecOf<R, MODE>::type;
-  const int rec_bytes = (int)sizeof(Rec) * kmax;
-  const int fw_off = (rec_bytes + 15) & ~15;
-  const int cw_off = (fw_off + (int)sizeof(R) * fwmax + 15) & ~15;
-  const int per_warp = (cw_off + (int)sizeof(R) * cwmax + 15) & ~15;
+  if (L.total <= 0) return 0;
+  if (!L.rscr) return (int)cudaErrorInvalidValue;
+  // per warp: record ring (2 x 32), fine and channel buffers, Kahan line depths
+  const int ring_bytes = 2 * 32 * (int)sizeof(Rec);
+  const int fw_off = (ring_bytes + 15) & ~15;
+  const int cw_off = (fw_off + (int)sizeof(R) * L.fwmax + 15) & ~15;
+  const int kb_off = (cw_off + (int)sizeof(R) * L.cwmax + 15) & ~15;
+  const int kb_bytes = (sizeof(R) == 4 && MODE == M_FORMAL_KAHAN) ? 2 * 32 * NI * 4 : 0;
+  const int per_warp = (kb_off + kb_bytes + 15) & ~15;
   const size_t smem = (size_t)per_warp * kWarpsPerBlock;
+  const long long rstride = ((long long)L.kmax * (long long)sizeof(Rec) + 255) & ~255ll;
   auto kern = dev::fwd_kernel<R, NI, ST, MODE>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return (int)e;
-  long long blocks = grid_blocks;
-  if (!queue) {
-    blocks = (total_items + kWarpsPerBlock - 1) / kWarpsPerBlock;
-  } else if (blocks <= 0) {
+  long long blocks = L.grid_blocks;
+  if (blocks <= 0) {
     int per_sm = 0, sms = 0, dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kWarpsPerBlock * 32, smem);
     blocks = (long long)std::max(per_sm, 1) * sms;
   }
-  if (blocks < 1) return 0;
-  kern<<<(unsigned)blocks, kWarpsPerBlock * 32, smem, stream>>>(tab, njobs, P, PF, total_items,
-                                                                 queue, per_warp, fw_off, cw_off,
-                                                                 flags, stats);
+  blocks = std::min(blocks, (long long)(L.rbytes / ((size_t)rstride * kWarpsPerBlock)));
+  blocks = std::min(blocks, (L.total + kWarpsPerBlock - 1) / kWarpsPerBlock);
+  if (blocks < 1) return (int)cudaErrorInvalidValue;   // scratch below one block
+  kern<<<(unsigned)blocks, kWarpsPerBlock * 32, smem, stream>>>(
+      tab, njobs, P, PF, L.total, L.queue, per_warp, fw_off, cw_off, kb_off, L.flags, L.stats,
+      L.rscr, rstride);
   return (int)cudaGetLastError();
 }
 

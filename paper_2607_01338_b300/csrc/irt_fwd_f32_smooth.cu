@@ -4,14 +4,11 @@
 namespace irt {
 
 int dispatch_fwd_f32_smooth(int store, int ni, const JobTable& jobs, int njobs,
-                             const PhysParams& P, const PhysF& PF, long long total, unsigned long long* queue,
-                             int grid_blocks, int kmax, int fwmax, int cwmax, unsigned flags,
-                             unsigned long long* stats,
-                             cudaStream_t s) {
+                           const PhysParams& P, const PhysF& PF, const FwdLaunch& L,
+                           cudaStream_t s) {
 #define IRT_CASE(NI_, ST_)                                                                  \
   if (ni == NI_ && store == ST_)                                                            \
-    return launch_fwd_inst<float, NI_, ST_, M_SMOOTH>(jobs, njobs, P, PF, total, queue, grid_blocks, \
-                                                  kmax, fwmax, cwmax, flags, stats, s);
+    return launch_fwd_inst<float, NI_, ST_, M_SMOOTH>(jobs, njobs, P, PF, L, s);
   IRT_CASE(9, ST_F32) IRT_CASE(17, ST_F32) IRT_CASE(33, ST_F32)
   IRT_CASE(9, ST_H16) IRT_CASE(17, ST_H16) IRT_CASE(33, ST_H16)
   IRT_CASE(9, ST_F64) IRT_CASE(17, ST_F64) IRT_CASE(33, ST_F64)

@@ -5,19 +5,14 @@
 namespace irt {
 
 int dispatch_fwd_f64(int mode, int store, int ni, const JobTable& jobs, int njobs,
-                     const PhysParams& P, const PhysF& PF, long long total, unsigned long long* queue,
-                     int grid_blocks, int kmax, int fwmax, int cwmax, unsigned flags,
-                     unsigned long long* stats, cudaStream_t s) {
+                     const PhysParams& P, const PhysF& PF, const FwdLaunch& L,
+                     cudaStream_t s) {
   if (store != ST_F64 || ni != 17) return (int)cudaErrorInvalidValue;
   if (mode == M_SMOOTH)
-    return launch_fwd_inst<double, 17, ST_F64, M_SMOOTH>(jobs, njobs, P, PF, total, queue,
-                                                         grid_blocks, kmax, fwmax, cwmax, flags, stats, s);
+    return launch_fwd_inst<double, 17, ST_F64, M_SMOOTH>(jobs, njobs, P, PF, L, s);
   if (mode == M_FORMAL)
-    return launch_fwd_inst<double, 17, ST_F64, M_FORMAL>(jobs, njobs, P, PF, total, queue,
-                                                         grid_blocks, kmax, fwmax, cwmax, flags, stats, s);
-  return launch_fwd_inst<double, 17, ST_F64, M_FORMAL_KAHAN>(jobs, njobs, P, PF, total, queue,
-                                                             grid_blocks, kmax, fwmax, cwmax,
-                                                             flags, stats, s);
+    return launch_fwd_inst<double, 17, ST_F64, M_FORMAL>(jobs, njobs, P, PF, L, s);
+  return launch_fwd_inst<double, 17, ST_F64, M_FORMAL_KAHAN>(jobs, njobs, P, PF, L, s);
 }
 
 }  // namespace irt

@@ -78,6 +78,11 @@ struct JobDev {
 
 constexpr int kWarpsPerBlock = 4;
 constexpr int kMaxJobs = 64;
+// Forward per-sample record sizes (float and double kernels) and the most
+// warps a forward kernel keeps resident on one SM (128 registers a thread).
+constexpr int kRecBytesF32 = 48;
+constexpr int kRecBytesF64 = 64;
+constexpr int kFwdWarpsPerSm = 16;
 
 // Adjoint: checkpoint spacing and stored sub-segment (samples), warps per
 // block, chain-rule factors per sample.
@@ -101,6 +106,19 @@ struct JobTable {
 
 // Launch entry points implemented in the .cu files.
 // Returns a cudaError_t value (0 = success).
+
+// Launch arguments of one forward kernel instance.
+struct FwdLaunch {
+  long long total;             // work items of the job table
+  unsigned long long* queue;   // work-queue counter, zero at launch (nullptr: round-robin)
+  int grid_blocks;             // 0: as many blocks as are resident at once
+  int kmax;                    // most samples on a ray of the table
+  int fwmax, cwmax;            // most fine velocities / channels of a window
+  unsigned flags;
+  unsigned long long* stats;   // 6 work counters or nullptr
+  unsigned char* rscr;         // per-warp sample records (global memory)
+  size_t rbytes;               // size of rscr; bounds the resident warps
+};
 
 int launch_pack(int store, const void* const* src, const int* dtypes, const double* scale,
                 void* cells, long long ncell, void* stream);

@@ -108,7 +108,7 @@ def test_ragged_oblique_view(integration):
     assert_parity(gpu, orc, pix)
 
 
-@pytest.mark.parametrize("integration", ["smooth", "formal"])
+@pytest.mark.parametrize("integration", ["smooth", "formal", "formal_kahan"])
 def test_many_windows_and_f0(integration):
     fs = small_fields((20, 12, 14), seed=21)
     f32, deq = to_storage(fs, np.float32)
@@ -116,6 +116,33 @@ def test_many_windows_and_f0(integration):
     view = View(0.0, 0.0, 14, 12, dx, 0)
     for va in (VelocityAxis(600, -150.0, 0.5, 1), VelocityAxis(1200, -150.0, 0.25, 0),
                VelocityAxis(90, -120.0, 3.0, 3)):
+        gpu = gpu_render(torch_fields(f32), dx, view, va, LINE, DUST, integration=integration)
+        pix = all_pixels(view.npx, view.npy)
+        orc = oracle_pixels(deq.as_tuple(), dx, view, va, LINE, DUST, pix,
+                            integration=integration)
+        assert_parity(gpu, orc, pix)
+
+
+def long_column(nz, ny, nx, seed):
+    """A tall column: 32^3 fields of several seeds stacked along z."""
+    from synth import FieldSet
+    parts = [make_fields(32, seed + i).as_tuple() for i in range((nz + 31) // 32)]
+    arrs = [np.concatenate([p[q] for p in parts], axis=0)[:nz, :ny, :nx].copy()
+            for q in range(5)]
+    return FieldSet(*arrs)
+
+
+@pytest.mark.parametrize("integration", ["smooth", "formal", "formal_kahan"])
+def test_long_rays_stream_their_records(integration):
+    """Rays of 700 and about 560 samples: longer than the records a warp keeps
+    in shared memory, so the tail of each ray streams through global memory
+    (forward sweeps, and the backward sweep of the Kahan transfer)."""
+    fs = long_column(700, 5, 4, seed=61)
+    f32, deq = to_storage(fs, np.float32)
+    dx = 0.1 * PC
+    va = VelocityAxis(96, -48.0, 1.0, 1)
+    for view in (View(0.0, 0.0, 4, 5, dx, 0),
+                 View(math.radians(0.15), math.radians(30.0), 6, 6, 0.6 * dx, 1)):
         gpu = gpu_render(torch_fields(f32), dx, view, va, LINE, DUST, integration=integration)
         pix = all_pixels(view.npx, view.npy)
         orc = oracle_pixels(deq.as_tuple(), dx, view, va, LINE, DUST, pix,
@@ -138,7 +165,7 @@ def test_explicit_channels_flag_matches_shortcut(integration):
     assert_parity(b, orc, pix)
 
 
-@pytest.mark.parametrize("integration", ["smooth", "formal"])
+@pytest.mark.parametrize("integration", ["smooth", "formal", "formal_kahan"])
 def test_dense_dusty_fallback(integration):
     """kappa x 3000 on dense gas: h alpha_D > 1/2 on some samples, so the
     smooth path integrates every channel explicitly."""

@@ -3,8 +3,9 @@
 Some callers may not allocate device memory: a plugin whose host application
 owns every device buffer, or a real-time loop that must neither wait on the
 allocator nor risk running out of memory once it is running.  For them the
-library packs the fields into a fixed device array it owns (32 MiB plus 256
-bytes of control words) instead of a grid from irt_create_grid.  These tests
+library packs the fields into a fixed device array it owns (32 MiB of cells,
+16 MiB of sample records and 256 bytes of control words) instead of a grid
+from irt_create_grid.  These tests
 call that entry point through the C ABI and compare it with the regular path
 (irt_create_grid + irt_forward_ppv) on two calls in a row, the second call
 reusing the array the first one filled.
