@@ -10,6 +10,7 @@
 #include <cstdarg>
 #include <cstring>
 #include <mutex>
+#include <numeric>
 #include <string>
 #include <vector>
 
@@ -272,6 +273,12 @@ irt_status check_job(const irt_job& jb, int precision) {
   if (!std::isfinite(va.v_first_edge_kms)) return fail(IRT_EINVAL, "v_first_edge not finite");
   if (va.subsample_f < 0) return fail(IRT_EINVAL, "subsample_f < 0");
   if (va.subsample_f > 64) return fail(IRT_EUNSUPPORTED, "subsample_f > 64");
+  {
+    // fine velocity indices of the whole axis are kept in 16 bits
+    const long long nfw = va.subsample_f >= 1 ? 2LL * va.subsample_f * va.nchan + 1 : va.nchan;
+    if (nfw > 32000)
+      return fail(IRT_EUNSUPPORTED, "%lld fine velocities (2 f nchan + 1) exceed 32000", nfw);
+  }
   const irt_view& vw = jb.view;
   if (vw.trilinear == 0) {
     if (vw.theta_rad != 0.0 || vw.phi_rad != 0.0)
@@ -308,9 +315,14 @@ Plan plan_job(const irt_job& jb, int precision, int force_ni) {
   Plan p;
   const int f = jb.vaxis.subsample_f, nch = jb.vaxis.nchan;
   auto fine_of = [&](int cw) { return f >= 1 ? 2 * f * cw + 1 : cw; };
+  // channels of a window of ni register blocks (general path); windows start
+  // on a 32-velocity block boundary (2 f cw a multiple of 32)
   auto cw_for = [&](int ni) {
     const int slots = 32 * ni;
-    return f >= 1 ? (slots - 1) / (2 * f) : slots;
+    if (f < 1) return slots;
+    const int cw = (slots - 1) / (2 * f);
+    const int q = 32 / std::gcd(2 * f, 32);
+    return std::max(cw - cw % q, 1);
   };
   if (precision == IRT_PREC_F64) {
     p.ni = 17;
@@ -319,7 +331,7 @@ Plan plan_job(const irt_job& jb, int precision, int force_ni) {
   } else {
     p.ni = 33;
     for (int ni : kNiF32)
-      if (fine_of(nch) <= 32 * ni) { p.ni = ni; break; }
+      if (nch <= cw_for(ni)) { p.ni = ni; break; }
   }
   p.cw = std::min(nch, cw_for(p.ni));
   p.nwin = (nch + p.cw - 1) / p.cw;
@@ -389,7 +401,7 @@ JobDev make_jobdev(const irt_job& jb, const Plan& p) {
   d.th = std::max(1, p.th);
   d.ntx = (d.npx + d.tw - 1) / d.tw;
   const long long nty = (d.npy + d.th - 1) / d.th;
-  d.nitems = (long long)d.ntx * d.tw * nty * d.th * d.nwin;
+  d.nitems = (long long)d.ntx * d.tw * nty * d.th;   // one item per ray (tile padding included)
   return d;
 }
 
@@ -603,27 +615,14 @@ irt_status run_forward(const irt_job* jobs, int njobs, const PhysParams& P, cons
 }
 
 // Times the candidate plans on the given stream (synchronous) and returns the
-// fastest.  Candidates: window sizes NI = 9, 17, 33 (where they hold the
-// channel count of some job in few windows) x ray tiles 1x1, 2x2, 4x1, 4x4.
+// fastest.  Candidates: register blocks NI = 9, 17, 33 (the widest line hull
+// the fast path holds, and the window of the general path) x ray tiles 1x1,
+// 2x2, 4x1, 4x4.
 irt_status autotune(const irt_job* jobs, int njobs, const PhysParams& P, const PhysF& PF,
                     const irt_opts* opts, cudaStream_t s, Tuned* best) {
-  int ni_min = 9;
-  {
-    // smallest NI that still needs at most 4 windows for every job
-    for (int ni : {9, 17, 33}) {
-      bool ok = true;
-      for (int j = 0; j < njobs && ok; ++j) {
-        const Plan p = plan_job(jobs[j], opts->precision, ni);
-        ok = p.nwin <= 4;
-      }
-      if (ok) { ni_min = ni; break; }
-      ni_min = 33;
-    }
-  }
   std::vector<Tuned> cands;
   const int tiles[4][2] = {{1, 1}, {2, 2}, {4, 1}, {4, 4}};
   for (int ni : {9, 17, 33}) {
-    if (ni < ni_min) continue;
     for (const auto& t : tiles) {
       Tuned c;
       c.ni = ni;

@@ -192,10 +192,12 @@ struct Fwd {
 
   // Total-intensity transfer of the hull blocks [hlo, hhi] (or, with
   // line == false, dust-only transfer of the blocks at velocities u[]).
-  // Records come from `gen` in chunks of 32 samples.  On return s1[i] holds
-  // the final intensity of block i.
+  // Records come from `gen` in chunks of 32 samples.  lg = lane + 32 x the
+  // global index of register block 0, so that register block i of this lane
+  // holds the global fine velocity 32 i + lg (records carry global indices).
+  // On return s1[i] holds the final intensity of block i.
   template <bool LINE, class Gen>
-  static __device__ __forceinline__ void transfer(const PP& P, const VGrid& G, int lane,
+  static __device__ __forceinline__ void transfer(const PP& P, const VGrid& G, int lg,
                                                   const Gen& gen, int K, const R* u, int hlo,
                                                   int hhi, R* s0, R* s1, R* s2) {
     if constexpr (MODE == M_SMOOTH) {
@@ -213,7 +215,7 @@ struct Fwd {
         for (int i = 0; i < NI; ++i) {
           if (i < hlo || i > hhi) continue;
           R jt, d;
-          coeffs<LINE>(P, G, lane, r, i, u[i], &jt, &d);
+          coeffs<LINE>(P, G, lg, r, i, u[i], &jt, &d);
           s1[i] = jt + ((R)7 - d) * s0[i];
         }
       }
@@ -224,7 +226,7 @@ struct Fwd {
         for (int i = 0; i < NI; ++i) {
           if (i < hlo || i > hhi) continue;
           R jt, d;
-          coeffs<LINE>(P, G, lane, r, i, u[i], &jt, &d);
+          coeffs<LINE>(P, G, lg, r, i, u[i], &jt, &d);
           s1[i] = relu((s1[i] + jt) * recip((R)1 + d));
         }
       }
@@ -234,8 +236,8 @@ struct Fwd {
       for (int k0 = 0;;) {
 #pragma unroll 1
         for (; kk + 1 < n; kk += 2) {
-          bdf2_step<LINE>(P, G, lane, ring[kk], u, hlo, hhi, s0, s1);      // s0 <- I_k
-          bdf2_step<LINE>(P, G, lane, ring[kk + 1], u, hlo, hhi, s1, s0);  // s1 <- I_{k+1}
+          bdf2_step<LINE>(P, G, lg, ring[kk], u, hlo, hhi, s0, s1);      // s0 <- I_k
+          bdf2_step<LINE>(P, G, lg, ring[kk + 1], u, hlo, hhi, s1, s0);  // s1 <- I_{k+1}
         }
         if (k0 + 32 >= K) break;
         k0 += 32;
@@ -244,7 +246,7 @@ struct Fwd {
         n = min(32, K - k0);
       }
       if (kk < n) {
-        bdf2_step<LINE>(P, G, lane, ring[kk], u, hlo, hhi, s0, s1);
+        bdf2_step<LINE>(P, G, lg, ring[kk], u, hlo, hhi, s0, s1);
 #pragma unroll
         for (int i = 0; i < NI; ++i) s1[i] = s0[i];
       }
@@ -259,7 +261,7 @@ struct Fwd {
 #pragma unroll
           for (int i = 0; i < NI; ++i) {
             if (i < hlo || i > hhi) continue;
-            s0[i] = formal_step<LINE>(P, G, lane, r, i, u[i], s0[i]);
+            s0[i] = formal_step<LINE>(P, G, lg, r, i, u[i], s0[i]);
           }
         }
       }
@@ -286,7 +288,7 @@ struct Fwd {
           for (int i = 0; i < NI; ++i) {
             if (i < hlo || i > hhi) continue;
             R jt, tau;
-            coeffs_formal<LINE>(P, G, lane, r, i, u[i], &jt, &tau);
+            coeffs_formal<LINE>(P, G, lg, r, i, u[i], &jt, &tau);
             s0[i] += jt * psi(tau) * expneg(s1[i]);
             // Kahan summation of tau
             const R y = tau - s2[i];
@@ -317,7 +319,7 @@ struct Fwd {
 
   // smooth-mode coefficients (2h j, 3 + 2h alpha) of block i at velocity u
   template <bool LINE>
-  static __device__ __forceinline__ void coeffs(const PP& P, const VGrid& G, int lane,
+  static __device__ __forceinline__ void coeffs(const PP& P, const VGrid& G, int lg,
                                                 const Rec& r, int i, R u, R* jt, R* d) {
     if constexpr (kDouble) {
       const double bk = planck_k(P, r.td, u);
@@ -332,8 +334,8 @@ struct Fwd {
         *d = 3.0 + two_ad;
       }
     } else {
-      if (LINE && block_in_window(i, r.win)) {
-        coeff_line(r, G, 32 * i + lane, u, jt, d);
+      if (LINE && block_in_window(i + (lg >> 5), r.win)) {
+        coeff_line(r, G, 32 * i + lg, u, jt, d);
       } else {
         *jt = fmaf(r.jd1, u, r.jd0);
         *d = r.d0;
@@ -342,7 +344,7 @@ struct Fwd {
   }
 
   template <bool LINE>
-  static __device__ __forceinline__ void bdf2_step(const PP& P, const VGrid& G, int lane,
+  static __device__ __forceinline__ void bdf2_step(const PP& P, const VGrid& G, int lg,
                                                    const Rec& r, const R* u, int hlo, int hhi,
                                                    R* sa, const R* sb) {
     // sa holds I_{n}, sb holds I_{n+1}; sa <- I_{n+2}
@@ -353,11 +355,11 @@ struct Fwd {
       if (i < hlo || i > hhi) continue;
       R jt, d, rd;
       if constexpr (kDouble) {
-        coeffs<LINE>(P, G, lane, r, i, u[i], &jt, &d);
+        coeffs<LINE>(P, G, lg, r, i, u[i], &jt, &d);
         rd = (R)1 / d;
       } else {
-        if (LINE && block_in_window(i, r.win)) {
-          coeff_line(r, G, 32 * i + lane, u[i], &jt, &d);
+        if (LINE && block_in_window(i + (lg >> 5), r.win)) {
+          coeff_line(r, G, 32 * i + lg, u[i], &jt, &d);
           rd = recip(d);
         } else {
           jt = fmaf(r.jd1, u[i], r.jd0);
@@ -370,7 +372,7 @@ struct Fwd {
 
   // formal-mode per-step emission and optical depth of block i
   template <bool LINE>
-  static __device__ __forceinline__ void coeffs_formal(const PP& P, const VGrid& G, int lane,
+  static __device__ __forceinline__ void coeffs_formal(const PP& P, const VGrid& G, int lg,
                                                        const Rec& r, int i, R u, R* jt, R* tau) {
     if constexpr (kDouble) {
       const double bk = planck_k(P, r.td, u);
@@ -384,8 +386,8 @@ struct Fwd {
         *tau = r.ad;
       }
     } else {
-      if (LINE && block_in_window(i, r.win)) {
-        coeff_line(r, G, 32 * i + lane, u, jt, tau);
+      if (LINE && block_in_window(i + (lg >> 5), r.win)) {
+        coeff_line(r, G, 32 * i + lg, u, jt, tau);
       } else {
         *jt = r.ad * fmaf(r.bk1, u, r.bk0);
         *tau = r.ad;
@@ -394,16 +396,16 @@ struct Fwd {
   }
 
   template <bool LINE>
-  static __device__ __forceinline__ R formal_step(const PP& P, const VGrid& G, int lane,
+  static __device__ __forceinline__ R formal_step(const PP& P, const VGrid& G, int lg,
                                                   const Rec& r, int i, R u, R I) {
     if constexpr (kDouble) {
       R jt, tau;
-      coeffs_formal<LINE>(P, G, lane, r, i, u, &jt, &tau);
+      coeffs_formal<LINE>(P, G, lg, r, i, u, &jt, &tau);
       return I + (jt - tau * I) * psi_d(tau);
     } else {
-      if (LINE && block_in_window(i, r.win)) {
+      if (LINE && block_in_window(i + (lg >> 5), r.win)) {
         float jt, tau;
-        coeff_line(r, G, 32 * i + lane, u, &jt, &tau);
+        coeff_line(r, G, 32 * i + lg, u, &jt, &tau);
         return fmaf(fmaf(-tau, I, jt), psi_f(tau), I);
       }
       // dust only: I <- I + (S - I)(1 - e^{-tau_D})
@@ -571,8 +573,8 @@ struct FastSmooth {
     xa = fmaf(4.0f, xb, jb - xa) * rd0;
   }
 
-  // Runs the whole ray; writes the fine intensities of its blocks to fbuf and
-  // returns this lane's basis value.
+  // Runs the whole ray; writes the fine intensities of its blocks to fbuf
+  // (hull-relative: fbuf[32 j + lane]) and returns this lane's basis value.
   template <class Gen>
   static __device__ __forceinline__ float run(const PhysF& P, const Gen& gen, int K, int hb,
                                               int lane, const VGrid& G, int nfw, float* fbuf) {
@@ -655,7 +657,7 @@ struct FastSmooth {
 #pragma unroll
     for (int j = 0; j < NA; ++j) {
       const int g = 32 * (hb + j) + lane;
-      if (g < nfw) fbuf[g] = s1[j];
+      if (g < nfw) fbuf[32 * j + lane] = s1[j];
     }
     return x1;
   }
@@ -705,7 +707,7 @@ struct FastFormal {
 #pragma unroll
     for (int j = 0; j < NA; ++j) {
       const int g = 32 * (hb + j) + lane;
-      if (g < nfw) fbuf[g] = I[j];
+      if (g < nfw) fbuf[32 * j + lane] = I[j];
     }
     return x;
   }
@@ -805,7 +807,7 @@ struct FastKahan {
     for (int j = 0; j < NA; ++j) {
       const int g = 32 * (hb + j) + lane;
       const float u = fmaf((float)g, G.dvf_hi, G.ufw_hi);
-      if (g < nfw) fbuf[g] = fmaf(planck_k(P, P.t_bg, u) * ED, EL[j], acc[j]);
+      if (g < nfw) fbuf[32 * j + lane] = fmaf(planck_k(P, P.t_bg, u) * ED, EL[j], acc[j]);
     }
     return (lane == 0) ? ED : xb;
   }
@@ -879,13 +881,13 @@ template <> struct PSel<false> {
 };
 
 // ---------------------------------------------------------------------------
-// one work item: ray (px, py) of job J, channel window `win`
+// one work item: ray (px, py) of job J, every channel
 // ---------------------------------------------------------------------------
 template <typename R, int NI, int ST, int MODE>
-__device__ void render_item(const JobDev& J, const PhysParams& PD, const PhysF& PF, int px,
-                            int py, int win, unsigned char* wsm, int fw_off, int cw_off,
-                            int kb_off, typename RecOf<R, MODE>::type* grec, int lane,
-                            unsigned flags, unsigned long long* stats) {
+__device__ void render_ray(const JobDev& J, const PhysParams& PD, const PhysF& PF, int px,
+                           int py, unsigned char* wsm, int fw_off, int cw_off, int kb_off,
+                           typename RecOf<R, MODE>::type* grec, int lane, unsigned flags,
+                           unsigned long long* stats) {
   using F = Fwd<R, NI, MODE>;
   using Rec = typename F::Rec;
   using Gen = RecStream<Rec>;
@@ -894,22 +896,18 @@ __device__ void render_item(const JobDev& J, const PhysParams& PD, const PhysF& 
   R* fbuf = reinterpret_cast<R*>(wsm + fw_off);
   R* cbuf = reinterpret_cast<R*>(wsm + cw_off);
 
-  // ---- window geometry
-  const int c0 = win * J.cw;
-  const int cwn = min(J.cw, J.nchan - c0);
+  // ---- the fine velocity grid of the whole axis: u(g) = J.ufirst + g J.dvf;
+  // the records carry global fine indices, so one sample pass serves every
+  // channel of the ray
   const int f = J.f;
-  const int gw0 = (f >= 1) ? 2 * f * c0 : c0;
-  const int nfw = (f >= 1) ? 2 * f * cwn + 1 : cwn;
+  const int nch = J.nchan;
+  const int nfw = (f >= 1) ? 2 * f * nch + 1 : nch;
   const int nblk = (nfw + 31) >> 5;
-  // fine velocities of the window: u(g) = J.ufirst + (gw0 + g) J.dvf
   VGrid G;
-  {
-    const double ufw_d = J.ufirst + (double)gw0 * J.dvf;
-    G.ufw_hi = (float)ufw_d;
-    G.ufw_lo = (float)(ufw_d - (double)G.ufw_hi);
-    G.dvf_hi = (float)J.dvf;
-    G.dvf_lo = (float)(J.dvf - (double)G.dvf_hi);
-  }
+  G.ufw_hi = (float)J.ufirst;
+  G.ufw_lo = (float)(J.ufirst - (double)G.ufw_hi);
+  G.dvf_hi = (float)J.dvf;
+  G.dvf_lo = (float)(J.dvf - (double)G.dvf_hi);
 
   // ---- sample pass: lane l evaluates samples l, l + 32, ... into this warp's
   // record slot; the hull of the line windows, the widest window and the
@@ -961,17 +959,15 @@ __device__ void render_item(const JobDev& J, const PhysParams& PD, const PhysF& 
 
   const bool explicit_all = kDouble || (flags & IRT_FLAG_EXPLICIT_CHANNELS) ||
                             (MODE == M_SMOOTH && admax > (R)0.5);
-  if (explicit_all) {
-    hlo = 0;
-    hhi = nblk - 1;
-  }
   if (stats) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) nline += __shfl_xor_sync(0xffffffffu, nline, o);
     if (lane == 0) {
-      const unsigned long long nh = (hhi >= hlo) ? (unsigned long long)(hhi - hlo + 1) : 0ull;
+      const unsigned long long nh =
+          explicit_all ? (unsigned long long)nblk
+                       : ((hhi >= hlo) ? (unsigned long long)(hhi - hlo + 1) : 0ull);
       atomicAdd(stats + 0, 1ull);
-      if (win == 0) atomicAdd(stats + 1, (unsigned long long)K);   // once per ray
+      atomicAdd(stats + 1, (unsigned long long)K);
       atomicAdd(stats + 2, nline);
       atomicAdd(stats + 3, nh * (unsigned long long)K);
       atomicAdd(stats + 4, explicit_all ? 1ull : 0ull);
@@ -979,111 +975,15 @@ __device__ void render_item(const JobDev& J, const PhysParams& PD, const PhysF& 
     }
   }
 
-  // ---- total intensity on the blocks the line reaches
-  R X0 = (R)0, X1 = (R)0, X2 = (R)0;
-  bool fast = false;
-  int hb = 0, nb = 0;
-  if constexpr (!kDouble) {
-    const int ns = (wmax <= 32) ? 1 : ((wmax <= 64) ? 2 : 3);
-    if (!explicit_all && ns <= 2) {
-      const bool none = hhi < hlo;
-      const int na = none ? 1 : hhi - hlo + 1;
-      nb = fast_bucket(na, ns);
-      if (nb <= NI) {
-        hb = none ? 0 : min(hlo, max(nblk - nb, 0));
-        float xb = 0.0f;
-        float* kb = reinterpret_cast<float*>(wsm + kb_off);
-        fast = (ns == 1)
-                   ? run_fast<NI, MODE, 1>(nb, PF, gen, K, hb, lane, G, nfw, fbuf, kb, &xb)
-                   : run_fast<NI, MODE, 2>(nb, PF, gen, K, hb, lane, G, nfw, fbuf, kb, &xb);
-        if (fast) {
-          X0 = __shfl_sync(0xffffffffu, xb, 0);
-          X1 = __shfl_sync(0xffffffffu, xb, 1);
-          X2 = __shfl_sync(0xffffffffu, xb, 2);
-        }
-      }
-    }
-  }
-
-  R u[NI];
-#pragma unroll
-  for (int i = 0; i < NI; ++i) {
-    const int g = min(lane + 32 * i, nfw - 1);
-    if constexpr (kDouble) u[i] = J.ufirst + (double)(gw0 + g) * J.dvf;
-    else u[i] = fmaf((float)g, G.dvf_hi, G.ufw_hi);
-  }
-  if (!fast) {
-    R s0[NI], s1[NI], s2[NI];
-#pragma unroll
-    for (int i = 0; i < NI; ++i) {
-      s0[i] = (i >= hlo && i <= hhi) ? planck_k(P, (R)P.t_bg, u[i]) : (R)0;
-      s1[i] = (R)0;
-      s2[i] = (R)0;
-    }
-    F::template transfer<true>(P, G, lane, gen, K, u, hlo, hhi, s0, s1, s2);
-    if constexpr (!kDouble) {
-      if (!explicit_all) {
-        const float xb = F::basis(gen, K, lane);
-        X0 = __shfl_sync(0xffffffffu, xb, 0);
-        X1 = __shfl_sync(0xffffffffu, xb, 1);
-        X2 = __shfl_sync(0xffffffffu, xb, 2);
-      }
-    }
-#pragma unroll
-    for (int i = 0; i < NI; ++i) {
-      const int g = lane + 32 * i;
-      if (g < nfw && i >= hlo && i <= hhi) fbuf[g] = s1[i];
-    }
-    hb = hlo;
-    nb = (hhi >= hlo) ? hhi - hlo + 1 : 0;
-  }
-  // velocities outside the explicit blocks: continuum basis
-#pragma unroll
-  for (int i = 0; i < NI; ++i) {
-    const int g = lane + 32 * i;
-    if (g < nfw && (i < hb || i >= hb + nb))
-      fbuf[g] = X0 * planck_k(P, (R)P.t_bg, u[i]) + X1 + X2 * u[i];
-  }
-
-  // ---- continuum at channel centres when every channel is explicit
-  if (explicit_all) {
-    R uc[NI], s0[NI], s1[NI], s2[NI];
-    const int cblk = (cwn + 31) >> 5;
-#pragma unroll
-    for (int i = 0; i < NI; ++i) {
-      const int c = min(lane + 32 * i, cwn - 1);
-      uc[i] = (R)J.v0 + ((R)(c0 + c) + (R)0.5) * (R)J.dv;
-      s0[i] = (i < cblk) ? planck_k(P, (R)P.t_bg, uc[i]) : (R)0;
-      s1[i] = (R)0;
-      s2[i] = (R)0;
-    }
-    F::template transfer<false>(P, G, lane, gen, K, uc, 0, cblk - 1, s0, s1, s2);
-#pragma unroll
-    for (int i = 0; i < NI; ++i) {
-      const int c = lane + 32 * i;
-      if (c < cwn) cbuf[c] = s1[i];
-    }
-  }
-  __syncwarp();
-
-  // ---- epilogue: channel values and the five components
+  // ---- output of channel c from its channel-averaged total intensity and
+  // the continuum at the channel centre
   const long long plane = (long long)J.npx * J.npy;
   const long long pix = (long long)py * J.npx + px;
-  for (int cl = lane; cl < cwn; cl += 32) {
-    const int c = c0 + cl;
+  R* const* out = reinterpret_cast<R* const*>(J.out);
+  auto emit = [&](int c, R ibar, R ic_or_nan, bool have_ic, R X0, R X1, R X2) {
     const R uc = (R)J.v0 + ((R)c + (R)0.5) * (R)J.dv;
-    R ibar;
-    if (f >= 1) {
-      const R* F6 = fbuf + 2 * f * cl;
-      R acc = F6[0] + F6[2 * f];
-      for (int m = 1; m < 2 * f; m += 2) acc += (R)4 * F6[m];
-      for (int m = 2; m < 2 * f; m += 2) acc += (R)2 * F6[m];
-      ibar = acc / (R)(6 * f);
-    } else {
-      ibar = fbuf[cl];
-    }
     const R ib = planck_k(P, (R)P.t_bg, uc);
-    const R ic = explicit_all ? cbuf[cl] : X0 * ib + X1 + X2 * uc;
+    const R ic = have_ic ? ic_or_nan : X0 * ib + X1 + X2 * uc;
     R s = (R)P.out_scale;
     if (P.units == IRT_UNITS_TRJ) {
       const R y = (R)1 - uc * (R)P.inv_c_kms;
@@ -1091,14 +991,131 @@ __device__ void render_item(const JobDev& J, const PhysParams& PD, const PhysF& 
     }
     const R vT = ibar * s, vC = ic * s, vB = ib * s;
     const long long o = (long long)c * plane + pix;
-    R* const* out = reinterpret_cast<R* const*>(J.out);
     if (out[0]) out[0][o] = vT;
     if (out[1]) out[1][o] = vC;
     if (out[2]) out[2][o] = vC - vB;
     if (out[3]) out[3][o] = vT - vC;
     if (out[4]) out[4][o] = vB;
+  };
+  // Simpson channel average over the fine values fv(g), g = 2 f c .. 2 f (c+1)
+  auto simpson = [&](int c, auto&& fv) -> R {
+    if (f < 1) return fv(c);
+    const int g0 = 2 * f * c;
+    R acc = fv(g0) + fv(g0 + 2 * f);
+    for (int m = 1; m < 2 * f; m += 2) acc += (R)4 * fv(g0 + m);
+    for (int m = 2; m < 2 * f; m += 2) acc += (R)2 * fv(g0 + m);
+    return acc / (R)(6 * f);
+  };
+
+  // ---- fast path: the hull blocks of the whole axis in registers
+  if constexpr (!kDouble) {
+    const int ns = (wmax <= 32) ? 1 : ((wmax <= 64) ? 2 : 3);
+    if (!explicit_all && ns <= 2) {
+      const bool none = hhi < hlo;
+      const int na = none ? 1 : hhi - hlo + 1;
+      const int nb = fast_bucket(na, ns);
+      if (nb <= NI) {
+        const int hb = none ? 0 : min(hlo, max(nblk - nb, 0));
+        float xb = 0.0f;
+        float* kb = reinterpret_cast<float*>(wsm + kb_off);
+        const bool fast =
+            (ns == 1) ? run_fast<NI, MODE, 1>(nb, PF, gen, K, hb, lane, G, nfw, fbuf, kb, &xb)
+                      : run_fast<NI, MODE, 2>(nb, PF, gen, K, hb, lane, G, nfw, fbuf, kb, &xb);
+        if (fast) {
+          const float X0 = __shfl_sync(0xffffffffu, xb, 0);
+          const float X1 = __shfl_sync(0xffffffffu, xb, 1);
+          const float X2 = __shfl_sync(0xffffffffu, xb, 2);
+          __syncwarp();
+          const int e0 = 32 * hb, e1 = 32 * (hb + nb);
+          auto fv = [&](int g) -> float {
+            if (g >= e0 && g < e1) return fbuf[g - e0];
+            const float u = fmaf((float)g, G.dvf_hi, G.ufw_hi);
+            return X0 * planck_k(PF, PF.t_bg, u) + X1 + X2 * u;
+          };
+          for (int c = lane; c < nch; c += 32) emit(c, simpson(c, fv), 0.0f, false, X0, X1, X2);
+          __syncwarp();
+          return;
+        }
+      }
+    }
   }
-  __syncwarp();
+
+  // ---- general path: channel windows of NI register blocks (aligned to the
+  // 32-velocity blocks); the continuum basis, or with every channel
+  // explicit the dust-only transfer at the channel centres
+  R X0 = (R)0, X1 = (R)0, X2 = (R)0;
+  if constexpr (!kDouble) {
+    if (!explicit_all) {
+      const float xb = F::basis(gen, K, lane);
+      X0 = __shfl_sync(0xffffffffu, xb, 0);
+      X1 = __shfl_sync(0xffffffffu, xb, 1);
+      X2 = __shfl_sync(0xffffffffu, xb, 2);
+    }
+  }
+  for (int win = 0; win < J.nwin; ++win) {
+    const int c0 = win * J.cw;
+    const int cwn = min(J.cw, nch - c0);
+    const int gw0 = (f >= 1) ? 2 * f * c0 : c0;   // a multiple of 32
+    const int nfw_w = (f >= 1) ? 2 * f * cwn + 1 : cwn;
+    const int nblk_w = (nfw_w + 31) >> 5;
+    const int bw0 = gw0 >> 5;
+    const int lo_w = explicit_all ? 0 : max(hlo - bw0, 0);
+    const int hi_w = explicit_all ? nblk_w - 1 : min(hhi - bw0, nblk_w - 1);
+    R u[NI];
+#pragma unroll
+    for (int i = 0; i < NI; ++i) {
+      const int g = gw0 + min(lane + 32 * i, nfw_w - 1);
+      if constexpr (kDouble) u[i] = J.ufirst + (double)g * J.dvf;
+      else u[i] = fmaf((float)g, G.dvf_hi, G.ufw_hi);
+    }
+    if (lo_w <= hi_w) {
+      R s0[NI], s1[NI], s2[NI];
+#pragma unroll
+      for (int i = 0; i < NI; ++i) {
+        s0[i] = (i >= lo_w && i <= hi_w) ? planck_k(P, (R)P.t_bg, u[i]) : (R)0;
+        s1[i] = (R)0;
+        s2[i] = (R)0;
+      }
+      F::template transfer<true>(P, G, lane + 32 * bw0, gen, K, u, lo_w, hi_w, s0, s1, s2);
+#pragma unroll
+      for (int i = 0; i < NI; ++i) {
+        const int g = lane + 32 * i;
+        if (g < nfw_w && i >= lo_w && i <= hi_w) fbuf[g] = s1[i];
+      }
+    }
+    // velocities outside the explicit blocks: continuum basis
+#pragma unroll
+    for (int i = 0; i < NI; ++i) {
+      const int g = lane + 32 * i;
+      if (g < nfw_w && (i < lo_w || i > hi_w))
+        fbuf[g] = X0 * planck_k(P, (R)P.t_bg, u[i]) + X1 + X2 * u[i];
+    }
+    if (explicit_all) {
+      R uc[NI], s0[NI], s1[NI], s2[NI];
+      const int cblk = (cwn + 31) >> 5;
+#pragma unroll
+      for (int i = 0; i < NI; ++i) {
+        const int c = min(lane + 32 * i, cwn - 1);
+        uc[i] = (R)J.v0 + ((R)(c0 + c) + (R)0.5) * (R)J.dv;
+        s0[i] = (i < cblk) ? planck_k(P, (R)P.t_bg, uc[i]) : (R)0;
+        s1[i] = (R)0;
+        s2[i] = (R)0;
+      }
+      F::template transfer<false>(P, G, lane, gen, K, uc, 0, cblk - 1, s0, s1, s2);
+#pragma unroll
+      for (int i = 0; i < NI; ++i) {
+        const int c = lane + 32 * i;
+        if (c < cwn) cbuf[c] = s1[i];
+      }
+    }
+    __syncwarp();
+    auto fv = [&](int g) -> R { return fbuf[g - gw0]; };
+    for (int cl = lane; cl < cwn; cl += 32) {
+      const int c = c0 + cl;
+      emit(c, simpson(c, fv), explicit_all ? cbuf[cl] : (R)0, explicit_all, X0, X1, X2);
+    }
+    __syncwarp();
+  }
 }
 
 template <typename R, int NI, int ST, int MODE>
@@ -1129,9 +1146,7 @@ fwd_kernel(const __grid_constant__ JobTable tab, int njobs, const PhysParams PD,
     int j = 0;
     while (j + 1 < njobs && item >= tab.j[j + 1].item_begin) ++j;
     const JobDev& J = tab.j[j];
-    const long long local = item - J.item_begin;
-    const int win = (int)(local % J.nwin);
-    const long long ray = local / J.nwin;
+    const long long ray = item - J.item_begin;
     // rays come in tiles of tw x th pixels (row-major inside the tile and
     // over the tiles); pixels past the image edge are padding
     const int tsz = J.tw * J.th;
@@ -1141,8 +1156,8 @@ fwd_kernel(const __grid_constant__ JobTable tab, int njobs, const PhysParams PD,
     const int py = (int)(tile / J.ntx) * J.th + within / J.tw;
     if constexpr (ST == ST_F64 || sizeof(R) == 4) {
       if (px < J.npx && py < J.npy)
-        render_item<R, NI, ST, MODE>(J, PD, PF, px, py, win, wsm, fw_off, cw_off, kb_off, grec,
-                                     lane, flags, stats);
+        render_ray<R, NI, ST, MODE>(J, PD, PF, px, py, wsm, fw_off, cw_off, kb_off, grec, lane,
+                                    flags, stats);
     }
     if (queue) {
       unsigned long long t = 0;
