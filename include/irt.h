@@ -211,7 +211,12 @@ irt_status irt_tuned_plan(const irt_job* jobs, int njobs, const irt_opts* opts, 
  * completely (overwritten, not accumulated).  The forward transfer state is
  * recomputed from per-ray checkpoints every 32 samples held in device
  * scratch owned by the grid.  IRT_EINVAL as irt_forward_ppv plus NULL
- * gradients; IRT_EUNSUPPORTED for oblique views or IRT_PREC_F64.
+ * gradients; IRT_EUNSUPPORTED for oblique views, IRT_PREC_F64, integrators
+ * other than IRT_SMOOTH, f = 0, or channel counts needing more than one
+ * window.  The cells of a ray whose render needs every channel explicit
+ * (h alpha_D > 1/2 on some sample, or a line window wider than 64 fine
+ * velocities) or whose line hull is wider than the kernel's register blocks
+ * get NaN gradients; a ray of one sample gets zero.
  */
 irt_status irt_adjoint_ppv(const irt_job* job, const irt_line* line, const irt_dust* dust,
                            const irt_opts* opts, const irt_cubes* cotangent,
