@@ -215,8 +215,9 @@ irt_status irt_tuned_plan(const irt_job* jobs, int njobs, const irt_opts* opts, 
  * other than IRT_SMOOTH, f = 0, or channel counts needing more than one
  * window.  The cells of a ray whose render needs every channel explicit
  * (h alpha_D > 1/2 on some sample, or a line window wider than 64 fine
- * velocities) or whose line hull is wider than the kernel's register blocks
- * get NaN gradients; a ray of one sample gets zero.
+ * velocities) get NaN gradients; a ray of one sample gets zero.  The
+ * rays run in two launches: 9 register blocks first, then the rays whose line
+ * hull is wider, with the job's full width.
  */
 irt_status irt_adjoint_ppv(const irt_job* job, const irt_line* line, const irt_dust* dust,
                            const irt_opts* opts, const irt_cubes* cotangent,

@@ -509,8 +509,11 @@ __device__ __noinline__ void adj_ray(const JobDev& J, const PhysF& P, const AdjA
 
 __device__ __forceinline__ int J0kmax(const JobTable& t) { return t.j[0].kmax; }
 
+// Pass 0 (A.pass == 0) takes every ray of the image from the queue and
+// defers the rays whose hull is wider than NI blocks to the list A.defer
+// ([0] = count, then ray indices); pass 1 takes the rays of that list.
 template <int NI, int ST>
-__global__ void __launch_bounds__(kAdjWarps * 32, 1)
+__global__ void __launch_bounds__(kAdjWarps * 32, (NI <= 9) ? 8 : 1)
 adj_kernel(const __grid_constant__ JobTable tab, const PhysF PF, const AdjArgs A,
            long long total_items, unsigned long long* queue, int per_warp, int fw_off,
            int cw_off, int pb_off) {
@@ -528,11 +531,13 @@ adj_kernel(const __grid_constant__ JobTable tab, const PhysF PF, const AdjArgs A
   float* chainf = scr + A.scratch_per_warp - (long long)kNC * J0kmax(tab);
   const JobDev& J = tab.j[0];
 
+  const long long n_items = (A.pass == 0) ? total_items : (long long)A.defer[0];
   for (;;) {
     unsigned long long t = 0;
     if (lane == 0) t = atomicAdd(queue, 1ull);
-    const long long item = (long long)__shfl_sync(0xffffffffu, t, 0);
-    if (item >= total_items) break;
+    const long long slot = (long long)__shfl_sync(0xffffffffu, t, 0);
+    if (slot >= n_items) break;
+    const long long item = (A.pass == 0) ? slot : (long long)A.defer[1 + slot];
     const int px = (int)(item % J.npx), py = (int)(item / J.npx);
     const int cwn = J.nchan;      // one window
     const int f = J.f;
@@ -606,7 +611,17 @@ adj_kernel(const __grid_constant__ JobTable tab, const PhysF PF, const AdjArgs A
     const bool none = hhi < hlo;
     int nb = fast_bucket(none ? 1 : hhi - hlo + 1, ns);
     const int hb = none ? 0 : min(hlo, max(nblk - nb, 0));
-    bool ok = (ns <= 2) && admax <= 0.5f && nb <= NI && K >= 2;
+    const bool fits = (ns <= 2) && admax <= 0.5f && K >= 2;
+    if (A.pass == 0 && fits && nb > NI && nb <= A.defer_max_nb) {
+      // wider hull: the second pass (more register blocks) takes this ray
+      if (lane == 0) {
+        const unsigned i = atomicAdd(A.defer, 1u);
+        A.defer[1 + i] = (unsigned)item;
+      }
+      __syncwarp();
+      continue;
+    }
+    const bool ok = fits && nb <= NI;
     // fine cotangents; velocities outside the explicit blocks go to the basis
     for (int g = lane; g < nfw; g += 32) {
       const float lf = fine_cotangent(g, f, cwn, lamc);

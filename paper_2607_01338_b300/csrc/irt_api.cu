@@ -82,6 +82,8 @@ struct irt_grid {
   size_t adj_bytes;
   unsigned char* fwd_scratch;   // forward sample records of launches led by this grid
   size_t fwd_bytes;
+  unsigned* adj_defer;          // adjoint: rays deferred to the wide pass
+  size_t adj_defer_bytes;
 };
 
 using namespace irt;
@@ -141,6 +143,8 @@ irt_status irt_create_grid(const irt_grid_desc* desc, const irt_fields* fields,
   g->adj_bytes = 0;
   g->fwd_scratch = nullptr;
   g->fwd_bytes = 0;
+  g->adj_defer = nullptr;
+  g->adj_defer_bytes = 0;
   cudaGetDevice(&g->device);
   if (cudaMalloc(&g->cells, g->cell_bytes) != cudaSuccess) {
     cudaGetLastError();
@@ -190,6 +194,7 @@ irt_status irt_destroy(irt_grid* g) {
   cudaFree(g->ctl);
   if (g->adj_scratch) cudaFree(g->adj_scratch);
   if (g->fwd_scratch) cudaFree(g->fwd_scratch);
+  if (g->adj_defer) cudaFree(g->adj_defer);
   delete g;
   return IRT_OK;
 }
@@ -858,20 +863,27 @@ extern "C" irt_status irt_adjoint_ppv(const irt_job* job, const irt_line* line,
   A.grad[0] = grad_n_h2;
   A.grad[1] = grad_t_gas;
   A.grad[2] = grad_v_los;
-  int e = launch_adjoint(g->store, p.ni, tab, PF, A, 0, nullptr, 0, p.kmax, p.nfw,
+  // pass 0 runs with 9 register blocks (128 registers, 16 warps per SM) and
+  // defers the rays with wider hulls to pass 1 with the job's full width
+  const int ni0 = 9;
+  const int ni1 = p.ni > ni0 ? p.ni : 0;
+  int e = launch_adjoint(g->store, ni0, tab, PF, A, 0, nullptr, 0, p.kmax, p.nfw,
                          jb.vaxis.nchan, s, &per_warp);
   if (e) return cuda_fail(e, "irt_adjoint_ppv: kernel attributes");
   const size_t smem = (size_t)per_warp * kAdjWarps;
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const int per_sm = std::max(1, adjoint_blocks_per_sm(g->store, p.ni, smem));
-  const int blocks = per_sm * sms;
+  const int blocks0 = std::max(1, adjoint_blocks_per_sm(g->store, ni0, smem)) * sms;
+  const int blocks1 = ni1 ? std::max(1, adjoint_blocks_per_sm(g->store, ni1, smem)) * sms : 0;
   const int nseg = (p.kmax + kAdjSeg - 1) / kAdjSeg;
   // checkpoints, one stored sub-segment, the per-sample chain-rule factors
-  const long long per_warp_floats =
-      (long long)(2 * nseg + kAdjSub) * (p.ni + 1) * 32 + (long long)kAdjChain * p.kmax;
-  const size_t need = (size_t)blocks * kAdjWarps * (size_t)per_warp_floats * sizeof(float);
+  const int nb_alloc = std::max(ni0, ni1) + 1;
+  long long per_warp_floats =
+      (long long)(2 * nseg + kAdjSub) * nb_alloc * 32 + (long long)kAdjChain * p.kmax;
+  per_warp_floats = (per_warp_floats + 63) & ~63ll;
+  const size_t need =
+      (size_t)std::max(blocks0, blocks1) * kAdjWarps * (size_t)per_warp_floats * sizeof(float);
   if (g->adj_bytes < need) {
     if (g->adj_scratch) {
       cudaStreamSynchronize(s);
@@ -885,14 +897,41 @@ extern "C" irt_status irt_adjoint_ppv(const irt_job* job, const irt_line* line,
     }
     g->adj_bytes = need;
   }
+  const long long total = (long long)jb.view.npx * jb.view.npy;
+  const size_t defer_need = (size_t)(total + 1) * sizeof(unsigned);
+  if (g->adj_defer_bytes < defer_need) {
+    if (g->adj_defer) {
+      cudaStreamSynchronize(s);
+      cudaFree(g->adj_defer);
+      g->adj_defer = nullptr;
+      g->adj_defer_bytes = 0;
+    }
+    if (cudaMalloc((void**)&g->adj_defer, defer_need) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(IRT_ENOMEM, "irt_adjoint_ppv: cannot allocate the deferred-ray list");
+    }
+    g->adj_defer_bytes = defer_need;
+  }
   A.scratch = g->adj_scratch;
   A.scratch_per_warp = per_warp_floats;
+  A.defer = g->adj_defer;
+  A.defer_max_nb = ni1;
+  // control words: [0] pass-0 queue, [7] pass-1 queue; defer[0] = 0
   cudaError_t ce = cudaMemsetAsync(g->ctl, 0, sizeof(unsigned long long), s);
+  if (ce == cudaSuccess) ce = cudaMemsetAsync(g->ctl + 7, 0, sizeof(unsigned long long), s);
+  if (ce == cudaSuccess) ce = cudaMemsetAsync(g->adj_defer, 0, sizeof(unsigned), s);
   if (ce != cudaSuccess) return cuda_fail(ce, "irt_adjoint_ppv: queue reset");
-  const long long total = (long long)jb.view.npx * jb.view.npy;
-  e = launch_adjoint(g->store, p.ni, tab, PF, A, total, g->ctl, blocks, p.kmax, p.nfw,
+  A.pass = 0;
+  e = launch_adjoint(g->store, ni0, tab, PF, A, total, g->ctl, blocks0, p.kmax, p.nfw,
                      jb.vaxis.nchan, s, nullptr);
   ++g_launches;
+  if (e) return cuda_fail(e, "irt_adjoint_ppv: adjoint kernel");
+  if (ni1) {
+    A.pass = 1;
+    e = launch_adjoint(g->store, ni1, tab, PF, A, total, g->ctl + 7, blocks1, p.kmax, p.nfw,
+                       jb.vaxis.nchan, s, nullptr);
+    ++g_launches;
+  }
   if (e) return cuda_fail(e, "irt_adjoint_ppv: adjoint kernel");
   return IRT_OK;
 }

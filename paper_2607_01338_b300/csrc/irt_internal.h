@@ -94,8 +94,11 @@ constexpr int kAdjChain = 5;
 struct AdjArgs {
   const float* cot[5];          // cotangent cubes T, C, D, L, B (NULL = 0)
   float* grad[3];               // n_H2, T_gas, v_los
-  float* scratch;               // per-warp scratch
-  long long scratch_per_warp;   // floats
+  float* scratch;               // per-warp scratch (16-byte aligned slots)
+  long long scratch_per_warp;   // floats, a multiple of 4
+  int pass;                     // 0: every ray, wide hulls deferred; 1: the deferred rays
+  int defer_max_nb;             // widest hull bucket the second pass handles (0: none)
+  unsigned* defer;              // [0] = count, then deferred ray indices
 };
 
 // Job table passed to the kernels by value (__grid_constant__ parameter).

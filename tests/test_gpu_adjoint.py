@@ -111,6 +111,32 @@ def test_adjoint_matches_fp64_finite_differences_128cube():
     assert all(v <= 1.0 for v in worst.values()), worst
 
 
+def test_adjoint_wide_hulls_take_the_second_pass():
+    """Columns whose v_los ramps over +-80 km/s have line hulls wider than the
+    9 register blocks of the first adjoint pass; they are deferred to the wide
+    pass.  Flat columns stay in the first pass.  Both against the oracle."""
+    n, nz = 4, 16
+    fs = make_fields(16, 17)
+    arrs = [np.ascontiguousarray(a[:nz, :n, :n]) for a in fs.as_tuple()]
+    z = np.linspace(-1.0, 1.0, nz)[:, None, None]
+    steep = np.array([0.0, 0.3, 0.7, 1.0])[None, None, :]
+    arrs[3] = (80.0 * z * steep + 0.0 * arrs[3]).astype(np.float64) + arrs[3] * 0.1
+    f = FieldSet(*arrs)
+    f32, deq = to_storage(f, np.float32)
+    tf32, tdeq = to_storage(FieldSet(*[a * 1.0 for a in arrs[:3]] + [arrs[3] + 3.0, arrs[4]]),
+                            np.float32)
+    dx = 0.1 * PC
+    view = View(0.0, 0.0, n, n, dx, 0)
+    va = VelocityAxis(200, -100.0, 1.0, 1)
+    target = oracle.render_cube(tdeq.as_tuple(), dx, LINE, DUST, view, va)["L"]
+    loss, (gn, gt, gv) = _gpu_loss_grads(f32, dx, view, va, target)
+    oloss, on, ot, ov = oracle.loss_grad_zview(deq.as_tuple(), dx, LINE, DUST, va, target)
+    assert loss == pytest.approx(oloss, rel=1e-4)
+    assert np.isfinite(gn).all() and np.isfinite(gt).all() and np.isfinite(gv).all()
+    r = {k: _cmp(a, b) for k, a, b in (("n", gn, on), ("T", gt, ot), ("v", gv, ov))}
+    assert all(v <= 1.0 for v in r.values()), r
+
+
 def test_autograd_function_matches_adjoint():
     import paper_2607_01338_b300 as irt
     n = 12
