@@ -389,10 +389,18 @@ def gpu_arm(args):
     nx = w.n
     vw = w.views[0 if is_adj else dom]
     hbm_bytes = nx ** 3 * 32 + 5 * 4 * w.vaxis.nchan * vw.npx * vw.npy
-    kname = ("adj_kernel<17,F32> (z view)" if is_adj else
-             f"fwd_kernel<float,17,F32,smooth> ({['z', 'oblique'][dom]} view)")
+    kname = ("adjoint: adj_kernel<9,F32> + deferred-ray pass adj_kernel<17,F32> (z view)"
+             if is_adj else f"fwd_kernel<float,17,F32,smooth> ({['z', 'oblique'][dom]} view)")
+    # DRAM bytes per launch of the dominant kernel from one ncu capture of
+    # this workload (profiles/step_256cube_launches_and_dram.md); other sizes
+    # have no capture
+    traffic = None
+    if nx == 256 and is_adj:
+        traffic = 689.05e6 + 1.59e9 + 66.56e3
+    elif nx == 256 and not is_adj:
+        traffic = (569.2e6 + 392.2e6) if dom == 0 else (1.67e9 + 1.14e9)
     roofline = {"bound": "alu", "pipe": pipe, "achieved": ach, "peak": peak, "unit": "Top/s",
-                "frac": ach / peak, "traffic": None,
+                "frac": ach / peak, "traffic": traffic, "traffic_unit": "bytes per launch",
                 "kernel": kname,
                 "launch_ms": kern_ms[dom],
                 "peak_source": "148 SMs x (128 FP32 | 16 MUFU lanes) x sm_max_mhz "
