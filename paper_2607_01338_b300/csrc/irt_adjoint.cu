@@ -509,6 +509,56 @@ __device__ __noinline__ void adj_ray(const JobDev& J, const PhysF& P, const AdjA
 
 __device__ __forceinline__ int J0kmax(const JobTable& t) { return t.j[0].kmax; }
 
+// Hull buckets of the adjoint (each is its own reverse-sweep function).
+#ifndef IRT_ADJ_BUCKETS1
+#define IRT_ADJ_BUCKETS1 2, 4, 6, 8, 10, 12, 14, 17, 20, 24, 28, 33
+#endif
+#ifndef IRT_ADJ_BUCKETS2
+#define IRT_ADJ_BUCKETS2 4, 8, 12, 17, 24, 33
+#endif
+__device__ __forceinline__ int adj_bucket(int na, int ns) {
+  constexpr int b1[] = {IRT_ADJ_BUCKETS1};
+  constexpr int b2[] = {IRT_ADJ_BUCKETS2};
+  if (ns == 1) {
+#pragma unroll
+    for (int i = 0; i < (int)(sizeof(b1) / sizeof(int)); ++i)
+      if (na <= b1[i]) return b1[i];
+    return 33;
+  }
+#pragma unroll
+  for (int i = 0; i < (int)(sizeof(b2) / sizeof(int)); ++i)
+    if (na <= b2[i]) return b2[i];
+  return 33;
+}
+
+template <int NA, int NS, int NI, int ST>
+__device__ __forceinline__ bool adj_run_bucket(const JobDev& J, const PhysF& P,
+                                               const AdjArgs& A, const RecS32* rec,
+                                               const float* chainf, int K, int hb, int lane,
+                                               const VGrid& G, int nfw, const float* lamf,
+                                               float lx, float* pbuf, float* scr, int px,
+                                               int py) {
+  if constexpr (NA <= NI) {
+    adj_ray<NA, NS, ST>(J, P, A, rec, chainf, K, hb, lane, G, nfw, lamf, lx, pbuf, scr, px, py);
+    return true;
+  }
+  return false;
+}
+
+template <int NS, int NI, int ST, int... B>
+__device__ __forceinline__ void adj_dispatch(std::integer_sequence<int, B...>, int nb,
+                                             const JobDev& J, const PhysF& P, const AdjArgs& A,
+                                             const RecS32* rec, const float* chainf, int K,
+                                             int hb, int lane, const VGrid& G, int nfw,
+                                             const float* lamf, float lx, float* pbuf,
+                                             float* scr, int px, int py) {
+  bool done = false;
+  ((done = done || (nb == B && adj_run_bucket<B, NS, NI, ST>(J, P, A, rec, chainf, K, hb, lane,
+                                                             G, nfw, lamf, lx, pbuf, scr, px,
+                                                             py))),
+   ...);
+}
+
 // Pass 0 (A.pass == 0) takes every ray of the image from the queue and
 // defers the rays whose hull is wider than NI blocks to the list A.defer
 // ([0] = count, then ray indices); pass 1 takes the rays of that list.
@@ -609,7 +659,7 @@ adj_kernel(const __grid_constant__ JobTable tab, const PhysF PF, const AdjArgs A
     __syncwarp();
     const int ns = (wmax <= 32) ? 1 : ((wmax <= 64) ? 2 : 3);
     const bool none = hhi < hlo;
-    int nb = fast_bucket(none ? 1 : hhi - hlo + 1, ns);
+    int nb = adj_bucket(none ? 1 : hhi - hlo + 1, ns);
     const int hb = none ? 0 : min(hlo, max(nblk - nb, 0));
     const bool fits = (ns <= 2) && admax <= 0.5f && K >= 2;
     if (A.pass == 0 && fits && nb > NI && nb <= A.defer_max_nb) {
@@ -657,23 +707,12 @@ adj_kernel(const __grid_constant__ JobTable tab, const PhysF PF, const AdjArgs A
     }
     const float lx = (lane == 0) ? lx0 : ((lane == 1) ? lx1 : ((lane == 2) ? lx2 : 0.0f));
 
-#define IRT_ADJ(NA_)                                                                         \
-  case NA_:                                                                                  \
-    if constexpr (NA_ <= NI) {                                                               \
-      if (ns == 1)                                                                           \
-        adj_ray<NA_, 1, ST>(J, PF, A, rec, chainf, K, hb, lane, G, nfw, lamf, lx, pbuf, scr, px, \
-                            py);                                                              \
-      else                                                                                   \
-        adj_ray<NA_, 2, ST>(J, PF, A, rec, chainf, K, hb, lane, G, nfw, lamf, lx, pbuf, scr, px, \
-                            py);                                                              \
-    }                                                                                        \
-    break;
-    switch (nb) {
-      IRT_ADJ(2) IRT_ADJ(4) IRT_ADJ(6) IRT_ADJ(8) IRT_ADJ(10) IRT_ADJ(12) IRT_ADJ(14)
-      IRT_ADJ(17) IRT_ADJ(20) IRT_ADJ(24) IRT_ADJ(28) IRT_ADJ(33)
-      default: break;
-    }
-#undef IRT_ADJ
+    if (ns == 1)
+      adj_dispatch<1, NI, ST>(std::integer_sequence<int, IRT_ADJ_BUCKETS1>{}, nb, J, PF, A, rec,
+                              chainf, K, hb, lane, G, nfw, lamf, lx, pbuf, scr, px, py);
+    else
+      adj_dispatch<2, NI, ST>(std::integer_sequence<int, IRT_ADJ_BUCKETS2>{}, nb, J, PF, A, rec,
+                              chainf, K, hb, lane, G, nfw, lamf, lx, pbuf, scr, px, py);
     __syncwarp();
   }
 }
