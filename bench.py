@@ -62,6 +62,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-large", action="store_true")
     return ap.parse_args()
 
 
@@ -484,6 +485,10 @@ def gpu_arm(args):
     batch = None
     if not args.no_batch and args.n == 256:
         batch = batch_measure(args)
+    large = None
+    if not args.no_large and args.n == 256:
+        torch.cuda.empty_cache()
+        large = large_measure()
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
@@ -497,7 +502,7 @@ def gpu_arm(args):
                                  f"{w.n ** 3 * 32 / 1e6:.0f} MB > 126 MB)",
                            "parallelism": f"replicas x{ws}", "per_view_ms": view_ms,
                            "adjoint_ms": adj_ms, "units_adjoint": units_adj},
-                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "batch": batch,
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "batch": batch, "large": large,
                 "clocks": clk, "gpu_launches": launches}
         print(json.dumps(line), flush=True)
     if ws > 1:
@@ -577,6 +582,73 @@ def batch_measure(args, njobs=64, steps=3):
             "speedup_vs_fp32_single_cube": t_single / t_batch,
             "accuracy": "FP32 parity rule vs the FP64 oracle on the stored values "
                         "(tests/test_gpu_batch.py)"}
+
+
+# ---------------------------------------------------------------------------
+# large single render: 512^3, FP16 storage, 500 channels, forward + adjoint
+# ---------------------------------------------------------------------------
+def large_measure(steps=3):
+    """The 512^3 grid with five FP16-stored fields (per-field scales), 500
+    channels from -250 to +250 km/s, z view, smooth integration: forward and
+    the adjoint of mean(L^2), against the same fields stored as FP32."""
+    import torch
+    import paper_2607_01338_b300 as irt
+    from paper_2607_01338_b300 import binding as B
+    from synth import DUST, LINE_13CO_21, make_fields_torch, workload
+    w = workload(4)
+    view, va = w.views[0], w.vaxis
+    scales = (1.0e4, 1.0, 1.0, 1.0, 1.0e-6)
+    f = make_fields_torch(w.n, w.seed)
+    h = [(f[q] / scales[q]).to(torch.float16) for q in range(5)]
+    f32 = [x.float() for x in f]
+    del f
+    torch.cuda.empty_cache()
+    stream = torch.cuda.current_stream()
+    res = {}
+    for name, grid in (("fp16", irt.Grid(*h, w.cell_cm, scales=scales)),
+                       ("fp32", irt.Grid(*f32, w.cell_cm))):
+        out = irt.alloc_cubes(view, va)
+        B.irt_grid_stats(grid.handle, reset=True)
+        irt.forward(grid, view, va, LINE_13CO_21, DUST, out=out, flags=B.IRT_FLAG_STATS)
+        st = B.irt_grid_stats(grid.handle, reset=True)
+        units = st["samples"] * va.nchan
+        cot = {"L": 2.0 * out["L"] / out["L"].numel()}
+        grads = tuple(torch.empty((w.n,) * 3, dtype=torch.float32, device="cuda")
+                      for _ in range(3))
+        irt.adjoint(grid, view, va, LINE_13CO_21, DUST, cot, grads=grads)
+        torch.cuda.synchronize()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        tf = ta = 0.0
+        for _ in range(steps):
+            ev[0].record(stream)
+            irt.forward(grid, view, va, LINE_13CO_21, DUST, out=out)
+            ev[1].record(stream)
+            irt.adjoint(grid, view, va, LINE_13CO_21, DUST, cot, grads=grads)
+            ev[2].record(stream)
+            torch.cuda.synchronize()
+            tf += ev[0].elapsed_time(ev[1]) / steps
+            ta += ev[1].elapsed_time(ev[2]) / steps
+        fwd_fp32 = 32 * (OPS_LINE[0] * st["line_block_samples"]
+                         + OPS_DUST[0] * (st["hull_block_samples"] - st["line_block_samples"])) \
+            + OPS_SAMPLE[0] * st["samples"]
+        res[name] = {"forward_ms": tf, "adjoint_ms": ta,
+                     "value": 2 * units / ((tf + ta) / 1e3), "unit": UNIT,
+                     "forward_fp32_top_s": fwd_fp32 / (tf / 1e3) / 1e12,
+                     "forward_hbm_gbs": (grid_bytes(w.n, name) + 5 * 4 * va.nchan * w.n ** 2)
+                     / (tf / 1e3) / 1e9}
+        grid.close()
+        del out, cot, grads
+        torch.cuda.empty_cache()
+    return {"workload": f"{w.name}: 512^3, five FP16 fields with per-field scales, 500 channels "
+                        "-250..+250 km/s, z view, smooth; forward + adjoint of mean(L^2)",
+            "fp16_storage": res["fp16"], "fp32_storage": res["fp32"],
+            "speedup_fp16_vs_fp32": (res["fp32"]["forward_ms"] + res["fp32"]["adjoint_ms"])
+            / (res["fp16"]["forward_ms"] + res["fp16"]["adjoint_ms"]),
+            "accuracy": "FP32 parity rule on the stored values (tests/test_gpu_large.py)"}
+
+
+def grid_bytes(n, storage):
+    return n ** 3 * (16 if storage == "fp16" else 32)
 
 
 def main():
