@@ -424,12 +424,11 @@ __device__ __noinline__ void adj_ray(const JobDev& J, const PhysF& P, const AdjA
       // recompute the forward of the segment up to sub_hi, keeping the
       // pre-ReLU values of samples [sub_lo, sub_hi)
       float* pre_base = pre - (long long)sub_lo * NB * 32;   // indexed by absolute n
+      int n0;
       if (s == 0) {
         AD::start(P, rec, u, sa, sb, hb, lane, G, xa, xb, m0, m1, m2,
                   (sub_lo <= 1 && 1 < sub_hi) ? pre_base + 1 * NB * 32 + lane : nullptr);
-        if (sub_hi > 2)
-          AD::run(rec, 2, sub_hi, u, sa, sb, hb, lane, G, xa, xb, m1, m2, pre_base + lane,
-                  max(sub_lo, 2));
+        n0 = 2;
       } else {
         const float* c = ck + (long long)s * 2 * NB * 32;
 #pragma unroll
@@ -439,9 +438,11 @@ __device__ __noinline__ void adj_ray(const JobDev& J, const PhysF& P, const AdjA
         }
         xa = c[NA * 32 + lane];
         xb = c[NB * 32 + NA * 32 + lane];
-        AD::run(rec, seg_lo, sub_hi, u, sa, sb, hb, lane, G, xa, xb, m1, m2, pre_base + lane,
-                sub_lo);
+        n0 = seg_lo;
       }
+      if (sub_hi > n0)
+        AD::run(rec, n0, sub_hi, u, sa, sb, hb, lane, G, xa, xb, m1, m2, pre_base + lane,
+                max(sub_lo, n0));
       // reverse steps of the sub-segment, flushing the partials of every 16
       // samples (lane l reduces sample bot + l and writes its gradients)
       for (int top = sub_hi; top > sub_lo;) {
