@@ -73,6 +73,26 @@ def dist_env():
     return ws, rank, local
 
 
+def replica_seed(rank):
+    """Each rank renders its own snapshot (weak scaling, no data-path collective)."""
+    return 1000 + 17 * rank
+
+
+def max_over_ranks(x, ws, device=None):
+    """The slowest replica sets the whole job's time (all_reduce MAX)."""
+    if ws <= 1:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank, ws, seconds):
+    """Units of all ranks per second of the slowest rank."""
+    return units_per_rank * ws / seconds
+
+
 # ---------------------------------------------------------------------------
 # clocks during the timed region
 # ---------------------------------------------------------------------------
@@ -274,7 +294,7 @@ def gpu_arm(args):
     import paper_2607_01338_b300 as irt
     from paper_2607_01338_b300 import binding as B
 
-    seed = 1000 + 17 * rank
+    seed = replica_seed(rank)
     w, f32, deq = workload_inputs(args.n, seed)
     dev = torch.device("cuda", torch.cuda.current_device())
     fields_d = [torch.from_numpy(a).to(dev) for a in f32.as_tuple()]
@@ -352,13 +372,9 @@ def gpu_arm(args):
         torch.distributed.barrier()
     time.sleep(0.2)
     clocks.stop()
-    elapsed_ms = t_start.elapsed_time(t_end)
-    if ws > 1:
-        t = torch.tensor([elapsed_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        elapsed_ms = float(t.item())
+    elapsed_ms = max_over_ranks(t_start.elapsed_time(t_end), ws, dev)
     ms_step = elapsed_ms / args.steps
-    value = units_step * ws / (elapsed_ms / 1e3 / args.steps)
+    value = whole_job_rate(units_step, ws, elapsed_ms / 1e3 / args.steps)
     launch_ms = [[] for _ in range(nk)]
     for j, (a, b) in enumerate(ev):
         launch_ms[j % nk].append(a.elapsed_time(b))
@@ -456,12 +472,8 @@ def gpu_arm(args):
         for _ in range(e_steps):
             e2e_step()
         torch.cuda.synchronize()
-        dt = (time.perf_counter() - t0) / e_steps
-        e2e_v = units_step / dt
-        if ws > 1:
-            t = torch.tensor([dt], device=dev)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            e2e_v = units_step * ws / float(t.item())
+        dt = max_over_ranks((time.perf_counter() - t0) / e_steps, ws, dev)
+        e2e_v = whole_job_rate(units_step, ws, dt)
         e2e = {"value": e2e_v, "unit": UNIT, "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "ms_per_step": dt * 1e3,
                "path": "pinned host fields and target -> device, irt_create_grid, "
