@@ -2,19 +2,21 @@
 //
 // Gradients of a scalar loss with respect to n_H2, T_gas and v_los of every
 // cell, given the cotangents of the five output cubes.  One warp per ray
-// (one channel window).  The forward transfer of the ray is re-run exactly as
+// (the whole velocity axis in one channel window).  The records of the ray
+// sit in shared memory.  The forward transfer of the ray is re-run exactly as
 // the forward kernel runs it (hull blocks with line slots, the three
 // continuum basis recurrences), saving its state pair every 32 samples in
 // per-warp device scratch.  The reverse sweep then walks the segments from
-// the observer back: each segment is recomputed from its checkpoint in
-// sub-segments of 16 samples whose pre-ReLU values go to scratch (L2
-// resident), and the TR / BDF2 steps are reversed sample by sample
-// (Sec. 4.8: I_{n+2} = max(0, (2h j + 4 I_{n+1} - I_n) / (3 + 2h alpha))).
-// Per-sample partial derivatives with respect to the record quantities
-// (h alpha_D, 2h j_line, 2h alpha_line, v_los, b) are reduced across the
-// lanes through shared memory and chained to the cell fields through the LTE
-// populations (Sec. 5.10), the partition function and the Doppler width.
-// The ReLU derivative is 1 for a non-negative argument, 0 otherwise.
+// the observer back: each segment is recomputed from its checkpoint with its
+// pre-ReLU values stored in scratch (L2 resident), and the TR / BDF2 steps
+// are reversed sample by sample (Sec. 4.8: I_{n+2} = max(0, (2h j + 4 I_{n+1}
+// - I_n) / (3 + 2h alpha))).  Per-sample partial derivatives with respect to
+// the record quantities (h alpha_D, 2h j_line, 2h alpha_line, v_los, b) are
+// reduced across the lanes through shared memory and chained to the cell
+// fields through the LTE populations (Sec. 5.10), the partition function and
+// the Doppler width.  The ReLU derivative is 1 for a non-negative argument,
+// 0 otherwise.  Two launches: 9 register blocks for every ray, then the
+// job's full width for the rays whose line hull is wider (a device list).
 #include "irt_forward_impl.cuh"
 
 namespace irt {
@@ -443,8 +445,8 @@ __device__ __noinline__ void adj_ray(const JobDev& J, const PhysF& P, const AdjA
       if (sub_hi > n0)
         AD::run(rec, n0, sub_hi, u, sa, sb, hb, lane, G, xa, xb, m1, m2, pre_base + lane,
                 max(sub_lo, n0));
-      // reverse steps of the sub-segment, flushing the partials of every 16
-      // samples (lane l reduces sample bot + l and writes its gradients)
+      // reverse steps of the sub-segment, flushing the partials of every
+      // kFlush samples (lane l reduces sample bot + l and writes its gradients)
       for (int top = sub_hi; top > sub_lo;) {
         const int bot = max(sub_lo, top - kFlush);
         const int nlo = max(bot, 2);

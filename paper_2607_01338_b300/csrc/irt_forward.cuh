@@ -1,13 +1,16 @@
 // Forward PPV kernel of the IRIS-SO transfer (sm_103a): device helpers.
 //
-// Work item = (ray, channel window).  One warp renders one item:
+// Work item = one ray, every channel.  One warp renders one item:
 //   1. sample pass: lane l evaluates samples k = l, l+32, ... of the ray (field
 //      load or trilinear interpolation, LTE populations, line and dust
-//      coefficients, Sec. 3.2-3.7, 5.10) into a per-warp shared-memory record;
-//   2. transfer pass: lane l owns the fine velocities g = l + 32 i of the
-//      window (register blocks i) and integrates them sample by sample
-//      (Sec. 4.8, formal or smooth), evaluating the Gaussian profile only at
-//      the velocities the sample's line reaches;
+//      coefficients, Sec. 3.2-3.7, 5.10) into a per-sample record (global
+//      fine-velocity indices, so one pass serves every channel), written to
+//      the warp's slot of an L2-resident scratch buffer;
+//   2. transfer pass: the records stream back 32 at a time through shared
+//      memory; lane l owns the fine velocities g = 32 (hb + j) + l of the
+//      blocks the line reaches (register blocks j) and integrates them sample
+//      by sample (Sec. 4.8, formal or smooth), evaluating the Gaussian profile
+//      only at the velocities the sample's line reaches;
 //   3. epilogue: Simpson channel average (Sec. 4.5), continuum and background
 //      at the channel centre (Sec. 4.4), [L] = [T] - [C] (Sec. 4.10), [D] =
 //      [C] - [B], Rayleigh-Jeans conversion (Sec. 4.9).
