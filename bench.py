@@ -336,6 +336,7 @@ def gpu_arm(args):
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
+    pipe_peaks = B.irt_measure_pipe_peaks(int(torch.cuda.current_stream().cuda_stream))
 
     clocks = ClockSampler(torch.cuda.current_device())
     clocks.start()
@@ -394,8 +395,12 @@ def gpu_arm(args):
         + os_[0] * st["samples"]
     mufu = 32 * ol[1] * st["line_block_samples"] + os_[1] * st["samples"]
     fclk = float(pk.get("sm_max_mhz", 2032.0)) * 1e6
-    peak_fp32 = 148 * 128 * fclk / 1e12          # Top/s
-    peak_mufu = 148 * 16 * fclk / 1e12
+    nom_fp32 = 148 * 128 * fclk / 1e12          # Top/s, lane count x clock
+    nom_mufu = 148 * 16 * fclk / 1e12
+    # denominators: the pipes measured by the library's microbenchmark on
+    # this GPU at its present clock
+    peak_fp32 = pipe_peaks["fp32_ops_per_s"] / 1e12
+    peak_mufu = pipe_peaks["mufu_ops_per_s"] / 1e12
     t_dom = kern_ms[dom] / 1e3
     a_fp32 = fp32 / t_dom / 1e12
     a_mufu = mufu / t_dom / 1e12
@@ -420,8 +425,10 @@ def gpu_arm(args):
                 "frac": ach / peak, "traffic": traffic, "traffic_unit": "bytes per launch",
                 "kernel": kname,
                 "launch_ms": kern_ms[dom],
-                "peak_source": "148 SMs x (128 FP32 | 16 MUFU lanes) x sm_max_mhz "
-                               f"{pk.get('sm_max_mhz', 2032.0)} (MEASURED_PEAKS.json clocks)",
+                "peak_source": "measured: irt_measure_pipe_peaks (FP32 FMA and ex2 chains on "
+                               "every SM) in this run",
+                "peak_fp32_top_s": peak_fp32, "peak_mufu_top_s": peak_mufu,
+                "nominal_fp32_top_s": nom_fp32, "nominal_mufu_top_s": nom_mufu,
                 "fp32_top_s": a_fp32, "mufu_top_s": a_mufu,
                 "hbm_gbs": hbm_bytes / t_dom / 1e9, "hbm_peak_gbs": pk.get("hbm_gbs"),
                 "hbm_frac": hbm_bytes / t_dom / 1e9 / float(pk.get("hbm_gbs", 6400.0)),

@@ -276,6 +276,19 @@ const char* irt_last_error(void);
  * call (for launch accounting in benchmarks). */
 long long irt_launch_count(void);
 
+/*
+ * irt_measure_pipe_peaks - microbenchmark of the two pipes that bound the
+ * transfer kernels on the current device at its present clock: FP32 fused
+ * multiply-adds and special-function (ex2.approx) results, each as lane
+ * operations per second (best of three timed launches after a warm-up, about
+ * a millisecond of kernels in all, on cuda_stream, synchronised).  The paper
+ * has no counterpart: the measurement harness divides by these numbers.
+ * Allocates and frees a small device buffer.  IRT_EINVAL for NULL outputs,
+ * IRT_ENOMEM, IRT_ECUDA.
+ */
+irt_status irt_measure_pipe_peaks(double* fp32_ops_per_s, double* mufu_ops_per_s,
+                                  void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

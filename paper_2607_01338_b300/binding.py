@@ -30,7 +30,7 @@ STATUS_NAMES = {0: "IRT_OK", 1: "IRT_EINVAL", 2: "IRT_ENOMEM", 3: "IRT_ECUDA",
 EXPORTED = ("irt_create_grid", "irt_forward_ppv", "irt_adjoint_ppv", "irt_destroy",
             "irt_grid_stats", "irt_forward_ppv_static", "irt_forward_graph_create",
             "irt_forward_graph_launch", "irt_forward_graph_destroy", "irt_tuned_plan",
-            "irt_last_error", "irt_launch_count")
+            "irt_last_error", "irt_launch_count", "irt_measure_pipe_peaks")
 
 
 class irt_grid_desc(ctypes.Structure):
@@ -119,6 +119,8 @@ def _load():
     L.irt_forward_graph_destroy.argtypes = [ctypes.c_void_p]
     L.irt_tuned_plan.restype = ctypes.c_int
     L.irt_tuned_plan.argtypes = [P(irt_job), ctypes.c_int, P(irt_opts), P(ctypes.c_int)]
+    L.irt_measure_pipe_peaks.restype = ctypes.c_int
+    L.irt_measure_pipe_peaks.argtypes = [P(ctypes.c_double), P(ctypes.c_double), ctypes.c_void_p]
     L.irt_grid_stats.restype = ctypes.c_int
     L.irt_grid_stats.argtypes = [ctypes.c_void_p, P(ctypes.c_ulonglong), ctypes.c_int]
     L.irt_last_error.restype = ctypes.c_char_p
@@ -206,3 +208,10 @@ def irt_grid_stats(handle: int, reset: bool = True) -> dict:
 
 def irt_launch_count() -> int:
     return int(lib.irt_launch_count())
+
+
+def irt_measure_pipe_peaks(stream: int = 0) -> dict:
+    """Measured FP32 FMA and ex2 lane-operations per second on this device."""
+    a, b = ctypes.c_double(), ctypes.c_double()
+    _check(lib.irt_measure_pipe_peaks(ctypes.byref(a), ctypes.byref(b), ctypes.c_void_p(stream)))
+    return {"fp32_ops_per_s": a.value, "mufu_ops_per_s": b.value}

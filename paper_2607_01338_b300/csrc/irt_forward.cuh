@@ -150,6 +150,11 @@ __device__ __forceinline__ void trilinear(const JobDev& J, const int i0[3], cons
   }
 #pragma unroll
   for (int q = 0; q < 5; ++q) v[q] = (R)0;
+  // v_los is blended as differences from the first corner: the profile is
+  // steep in v, and rounding the blend of values of tens of km/s would move
+  // the line by ~1e-5 km/s; the differences between neighbouring cells are
+  // small, so their rounding is not
+  R vref = (R)0;
 #pragma unroll
   for (int c = 0; c < 8; ++c) {
     const int ix = (c & 1) ? hi[0] : lo[0];
@@ -161,9 +166,12 @@ __device__ __forceinline__ void trilinear(const JobDev& J, const int i0[3], cons
     const R ww = wx * wy * wz;
     R cv[5];
     load_cell<R, ST>(J.cells, ((long long)iz * J.ny + iy) * J.nx + ix, J.bf16_mask, J.scale, cv);
+    if (c == 0) vref = cv[3];
+    cv[3] -= vref;
 #pragma unroll
     for (int q = 0; q < 5; ++q) v[q] += ww * cv[q];
   }
+  v[3] += vref;
 }
 
 // Raw sample values (n_H2, T_gas, T_dust, v_los, x) of sample k of a ray,

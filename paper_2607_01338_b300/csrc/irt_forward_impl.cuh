@@ -156,6 +156,13 @@ __device__ __forceinline__ void coeff_line(const RecF32& r, const VGrid& G, int 
   *tau = fmaf(r.al, g, r.ad);
 }
 
+// 1/x from the hardware approximation refined by one Newton-Raphson step
+// (r <- r + r (1 - x r)): about half an ulp instead of the approximation's one.
+__device__ __forceinline__ float rcp_refined(float x) {
+  const float r = rcp_approx(x);
+  return fmaf(r, fmaf(-x, r, 1.0f), r);
+}
+
 // (1 - exp(-tau)) / tau, well conditioned for all tau (own expansion below
 // |tau| = 1/4: the Taylor series of the function truncated after tau^6, error
 // below 2e-9 relative; above, 1 - 2^(-tau log2 e) loses at most 4 ulp).
@@ -308,7 +315,7 @@ struct Fwd {
 
   static __device__ __forceinline__ R relu(R x) { return x > (R)0 ? x : (R)0; }
   static __device__ __forceinline__ R recip(R x) {
-    if constexpr (kDouble) return (R)1 / x; else return rcp_approx(x);
+    if constexpr (kDouble) return (R)1 / x; else return rcp_refined(x);
   }
   static __device__ __forceinline__ R psi(R tau) {
     if constexpr (kDouble) return psi_d(tau); else return psi_f(tau);
@@ -434,7 +441,7 @@ struct Fwd {
         const RecS32 r1 = ring[1];
         const float j0 = fmaf(m2, r0.jd1, m1 * r0.jd0);
         const float j1 = fmaf(m2, r1.jd1, m1 * r1.jd0);
-        x1 = (j0 + (7.0f - r0.d0) * x0 + j1) * rcp_approx(1.0f + r1.d0);
+        x1 = (j0 + (7.0f - r0.d0) * x0 + j1) * rcp_refined(1.0f + r1.d0);
       }
       for (int k0 = 0; k0 < K; k0 += 32) {
         if (k0 > 0) ring = gen.take_fwd(k0);
@@ -443,7 +450,7 @@ struct Fwd {
         for (int kk = (k0 == 0) ? 2 : 0; kk < n; ++kk) {
           const RecS32 r = ring[kk];
           const float jt = fmaf(m2, r.jd1, m1 * r.jd0);
-          const float x2 = fmaf(4.0f, x1, jt - x0) * rcp_approx(r.d0);
+          const float x2 = fmaf(4.0f, x1, jt - x0) * rcp_refined(r.d0);
           x0 = x1;
           x1 = x2;
         }
@@ -553,10 +560,10 @@ struct FastSmooth {
                                               int lane, const VGrid& G, float& xa, float xb,
                                               float m1, float m2) {
     const Slots<NS> sl = slots_smooth<NS>(r, hb, lane, G);
-    const float rd0 = rcp_approx(r.d0);
+    const float rd0 = rcp_refined(r.d0);
     float rl[NS];
 #pragma unroll
-    for (int q = 0; q < NS; ++q) rl[q] = rcp_approx(sl.b[q]);
+    for (int q = 0; q < NS; ++q) rl[q] = rcp_refined(sl.b[q]);
 #pragma unroll
     for (int j = 0; j < NA; ++j) {
       float t = fmaf(r.jd1, u[j], r.jd0) - sa[j];
@@ -615,10 +622,10 @@ struct FastSmooth {
       {
         const RecS32 r = ring[1];
         const Slots<NS> sl = slots_smooth<NS>(r, hb, lane, G);
-        const float r1 = rcp_approx(1.0f + r.d0);
+        const float r1 = rcp_refined(1.0f + r.d0);
         float rl[NS];
 #pragma unroll
-        for (int q = 0; q < NS; ++q) rl[q] = rcp_approx(1.0f + sl.b[q]);
+        for (int q = 0; q < NS; ++q) rl[q] = rcp_refined(1.0f + sl.b[q]);
 #pragma unroll
         for (int j = 0; j < NA; ++j) {
           float t = fmaf(r.jd1, u[j], r.jd0);

@@ -1,9 +1,9 @@
 """The large single render: a 512^3 grid with five FP16-stored fields (per-field
 scales), 500 channels from -250 to +250 km/s at 1 km/s, z view, forward and
 adjoint.  The oracle cannot render the whole cube in a test, so it checks
-seeded samples: 24 ray columns of the forward (FP32 parity rule on the stored
-values), and central differences of a mean(L^2) loss on 20 cells per field
-for the adjoint (1e-3 relative)."""
+seeded samples: a 32 x 32 pixel window of the forward at full depth (FP32
+parity rule on the stored values), and central differences of a mean(L^2)
+loss on 20 cells per field for the adjoint (1e-3 relative)."""
 import numpy as np
 import pytest
 
@@ -46,7 +46,8 @@ def _columns(h, cols):
     return out
 
 
-def test_512cube_fp16_forward_on_sampled_columns(big):
+def test_512cube_fp16_forward_on_a_32x32_window(big):
+    """A 32 x 32 pixel window at a seeded offset, every channel, full depth."""
     import paper_2607_01338_b300 as irt
     w, h, g = big
     view, va = w.views[0], w.vaxis
@@ -54,16 +55,17 @@ def test_512cube_fp16_forward_on_sampled_columns(big):
     cubes = irt.forward(g, view, va, LINE, DUST)
     torch.cuda.synchronize()
     rng = np.random.default_rng(44)
-    xs, ys = rng.integers(0, w.n, 24), rng.integers(0, w.n, 24)
-    cols = list(zip(xs.tolist(), ys.tolist()))
-    mini = View(0.0, 0.0, len(cols), 1, w.cell_cm, 0)
-    pix = np.stack([np.arange(len(cols)), np.zeros(len(cols), dtype=int)], axis=1)
-    orc = oracle.render(_columns(h, cols), w.cell_cm, LINE, DUST, mini, va, pix)
-    xi, yi = torch.as_tensor(xs, device="cuda"), torch.as_tensor(ys, device="cuda")
-    gpu = {k: cubes[k][:, yi, xi].double().cpu().numpy()[:, None, :] for k in cubes}
+    x0, y0 = (int(v) for v in rng.integers(0, w.n - 32, 2))
+    fields = [np.ascontiguousarray(h[q][:, y0:y0 + 32, x0:x0 + 32].double().cpu().numpy()
+                                   * SCALES[q]) for q in range(5)]
+    mini = View(0.0, 0.0, 32, 32, w.cell_cm, 0)
+    py, px = np.meshgrid(np.arange(32), np.arange(32), indexing="ij")
+    pix = np.stack([px.ravel(), py.ravel()], axis=1)
+    orc = oracle.render(fields, w.cell_cm, LINE, DUST, mini, va, pix)
+    gpu = {k: cubes[k][:, y0:y0 + 32, x0:x0 + 32].double().cpu().numpy() for k in cubes}
     worst = compare(gpu, orc, pix)
     assert all(v <= 1.0 for v in worst.values()), worst
-    # the line is present on the sampled rays
+    # the line is present in the window
     assert float(np.abs(orc["L"]).max()) > 0.1
 
 
