@@ -71,29 +71,31 @@ def oblique_view(n: int, cell_cm: float, theta_deg: float, phi_deg: float) -> Vi
     return View(math.radians(theta_deg), math.radians(phi_deg), n, n, cell_cm, 1)
 
 
-def workload(cfg: int, s: int = 0, n: int | None = None) -> Workload:
-    """The five benchmark workloads (cfg 0..4); ``n`` overrides the grid side
-    (used to build small cases with the same recipe)."""
+def workload(k: int, s: int = 0, n: int | None = None) -> Workload:
+    """The single-snapshot workloads, numbered 0 (32^3 FP64 parity), 1 (256^3
+    z and oblique views), 3 (128^3 adjoint) and 4 (512^3 FP16); number 2, the
+    batch of uneven snapshots, is batch_jobs().  Seeds are 1000 k + s.  ``n``
+    overrides the grid side (small cases with the same recipe)."""
     cell = 0.1 * PC_CM
-    seed = 1000 * cfg + s
-    if cfg == 0:
+    seed = 1000 * k + s
+    if k == 0:
         nn = n or 32
-        return Workload("cfg0-32cube-64ch-f4-fp64", nn, cell, seed,
+        return Workload("32cube-64ch-f4-fp64", nn, cell, seed,
                         VelocityAxis(64, -100.0, 3.125, 4), [z_view(nn, cell)], "f64")
-    if cfg == 1:
+    if k == 1:
         nn = n or 256
-        return Workload("cfg1-256cube-256ch-f1-fp32", nn, cell, seed,
+        return Workload("256cube-256ch-f1-fp32", nn, cell, seed,
                         VelocityAxis(256, -128.0, 1.0, 1),
                         [z_view(nn, cell), oblique_view(nn, cell, 30.0, 45.0)], "f32")
-    if cfg == 3:
+    if k == 3:
         nn = n or 128
-        return Workload("cfg3-128cube-128ch-f2-adjoint", nn, cell, seed,
+        return Workload("128cube-128ch-f2-fp32-adjoint", nn, cell, seed,
                         VelocityAxis(128, -100.0, 1.5625, 2), [z_view(nn, cell)], "f32")
-    if cfg == 4:
+    if k == 4:
         nn = n or 512
-        return Workload("cfg4-512cube-500ch-f1-fp16", nn, cell, seed,
+        return Workload("512cube-500ch-f1-fp16", nn, cell, seed,
                         VelocityAxis(500, -250.0, 1.0, 1), [z_view(nn, cell)], "f16")
-    raise ValueError(f"no single workload for cfg {cfg} (cfg 2 is batch_jobs())")
+    raise ValueError(f"no single-snapshot workload {k} (the batch is batch_jobs())")
 
 
 @dataclass

@@ -34,7 +34,7 @@ def all_pixels(npx, npy):
 # 32^3, 64 channels, f = 4: double-precision kernels against the oracle
 # ---------------------------------------------------------------------------
 @pytest.mark.parametrize("integration", ["smooth", "formal", "formal_kahan"])
-def test_cfg0_double_precision_full_cube(integration):
+def test_32cube_double_precision_full_cube(integration):
     w = workload(0)
     fs = make_fields(w.n, w.seed)
     view, va = w.views[0], w.vaxis
@@ -47,7 +47,7 @@ def test_cfg0_double_precision_full_cube(integration):
 
 
 @pytest.mark.parametrize("integration", ["smooth", "formal", "formal_kahan"])
-def test_cfg0_float_full_cube(integration):
+def test_32cube_float_full_cube(integration):
     w = workload(0)
     fs = make_fields(w.n, w.seed)
     f32, deq = to_storage(fs, np.float32)
@@ -64,7 +64,7 @@ def test_cfg0_float_full_cube(integration):
 # view, checked on a seeded 32 x 32 pixel crop at full depth, all channels
 # ---------------------------------------------------------------------------
 @pytest.fixture(scope="module")
-def cfg1():
+def views256():
     w = workload(1)
     fs = make_fields(w.n, w.seed)
     f32, deq = to_storage(fs, np.float32)
@@ -72,8 +72,8 @@ def cfg1():
 
 
 @pytest.mark.parametrize("vi", [0, 1])
-def test_cfg1_crop(cfg1, vi):
-    w, f32, deq = cfg1
+def test_256cube_crop(views256, vi):
+    w, f32, deq = views256
     view, va = w.views[vi], w.vaxis
     gpu = gpu_render(torch_fields(f32), w.cell_cm, view, va, LINE, DUST, integration="smooth")
     pix = crop_pixels(view.npx, view.npy, 32, 32, seed=100 + vi)
