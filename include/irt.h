@@ -166,16 +166,25 @@ irt_status irt_create_grid(const irt_grid_desc* desc, const irt_fields* fields,
                            void* cuda_stream, irt_grid** out);
 
 /*
- * irt_forward_ppv - render njobs >= 1 jobs (Sec. 4.4-4.10).  njobs == 1 runs
- * one launch over the job's (ray, channel-window) work items; njobs > 1 runs
- * one persistent launch over the work items of every job, taken from a
- * device work queue.  The output cubes are written completely (every channel
- * of every pixel).  IRT_EINVAL before any launch for: njobs < 1, NULL job,
- * grid or constants, nchan < 1, dv <= 0, f < 0, a non-finite or negative
+ * irt_forward_ppv - render njobs >= 1 jobs (Sec. 4.4-4.10).  A work item is
+ * one ray with every channel.  njobs == 1 runs one persistent launch whose
+ * warps take the rays round-robin; njobs > 1 runs one persistent launch per
+ * table of up to 64 jobs, its warps pulling rays from a device work queue
+ * (longest rays first).  The output cubes are written completely (every
+ * channel of every pixel).  A grid takes part in one launch at a time (its
+ * work-queue counter).  IRT_EINVAL before any launch for: njobs < 1, NULL
+ * job, grid or constants, nchan < 1, dv <= 0, f < 0, a non-finite or negative
  * constant, a z view whose size differs from the grid or whose angles are
  * non-zero, an oblique view with npx/npy < 1 or pixel <= 0; all output
  * pointers NULL.  IRT_EUNSUPPORTED for IRT_PREC_F64 on a grid that is not
- * stored as double, or a channel count beyond the compiled window sizes.
+ * stored as double, f > 64, or more than 32000 fine velocities (2 f nchan + 1).
+ *
+ * Scratch: the per-warp sample records (and the adjoint's checkpoints) live in
+ * device buffers the library keeps per (device, stream) and reuses across
+ * grids and calls; they grow on demand (a growth waits for the device) and
+ * are held until the process exits.  A call that would grow them during
+ * stream capture fails with IRT_EUNSUPPORTED: run it once uncaptured first.
+ * Graphs from irt_forward_graph_create own their buffer.
  */
 irt_status irt_forward_ppv(const irt_job* jobs, int njobs, const irt_line* line,
                            const irt_dust* dust, const irt_opts* opts, void* cuda_stream);
@@ -210,7 +219,7 @@ irt_status irt_tuned_plan(const irt_job* jobs, int njobs, const irt_opts* opts, 
  * [nchan][npy][npx], NULL = zero).  grad_* are float [nz][ny][nx], written
  * completely (overwritten, not accumulated).  The forward transfer state is
  * recomputed from per-ray checkpoints every 32 samples held in device
- * scratch owned by the grid.  IRT_EINVAL as irt_forward_ppv plus NULL
+ * scratch kept per (device, stream).  IRT_EINVAL as irt_forward_ppv plus NULL
  * gradients; IRT_EUNSUPPORTED for oblique views, IRT_PREC_F64, integrators
  * other than IRT_SMOOTH, f = 0, or channel counts needing more than one
  * window.  The cells of a ray whose render needs every channel explicit

@@ -8,7 +8,9 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstdarg>
+#include <cstdint>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <numeric>
 #include <string>
@@ -78,12 +80,6 @@ struct irt_grid {
   size_t cell_bytes;
   unsigned long long* ctl;   // device control words (work-queue counter)
   int device;
-  float* adj_scratch;        // adjoint checkpoints (grown on demand)
-  size_t adj_bytes;
-  unsigned char* fwd_scratch;   // forward sample records of launches led by this grid
-  size_t fwd_bytes;
-  unsigned* adj_defer;          // adjoint: rays deferred to the wide pass
-  size_t adj_defer_bytes;
 };
 
 using namespace irt;
@@ -139,12 +135,6 @@ irt_status irt_create_grid(const irt_grid_desc* desc, const irt_fields* fields,
   for (int q = 0; q < 5; ++q) g->scale[q] = scale[q];
   g->cell_bytes = cb * (size_t)ncell;
   g->ctl = nullptr;
-  g->adj_scratch = nullptr;
-  g->adj_bytes = 0;
-  g->fwd_scratch = nullptr;
-  g->fwd_bytes = 0;
-  g->adj_defer = nullptr;
-  g->adj_defer_bytes = 0;
   cudaGetDevice(&g->device);
   if (cudaMalloc(&g->cells, g->cell_bytes) != cudaSuccess) {
     cudaGetLastError();
@@ -192,9 +182,6 @@ irt_status irt_destroy(irt_grid* g) {
   if (!g) return IRT_OK;
   cudaFree(g->cells);
   cudaFree(g->ctl);
-  if (g->adj_scratch) cudaFree(g->adj_scratch);
-  if (g->fwd_scratch) cudaFree(g->fwd_scratch);
-  if (g->adj_defer) cudaFree(g->adj_defer);
   delete g;
   return IRT_OK;
 }
@@ -515,30 +502,47 @@ struct Scratch {
   size_t bytes = 0;
 };
 
-// The first job's grid holds the record scratch of a direct call; it grows on
-// demand (cudaFree waits for the launches that used the old buffer).
-irt_status grid_fwd_scratch(irt_grid* g, size_t need, cudaStream_t s, Scratch* out) {
-  if (g->fwd_bytes < need) {
-    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
-    cudaStreamIsCapturing(s, &cap);
-    if (cap != cudaStreamCaptureStatusNone)
-      return fail(IRT_EUNSUPPORTED,
-                  "irt_forward_ppv: the record scratch of the grid must grow (%zu bytes), which "
-                  "cannot happen during stream capture; run the call once before capturing it",
-                  need);
-    if (g->fwd_scratch) cudaFree(g->fwd_scratch);
-    g->fwd_scratch = nullptr;
-    g->fwd_bytes = 0;
-    if (cudaMalloc((void**)&g->fwd_scratch, need) != cudaSuccess) {
-      cudaGetLastError();
-      return fail(IRT_ENOMEM, "irt_forward_ppv: cannot allocate %zu bytes of record scratch",
-                  need);
-    }
-    g->fwd_bytes = need;
+// Scratch of direct calls, kept per (device, stream) and reused by every
+// grid: the forward's sample records, the adjoint's checkpoints and its
+// deferred-ray list.  Launches on one stream run in order, so they can share
+// a buffer; launches on different streams get different ones.  A buffer only
+// grows (cudaFree waits for the launches that used the old one), never during
+// stream capture.
+struct StreamScratch {
+  unsigned char* fwd = nullptr;
+  size_t fwd_bytes = 0;
+  unsigned char* adj = nullptr;
+  size_t adj_bytes = 0;
+  unsigned char* defer = nullptr;
+  size_t defer_bytes = 0;
+};
+std::mutex g_scratch_mu;
+std::map<std::pair<int, unsigned long long>, StreamScratch> g_scratch;
+
+irt_status grow(unsigned char** p, size_t* have, size_t need, cudaStream_t s, const char* what) {
+  if (*have >= need) return IRT_OK;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  cudaStreamIsCapturing(s, &cap);
+  if (cap != cudaStreamCaptureStatusNone)
+    return fail(IRT_EUNSUPPORTED,
+                "%s: the scratch of this stream must grow (%zu bytes), which cannot happen during "
+                "stream capture; run the call once before capturing it", what, need);
+  if (*p) cudaFree(*p);
+  *p = nullptr;
+  *have = 0;
+  if (cudaMalloc((void**)p, need) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(IRT_ENOMEM, "%s: cannot allocate %zu bytes of scratch", what, need);
   }
-  out->p = g->fwd_scratch;
-  out->bytes = g->fwd_bytes;
+  *have = need;
   return IRT_OK;
+}
+
+StreamScratch& stream_scratch(cudaStream_t s) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lock(g_scratch_mu);
+  return g_scratch[{dev, (unsigned long long)(uintptr_t)s}];
 }
 
 irt_status run_forward(const irt_job* jobs, int njobs, const PhysParams& P, const PhysF& PF,
@@ -577,8 +581,12 @@ irt_status run_forward(const irt_job* jobs, int njobs, const PhysParams& P, cons
   if (ext) {
     sc = *ext;
   } else {
-    const irt_status st = grid_fwd_scratch(jobs[0].grid, fwd_scratch_need(plans, prec), s, &sc);
+    StreamScratch& ss = stream_scratch(s);
+    const irt_status st = grow(&ss.fwd, &ss.fwd_bytes, fwd_scratch_need(plans, prec), s,
+                               "irt_forward_ppv");
     if (st) return st;
+    sc.p = ss.fwd;
+    sc.bytes = ss.fwd_bytes;
   }
   for (int base = 0; base < njobs; base += kMaxJobs) {
     const int nb = std::min(kMaxJobs, njobs - base);
@@ -884,42 +892,20 @@ extern "C" irt_status irt_adjoint_ppv(const irt_job* job, const irt_line* line,
   per_warp_floats = (per_warp_floats + 63) & ~63ll;
   const size_t need =
       (size_t)std::max(blocks0, blocks1) * kAdjWarps * (size_t)per_warp_floats * sizeof(float);
-  if (g->adj_bytes < need) {
-    if (g->adj_scratch) {
-      cudaStreamSynchronize(s);
-      cudaFree(g->adj_scratch);
-      g->adj_scratch = nullptr;
-      g->adj_bytes = 0;
-    }
-    if (cudaMalloc((void**)&g->adj_scratch, need) != cudaSuccess) {
-      cudaGetLastError();
-      return fail(IRT_ENOMEM, "irt_adjoint_ppv: cannot allocate %zu bytes of checkpoints", need);
-    }
-    g->adj_bytes = need;
-  }
   const long long total = (long long)jb.view.npx * jb.view.npy;
   const size_t defer_need = (size_t)(total + 1) * sizeof(unsigned);
-  if (g->adj_defer_bytes < defer_need) {
-    if (g->adj_defer) {
-      cudaStreamSynchronize(s);
-      cudaFree(g->adj_defer);
-      g->adj_defer = nullptr;
-      g->adj_defer_bytes = 0;
-    }
-    if (cudaMalloc((void**)&g->adj_defer, defer_need) != cudaSuccess) {
-      cudaGetLastError();
-      return fail(IRT_ENOMEM, "irt_adjoint_ppv: cannot allocate the deferred-ray list");
-    }
-    g->adj_defer_bytes = defer_need;
-  }
-  A.scratch = g->adj_scratch;
+  StreamScratch& ss = stream_scratch(s);
+  irt_status gs = grow(&ss.adj, &ss.adj_bytes, need, s, "irt_adjoint_ppv");
+  if (!gs) gs = grow(&ss.defer, &ss.defer_bytes, defer_need, s, "irt_adjoint_ppv");
+  if (gs) return gs;
+  A.scratch = reinterpret_cast<float*>(ss.adj);
   A.scratch_per_warp = per_warp_floats;
-  A.defer = g->adj_defer;
+  A.defer = reinterpret_cast<unsigned*>(ss.defer);
   A.defer_max_nb = ni1;
   // control words: [0] pass-0 queue, [7] pass-1 queue; defer[0] = 0
   cudaError_t ce = cudaMemsetAsync(g->ctl, 0, sizeof(unsigned long long), s);
   if (ce == cudaSuccess) ce = cudaMemsetAsync(g->ctl + 7, 0, sizeof(unsigned long long), s);
-  if (ce == cudaSuccess) ce = cudaMemsetAsync(g->adj_defer, 0, sizeof(unsigned), s);
+  if (ce == cudaSuccess) ce = cudaMemsetAsync(A.defer, 0, sizeof(unsigned), s);
   if (ce != cudaSuccess) return cuda_fail(ce, "irt_adjoint_ppv: queue reset");
   A.pass = 0;
   e = launch_adjoint(g->store, ni0, tab, PF, A, total, g->ctl, blocks0, p.kmax, p.nfw,
