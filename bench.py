@@ -315,10 +315,15 @@ def gpu_arm(args):
     grads = tuple(torch.empty((w.n, w.n, w.n), dtype=torch.float32, device=dev)
                   for _ in range(3))
 
+    # the z-view render keeps its transfer checkpoints for the adjoint that
+    # follows it (smooth integration), as the autograd function does
+    save = B.IRT_FLAG_SAVE_CHECKPOINTS if args.integration == "smooth" else 0
+    vflags = [save if vi == 0 else 0 for vi in range(len(w.views))]
+
     def step(flags=0):
-        for view, out in zip(w.views, outs):
+        for view, out, vf in zip(w.views, outs, vflags):
             irt.forward(grid, view, w.vaxis, w.line, w.dust, integration=args.integration,
-                        out=out, flags=flags)
+                        out=out, flags=flags | vf)
         irt.adjoint(grid, w.views[0], w.vaxis, w.line, w.dust, cot,
                     integration=args.integration, grads=grads)
 
@@ -354,10 +359,10 @@ def gpu_arm(args):
     t_start.record(stream)
     i = 0
     for _ in range(args.steps):
-        for view, out in zip(w.views, outs):
+        for view, out, vf in zip(w.views, outs, vflags):
             ev[i][0].record(stream)
             irt.forward(grid, view, w.vaxis, w.line, w.dust, integration=args.integration,
-                        out=out)
+                        out=out, flags=vf)
             ev[i][1].record(stream)
             i += 1
         ev[i][0].record(stream)
@@ -485,9 +490,9 @@ def gpu_arm(args):
                     ms.wait_event(results_free[b])
                 g = irt.Grid(*dev_in[b], w.cell_cm)
                 grids.append(g)
-                for view, out, ho in zip(w.views, outs2[b], host_out):
+                for view, out, ho, vf in zip(w.views, outs2[b], host_out, vflags):
                     irt.forward(g, view, w.vaxis, w.line, w.dust, integration=args.integration,
-                                out=out)
+                                out=out, flags=vf)
                     done = ev()
                     done.record(ms)
                     with torch.cuda.stream(down):

@@ -83,6 +83,11 @@ typedef enum { IRT_MODE_THICK = 0 } irt_transfer_mode;
 #define IRT_FLAG_AUTOTUNE 4u           /* time the launch plans for this job mix
                                           (synchronous; not during stream capture)
                                           and cache the fastest */
+#define IRT_FLAG_SAVE_CHECKPOINTS 8u   /* one z-view job, smooth, float: also keep
+                                          the transfer state every 32 samples in
+                                          the grid, for irt_adjoint_ppv of the
+                                          same job, which then skips its own
+                                          forward sweep */
 
 typedef struct irt_grid irt_grid;   /* opaque */
 
@@ -178,6 +183,14 @@ irt_status irt_create_grid(const irt_grid_desc* desc, const irt_fields* fields,
  * non-zero, an oblique view with npx/npy < 1 or pixel <= 0; all output
  * pointers NULL.  IRT_EUNSUPPORTED for IRT_PREC_F64 on a grid that is not
  * stored as double, f > 64, or more than 32000 fine velocities (2 f nchan + 1).
+ *
+ * IRT_FLAG_SAVE_CHECKPOINTS (njobs == 1, z view, IRT_SMOOTH, float precision,
+ * else IRT_EUNSUPPORTED) stores, in a buffer the grid owns (npx x npy x
+ * ceil(nz / 32) x 2 x 10 x 32 floats, grown on demand), the transfer state of
+ * every ray every 32 samples, with a signature of the job (velocity axis,
+ * line, dust, background).  A later irt_adjoint_ppv of the same grid and an
+ * identical job on the same stream uses it instead of re-integrating the
+ * forward; any other job ignores it.
  *
  * Scratch: the per-warp sample records (and the adjoint's checkpoints) live in
  * device buffers the library keeps per (device, stream) and reuses across

@@ -215,8 +215,12 @@ class RenderPPV(torch.autograd.Function):
     def forward(ctx, n_h2, t_gas, v_los, t_dust, x_tracer, cfg: RenderConfig):
         grid = Grid(n_h2.detach().float(), t_gas.detach().float(), t_dust.detach().float(),
                     v_los.detach().float(), x_tracer.detach().float(), cfg.cell_cm)
+        # the z-view smooth render keeps its transfer checkpoints in the grid,
+        # so that backward skips re-integrating the forward
+        save = (cfg.integration == "smooth" and int(cfg.view.trilinear) == 0)
         cubes = forward(grid, cfg.view, cfg.vaxis, cfg.line, cfg.dust,
-                        integration=cfg.integration, units=cfg.units, t_bg=cfg.t_bg)
+                        integration=cfg.integration, units=cfg.units, t_bg=cfg.t_bg,
+                        flags=B.IRT_FLAG_SAVE_CHECKPOINTS if save else 0)
         ctx.grid = grid
         ctx.cfg = cfg
         return tuple(cubes[k] for k in COMPONENTS)

@@ -22,6 +22,7 @@ IRT_MODE_THICK = 0
 IRT_FLAG_EXPLICIT_CHANNELS = 1
 IRT_FLAG_STATS = 2
 IRT_FLAG_AUTOTUNE = 4
+IRT_FLAG_SAVE_CHECKPOINTS = 8
 
 STATUS_NAMES = {0: "IRT_OK", 1: "IRT_EINVAL", 2: "IRT_ENOMEM", 3: "IRT_ECUDA",
                 4: "IRT_EUNSUPPORTED", 5: "IRT_ETIMEOUT"}

@@ -386,19 +386,24 @@ __device__ __noinline__ void adj_ray(const JobDev& J, const PhysF& P, const AdjA
   const float m1 = (lane == 1) ? 1.0f : 0.0f;
   const float m2 = (lane == 2) ? 1.0f : 0.0f;
   const int nseg = (K + kSeg - 1) / kSeg;
-  float* ck = scr;                                        // [nseg][2][NB][32]
+  // checkpoints [nseg][2][cs][32]: saved by the forward render of this job
+  // (cs = their row count) or written below into the warp's scratch
+  const bool saved = A.ck_saved != nullptr && NA < A.ck_nb;
+  const int cs = saved ? A.ck_nb : NB;
+  const float* ck =
+      saved ? A.ck_saved + ((long long)py * J.npx + px) * A.ck_ray : scr;
   float* pre = scr + (long long)nseg * 2 * NB * 32;       // [kSub][NB][32]
   float sa[NA], sb[NA], xa, xb;
 
   // ---- forward with a checkpoint (I_{32s-2}, I_{32s-1}) at every segment s >= 1
-  AD::start(P, rec, u, sa, sb, hb, lane, G, xa, xb, m0, m1, m2, nullptr);
-  {
+  if (!saved) {
+    AD::start(P, rec, u, sa, sb, hb, lane, G, xa, xb, m0, m1, m2, nullptr);
     int n = 2;
     for (int s = 1; s < nseg; ++s) {
       const int ne = s * kSeg;
       if (n < ne) AD::run(rec, n, ne, u, sa, sb, hb, lane, G, xa, xb, m1, m2, pre, 1 << 30);
       n = ne;
-      float* c = ck + (long long)s * 2 * NB * 32;
+      float* c = scr + (long long)s * 2 * NB * 32;
 #pragma unroll
       for (int j = 0; j < NA; ++j) {
         c[j * 32 + lane] = sa[j];
@@ -432,14 +437,14 @@ __device__ __noinline__ void adj_ray(const JobDev& J, const PhysF& P, const AdjA
                   (sub_lo <= 1 && 1 < sub_hi) ? pre_base + 1 * NB * 32 + lane : nullptr);
         n0 = 2;
       } else {
-        const float* c = ck + (long long)s * 2 * NB * 32;
+        const float* c = ck + (long long)s * 2 * cs * 32;
 #pragma unroll
         for (int j = 0; j < NA; ++j) {
           sa[j] = c[j * 32 + lane];
-          sb[j] = c[NB * 32 + j * 32 + lane];
+          sb[j] = c[cs * 32 + j * 32 + lane];
         }
         xa = c[NA * 32 + lane];
-        xb = c[NB * 32 + NA * 32 + lane];
+        xb = c[cs * 32 + NA * 32 + lane];
         n0 = seg_lo;
       }
       if (sub_hi > n0)

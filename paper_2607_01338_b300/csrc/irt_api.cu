@@ -80,6 +80,9 @@ struct irt_grid {
   size_t cell_bytes;
   unsigned long long* ctl;   // device control words (work-queue counter)
   int device;
+  float* ck;                     // forward checkpoints kept for the adjoint
+  size_t ck_bytes;
+  unsigned long long ck_sig;     // signature of the job that wrote them (0: none)
 };
 
 using namespace irt;
@@ -135,6 +138,9 @@ irt_status irt_create_grid(const irt_grid_desc* desc, const irt_fields* fields,
   for (int q = 0; q < 5; ++q) g->scale[q] = scale[q];
   g->cell_bytes = cb * (size_t)ncell;
   g->ctl = nullptr;
+  g->ck = nullptr;
+  g->ck_bytes = 0;
+  g->ck_sig = 0;
   cudaGetDevice(&g->device);
   if (cudaMalloc(&g->cells, g->cell_bytes) != cudaSuccess) {
     cudaGetLastError();
@@ -182,6 +188,7 @@ irt_status irt_destroy(irt_grid* g) {
   if (!g) return IRT_OK;
   cudaFree(g->cells);
   cudaFree(g->ctl);
+  if (g->ck) cudaFree(g->ck);
   delete g;
   return IRT_OK;
 }
@@ -545,6 +552,26 @@ StreamScratch& stream_scratch(cudaStream_t s) {
   return g_scratch[{dev, (unsigned long long)(uintptr_t)s}];
 }
 
+// Signature of everything besides the grid that sets a z-view job's
+// transfer states: the velocity axis and the folded constants.
+unsigned long long checkpoint_signature(const irt_job& jb, const PhysParams& P) {
+  unsigned long long h = 1469598103934665603ull;
+  auto mix = [&](const void* p, size_t n) {
+    const unsigned char* b = static_cast<const unsigned char*>(p);
+    for (size_t i = 0; i < n; ++i) h = (h ^ b[i]) * 1099511628211ull;
+  };
+  // field by field: the ABI structs have padding a caller need not clear
+  mix(&jb.vaxis.nchan, sizeof(int));
+  mix(&jb.vaxis.v_first_edge_kms, sizeof(double));
+  mix(&jb.vaxis.dv_kms, sizeof(double));
+  mix(&jb.vaxis.subsample_f, sizeof(int));
+  mix(&jb.view.npx, sizeof(int));
+  mix(&jb.view.npy, sizeof(int));
+  mix(&jb.view.trilinear, sizeof(int));
+  mix(&P, sizeof P);   // doubles and two trailing ints: no padding
+  return h | 1ull;     // never 0 (0 = no checkpoints)
+}
+
 irt_status run_forward(const irt_job* jobs, int njobs, const PhysParams& P, const PhysF& PF,
                        const irt_opts* opts, const Tuned& tp, cudaStream_t s,
                        const Scratch* ext = nullptr) {
@@ -602,6 +629,23 @@ irt_status run_forward(const irt_job* jobs, int njobs, const PhysParams& P, cons
       kmax = std::max(kmax, plans[j].kmax);
       fwmax = std::max(fwmax, 32 * plans[j].ni);
       cwmax = std::max(cwmax, plans[j].cw);
+    }
+    if (opts->flags & IRT_FLAG_SAVE_CHECKPOINTS) {
+      // one z-view smooth job (checked by the caller): the grid keeps the
+      // states of every ray every 32 samples for the adjoint
+      irt_grid* g = jobs[0].grid;
+      const long long nseg = (plans[0].kmax + kAdjSeg - 1) / kAdjSeg;
+      const long long ck_ray = nseg * 2 * kCkRows * 32;
+      const size_t need =
+          (size_t)tab.j[0].npx * tab.j[0].npy * (size_t)ck_ray * sizeof(float);
+      unsigned char* buf = reinterpret_cast<unsigned char*>(g->ck);
+      const irt_status st = grow(&buf, &g->ck_bytes, need, s, "irt_forward_ppv");
+      g->ck = reinterpret_cast<float*>(buf);
+      if (st) return st;
+      tab.j[0].ck = g->ck;
+      tab.j[0].ck_nb = kCkRows;
+      tab.j[0].ck_ray = ck_ray;
+      g->ck_sig = checkpoint_signature(jobs[0], P);
     }
     FwdLaunch L;
     L.total = total;
@@ -688,6 +732,12 @@ extern "C" irt_status irt_forward_ppv(const irt_job* jobs, int njobs, const irt_
   for (int j = 0; j < njobs; ++j) {
     st = check_job(jobs[j], opts->precision);
     if (st) return st;
+  }
+  if (opts->flags & IRT_FLAG_SAVE_CHECKPOINTS) {
+    if (njobs != 1 || jobs[0].view.trilinear != 0 || opts->integration != IRT_SMOOTH ||
+        opts->precision != IRT_PREC_F32)
+      return fail(IRT_EUNSUPPORTED, "irt_forward_ppv: IRT_FLAG_SAVE_CHECKPOINTS needs one "
+                                    "z-view job, smooth integration, float precision");
   }
   const PhysParams P = fold_constants(line, dust, opts);
   const PhysF PF = to_float(P);
@@ -902,6 +952,11 @@ extern "C" irt_status irt_adjoint_ppv(const irt_job* job, const irt_line* line,
   A.scratch_per_warp = per_warp_floats;
   A.defer = reinterpret_cast<unsigned*>(ss.defer);
   A.defer_max_nb = ni1;
+  if (g->ck && g->ck_sig == checkpoint_signature(jb, P)) {
+    A.ck_saved = g->ck;
+    A.ck_nb = kCkRows;
+    A.ck_ray = (long long)nseg * 2 * kCkRows * 32;
+  }
   // control words: [0] pass-0 queue, [7] pass-1 queue; defer[0] = 0
   cudaError_t ce = cudaMemsetAsync(g->ctl, 0, sizeof(unsigned long long), s);
   if (ce == cudaSuccess) ce = cudaMemsetAsync(g->ctl + 7, 0, sizeof(unsigned long long), s);

@@ -582,9 +582,13 @@ struct FastSmooth {
 
   // Runs the whole ray; writes the fine intensities of its blocks to fbuf
   // (hull-relative: fbuf[32 j + lane]) and returns this lane's basis value.
+  // ck (optional): this ray's checkpoint slot; after every full 32-sample
+  // chunk the state pair (I_{32s-2}, I_{32s-1}) of the hull blocks and the
+  // lane's basis pair go to segment s (the adjoint's layout, ck_nb rows)
   template <class Gen>
   static __device__ __forceinline__ float run(const PhysF& P, const Gen& gen, int K, int hb,
-                                              int lane, const VGrid& G, int nfw, float* fbuf) {
+                                              int lane, const VGrid& G, int nfw, float* fbuf,
+                                              float* ck = nullptr, int ck_nb = 0) {
     float u[NA], s0[NA], s1[NA];
 #pragma unroll
     for (int j = 0; j < NA; ++j) {
@@ -649,6 +653,16 @@ struct FastSmooth {
           step(ring[kk + 1], u, s1, s0, hb, lane, G, x1, x0, m1, m2);
         }
         if (k0 + 32 >= K) break;
+        if (NA < kCkRows && ck) {
+          float* c = ck + (long long)((k0 + 32) >> 5) * 2 * ck_nb * 32;
+#pragma unroll
+          for (int j = 0; j < NA; ++j) {
+            c[j * 32 + lane] = s0[j];
+            c[ck_nb * 32 + j * 32 + lane] = s1[j];
+          }
+          c[NA * 32 + lane] = x0;
+          c[ck_nb * 32 + NA * 32 + lane] = x1;
+        }
         k0 += 32;
         ring = gen.take_fwd(k0);
         kk = 0;
@@ -847,12 +861,12 @@ __device__ __forceinline__ int fast_bucket(int na, int ns) {
 template <int NI, int MODE, int NS, class Gen>
 __device__ __forceinline__ bool run_fast(int nb, const PhysF& P, const Gen& gen, int K, int hb,
                                          int lane, const VGrid& G, int nfw, float* fbuf,
-                                         float* kb, float* xb) {
+                                         float* kb, float* xb, float* ck, int ck_nb) {
 #define IRT_FAST(NA_)                                                                        \
   case NA_:                                                                                  \
     if constexpr (NA_ <= NI) {                                                               \
       if constexpr (MODE == M_SMOOTH)                                                        \
-        *xb = FastSmooth<NA_, NS>::run(P, gen, K, hb, lane, G, nfw, fbuf);                  \
+        *xb = FastSmooth<NA_, NS>::run(P, gen, K, hb, lane, G, nfw, fbuf, ck, ck_nb);       \
       else if constexpr (MODE == M_FORMAL)                                                   \
         *xb = FastFormal<NA_, NS>::run(P, gen, K, hb, lane, G, nfw, fbuf);                  \
       else                                                                                   \
@@ -1025,9 +1039,11 @@ __device__ void render_ray(const JobDev& J, const PhysParams& PD, const PhysF& P
         const int hb = none ? 0 : min(hlo, max(nblk - nb, 0));
         float xb = 0.0f;
         float* kb = reinterpret_cast<float*>(wsm + kb_off);
-        const bool fast =
-            (ns == 1) ? run_fast<NI, MODE, 1>(nb, PF, gen, K, hb, lane, G, nfw, fbuf, kb, &xb)
-                      : run_fast<NI, MODE, 2>(nb, PF, gen, K, hb, lane, G, nfw, fbuf, kb, &xb);
+        float* ck = J.ck ? J.ck + ((long long)py * J.npx + px) * J.ck_ray : nullptr;
+        const bool fast = (ns == 1) ? run_fast<NI, MODE, 1>(nb, PF, gen, K, hb, lane, G, nfw,
+                                                             fbuf, kb, &xb, ck, J.ck_nb)
+                                    : run_fast<NI, MODE, 2>(nb, PF, gen, K, hb, lane, G, nfw,
+                                                             fbuf, kb, &xb, ck, J.ck_nb);
         if (fast) {
           const float X0 = __shfl_sync(0xffffffffu, xb, 0);
           const float X1 = __shfl_sync(0xffffffffu, xb, 1);

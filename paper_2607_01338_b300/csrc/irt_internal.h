@@ -70,7 +70,9 @@ struct JobDev {
   int tw, th;            // rays are handed out in tiles of tw x th pixels
   int ntx;               // tiles per image row
   int kmax;              // upper bound of samples per ray
-  int pad0;
+  int ck_nb;             // rows of a saved checkpoint (hull blocks < ck_nb) or 0
+  float* ck;             // saved smooth-transfer checkpoints [ray][seg][2][ck_nb][32]
+  long long ck_ray;      // floats per ray of ck
   void* out[5];          // T, C, D, L, B cubes [nchan][npy][npx]
   long long item_begin;  // first global work item of this job
   long long nitems;      // npx * npy * nwin
@@ -80,6 +82,9 @@ constexpr int kWarpsPerBlock = 4;
 constexpr int kMaxJobs = 64;
 // Forward per-sample record sizes (float and double kernels) and the most
 // warps a forward kernel keeps resident on one SM (128 registers a thread).
+// Rows of a saved forward checkpoint: hull blocks of at most 9 (the first
+// adjoint pass) plus the basis row.
+constexpr int kCkRows = 10;
 constexpr int kRecBytesF32 = 48;
 constexpr int kRecBytesF64 = 64;
 constexpr int kFwdWarpsPerSm = 16;
@@ -96,6 +101,9 @@ struct AdjArgs {
   float* grad[3];               // n_H2, T_gas, v_los
   float* scratch;               // per-warp scratch (16-byte aligned slots)
   long long scratch_per_warp;   // floats, a multiple of 4
+  const float* ck_saved;        // checkpoints saved by the forward render, or nullptr
+  int ck_nb;                    // their rows (hull blocks < ck_nb)
+  long long ck_ray;             // floats per ray
   int pass;                     // 0: every ray, wide hulls deferred; 1: the deferred rays
   int defer_max_nb;             // widest hull bucket the second pass handles (0: none)
   unsigned* defer;              // [0] = count, then deferred ray indices

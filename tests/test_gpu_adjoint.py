@@ -26,12 +26,15 @@ def _cuda():
     import paper_2607_01338_b300  # noqa: F401
 
 
-def _gpu_loss_grads(f32, dx, view, va, target_L, integration="smooth"):
-    """GPU forward + adjoint of Loss = mean((L - target)^2)."""
+def _gpu_loss_grads(f32, dx, view, va, target_L, integration="smooth", save=False):
+    """GPU forward + adjoint of Loss = mean((L - target)^2); ``save`` lets the
+    forward keep its transfer checkpoints for the adjoint."""
     import paper_2607_01338_b300 as irt
+    from paper_2607_01338_b300 import binding as B
     ts = [torch.from_numpy(a).cuda() for a in f32.as_tuple()]
     g = irt.Grid(*ts, dx)
-    cubes = irt.forward(g, view, va, LINE, DUST, integration=integration)
+    cubes = irt.forward(g, view, va, LINE, DUST, integration=integration,
+                        flags=B.IRT_FLAG_SAVE_CHECKPOINTS if save else 0)
     tgt = torch.from_numpy(target_L.astype(np.float32)).cuda()
     L = cubes["L"]
     gL = 2.0 * (L - tgt) / L.numel()
@@ -57,8 +60,10 @@ def crop_fields(fs, n, seed=0):
     return FieldSet(*[np.ascontiguousarray(a[sl]) for a in fs.as_tuple()])
 
 
-def test_adjoint_matches_oracle_gradient_16cube():
-    """16^3 crop of the 128^3 adjoint workload (128 channels, f = 2)."""
+@pytest.mark.parametrize("save", [False, True])
+def test_adjoint_matches_oracle_gradient_16cube(save):
+    """16^3 crop of the 128^3 adjoint workload (128 channels, f = 2), with the
+    adjoint's own forward sweep and with the forward render's checkpoints."""
     w = workload(3, n=48)
     fs = crop_fields(make_fields(48, w.seed), 16, seed=3)
     tfs = crop_fields(make_fields(48, w.seed + 7), 16, seed=3)
@@ -67,11 +72,41 @@ def test_adjoint_matches_oracle_gradient_16cube():
     view = View(0.0, 0.0, 16, 16, w.cell_cm, 0)
     va = w.vaxis
     target = oracle.render_cube(tdeq.as_tuple(), w.cell_cm, LINE, DUST, view, va)["L"]
-    loss, (gn, gt, gv) = _gpu_loss_grads(f32, w.cell_cm, view, va, target)
+    loss, (gn, gt, gv) = _gpu_loss_grads(f32, w.cell_cm, view, va, target, save=save)
     oloss, on, ot, ov = oracle.loss_grad_zview(deq.as_tuple(), w.cell_cm, LINE, DUST, va, target)
     assert loss == pytest.approx(oloss, rel=1e-4)
     r = {k: _cmp(a, b) for k, a, b in (("n", gn, on), ("T", gt, ot), ("v", gv, ov))}
     assert all(v <= 1.0 for v in r.values()), r
+
+
+def test_saved_checkpoints_serve_only_the_same_job():
+    """Checkpoints written by one render are used by the adjoint of the same
+    job (results within float rounding of the self-contained adjoint) and
+    ignored for another job (different background): then the adjoint is
+    bit-identical to one without checkpoints."""
+    import paper_2607_01338_b300 as irt
+    from paper_2607_01338_b300 import binding as B
+    fs = make_fields(48, 91)
+    f32, _ = to_storage(crop_fields(fs, 24, seed=2), np.float32)
+    ts = [torch.from_numpy(a).cuda() for a in f32.as_tuple()]
+    dx = 0.1 * PC
+    view = View(0.0, 0.0, 24, 24, dx, 0)
+    va = VelocityAxis(96, -60.0, 1.25, 2)
+    g0, g1 = irt.Grid(*ts, dx), irt.Grid(*ts, dx)
+    L = irt.forward(g0, view, va, LINE, DUST)["L"]
+    cot = {"L": L * 1e-3}
+    ref = irt.adjoint(g0, view, va, LINE, DUST, cot)
+    irt.forward(g1, view, va, LINE, DUST, flags=B.IRT_FLAG_SAVE_CHECKPOINTS)
+    used = irt.adjoint(g1, view, va, LINE, DUST, cot)
+    other = irt.adjoint(g1, view, va, LINE, DUST, cot, t_bg=2.7)
+    ref_other = irt.adjoint(g0, view, va, LINE, DUST, cot, t_bg=2.7)
+    torch.cuda.synchronize()
+    for a, b in zip(used, ref):
+        assert torch.allclose(a, b, rtol=1e-4, atol=1e-4 * float(b.abs().max()))
+    for a, b in zip(other, ref_other):
+        assert torch.equal(a, b)
+    g0.close()
+    g1.close()
 
 
 def test_adjoint_matches_fp64_finite_differences_128cube():
