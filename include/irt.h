@@ -261,7 +261,8 @@ irt_status irt_adjoint_ppv(const irt_job* job, const irt_line* line, const irt_d
  * ray).  A grid needing more than 32 MiB of packed cells (32, 16 or
  * 64 bytes per cell for float, 16-bit or double storage; e.g. 1,048,576 float
  * cells) is rejected with IRT_EINVAL and a message giving both sizes.  The
- * call issues no cudaMalloc/cudaFree.  The first call on a device looks up the
+ * call issues no cudaMalloc/cudaFree.  IRT_FLAG_SAVE_CHECKPOINTS gives
+ * IRT_EUNSUPPORTED (no grid keeps them).  The first call on a device looks up the
  * array's device address (cudaGetSymbolAddress); make that first call before
  * any stream capture.  All calls share the array and it keeps the last call's
  * contents (the counter is cleared by each call): calls whose kernels overlap

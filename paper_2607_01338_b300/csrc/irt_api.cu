@@ -1070,6 +1070,8 @@ extern "C" irt_status irt_forward_ppv_static(const irt_grid_desc* desc, const ir
                 need, ncell, cb, kStaticCellBytes, kStaticCellBytes / cb);
   irt_status st = check_line(line, dust, opts);
   if (st) return st;
+  if (opts->flags & IRT_FLAG_SAVE_CHECKPOINTS)
+    return fail(IRT_EUNSUPPORTED, "irt_forward_ppv_static: no checkpoints (no grid keeps them)");
 
   // a grid descriptor on the host stack pointing into the static array
   irt_grid g;

@@ -585,10 +585,10 @@ struct FastSmooth {
   // ck (optional): this ray's checkpoint slot; after every full 32-sample
   // chunk the state pair (I_{32s-2}, I_{32s-1}) of the hull blocks and the
   // lane's basis pair go to segment s (the adjoint's layout, ck_nb rows)
-  template <class Gen>
+  template <bool CK, class Gen>
   static __device__ __forceinline__ float run(const PhysF& P, const Gen& gen, int K, int hb,
                                               int lane, const VGrid& G, int nfw, float* fbuf,
-                                              float* ck = nullptr, int ck_nb = 0) {
+                                              float* ck, int ck_nb) {
     float u[NA], s0[NA], s1[NA];
 #pragma unroll
     for (int j = 0; j < NA; ++j) {
@@ -653,7 +653,7 @@ struct FastSmooth {
           step(ring[kk + 1], u, s1, s0, hb, lane, G, x1, x0, m1, m2);
         }
         if (k0 + 32 >= K) break;
-        if (NA < kCkRows && ck) {
+        if (CK && NA < kCkRows && ck) {
           float* c = ck + (long long)((k0 + 32) >> 5) * 2 * ck_nb * 32;
 #pragma unroll
           for (int j = 0; j < NA; ++j) {
@@ -858,7 +858,7 @@ __device__ __forceinline__ int fast_bucket(int na, int ns) {
 
 // Runs the fast path for bucket `nb` (<= NI); returns false if nb is not
 // compiled for this NI.
-template <int NI, int MODE, int NS, class Gen>
+template <int NI, int MODE, int NS, bool CK, class Gen>
 __device__ __forceinline__ bool run_fast(int nb, const PhysF& P, const Gen& gen, int K, int hb,
                                          int lane, const VGrid& G, int nfw, float* fbuf,
                                          float* kb, float* xb, float* ck, int ck_nb) {
@@ -866,7 +866,7 @@ __device__ __forceinline__ bool run_fast(int nb, const PhysF& P, const Gen& gen,
   case NA_:                                                                                  \
     if constexpr (NA_ <= NI) {                                                               \
       if constexpr (MODE == M_SMOOTH)                                                        \
-        *xb = FastSmooth<NA_, NS>::run(P, gen, K, hb, lane, G, nfw, fbuf, ck, ck_nb);       \
+        *xb = FastSmooth<NA_, NS>::template run<CK>(P, gen, K, hb, lane, G, nfw, fbuf, ck, ck_nb); \
       else if constexpr (MODE == M_FORMAL)                                                   \
         *xb = FastFormal<NA_, NS>::run(P, gen, K, hb, lane, G, nfw, fbuf);                  \
       else                                                                                   \
@@ -904,7 +904,7 @@ template <> struct PSel<false> {
 // ---------------------------------------------------------------------------
 // one work item: ray (px, py) of job J, every channel
 // ---------------------------------------------------------------------------
-template <typename R, int NI, int ST, int MODE>
+template <typename R, int NI, int ST, int MODE, bool CK>
 __device__ void render_ray(const JobDev& J, const PhysParams& PD, const PhysF& PF, int px,
                            int py, unsigned char* wsm, int fw_off, int cw_off, int kb_off,
                            typename RecOf<R, MODE>::type* grec, int lane, unsigned flags,
@@ -1039,11 +1039,11 @@ __device__ void render_ray(const JobDev& J, const PhysParams& PD, const PhysF& P
         const int hb = none ? 0 : min(hlo, max(nblk - nb, 0));
         float xb = 0.0f;
         float* kb = reinterpret_cast<float*>(wsm + kb_off);
-        float* ck = J.ck ? J.ck + ((long long)py * J.npx + px) * J.ck_ray : nullptr;
-        const bool fast = (ns == 1) ? run_fast<NI, MODE, 1>(nb, PF, gen, K, hb, lane, G, nfw,
-                                                             fbuf, kb, &xb, ck, J.ck_nb)
-                                    : run_fast<NI, MODE, 2>(nb, PF, gen, K, hb, lane, G, nfw,
-                                                             fbuf, kb, &xb, ck, J.ck_nb);
+        float* ck = (CK && J.ck) ? J.ck + ((long long)py * J.npx + px) * J.ck_ray : nullptr;
+        const bool fast = (ns == 1) ? run_fast<NI, MODE, 1, CK>(nb, PF, gen, K, hb, lane, G,
+                                                                 nfw, fbuf, kb, &xb, ck, J.ck_nb)
+                                    : run_fast<NI, MODE, 2, CK>(nb, PF, gen, K, hb, lane, G,
+                                                                 nfw, fbuf, kb, &xb, ck, J.ck_nb);
         if (fast) {
           const float X0 = __shfl_sync(0xffffffffu, xb, 0);
           const float X1 = __shfl_sync(0xffffffffu, xb, 1);
@@ -1141,7 +1141,9 @@ __device__ void render_ray(const JobDev& J, const PhysParams& PD, const PhysF& P
   }
 }
 
-template <typename R, int NI, int ST, int MODE>
+// CK: the job saves smooth-transfer checkpoints (a separate instance, so that
+// renders without them run no checkpoint code)
+template <typename R, int NI, int ST, int MODE, bool CK>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32, (sizeof(R) == 4 && NI <= 17) ? 4 : 1)
 fwd_kernel(const __grid_constant__ JobTable tab, int njobs, const PhysParams PD, const PhysF PF,
            long long total_items, unsigned long long* queue, int per_warp, int fw_off, int cw_off,
@@ -1179,8 +1181,8 @@ fwd_kernel(const __grid_constant__ JobTable tab, int njobs, const PhysParams PD,
     const int py = (int)(tile / J.ntx) * J.th + within / J.tw;
     if constexpr (ST == ST_F64 || sizeof(R) == 4) {
       if (px < J.npx && py < J.npy)
-        render_ray<R, NI, ST, MODE>(J, PD, PF, px, py, wsm, fw_off, cw_off, kb_off, grec, lane,
-                                    flags, stats);
+        render_ray<R, NI, ST, MODE, CK>(J, PD, PF, px, py, wsm, fw_off, cw_off, kb_off, grec,
+                                        lane, flags, stats);
     }
     if (queue) {
       unsigned long long t = 0;
@@ -1198,7 +1200,7 @@ fwd_kernel(const __grid_constant__ JobTable tab, int njobs, const PhysParams PD,
 // is the resident maximum, capped by the record scratch: each warp needs kmax
 // records.  L.queue (zero at launch) selects the dynamic schedule, nullptr the
 // round-robin one.
-template <typename R, int NI, int ST, int MODE>
+template <typename R, int NI, int ST, int MODE, bool CK = false>
 int launch_fwd_inst(const JobTable& tab, int njobs, const PhysParams& P, const PhysF& PF,
                     const FwdLaunch& L, cudaStream_t stream) {
   using Rec = typename dev::RecOf<R, MODE>::type;
@@ -1213,7 +1215,7 @@ int launch_fwd_inst(const JobTable& tab, int njobs, const PhysParams& P, const P
   const int per_warp = (kb_off + kb_bytes + 15) & ~15;
   const size_t smem = (size_t)per_warp * kWarpsPerBlock;
   const long long rstride = ((long long)L.kmax * (long long)sizeof(Rec) + 255) & ~255ll;
-  auto kern = dev::fwd_kernel<R, NI, ST, MODE>;
+  auto kern = dev::fwd_kernel<R, NI, ST, MODE, CK>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return (int)e;

@@ -113,6 +113,15 @@ def test_validation_before_any_launch(B):
     nan_opts = B.irt_opts(0, 1, 0, float("nan"), 0, 0)
     assert L.irt_forward_ppv(ctypes.byref(job), 1, ctypes.byref(line), ctypes.byref(dust),
                              ctypes.byref(nan_opts), None) == B.IRT_EINVAL
+    # the allocation-free entry keeps no checkpoints: refused before any CUDA call
+    sdesc = B.irt_grid_desc(4, 4, 4, 1.0, (ctypes.c_int * 5)(0, 0, 0, 0, 0))
+    save = B.irt_opts(0, 1, 0, 2.725, 0, B.IRT_FLAG_SAVE_CHECKPOINTS)
+    cubes = B.irt_cubes(1, None, None, None, None)
+    assert L.irt_forward_ppv_static(ctypes.byref(sdesc), ctypes.byref(f), ctypes.byref(job.view),
+                                    ctypes.byref(job.vaxis), ctypes.byref(cubes),
+                                    ctypes.byref(line), ctypes.byref(dust), ctypes.byref(save),
+                                    None) == B.IRT_EUNSUPPORTED
+    assert b"checkpoints" in L.irt_last_error()
     assert L.irt_destroy(None) == B.IRT_OK
 
 
