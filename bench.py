@@ -423,9 +423,9 @@ def gpu_arm(args):
     # have no capture
     traffic = None
     if nx == 256 and is_adj:
-        traffic = 1.35e9 + 956.22e6 + 66.05e3
+        traffic = 1.35e9 + 1.01e9 + 66.56e3
     elif nx == 256 and not is_adj:
-        traffic = (586.57e6 + 1.35e9) if dom == 0 else (1.99e9 + 1.27e9)
+        traffic = (604.34e6 + 1.38e9) if dom == 0 else (1.73e9 + 1.14e9)
     roofline = {"bound": "alu", "pipe": pipe, "achieved": ach, "peak": peak, "unit": "Top/s",
                 "frac": ach / peak, "traffic": traffic, "traffic_unit": "bytes per launch",
                 "kernel": kname,
