@@ -370,14 +370,33 @@ __device__ __forceinline__ float fine_cotangent(int g, int f, int cwn, const flo
   return acc / (float)(6 * f);
 }
 
+// Launch constants the reverse sweep reads, kept in shared memory: the sweep
+// is a separate (non-inlined) function per hull bucket, and a reference to
+// the kernel's parameters would make the compiler copy them to the stack,
+// turning every read into a local-memory load.
+struct AdjRayArgs {
+  const float* ck_saved;   // forward checkpoints of the job or nullptr
+  long long ck_ray;        // floats per ray of ck_saved
+  float* grad[3];          // n_H2, T_gas, v_los
+  int ck_nb;               // rows of a saved checkpoint
+  int npx, nx, ny;         // image width, grid extent in x and y
+  float cad_h;             // cad * cell size: d(h alpha_D) / d n_H2
+  float T0, inv_c_kms, t_bg;   // background Planck function (K units)
+};
+
 // Reverse sweep of one ray with NA explicit hull blocks and NS line slots.
 template <int NA, int NS, int ST>
-__device__ __noinline__ void adj_ray(const JobDev& J, const PhysF& P, const AdjArgs& A,
-                                     const RecS32* rec, const float* chainf, int K, int hb,
-                                     int lane, const VGrid& G, int nfw, const float* lamf,
-                                     float lx, float* pbuf, float* scr, int px, int py) {
+__device__ __noinline__ void adj_ray(const AdjRayArgs* __restrict__ Ap, const RecS32* rec,
+                                     const float* chainf, int K, int hb, int lane, const VGrid G,
+                                     int nfw, const float* lamf, float lx, float* pbuf, float* scr,
+                                     int px, int py) {
   using AD = Adj<NA, NS>;
   constexpr int NB = NA + 1;
+  const AdjRayArgs& A = *Ap;
+  PhysF P;   // the fields planck_k reads
+  P.T0 = A.T0;
+  P.inv_c_kms = A.inv_c_kms;
+  P.t_bg = A.t_bg;
   float u[NA];
 #pragma unroll
   for (int j = 0; j < NA; ++j) {
@@ -393,7 +412,7 @@ __device__ __noinline__ void adj_ray(const JobDev& J, const PhysF& P, const AdjA
   const bool saved = A.ck_saved != nullptr && NA < A.ck_nb;
   const int cs = saved ? A.ck_nb : NB;
   const float* ck =
-      saved ? A.ck_saved + ((long long)py * J.npx + px) * A.ck_ray : scr;
+      saved ? A.ck_saved + ((long long)py * A.npx + px) * A.ck_ray : scr;
   float* pre = scr + (long long)nseg * 2 * NB * 32;       // [kSub][NB][32]
   float sa[NA], sb[NA], xa, xb;
 
@@ -424,6 +443,7 @@ __device__ __noinline__ void adj_ray(const JobDev& J, const PhysF& P, const AdjA
     ln[j] = (g < nfw) ? lamf[g] : 0.0f;
     lm[j] = 0.0f;
   }
+  __syncwarp();   // the partial buffer below overlays the fine cotangents
   float xln = lx, xlm = 0.0f;
   for (int s = nseg - 1; s >= 0; --s) {
     const int seg_lo = s * kSeg;
@@ -502,9 +522,9 @@ __device__ __noinline__ void adj_ray(const JobDev& J, const PhysF& P, const AdjA
           // d/dT = G_jl d(2h j_L)/dT + G_al d(2h alpha_L)/dT + G_b db/dT; d/dv = G_v
           const float gad = g5[0 * kPStride], gjl = g5[1 * kPStride], gal = g5[2 * kPStride];
           const float gvv = g5[3 * kPStride], gb = g5[4 * kPStride];
-          const float gn = fmaf(gjl, cf[0], fmaf(gal, cf[1], gad * P.cad * (float)J.dx));
+          const float gn = fmaf(gjl, cf[0], fmaf(gal, cf[1], gad * A.cad_h));
           const float gt = fmaf(gjl, cf[2], fmaf(gal, cf[3], gb * cf[4]));
-          const long long idx = ((long long)n * J.ny + py) * J.nx + px;
+          const long long idx = ((long long)n * A.ny + py) * A.nx + px;
           A.grad[0][idx] = gn;
           A.grad[1][idx] = gt;
           A.grad[2][idx] = gvv;
@@ -542,14 +562,13 @@ __device__ __forceinline__ int adj_bucket(int na, int ns) {
 }
 
 template <int NA, int NS, int NI, int ST>
-__device__ __forceinline__ bool adj_run_bucket(const JobDev& J, const PhysF& P,
-                                               const AdjArgs& A, const RecS32* rec,
+__device__ __forceinline__ bool adj_run_bucket(const AdjRayArgs* A, const RecS32* rec,
                                                const float* chainf, int K, int hb, int lane,
                                                const VGrid& G, int nfw, const float* lamf,
                                                float lx, float* pbuf, float* scr, int px,
                                                int py) {
   if constexpr (NA <= NI) {
-    adj_ray<NA, NS, ST>(J, P, A, rec, chainf, K, hb, lane, G, nfw, lamf, lx, pbuf, scr, px, py);
+    adj_ray<NA, NS, ST>(A, rec, chainf, K, hb, lane, G, nfw, lamf, lx, pbuf, scr, px, py);
     return true;
   }
   return false;
@@ -557,14 +576,14 @@ __device__ __forceinline__ bool adj_run_bucket(const JobDev& J, const PhysF& P,
 
 template <int NS, int NI, int ST, int... B>
 __device__ __forceinline__ void adj_dispatch(std::integer_sequence<int, B...>, int nb,
-                                             const JobDev& J, const PhysF& P, const AdjArgs& A,
-                                             const RecS32* rec, const float* chainf, int K,
-                                             int hb, int lane, const VGrid& G, int nfw,
-                                             const float* lamf, float lx, float* pbuf,
-                                             float* scr, int px, int py) {
+                                             const AdjRayArgs* A, const RecS32* rec,
+                                             const float* chainf, int K, int hb, int lane,
+                                             const VGrid& G, int nfw, const float* lamf,
+                                             float lx, float* pbuf, float* scr, int px,
+                                             int py) {
   bool done = false;
-  ((done = done || (nb == B && adj_run_bucket<B, NS, NI, ST>(J, P, A, rec, chainf, K, hb, lane,
-                                                             G, nfw, lamf, lx, pbuf, scr, px,
+  ((done = done || (nb == B && adj_run_bucket<B, NS, NI, ST>(A, rec, chainf, K, hb, lane, G,
+                                                             nfw, lamf, lx, pbuf, scr, px,
                                                              py))),
    ...);
 }
@@ -573,10 +592,10 @@ __device__ __forceinline__ void adj_dispatch(std::integer_sequence<int, B...>, i
 // defers the rays whose hull is wider than NI blocks to the list A.defer
 // ([0] = count, then ray indices); pass 1 takes the rays of that list.
 template <int NI, int ST>
-__global__ void __launch_bounds__(kAdjWarps * 32, (NI <= 9) ? 8 : 1)
+__global__ void __launch_bounds__(kAdjWarps * 32, (NI <= 9) ? 6 : 1)
 adj_kernel(const __grid_constant__ JobTable tab, const PhysF PF, const AdjArgs A,
            long long total_items, unsigned long long* queue, int per_warp, int fw_off,
-           int cw_off, int pb_off) {
+           int cw_off, int pb_off, int ra_off) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
@@ -584,12 +603,29 @@ adj_kernel(const __grid_constant__ JobTable tab, const PhysF PF, const AdjArgs A
   RecS32* rec = reinterpret_cast<RecS32*>(wsm);
   float* lamf = reinterpret_cast<float*>(wsm + fw_off);   // fine cotangents
   float* lamc = reinterpret_cast<float*>(wsm + cw_off);   // channel cotangents (T total)
-  float* pbuf = reinterpret_cast<float*>(wsm + pb_off);   // [kFlush][kNP][kPStride]
+  float* pbuf = reinterpret_cast<float*>(wsm + pb_off);   // [kFlush][kNP][kPStride], over lamf
+  AdjRayArgs* RA = reinterpret_cast<AdjRayArgs*>(wsm + ra_off);
   const long long gw = (long long)blockIdx.x * kAdjWarps + warp;
   float* scr = A.scratch + gw * A.scratch_per_warp;
   // chain-rule factors [K][kNC] at the end of the warp's scratch
   float* chainf = scr + A.scratch_per_warp - (long long)kNC * J0kmax(tab);
   const JobDev& J = tab.j[0];
+  if (lane == 0) {
+    RA->ck_saved = A.ck_saved;
+    RA->ck_ray = A.ck_ray;
+    RA->grad[0] = A.grad[0];
+    RA->grad[1] = A.grad[1];
+    RA->grad[2] = A.grad[2];
+    RA->ck_nb = A.ck_nb;
+    RA->npx = J.npx;
+    RA->nx = J.nx;
+    RA->ny = J.ny;
+    RA->cad_h = PF.cad * (float)J.dx;
+    RA->T0 = PF.T0;
+    RA->inv_c_kms = PF.inv_c_kms;
+    RA->t_bg = PF.t_bg;
+  }
+  __syncwarp();
 
   const long long n_items = (A.pass == 0) ? total_items : (long long)A.defer[0];
   for (;;) {
@@ -722,11 +758,11 @@ adj_kernel(const __grid_constant__ JobTable tab, const PhysF PF, const AdjArgs A
     const float lx = (lane == 0) ? lx0 : ((lane == 1) ? lx1 : ((lane == 2) ? lx2 : 0.0f));
 
     if (ns == 1)
-      adj_dispatch<1, NI, ST>(std::integer_sequence<int, IRT_ADJ_BUCKETS1>{}, nb, J, PF, A, rec,
-                              chainf, K, hb, lane, G, nfw, lamf, lx, pbuf, scr, px, py);
+      adj_dispatch<1, NI, ST>(std::integer_sequence<int, IRT_ADJ_BUCKETS1>{}, nb, RA, rec, chainf,
+                              K, hb, lane, G, nfw, lamf, lx, pbuf, scr, px, py);
     else
-      adj_dispatch<2, NI, ST>(std::integer_sequence<int, IRT_ADJ_BUCKETS2>{}, nb, J, PF, A, rec,
-                              chainf, K, hb, lane, G, nfw, lamf, lx, pbuf, scr, px, py);
+      adj_dispatch<2, NI, ST>(std::integer_sequence<int, IRT_ADJ_BUCKETS2>{}, nb, RA, rec, chainf,
+                              K, hb, lane, G, nfw, lamf, lx, pbuf, scr, px, py);
     __syncwarp();
   }
 }
@@ -740,8 +776,13 @@ int launch_adjoint(int store, int ni, const JobTable& tab, const PhysF& PF, cons
   const int rec_bytes = (int)sizeof(dev::RecS32) * kmax;
   const int fw_off = (rec_bytes + 15) & ~15;
   const int cw_off = (fw_off + 4 * nfw + 15) & ~15;
-  const int pb_off = (cw_off + 4 * nchan + 15) & ~15;
-  const int per_warp = (pb_off + 4 * dev::kFlush * dev::kNP * dev::kPStride + 15) & ~15;
+  const int co_end = cw_off + 4 * nchan;
+  // the reverse sweep's partial buffer reuses the cotangent arrays, which
+  // are dead once the sweep has read its fine cotangents
+  const int pb_off = fw_off;
+  const int pb_end = pb_off + 4 * dev::kFlush * dev::kNP * dev::kPStride;
+  const int ra_off = ((co_end > pb_end ? co_end : pb_end) + 15) & ~15;
+  const int per_warp = (ra_off + (int)sizeof(dev::AdjRayArgs) + 15) & ~15;
   if (per_warp_smem) *per_warp_smem = per_warp;
   const size_t smem = (size_t)per_warp * kAdjWarps;
 #define IRT_LAUNCH(NI_, ST_)                                                                  \
@@ -752,7 +793,7 @@ int launch_adjoint(int store, int ni, const JobTable& tab, const PhysF& PF, cons
     if (e != cudaSuccess) return (int)e;                                                      \
     if (blocks <= 0) return 0;                                                                \
     kern<<<blocks, kAdjWarps * 32, smem, stream>>>(tab, PF, A, total_items, queue,            \
-                                                   per_warp, fw_off, cw_off, pb_off);         \
+                                                   per_warp, fw_off, cw_off, pb_off, ra_off); \
     return (int)cudaGetLastError();                                                           \
   }
   IRT_LAUNCH(9, ST_F32) IRT_LAUNCH(17, ST_F32) IRT_LAUNCH(33, ST_F32)
