@@ -63,8 +63,13 @@ def lib():
             L.oracle_render.argtypes = ([ctypes.POINTER(_dp), ctypes.c_int, ctypes.c_int,
                                          ctypes.c_int, ctypes.c_double, _dp, _dp, _dp,
                                          ctypes.c_int, ctypes.c_double, ctypes.c_double,
-                                         ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                         ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                          ctypes.c_double, ctypes.c_int, _ip] + [_dp] * 5)
+            L.oracle_ray_thin.restype = None
+            L.oracle_ray_thin.argtypes = ([_dp, _dp, ctypes.c_int, ctypes.c_double,
+                                           ctypes.c_double, ctypes.c_int, ctypes.c_int,
+                                           ctypes.c_int, ctypes.c_double, ctypes.c_int]
+                                          + [_dp] * 5 + [ctypes.c_double] + [_dp] * 5)
             L.oracle_loss_grad_zview.restype = ctypes.c_double
             L.oracle_loss_grad_zview.argtypes = ([ctypes.POINTER(_dp), ctypes.c_int, ctypes.c_int,
                                                   ctypes.c_int, ctypes.c_double, _dp, _dp,
@@ -84,6 +89,7 @@ LINE_KEYS = ("nu_ul_hz", "a_ul_s", "e_u_k", "b0_hz", "g_u", "g_l", "mass_amu", "
              "sigma_turb_kms")
 DUST_KEYS = ("kappa_cm2_per_g_gas", "mu_mass_per_h2_amu")
 FORMAL, SMOOTH = 0, 1
+THICK, SELECTIVELY_THIN, THIN = 0, 1, 2   # transfer modes (Sec. 4.5-4.7)
 TRJ, INTENSITY = 0, 1
 
 
@@ -166,8 +172,26 @@ def ray_samples(fields, cell_cm, view, px, py, kmax=100000):
     return buf[:K].copy(), float(h[0])
 
 
+def ray_thin(line, dust, vaxis, samples, h, transfer=SELECTIVELY_THIN, integration=SMOOTH,
+             units=TRJ, t_bg=2.725):
+    """One ray from explicit samples in a thin transfer mode (no velocity
+    subsampling: the channel-averaged profile is analytic).  Returns dict of
+    [nchan] arrays T, C, D, L, B."""
+    kl, pl = _line(line)
+    kd, pd = _dust(dust)
+    cols = [np.ascontiguousarray(np.asarray(samples[k], dtype=np.float64))
+            for k in ("n_h2", "t_gas", "t_dust", "v_los", "x_tr")]
+    K = len(cols[0])
+    nch = vaxis.nchan
+    outs = [np.zeros(nch) for _ in range(5)]
+    lib().oracle_ray_thin(pl, pd, nch, vaxis.v_first_edge_kms, vaxis.dv_kms, transfer,
+                          integration, units, t_bg, K, *[c.ctypes.data_as(_dp) for c in cols], h,
+                          *[o.ctypes.data_as(_dp) for o in outs])
+    return dict(zip("TCDLB", outs))
+
+
 def render(fields, cell_cm, line, dust, view, vaxis, pixels, integration=SMOOTH, units=TRJ,
-           t_bg=2.725):
+           t_bg=2.725, transfer=THICK):
     """Render the pixels ``pixels`` (int array [npix, 2] of (px, py)).
     Returns dict of [npix, nchan] float64 arrays T, C, D, L, B."""
     nz, ny, nx = np.asarray(fields[0]).shape
@@ -180,7 +204,7 @@ def render(fields, cell_cm, line, dust, view, vaxis, pixels, integration=SMOOTH,
     nch = vaxis.nchan
     outs = [np.zeros((npix, nch)) for _ in range(5)]
     lib().oracle_render(ptrs, nx, ny, nz, cell_cm, pl, pd, pv, nch, vaxis.v_first_edge_kms,
-                        vaxis.dv_kms, vaxis.subsample_f, integration, units, t_bg, npix,
+                        vaxis.dv_kms, vaxis.subsample_f, transfer, integration, units, t_bg, npix,
                         pix.ctypes.data_as(_ip), *[o.ctypes.data_as(_dp) for o in outs])
     return dict(zip("TCDLB", outs))
 

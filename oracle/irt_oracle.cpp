@@ -17,6 +17,10 @@
 //   Sec. 4.5  fine velocity grid + Simpson rule for the total intensity
 //   Sec. 4.8  formal step and smooth (TR first step, BDF2, ReLU) integration
 //   Sec. 4.9  Rayleigh-Jeans temperature;  Sec. 4.10  continuum subtraction
+//   Sec. 4.6  selectively thin transfer (channel-averaged profile by erf, the
+//             line sees the continuum only), Sec. 4.7 optically thin transfer
+//             (direct integral: midpoint sum or Simpson), with the step
+//             substitutions of Sec. 4.8
 //
 // Readings taken where the paper is silent (each is listed with its reason
 // in the design notes):
@@ -31,6 +35,13 @@
 //   * Smooth integration places the background at the first sample node, so
 //     it integrates (K-1) h; formal integration integrates K h.
 //   * [D] = [C] - [B] (continuum excess over the background), [L] = [T] - [C].
+//   * Thin modes: dust source and background at the channel centre; the
+//     channel-averaged profile is the Gaussian's probability mass inside the
+//     channel over the channel width in Hz (the printed erf expression is the
+//     antiderivative); the selectively thin formal step of the total uses the
+//     continuum after its own step (continuum solved first); the optically
+//     thin Simpson sum covers the node pairs and a trapezoid closes an odd
+//     last interval.
 //   * Geometry: z view = one ray per cell column, samples at the cells;
 //     oblique view = orthographic rays, chord split into K = ceil(chord/dx)
 //     equal steps, samples at step midpoints, trilinear field sampling with
@@ -142,6 +153,7 @@ struct VAxis {
   int f;
 };
 enum { FORMAL = 0, SMOOTH = 1 };
+enum { MODE_THICK = 0, MODE_SELECTIVELY_THIN = 1, MODE_THIN = 2 };
 enum { UNITS_TRJ = 0, UNITS_INTENSITY = 1 };
 
 // Sample values along one ray, in the order the ray travels (background side
@@ -345,6 +357,114 @@ void ray_outputs(const Line& ln, const DustP& du, const VAxis& va, int mode, int
   }
 }
 
+// Channel average of the line profile per Hz over [u_lo, u_hi] (Sec. 4.6):
+// the probability mass of the Gaussian inside the channel, divided by the
+// channel width in Hz.
+double channel_profile(const Line& ln, const Sample<double>& s, double u_lo, double u_hi) {
+  const double m = ln.mass_amu * AMU;
+  const double b2_cms = 2.0 * K_BOLTZ * s.t_gas / m
+                      + 2.0 * (ln.sigma_turb * 1e5) * (ln.sigma_turb * 1e5);
+  const double b_kms = std::sqrt(b2_cms) / 1e5;
+  const double x_lo = (u_lo - s.v_los) / b_kms;
+  const double x_hi = (u_hi - s.v_los) / b_kms;
+  const double mass = 0.5 * (std::erf(x_hi) - std::erf(x_lo));
+  const double width_hz = ln.nu_ul * (u_hi - u_lo) / C_KMS;
+  return mass / width_hz;
+}
+
+// Intensities along the ray of one frequency with coefficients j[k], a[k]:
+// formal, the value after each step k; smooth, the value at each node k
+// (node 0 = background, TR to node 1, BDF2 after, ReLU on each step).
+std::vector<double> path(int mode, const std::vector<double>& j, const std::vector<double>& a,
+                         double h, double I0) {
+  const int K = (int)j.size();
+  std::vector<double> I(K);
+  if (mode == FORMAL) {
+    double x = I0;
+    for (int k = 0; k < K; ++k) {
+      x = formal_step(x, j[k], a[k], h);
+      I[k] = x;
+    }
+    return I;
+  }
+  if (K >= 1) I[0] = I0;
+  if (K >= 2) I[1] = relu((h * (j[0] + j[1]) + (2.0 - h * a[0]) * I[0]) / (2.0 + h * a[1]));
+  for (int n = 0; n + 2 < K; ++n)
+    I[n + 2] = relu((2.0 * h * j[n + 2] + 4.0 * I[n + 1] - I[n]) / (3.0 + 2.0 * h * a[n + 2]));
+  return I;
+}
+
+// Direct integral of f over the ray (Sec. 4.7): formal = midpoint sum over
+// the K steps; smooth = composite Simpson over the K nodes (spacing h), the
+// last interval by the trapezoid rule when K - 1 is odd.
+double direct_integral(int mode, const std::vector<double>& f, double h) {
+  const int K = (int)f.size();
+  double acc = 0.0;
+  if (mode == FORMAL) {
+    for (int k = 0; k < K; ++k) acc += h * f[k];
+    return acc;
+  }
+  const int M = K - 1;                 // intervals
+  const int Ms = (M % 2 == 0) ? M : M - 1;   // covered by Simpson panels
+  for (int p = 0; p + 2 <= Ms; p += 2) acc += (h / 3.0) * (f[p] + 4.0 * f[p + 1] + f[p + 2]);
+  if (Ms < M) acc += 0.5 * h * (f[M - 1] + f[M]);
+  return acc;
+}
+
+// Outputs of one ray in the selectively thin or optically thin mode (no
+// fine velocities: every channel is solved at its own averaged coefficients).
+void ray_outputs_thin(const Line& ln, const DustP& du, const VAxis& va, int transfer, int mode,
+                      int units, double t_bg, const std::vector<Sample<double>>& smp, double h,
+                      double* oT, double* oC, double* oD, double* oL, double* oB) {
+  const int K = (int)smp.size();
+  std::vector<double> jL(K), aL(K), aD(K);
+  for (int k = 0; k < K; ++k) {
+    line_coefficients(ln, smp[k], &jL[k], &aL[k]);
+    aD[k] = dust_alpha(du, smp[k]);
+  }
+  std::vector<double> jLb(K), aLb(K), jD(K), jT(K), aT(K);
+  for (int c = 0; c < va.nchan; ++c) {
+    const double u_lo = va.v0 + c * va.dv, u_hi = u_lo + va.dv;
+    const double uc = va.v0 + (c + 0.5) * va.dv;
+    const double nuc = nu_of_u(ln, uc);
+    for (int k = 0; k < K; ++k) {
+      const bool no_line = jL[k] == 0.0 && aL[k] == 0.0;
+      const double phib = no_line ? 0.0 : channel_profile(ln, smp[k], u_lo, u_hi);
+      jLb[k] = jL[k] * phib;
+      aLb[k] = aL[k] * phib;
+      jD[k] = aD[k] * planck(nuc, smp[k].t_dust);
+    }
+    const double IB = planck(nuc, t_bg);
+    double IT, IC;
+    if (transfer == MODE_THIN) {
+      // absorption and stimulation ignored: I = I_bg + integral of j
+      for (int k = 0; k < K; ++k) jT[k] = jLb[k] + jD[k];
+      IT = IB + direct_integral(mode, jT, h);
+      IC = IB + direct_integral(mode, jD, h);
+    } else {
+      // continuum first, then the total with j = jL + jD - aL I_C, a = aD
+      const std::vector<double> Ic = path(mode, jD, aD, h, IB);
+      for (int k = 0; k < K; ++k) {
+        jT[k] = jLb[k] + jD[k] - aLb[k] * Ic[k];
+        aT[k] = aD[k];
+      }
+      const std::vector<double> It = path(mode, jT, aT, h, IB);
+      IC = (K >= 1) ? Ic[K - 1] : IB;
+      IT = (K >= 1) ? It[K - 1] : IB;
+    }
+    double vT = IT, vC = IC, vB = IB;
+    if (units == UNITS_TRJ) {
+      const double sc = rj_temperature(nuc, 1.0);
+      vT *= sc; vC *= sc; vB *= sc;
+    }
+    oT[c] = vT;
+    oC[c] = vC;
+    oB[c] = vB;
+    oL[c] = vT - vC;
+    oD[c] = vC - vB;
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Geometry
 // ---------------------------------------------------------------------------
@@ -528,6 +648,19 @@ void oracle_ray(const double* line, const double* dust, int nchan, double v0, do
               t_bg, smp, h, oT, oC, oD, oL, oB);
 }
 
+// One ray in a thin transfer mode (transfer = 1 selectively thin, 2
+// optically thin); arguments as oracle_ray.
+void oracle_ray_thin(const double* line, const double* dust, int nchan, double v0, double dv,
+                     int transfer, int integration, int units, double t_bg, int K,
+                     const double* n_h2, const double* t_gas, const double* t_dust,
+                     const double* v_los, const double* x_tr, double h, double* oT, double* oC,
+                     double* oD, double* oL, double* oB) {
+  std::vector<Sample<double>> smp(K);
+  for (int k = 0; k < K; ++k) smp[k] = {n_h2[k], t_gas[k], t_dust[k], v_los[k], x_tr[k]};
+  ray_outputs_thin(line_from(line), dust_from(dust), vaxis_from(nchan, v0, dv, 0), transfer,
+                   integration, units, t_bg, smp, h, oT, oC, oD, oL, oB);
+}
+
 // Sample list of a pixel: returns K (<= kmax), fills h and samples.
 int oracle_ray_samples(const double* const* fields, int nx, int ny, int nz, double cell_cm,
                        const double* view, int px, int py, int kmax, double* h_out,
@@ -555,9 +688,9 @@ int oracle_ray_samples(const double* const* fields, int nx, int ny, int nz, doub
 // [npix][nchan] per component (NULL = not wanted).
 int oracle_render(const double* const* fields, int nx, int ny, int nz, double cell_cm,
                   const double* line, const double* dust, const double* view, int nchan,
-                  double v0, double dv, int f, int integration, int units, double t_bg,
-                  int npix, const int* pix, double* oT, double* oC, double* oD, double* oL,
-                  double* oB) {
+                  double v0, double dv, int f, int transfer, int integration, int units,
+                  double t_bg, int npix, const int* pix, double* oT, double* oC, double* oD,
+                  double* oL, double* oB) {
   Grid g;
   for (int q = 0; q < 5; ++q) g.f[q] = fields[q];
   g.nx = nx; g.ny = ny; g.nz = nz; g.dx = cell_cm;
@@ -571,8 +704,12 @@ int oracle_render(const double* const* fields, int nx, int ny, int nz, double ce
     double h = 0.0;
     ray_samples(g, v, pix[2 * i], pix[2 * i + 1], &smp, &h);
     std::vector<double> T(nchan), C(nchan), D(nchan), L(nchan), B(nchan);
-    ray_outputs(ln, du, va, integration, units, t_bg, smp, h, T.data(), C.data(), D.data(),
-                L.data(), B.data());
+    if (transfer == MODE_THICK)
+      ray_outputs(ln, du, va, integration, units, t_bg, smp, h, T.data(), C.data(), D.data(),
+                  L.data(), B.data());
+    else
+      ray_outputs_thin(ln, du, va, transfer, integration, units, t_bg, smp, h, T.data(),
+                       C.data(), D.data(), L.data(), B.data());
     const int64_t off = (int64_t)i * nchan;
     for (int c = 0; c < nchan; ++c) {
       if (oT) oT[off + c] = T[c];
