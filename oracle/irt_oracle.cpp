@@ -404,6 +404,7 @@ double direct_integral(int mode, const std::vector<double>& f, double h) {
     for (int k = 0; k < K; ++k) acc += h * f[k];
     return acc;
   }
+  if (K <= 1) return 0.0;              // no interval (a missed ray has no samples)
   const int M = K - 1;                 // intervals
   const int Ms = (M % 2 == 0) ? M : M - 1;   // covered by Simpson panels
   for (int p = 0; p + 2 <= Ms; p += 2) acc += (h / 3.0) * (f[p] + 4.0 * f[p + 1] + f[p + 2]);

@@ -202,3 +202,22 @@ def test_thin_component_identities(transfer, mode):
     assert np.all(r0["L"] == 0.0)
     rn = oracle.ray_thin(LINE, NO_DUST, va, smp, 1e17, transfer=transfer, integration=mode)
     assert np.all(np.abs(rn["D"]) <= 1e-15 * np.abs(rn["B"]))
+
+
+@pytest.mark.parametrize("transfer", [ST, OT])
+@pytest.mark.parametrize("mode", [oracle.FORMAL, oracle.SMOOTH])
+@pytest.mark.parametrize("K", [0, 1])
+def test_empty_and_single_sample_rays(transfer, mode, K):
+    """A ray that misses the box (no samples) shows the background; one
+    sample: the smooth node 0 is the background, the formal step is one
+    closed-form step."""
+    va = VelocityAxis(5, -2.5, 1.0, 0)
+    r = oracle.ray_thin(LINE, DUST, va, uniform_samples(K, 2e4, 30.0), 1e17, transfer=transfer,
+                        integration=mode)
+    for c in range(va.nchan):
+        nuc, s = trj(c, va)
+        if K == 0 or mode == oracle.SMOOTH:
+            assert r["T"][c] == pytest.approx(B(nuc, 2.725) * s, rel=1e-13)
+            assert r["C"][c] == pytest.approx(B(nuc, 2.725) * s, rel=1e-13)
+        else:
+            assert r["T"][c] > r["B"][c]
