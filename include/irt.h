@@ -73,7 +73,21 @@ typedef enum { IRT_F32 = 0, IRT_F16 = 1, IRT_BF16 = 2, IRT_F64 = 3 } irt_dtype;
 typedef enum { IRT_FORMAL = 0, IRT_SMOOTH = 1, IRT_FORMAL_KAHAN = 2 } irt_integration;
 typedef enum { IRT_UNITS_TRJ = 0, IRT_UNITS_INTENSITY = 1 } irt_units;
 typedef enum { IRT_PREC_F32 = 0, IRT_PREC_F64 = 1 } irt_precision;
-typedef enum { IRT_MODE_THICK = 0 } irt_transfer_mode;
+/* Transfer modes (Sec. 4.5-4.7).  THICK: line and dust interact at every
+ * fine velocity (velocity subsampling f, Simpson channel average).
+ * SELECTIVELY_THIN: no subsampling; each channel uses the channel-averaged
+ * line profile (Gaussian mass in the channel / channel width); the continuum
+ * is solved first and the total sees j_L + j_D - alpha_L I_C with absorption
+ * alpha_D (the line does not absorb itself).  THIN: absorption and
+ * stimulation ignored, I = I_bg + integral of j (formal: midpoint sum;
+ * smooth: Simpson over node pairs, trapezoid on an odd last interval).  The
+ * thin modes take IRT_FORMAL or IRT_SMOOTH, ignore subsample_f, and are
+ * rendered by irt_forward_ppv only (no graph, static entry or adjoint). */
+typedef enum {
+  IRT_MODE_THICK = 0,
+  IRT_MODE_SELECTIVELY_THIN = 1,
+  IRT_MODE_THIN = 2
+} irt_transfer_mode;
 
 /* opts.flags */
 #define IRT_FLAG_EXPLICIT_CHANNELS 1u  /* evaluate every channel explicitly (no
@@ -136,7 +150,7 @@ typedef struct {
 } irt_vaxis;
 
 typedef struct {
-  int mode;            /* irt_transfer_mode (IRT_MODE_THICK) */
+  int mode;            /* irt_transfer_mode */
   int integration;     /* irt_integration */
   int units;           /* irt_units */
   double t_bg_k;       /* background (CMB) temperature [K], >= 0 */

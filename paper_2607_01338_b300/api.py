@@ -14,6 +14,8 @@ _DTYPE = {torch.float32: B.IRT_F32, torch.float16: B.IRT_F16, torch.bfloat16: B.
 _INTEGRATION = {"formal": B.IRT_FORMAL, "smooth": B.IRT_SMOOTH, "formal_kahan": B.IRT_FORMAL_KAHAN}
 _UNITS = {"trj": B.IRT_UNITS_TRJ, "intensity": B.IRT_UNITS_INTENSITY}
 _PREC = {"f32": B.IRT_PREC_F32, "f64": B.IRT_PREC_F64}
+_TRANSFER = {"thick": B.IRT_MODE_THICK, "selectively_thin": B.IRT_MODE_SELECTIVELY_THIN,
+             "thin": B.IRT_MODE_THIN}
 COMPONENTS = ("T", "C", "D", "L", "B")
 
 
@@ -86,8 +88,8 @@ def vaxis_struct(va) -> B.irt_vaxis:
 
 
 def opts_struct(integration="smooth", units="trj", t_bg=2.725, precision="f32",
-                flags=0) -> B.irt_opts:
-    return B.irt_opts(B.IRT_MODE_THICK, _INTEGRATION[integration], _UNITS[units], float(t_bg),
+                flags=0, transfer="thick") -> B.irt_opts:
+    return B.irt_opts(_TRANSFER[transfer], _INTEGRATION[integration], _UNITS[units], float(t_bg),
                       _PREC[precision], int(flags))
 
 
@@ -109,20 +111,22 @@ def make_job(grid: Grid, view, vaxis, cubes: dict) -> B.irt_job:
 
 def forward(grid: Grid, view, vaxis, line: dict, dust: dict, *, integration="smooth",
             units="trj", t_bg=2.725, precision="f32", flags=0, out=None, stream=None,
-            components=COMPONENTS) -> dict:
+            components=COMPONENTS, transfer="thick") -> dict:
     """Render one job (``irt_forward_ppv`` with njobs = 1).  Returns the cubes
-    {"T","C","D","L","B"} as [nchan, npy, npx] tensors."""
+    {"T","C","D","L","B"} as [nchan, npy, npx] tensors.  ``transfer`` is
+    "thick", "selectively_thin" or "thin" (Sec. 4.5-4.7)."""
     cubes = out if out is not None else alloc_cubes(view, vaxis, precision,
                                                      components=components)
     job = make_job(grid, view, vaxis, cubes)
     B.irt_forward_ppv([job], line_struct(line), dust_struct(dust),
-                      opts_struct(integration, units, t_bg, precision, flags), _stream_ptr(stream))
+                      opts_struct(integration, units, t_bg, precision, flags, transfer),
+                      _stream_ptr(stream))
     return cubes
 
 
 def forward_batch(jobs, line: dict, dust: dict, *, integration="smooth", units="trj",
                   t_bg=2.725, precision="f32", flags=0, outs=None, stream=None,
-                  autotune=False) -> list:
+                  autotune=False, transfer="thick") -> list:
     """Render many jobs in one persistent launch.  ``jobs`` = [(grid, view,
     vaxis), ...]; returns one cube dict per job.  ``autotune`` times the
     launch plans for this job mix first (synchronous) and caches the best."""
@@ -132,7 +136,8 @@ def forward_batch(jobs, line: dict, dust: dict, *, integration="smooth", units="
     if autotune:
         flags |= B.IRT_FLAG_AUTOTUNE
     B.irt_forward_ppv(cj, line_struct(line), dust_struct(dust),
-                      opts_struct(integration, units, t_bg, precision, flags), _stream_ptr(stream))
+                      opts_struct(integration, units, t_bg, precision, flags, transfer),
+                      _stream_ptr(stream))
     return outs
 
 

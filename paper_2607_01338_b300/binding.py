@@ -19,6 +19,8 @@ IRT_FORMAL, IRT_SMOOTH, IRT_FORMAL_KAHAN = range(3)
 IRT_UNITS_TRJ, IRT_UNITS_INTENSITY = range(2)
 IRT_PREC_F32, IRT_PREC_F64 = range(2)
 IRT_MODE_THICK = 0
+IRT_MODE_SELECTIVELY_THIN = 1
+IRT_MODE_THIN = 2
 IRT_FLAG_EXPLICIT_CHANNELS = 1
 IRT_FLAG_STATS = 2
 IRT_FLAG_AUTOTUNE = 4

@@ -29,6 +29,9 @@ int dispatch_fwd_f32_formal(int store, int ni, const JobTable& jobs, int njobs,
 int dispatch_fwd_f32_kahan(int store, int ni, const JobTable& jobs, int njobs,
                            const PhysParams& P, const PhysF& PF, const FwdLaunch& L,
                            cudaStream_t s);
+int launch_thin(int precision, int store, int integ, int transfer, const JobTable& tab,
+                int njobs, const PhysParams& P, const PhysF& PF, long long total, int kmax,
+                unsigned long long* stats, cudaStream_t stream);
 int launch_adjoint(int store, int ni, const JobTable& tab, const PhysF& PF, const AdjArgs& A,
                    long long total_items, unsigned long long* queue, int blocks, int kmax,
                    int nfw, int nchan, cudaStream_t stream, int* per_warp_smem);
@@ -210,9 +213,12 @@ irt_status check_line(const irt_line* ln, const irt_dust* du, const irt_opts* op
   if (!finite_nonneg(du->kappa_cm2_per_g_gas) || !finite_nonneg(du->mu_mass_per_h2_amu))
     return fail(IRT_EINVAL, "dust constants must be finite and >= 0");
   if (!finite_nonneg(op->t_bg_k)) return fail(IRT_EINVAL, "t_bg_k must be finite and >= 0");
-  if (op->mode != IRT_MODE_THICK) return fail(IRT_EUNSUPPORTED, "transfer mode %d", op->mode);
+  if (op->mode < IRT_MODE_THICK || op->mode > IRT_MODE_THIN)
+    return fail(IRT_EINVAL, "unknown transfer mode %d", op->mode);
   if (op->integration < IRT_FORMAL || op->integration > IRT_FORMAL_KAHAN)
     return fail(IRT_EINVAL, "unknown integration %d", op->integration);
+  if (op->mode != IRT_MODE_THICK && op->integration == IRT_FORMAL_KAHAN)
+    return fail(IRT_EUNSUPPORTED, "thin transfer modes take IRT_FORMAL or IRT_SMOOTH");
   if (op->units != IRT_UNITS_TRJ && op->units != IRT_UNITS_INTENSITY)
     return fail(IRT_EINVAL, "unknown units %d", op->units);
   if (op->precision != IRT_PREC_F32 && op->precision != IRT_PREC_F64)
@@ -671,6 +677,43 @@ irt_status run_forward(const irt_job* jobs, int njobs, const PhysParams& P, cons
   return IRT_OK;
 }
 
+// Selectively thin / optically thin render: one item per ray, no velocity
+// windows; the launcher sizes its own blocks from the longest ray.
+irt_status run_thin(const irt_job* jobs, int njobs, const PhysParams& P, const PhysF& PF,
+                    const irt_opts* opts, cudaStream_t s) {
+  const int prec = opts->precision;
+  const int store = jobs[0].grid->store;
+  for (int j = 1; j < njobs; ++j)
+    if (jobs[j].grid->store != store)
+      return fail(IRT_EUNSUPPORTED, "batched jobs must share the field storage type");
+  const int integ = opts->integration == IRT_SMOOTH ? M_SMOOTH : M_FORMAL;
+  for (int base = 0; base < njobs; base += kMaxJobs) {
+    const int nb = std::min(kMaxJobs, njobs - base);
+    JobTable tab;
+    std::memset(&tab, 0, sizeof tab);
+    long long total = 0;
+    int kmax = 1;
+    for (int t = 0; t < nb; ++t) {
+      const Plan pl = plan_job(jobs[base + t], prec, 0);
+      tab.j[t] = make_jobdev(jobs[base + t], pl);
+      tab.j[t].item_begin = total;
+      tab.j[t].nitems = (long long)tab.j[t].npx * tab.j[t].npy;
+      total += tab.j[t].nitems;
+      kmax = std::max(kmax, pl.kmax);
+    }
+    unsigned long long* stats =
+        (opts->flags & IRT_FLAG_STATS) ? jobs[base].grid->ctl + 1 : nullptr;
+    const int e = launch_thin(prec == IRT_PREC_F64 ? 1 : 0, store, integ, opts->mode, tab, nb, P,
+                              PF, total, kmax, stats, s);
+    ++g_launches;
+    if (e == (int)cudaErrorInvalidValue)
+      return fail(IRT_EUNSUPPORTED, "irt_forward_ppv: thin-mode rays of %d samples exceed the "
+                                    "shared-memory record buffer", kmax);
+    if (e) return cuda_fail(e, "irt_forward_ppv: thin-mode kernel");
+  }
+  return IRT_OK;
+}
+
 // Times the candidate plans on the given stream (synchronous) and returns the
 // fastest.  Candidates: register blocks NI = 9, 17, 33 (the widest line hull
 // the fast path holds, and the window of the general path) x ray tiles 1x1,
@@ -742,6 +785,11 @@ extern "C" irt_status irt_forward_ppv(const irt_job* jobs, int njobs, const irt_
   const PhysParams P = fold_constants(line, dust, opts);
   const PhysF PF = to_float(P);
   cudaStream_t s = (cudaStream_t)cuda_stream;
+  if (opts->mode != IRT_MODE_THICK) {
+    if (opts->flags & IRT_FLAG_SAVE_CHECKPOINTS)
+      return fail(IRT_EUNSUPPORTED, "irt_forward_ppv: checkpoints belong to the thick mode");
+    return run_thin(jobs, njobs, P, PF, opts, s);
+  }
   Tuned tp;
   if (opts->precision != IRT_PREC_F64) {
     const unsigned long long sig = job_signature(jobs, njobs, opts);
@@ -773,6 +821,8 @@ extern "C" irt_status irt_forward_graph_create(const irt_job* jobs, int njobs,
   if (!jobs || njobs < 1) return fail(IRT_EINVAL, "irt_forward_graph_create: no jobs");
   irt_status st = check_line(line, dust, opts);
   if (st) return st;
+  if (opts->mode != IRT_MODE_THICK)
+    return fail(IRT_EUNSUPPORTED, "irt_forward_graph_create: optically thick mode only");
   for (int j = 0; j < njobs; ++j) {
     st = check_job(jobs[j], opts->precision);
     if (st) return st;
@@ -880,6 +930,8 @@ extern "C" irt_status irt_adjoint_ppv(const irt_job* job, const irt_line* line,
     return fail(IRT_EINVAL, "irt_adjoint_ppv: NULL gradient pointer");
   irt_status st = check_line(line, dust, opts);
   if (st) return st;
+  if (opts->mode != IRT_MODE_THICK)
+    return fail(IRT_EUNSUPPORTED, "irt_adjoint_ppv: optically thick mode only");
   if (!job->grid) return fail(IRT_EINVAL, "irt_adjoint_ppv: job without grid");
   // the cube pointers of the job are not written by the adjoint
   irt_job jb = *job;
@@ -1072,6 +1124,8 @@ extern "C" irt_status irt_forward_ppv_static(const irt_grid_desc* desc, const ir
   if (st) return st;
   if (opts->flags & IRT_FLAG_SAVE_CHECKPOINTS)
     return fail(IRT_EUNSUPPORTED, "irt_forward_ppv_static: no checkpoints (no grid keeps them)");
+  if (opts->mode != IRT_MODE_THICK)
+    return fail(IRT_EUNSUPPORTED, "irt_forward_ppv_static: optically thick mode only");
 
   // a grid descriptor on the host stack pointing into the static array
   irt_grid g;
