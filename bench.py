@@ -49,6 +49,12 @@ OPS_SAMPLE = (165, 9)
 OPS_ADJ_LINE = (2.5 * 10 + 12 + 30, 2.5 * 2 + 3)
 OPS_ADJ_DUST = (2.5 * 5 + 12, 0)
 OPS_ADJ_SAMPLE = (2.5 * 165 + 60, 2.5 * 9 + 6)
+# Thin transfer modes (Sec. 4.6, 4.7), smooth integration: FP32 operations per
+# (sample, channel) pair of the recurrences alone (dust source 2; selectively
+# thin: continuum and total BDF2 steps with their ReLU 2 x 5; optically thin:
+# the two Simpson sums 3).  The erf channel averages of the pairs the line
+# reaches are not counted, so the rate derived from these is a lower bound.
+OPS_THIN_PAIR = {"selectively_thin": 12, "thin": 5}
 
 
 def parse():
@@ -63,6 +69,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-large", action="store_true")
+    ap.add_argument("--no-thin", action="store_true")
     return ap.parse_args()
 
 
@@ -552,6 +559,10 @@ def gpu_arm(args):
                "sample": sample + f"; adjoint: dual-number gradient of {na} seeded z-view rays",
                "forward_rate": r, "adjoint_rate": ra, "seconds": dt + dta}
 
+    thin = None
+    if not args.no_thin and rank == 0:
+        thin = thin_measure(grid, w, deq, outs, units_view, pipe_peaks,
+                            cpu=ws == 1 and not args.no_cpu_baseline)
     grid.close()
     for t in list(outs) + [grads]:
         del t
@@ -577,6 +588,7 @@ def gpu_arm(args):
                            "parallelism": f"replicas x{ws}", "per_view_ms": view_ms,
                            "adjoint_ms": adj_ms, "units_adjoint": units_adj},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "batch": batch, "large": large,
+                "thin": thin,
                 "clocks": clk, "gpu_launches": launches}
         print(json.dumps(line), flush=True)
     if ws > 1:
@@ -586,6 +598,55 @@ def gpu_arm(args):
 # ---------------------------------------------------------------------------
 # batched workload: 64 uneven snapshots, BF16 storage, Kahan formal transfer
 # ---------------------------------------------------------------------------
+def thin_measure(grid, w, deq, outs, units_view, pipe_peaks, cpu=True, reps=5):
+    """Selectively thin and optically thin transfer (Sec. 4.6, 4.7), smooth
+    integration, on both views of the step's grid: each view timed with CUDA
+    events on the launching stream over ``reps`` warm launches (inputs larger
+    than L2).  Units as the thick step (samples x channels); the oracle's rate
+    in the same mode on a seeded sample of rays beside it."""
+    import torch
+    import oracle
+    import paper_2607_01338_b300 as irt
+    res = {"workload": f"{w.name}: z view + oblique (30,45) deg, smooth integration, "
+                       "no velocity subsampling (channel-averaged profile)"}
+    units = float(sum(units_view))
+    for tr in ("selectively_thin", "thin"):
+        ms = []
+        for view, out in zip(w.views, outs):
+            for _ in range(2):
+                irt.forward(grid, view, w.vaxis, w.line, w.dust, out=out, transfer=tr)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(reps):
+                irt.forward(grid, view, w.vaxis, w.line, w.dust, out=out, transfer=tr)
+            e1.record()
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1) / reps)
+        t = sum(ms) / 1e3
+        fp32 = OPS_THIN_PAIR[tr] * units / t / 1e12
+        r = {"per_view_ms": ms, "value": units / t, "unit": UNIT,
+             "fp32_lower_bound_top_s": fp32,
+             "frac_of_measured_fp32_lower_bound": fp32 / (pipe_peaks["fp32_ops_per_s"] / 1e12)}
+        if cpu:
+            rng = np.random.default_rng(5)
+            mode = {"selectively_thin": oracle.SELECTIVELY_THIN, "thin": oracle.THIN}[tr]
+            nr, done, t0 = 64, 0.0, time.perf_counter()
+            for view in w.views:
+                pix = np.stack([rng.integers(0, view.npx, nr), rng.integers(0, view.npy, nr)],
+                               axis=1)
+                oracle.render(deq.as_tuple(), w.cell_cm, w.line, w.dust, view, w.vaxis, pix,
+                              integration=oracle.SMOOTH, transfer=mode)
+                for px, py in pix:
+                    smp, _ = oracle.ray_samples(deq.as_tuple(), w.cell_cm, view, int(px), int(py))
+                    done += len(smp) * w.vaxis.nchan
+            r["oracle_rate"] = done / (time.perf_counter() - t0)
+            r["oracle_sample"] = f"{nr} seeded rays per view, all channels, full depth, " \
+                                 f"{oracle.num_threads()} threads"
+        res[tr] = r
+    return res
+
+
 def batch_measure(args, njobs=64, steps=3):
     """The 64-job batch (N in 64..256, 128..512 channels, random directions,
     BF16 fields with an FP16 velocity, Kahan-compensated formal transfer) as

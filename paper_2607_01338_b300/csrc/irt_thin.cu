@@ -10,14 +10,27 @@
 // absorption and integrates the emission directly (midpoint sum, or Simpson
 // over node pairs with a trapezoid closing an odd last interval).
 //
-// One warp per ray, lanes over channels (32 at a time).  The ray's samples
-// are turned into records in shared memory once (per-step line coefficients
-// at the profile peak, Doppler parameter, h alpha_D, dust Planck terms); the
-// channel loop then reads them as broadcasts.  What depends on the sample
-// alone (the BDF2 and TR reciprocals, the formal step's exponential) is the
-// same for every lane.  A warp evaluates the erf channel average only when
-// the line of the sample (centre +- 5.5 Doppler widths, where the Gaussian's
-// remaining mass is below 1e-14) reaches its block of 32 channels.
+// One warp per ray.  The ray's samples become records in shared memory once,
+// lanes over samples: the line coefficients premultiplied for the channel
+// average, 1 / b, the dust source terms, and what each mode needs per sample
+// alone (the BDF2 / TR reciprocals, the formal step's exponentials, the
+// Simpson weight), so the channel loop does no division or transcendental
+// per lane except the line's erfc.  The channel loop then puts lanes over
+// channels, 31 at a time: lane l holds the lower edge of channel c0 + l and
+// its erfc, lane 31 the upper edge of the last one, and each channel takes
+// its upper edge from the next lane by a shuffle.  A warp evaluates the
+// erfc only when the sample's line (centre +- 5.5 Doppler widths, beyond
+// which the Gaussian's mass is below 1e-14) reaches its 31 channels.  In a
+// block of channels that no sample of the ray reaches, [T] = [C] exactly
+// (the total's recurrence is the continuum's), and the float kernels take
+// the continuum there from three scalar recurrences per ray: the dust source
+// is linear in u (B(u) = bk0 + bk1 u), so C(u) = I_bg(u) A + B + u D with A,
+// B, D the recurrence of the background (1, no source) and of the sources
+// d0 and d1 (0 at the start).  That is exact for the formal and optically
+// thin integrals, and for the smooth steps while no ReLU clamps, which
+// h alpha_D <= 1/2 on every sample guarantees (BDF2 then keeps a continuum
+// with non-negative sources non-negative); rays beyond it run the
+// continuum per channel.
 #include "irt_forward_impl.cuh"
 
 namespace irt {
@@ -28,11 +41,13 @@ constexpr float kThinCut = 5.5f;   // Doppler widths beyond which the line mass 
 
 template <typename R>
 struct alignas(16) ThinRec {
-  R jl, al;   // per-step line emission (K units) and optical depth at the profile peak
-  R v, b;     // line centre and Doppler parameter [km/s]
-  R ad;       // h alpha_D
-  R bk0, bk1; // dust Planck source, float: B(u) = bk0 + bk1 u; double: bk0 = T_dust
-  R pad;
+  R jw, aw;   // per-step line emission (K units) / optical depth at the profile peak
+              // times b sqrt(pi) / (2 dv): times erf(x_hi) - erf(x_lo), the channel average
+  R v, ib;    // line centre [km/s] and 1 / b
+  R d0, d1;   // float: h alpha_D B_dust(u) = d0 + d1 u; double: d0 = h alpha_D, d1 = T_dust
+  R X, Y;     // per-sample step terms: selectively thin formal X = e^-tau, Y = (1 - e^-tau) / tau;
+              // smooth X = 1 / (2 + tau) (sample 1) or 1 / (3 + 2 tau), Y = tau;
+              // optically thin X = quadrature weight
 };
 
 __device__ __forceinline__ float erfc_(float x) { return erfcf(x); }
@@ -41,17 +56,6 @@ __device__ __forceinline__ float exp_(float x) { return expf(x); }
 __device__ __forceinline__ double exp_(double x) { return exp(x); }
 __device__ __forceinline__ float expm1_(float x) { return expm1f(x); }
 __device__ __forceinline__ double expm1_(double x) { return expm1(x); }
-__device__ __forceinline__ float rcp_(float x) { return __frcp_rn(x); }
-__device__ __forceinline__ double rcp_(double x) { return 1.0 / x; }
-
-// erf(x_hi) - erf(x_lo) for x_lo <= x_hi, from erfc of non-negative
-// arguments so that a channel in the far wing keeps its relative precision.
-template <typename R>
-__device__ __forceinline__ R erf_diff(R x_lo, R x_hi) {
-  if (x_lo >= (R)0) return erfc_(x_lo) - erfc_(x_hi);
-  if (x_hi <= (R)0) return erfc_(-x_hi) - erfc_(-x_lo);
-  return (R)2 - erfc_(-x_lo) - erfc_(x_hi);
-}
 
 // Optically thin Simpson weight of node k of K (in units of h): Simpson over
 // the first Ms intervals (Ms = K - 1 rounded down to even), the trapezoid
@@ -104,132 +108,233 @@ thin_kernel(const __grid_constant__ JobTable tab, int njobs, const PhysParams P,
     }
     // ---- records
     const R h = (R)g.h;
+    const R sq = (R)0.88622692545275801365 / (R)J.dv;   // sqrt(pi) / (2 dv)
     RayPos rp;
     if constexpr (!kD) rp = ray_pos(J, g);
+    int hlo = 1 << 30, hhi = -1;   // channels any sample's line reaches
+    R admax = (R)0;
     for (int k = lane; k < K; k += 32) {
       R raw[5];
       if constexpr (kD)
         sample_raw<ST>(J, g, px, py, k, raw);
       else
         sample_raw<ST>(J, rp, px, py, k, raw);
+      R jl, al, b, ad;
       Rec e;
       if constexpr (kD) {
-        line_coeffs(P, raw[0], raw[1], raw[4], h, &e.jl, &e.al, &e.b);
-        e.ad = (R)P.cad * raw[0] * h;
-        e.bk0 = raw[2];
-        e.bk1 = (R)0;
+        line_coeffs(P, raw[0], raw[1], raw[4], h, &jl, &al, &b);
+        ad = (R)P.cad * raw[0] * h;
+        e.d0 = ad;
+        e.d1 = raw[2];
       } else {
-        line_coeffs(PF, raw[0], raw[1], raw[4], h, &e.jl, &e.al, &e.b);
-        e.ad = PF.cad * raw[0] * h;
-        dust_source_lin(PF, raw[2], &e.bk0, &e.bk1);
+        line_coeffs(PF, raw[0], raw[1], raw[4], h, &jl, &al, &b);
+        ad = PF.cad * raw[0] * h;
+        R bk0, bk1;
+        dust_source_lin(PF, raw[2], &bk0, &bk1);
+        e.d0 = ad * bk0;
+        e.d1 = ad * bk1;
       }
+      admax = fmax(admax, ad);
+      e.jw = jl * b * sq;
+      e.aw = al * b * sq;
       e.v = raw[3];
-      e.pad = (R)0;
+      e.ib = (R)1 / b;
+      if constexpr (TRANSFER == IRT_MODE_THIN) {
+        e.X = (INTEG == M_FORMAL) ? (R)1 : simpson_weight<R>(k, K);
+        e.Y = (R)0;
+      } else if constexpr (INTEG == M_FORMAL) {
+        e.X = exp_(-ad);
+        e.Y = (ad > (R)0) ? -expm1_(-ad) / ad : (R)1;
+      } else {
+        e.X = (k == 1) ? (R)1 / ((R)2 + ad) : (R)1 / ((R)3 + (R)2 * ad);
+        e.Y = ad;
+      }
       rec[k] = e;
+      if (jl != (R)0 || al != (R)0) {
+        const double w = (double)kThinCut * (double)b;
+        const double clo = floor(((double)raw[3] - w - J.v0) / J.dv);
+        const double chi = floor(((double)raw[3] + w - J.v0) / J.dv);
+        if (chi >= 0.0 && clo <= (double)(J.nchan - 1)) {
+          hlo = min(hlo, (int)fmax(clo, 0.0));
+          hhi = max(hhi, (int)fmin(chi, (double)(J.nchan - 1)));
+        }
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      hlo = min(hlo, __shfl_xor_sync(0xffffffffu, hlo, o));
+      hhi = max(hhi, __shfl_xor_sync(0xffffffffu, hhi, o));
+      admax = fmax(admax, __shfl_xor_sync(0xffffffffu, admax, o));
     }
     __syncwarp();
+    // continuum basis (float kernels): C(u) = I_bg(u) bA + bB + u bD
+    R bA = (R)1, bB = (R)0, bD = (R)0;
+    const bool basis = !kD && (TRANSFER == IRT_MODE_THIN || INTEG == M_FORMAL ||
+                               admax <= (R)0.5);
+    if (basis && K >= 1) {
+      if constexpr (TRANSFER == IRT_MODE_THIN) {
+        for (int k = 0; k < K; ++k) {
+          const Rec e = rec[k];
+          bB = fma(e.X, e.d0, bB);
+          bD = fma(e.X, e.d1, bD);
+        }
+      } else if constexpr (INTEG == M_FORMAL) {
+        for (int k = 0; k < K; ++k) {
+          const Rec e = rec[k];
+          bA *= e.X;
+          bB = fma(bB, e.X, e.d0 * e.Y);
+          bD = fma(bD, e.X, e.d1 * e.Y);
+        }
+      } else if (K >= 2) {
+        const Rec e0 = rec[0], e1 = rec[1];
+        R A0 = (R)1, B0 = (R)0, D0 = (R)0;
+        R A1 = ((R)2 - e0.Y) * e1.X;
+        R B1 = (e0.d0 + e1.d0) * e1.X;
+        R D1 = (e0.d1 + e1.d1) * e1.X;
+        for (int k = 2; k < K; ++k) {
+          const Rec e = rec[k];
+          const R A2 = fma((R)4, A1, -A0) * e.X;
+          const R B2 = fma((R)2, e.d0, fma((R)4, B1, -B0)) * e.X;
+          const R D2 = fma((R)2, e.d1, fma((R)4, D1, -D0)) * e.X;
+          A0 = A1; B0 = B1; D0 = D1;
+          A1 = A2; B1 = B2; D1 = D2;
+        }
+        bA = A1;
+        bB = B1;
+        bD = D1;
+      }
+    }
     if (stats && lane == 0) {
       atomicAdd(&stats[0], 1ull);
       atomicAdd(&stats[1], (unsigned long long)K);
     }
-    // ---- channels, 32 per pass
-    const R sq = (R)0.88622692545275801365 / (R)J.dv;   // sqrt(pi) / (2 dv)
-    for (int c0 = 0; c0 < J.nchan; c0 += 32) {
+    // ---- channels, 31 per pass (lane 31 carries the last upper edge)
+    for (int c0 = 0; c0 < J.nchan; c0 += 31) {
       const int c = c0 + lane;
-      const bool act = c < J.nchan;
-      // channel edges u_lo, u_hi as a rounded value plus its residual, so
-      // that u - v keeps the line's position to far below a Doppler width
-      const double ulo_d = J.v0 + (double)c * J.dv, uhi_d = ulo_d + J.dv;
-      const R ulo = (R)ulo_d, uhi = (R)uhi_d;
-      const R ulo_r = (R)(ulo_d - (double)ulo), uhi_r = (R)(uhi_d - (double)uhi);
+      const int cend = min(c0 + 31, J.nchan);
+      const bool act = lane < 31 && c < J.nchan;
+      // lower edge of channel c as a rounded value plus its residual, so that
+      // u - v keeps the line's position to far below a Doppler width
+      const double ue_d = J.v0 + (double)c * J.dv;
+      const R ue = (R)ue_d, ue_r = (R)(ue_d - (double)ue);
       const R uc = (R)(J.v0 + ((double)c + 0.5) * J.dv);
       const R blo = (R)(J.v0 + (double)c0 * J.dv);
-      const R bhi = (R)(J.v0 + (double)min(c0 + 32, J.nchan) * J.dv);
+      const R bhi = (R)(J.v0 + (double)cend * J.dv);
+      const bool reached = hhi >= c0 && hlo < cend;
       R ib;
       if constexpr (kD)
         ib = planck_k(P, (R)P.t_bg, uc);
       else
         ib = planck_k(PF, PF.t_bg, uc);
-      // line and dust per-step coefficients of record k at this lane's channel
-      auto coeffs = [&](const Rec& e, R* jlb, R* alb, R* jd) {
+      // dust source of record e at this lane's channel (per step, K units)
+      auto dust = [&](const Rec& e) -> R {
+        if constexpr (kD)
+          return e.d0 * planck_k(P, e.d1, uc);
+        else
+          return fmaf(e.d1, uc, e.d0);
+      };
+      // channel average of the line of record e: erf(x_hi) - erf(x_lo) from
+      // erfc of |x| at this lane's lower edge and the next lane's
+      auto line = [&](const Rec& e, R* jlb, R* alb) {
         *jlb = (R)0;
         *alb = (R)0;
-        const bool line = (e.jl != (R)0 || e.al != (R)0) &&
-                          e.v + (R)kThinCut * e.b > blo && e.v - (R)kThinCut * e.b < bhi;
-        if (line) {
-          const R ibv = (R)1 / e.b;
-          const R xlo = ((ulo - e.v) + ulo_r) * ibv;
-          const R xhi = ((uhi - e.v) + uhi_r) * ibv;
-          const R w = sq * e.b * erf_diff(xlo, xhi);
-          *jlb = e.jl * w;
-          *alb = e.al * w;
-        }
-        if constexpr (kD)
-          *jd = e.ad * planck_k(P, e.bk0, uc);
-        else
-          *jd = e.ad * fmaf(e.bk1, uc, e.bk0);
+        if ((e.jw == (R)0 && e.aw == (R)0) || (bhi - e.v) * e.ib <= -(R)kThinCut ||
+            (blo - e.v) * e.ib >= (R)kThinCut)
+          return;   // warp-uniform
+        const R x = ((ue - e.v) + ue_r) * e.ib;
+        const R E = erfc_(x >= (R)0 ? x : -x);
+        const R xn = __shfl_down_sync(0xffffffffu, x, 1);
+        const R En = __shfl_down_sync(0xffffffffu, E, 1);
+        const R d = (x >= (R)0) ? E - En : ((xn <= (R)0) ? En - E : (R)2 - E - En);
+        *jlb = e.jw * d;
+        *alb = e.aw * d;
       };
       R IT = ib, IC = ib;
-      if (K >= 1) {
-        if constexpr (TRANSFER == IRT_MODE_THIN) {
-          // direct integral of the emission
-          R sT = (R)0, sC = (R)0;
-          for (int k = 0; k < K; ++k) {
-            R jlb, alb, jd;
-            coeffs(rec[k], &jlb, &alb, &jd);
-            const R w = (INTEG == M_FORMAL) ? (R)1 : simpson_weight<R>(k, K);
-            sT += w * (jlb + jd);
-            sC += w * jd;
-          }
-          IT = ib + sT;
-          IC = ib + sC;
-        } else if constexpr (INTEG == M_FORMAL) {
-          // continuum step, then the total step with that continuum
+      if constexpr (TRANSFER == IRT_MODE_THIN) {
+        // direct integral of the emission (weights: 1 formal, Simpson smooth)
+        R sT = (R)0, sC = (R)0;
+        if (reached) {
           for (int k = 0; k < K; ++k) {
             const Rec e = rec[k];
-            R jlb, alb, jd;
-            coeffs(e, &jlb, &alb, &jd);
-            const R tau = e.ad;
-            const R q = exp_(-tau);
-            const R gq = (tau > (R)0) ? -expm1_(-tau) / tau : (R)1;
-            IC = IC * q + jd * gq;
-            IT = IT * q + (jlb + jd - alb * IC) * gq;
+            R jlb, alb;
+            line(e, &jlb, &alb);
+            const R jd = dust(e);
+            sC = fma(e.X, jd, sC);
+            sT = fma(e.X, jlb + jd, sT);
           }
+        } else if (basis) {
+          sC = fma(uc, bD, bB);
+          sT = sC;
         } else {
-          // smooth: node 0 = background, TR to node 1, BDF2 after, ReLU
-          R jlb0, alb0, jd0;
-          const Rec e0 = rec[0];
-          coeffs(e0, &jlb0, &alb0, &jd0);
-          R Ca = ib, Ta = ib;          // node n - 2 (after the first steps)
-          R Cb = ib, Tb = ib;          // node n - 1
-          if (K >= 2) {
-            const Rec e1 = rec[1];
-            R jlb1, alb1, jd1;
-            coeffs(e1, &jlb1, &alb1, &jd1);
-            const R r1 = rcp_((R)2 + e1.ad);
-            const R c1 = fmax((jd0 + jd1 + ((R)2 - e0.ad) * ib) * r1, (R)0);
-            const R jt0 = jlb0 + jd0 - alb0 * ib;
-            const R jt1 = jlb1 + jd1 - alb1 * c1;
-            const R t1 = fmax((jt0 + jt1 + ((R)2 - e0.ad) * ib) * r1, (R)0);
-            Cb = c1;
-            Tb = t1;
+          for (int k = 0; k < K; ++k) {
+            const Rec e = rec[k];
+            sC = fma(e.X, dust(e), sC);
           }
+          sT = sC;
+        }
+        IT = ib + sT;
+        IC = ib + sC;
+      } else if constexpr (INTEG == M_FORMAL) {
+        // continuum step, then the total step with that continuum
+        if (reached) {
+          for (int k = 0; k < K; ++k) {
+            const Rec e = rec[k];
+            R jlb, alb;
+            line(e, &jlb, &alb);
+            const R jd = dust(e);
+            IC = fma(IC, e.X, jd * e.Y);
+            IT = fma(IT, e.X, (jlb + jd - alb * IC) * e.Y);
+          }
+        } else if (basis) {
+          IC = fma(ib, bA, fma(uc, bD, bB));
+          IT = IC;
+        } else {
+          for (int k = 0; k < K; ++k) {
+            const Rec e = rec[k];
+            IC = fma(IC, e.X, dust(e) * e.Y);
+          }
+          IT = IC;
+        }
+      } else if (K >= 2 && !reached && basis) {
+        IC = fma(ib, bA, fma(uc, bD, bB));
+        IT = IC;
+      } else if (K >= 2) {
+        // smooth: node 0 = background, TR to node 1, BDF2 after, ReLU
+        const Rec e0 = rec[0], e1 = rec[1];
+        const R jd0 = dust(e0), jd1 = dust(e1);
+        R jlb0, alb0, jlb1, alb1;
+        line(e0, &jlb0, &alb0);
+        line(e1, &jlb1, &alb1);
+        const R c1 = fmax((jd0 + jd1 + ((R)2 - e0.Y) * ib) * e1.X, (R)0);
+        R Ca = ib, Cb = c1;
+        if (reached) {
+          const R jt0 = jlb0 + jd0 - alb0 * ib;
+          const R jt1 = jlb1 + jd1 - alb1 * c1;
+          R Ta = ib, Tb = fmax((jt0 + jt1 + ((R)2 - e0.Y) * ib) * e1.X, (R)0);
           for (int k = 2; k < K; ++k) {
             const Rec e = rec[k];
-            R jlb, alb, jd;
-            coeffs(e, &jlb, &alb, &jd);
-            const R rr = rcp_((R)3 + (R)2 * e.ad);
-            const R cn = fmax(((R)2 * jd + (R)4 * Cb - Ca) * rr, (R)0);
+            R jlb, alb;
+            line(e, &jlb, &alb);
+            const R jd = dust(e);
+            const R cn = fmax(fma((R)2, jd, fma((R)4, Cb, -Ca)) * e.X, (R)0);
             const R jt = jlb + jd - alb * cn;
-            const R tn = fmax(((R)2 * jt + (R)4 * Tb - Ta) * rr, (R)0);
+            const R tn = fmax(fma((R)2, jt, fma((R)4, Tb, -Ta)) * e.X, (R)0);
             Ca = Cb;
             Cb = cn;
             Ta = Tb;
             Tb = tn;
           }
-          IC = Cb;
           IT = Tb;
+        } else {
+          for (int k = 2; k < K; ++k) {
+            const Rec e = rec[k];
+            const R cn = fmax(fma((R)2, dust(e), fma((R)4, Cb, -Ca)) * e.X, (R)0);
+            Ca = Cb;
+            Cb = cn;
+          }
+          IT = Cb;
         }
+        IC = Cb;
       }
       if (act) {
         R s;
