@@ -75,7 +75,7 @@ __device__ __forceinline__ R simpson_weight(int k, int K) {
 }
 
 template <typename R, int ST, int INTEG, int TRANSFER>
-__global__ void __launch_bounds__(kThinWarps * 32)
+__global__ void __launch_bounds__(kThinWarps * 32, 4)
 thin_kernel(const __grid_constant__ JobTable tab, int njobs, const PhysParams P, const PhysF PF,
             long long total, int kmax, int warps, unsigned long long* stats) {
   constexpr bool kD = sizeof(R) == 8;
@@ -112,6 +112,7 @@ thin_kernel(const __grid_constant__ JobTable tab, int njobs, const PhysParams P,
     RayPos rp;
     if constexpr (!kD) rp = ray_pos(J, g);
     int hlo = 1 << 30, hhi = -1;   // channels any sample's line reaches
+    const R v0r = (R)J.v0, inv_dv = (R)(1.0 / J.dv);
     R admax = (R)0;
     for (int k = lane; k < K; k += 32) {
       R raw[5];
@@ -151,12 +152,14 @@ thin_kernel(const __grid_constant__ JobTable tab, int njobs, const PhysParams P,
       }
       rec[k] = e;
       if (jl != (R)0 || al != (R)0) {
-        const double w = (double)kThinCut * (double)b;
-        const double clo = floor(((double)raw[3] - w - J.v0) / J.dv);
-        const double chi = floor(((double)raw[3] + w - J.v0) / J.dv);
-        if (chi >= 0.0 && clo <= (double)(J.nchan - 1)) {
-          hlo = min(hlo, (int)fmax(clo, 0.0));
-          hhi = max(hhi, (int)fmin(chi, (double)(J.nchan - 1)));
+        // channels the line reaches, widened by one on each side so that the
+        // rounding of this bound cannot drop a channel
+        const R w = (R)kThinCut * b;
+        const R clo = floor((raw[3] - w - v0r) * inv_dv) - (R)1;
+        const R chi = floor((raw[3] + w - v0r) * inv_dv) + (R)1;
+        if (chi >= (R)0 && clo <= (R)(J.nchan - 1)) {
+          hlo = min(hlo, (int)fmax(clo, (R)0));
+          hhi = max(hhi, (int)fmin(chi, (R)(J.nchan - 1)));
         }
       }
     }
