@@ -57,6 +57,20 @@ __device__ __forceinline__ double exp_(double x) { return exp(x); }
 __device__ __forceinline__ float expm1_(float x) { return expm1f(x); }
 __device__ __forceinline__ double expm1_(double x) { return expm1(x); }
 
+// Channel edge u(c) = v0 + c dv as a float plus the residual of its rounding
+// (error-free product and sum steps on the float-float parts of v0 and dv).
+__device__ __forceinline__ void edge_ff(int c, float v0h, float v0l, float dvh, float dvl,
+                                        float* hi, float* lo) {
+  const float q = (float)c;
+  const float p = q * dvh;
+  const float pe = fmaf(q, dvh, -p);
+  const float s = v0h + p;
+  const float bb = s - v0h;
+  const float se = (v0h - (s - bb)) + (p - bb);
+  *hi = s;
+  *lo = pe + se + fmaf(q, dvl, v0l);
+}
+
 // Optically thin Simpson weight of node k of K (in units of h): Simpson over
 // the first Ms intervals (Ms = K - 1 rounded down to even), the trapezoid
 // rule on a remaining last interval.
@@ -212,17 +226,29 @@ thin_kernel(const __grid_constant__ JobTable tab, int njobs, const PhysParams P,
       atomicAdd(&stats[1], (unsigned long long)K);
     }
     // ---- channels, 31 per pass (lane 31 carries the last upper edge)
+    const float v0h = (float)J.v0, v0l = (float)(J.v0 - (double)v0h);
+    const float dvh = (float)J.dv, dvl = (float)(J.dv - (double)dvh);
     for (int c0 = 0; c0 < J.nchan; c0 += 31) {
       const int c = c0 + lane;
       const int cend = min(c0 + 31, J.nchan);
       const bool act = lane < 31 && c < J.nchan;
       // lower edge of channel c as a rounded value plus its residual, so that
       // u - v keeps the line's position to far below a Doppler width
-      const double ue_d = J.v0 + (double)c * J.dv;
-      const R ue = (R)ue_d, ue_r = (R)(ue_d - (double)ue);
-      const R uc = (R)(J.v0 + ((double)c + 0.5) * J.dv);
-      const R blo = (R)(J.v0 + (double)c0 * J.dv);
-      const R bhi = (R)(J.v0 + (double)cend * J.dv);
+      R ue, ue_r, uc, blo, bhi;
+      if constexpr (kD) {
+        const double ue_d = J.v0 + (double)c * J.dv;
+        ue = ue_d;
+        ue_r = 0.0;
+        uc = J.v0 + ((double)c + 0.5) * J.dv;
+        blo = J.v0 + (double)c0 * J.dv;
+        bhi = J.v0 + (double)cend * J.dv;
+      } else {
+        float lo;
+        edge_ff(c, v0h, v0l, dvh, dvl, &ue, &ue_r);
+        uc = fmaf(0.5f, dvh, ue + ue_r);
+        edge_ff(c0, v0h, v0l, dvh, dvl, &blo, &lo);
+        edge_ff(cend, v0h, v0l, dvh, dvl, &bhi, &lo);
+      }
       const bool reached = hhi >= c0 && hlo < cend;
       R ib;
       if constexpr (kD)
