@@ -16,7 +16,8 @@
 //   Sec. 4.4  channel averaging; background and continuum at channel value
 //   Sec. 4.5  fine velocity grid + Simpson rule for the total intensity
 //   Sec. 4.8  formal step and smooth (TR first step, BDF2, ReLU) integration
-//   Sec. 4.9  Rayleigh-Jeans temperature;  Sec. 4.10  continuum subtraction
+//   Sec. 4.9  Rayleigh-Jeans and Planck brightness temperature;  Sec. 4.10
+//             continuum subtraction (in intensity / T_RJ space, or in T_B space)
 //   Sec. 4.6  selectively thin transfer (channel-averaged profile by erf, the
 //             line sees the continuum only), Sec. 4.7 optically thin transfer
 //             (direct integral: midpoint sum or Simpson), with the step
@@ -154,7 +155,7 @@ struct VAxis {
 };
 enum { FORMAL = 0, SMOOTH = 1 };
 enum { MODE_THICK = 0, MODE_SELECTIVELY_THIN = 1, MODE_THIN = 2 };
-enum { UNITS_TRJ = 0, UNITS_INTENSITY = 1 };
+enum { UNITS_TRJ = 0, UNITS_INTENSITY = 1, UNITS_TB = 2 };
 
 // Sample values along one ray, in the order the ray travels (background side
 // first, observer side last).
@@ -179,6 +180,13 @@ S planck(double nu, const S& T) {
 }
 
 // Rayleigh-Jeans temperature of an intensity at nu, Sec. 4.9.
+// Planck brightness temperature of an intensity at nu, Sec. 4.9 (Planck's
+// law solved for T); 0 for a non-positive intensity.
+double brightness_temperature(double nu, double I) {
+  if (!(I > 0.0)) return 0.0;
+  return H_PLANCK * nu / (K_BOLTZ * std::log1p(2.0 * H_PLANCK * nu * nu * nu / (C_LIGHT * C_LIGHT * I)));
+}
+
 double rj_temperature(double nu, double I) {
   return C_LIGHT * C_LIGHT * I / (2.0 * K_BOLTZ * nu * nu);
 }
@@ -348,6 +356,11 @@ void ray_outputs(const Line& ln, const DustP& du, const VAxis& va, int mode, int
     if (units == UNITS_TRJ) {
       const double s = rj_temperature(nuc, 1.0);
       vT = vT * s; vC = vC * s; vB = vB * s;
+    } else if (units == UNITS_TB) {
+      // subtraction in T_B space below ([L] = T_B(T) - T_B(C)); values only
+      vT = S(brightness_temperature(nuc, val(vT)));
+      vC = S(brightness_temperature(nuc, val(vC)));
+      vB = S(brightness_temperature(nuc, val(vB)));
     }
     oT[c] = vT;
     oC[c] = vC;
@@ -457,6 +470,10 @@ void ray_outputs_thin(const Line& ln, const DustP& du, const VAxis& va, int tran
     if (units == UNITS_TRJ) {
       const double sc = rj_temperature(nuc, 1.0);
       vT *= sc; vC *= sc; vB *= sc;
+    } else if (units == UNITS_TB) {
+      vT = brightness_temperature(nuc, vT);
+      vC = brightness_temperature(nuc, vC);
+      vB = brightness_temperature(nuc, vB);
     }
     oT[c] = vT;
     oC[c] = vC;
