@@ -18,6 +18,8 @@
 //   Sec. 4.8  formal step and smooth (TR first step, BDF2, ReLU) integration
 //   Sec. 4.9  Rayleigh-Jeans and Planck brightness temperature;  Sec. 4.10
 //             continuum subtraction (in intensity / T_RJ space, or in T_B space)
+//   Sec. 5.11 density tracing ("simple observation"): tracer column density
+//             per unit velocity
 //   Sec. 4.6  selectively thin transfer (channel-averaged profile by erf, the
 //             line sees the continuum only), Sec. 4.7 optically thin transfer
 //             (direct integral: midpoint sum or Simpson), with the step
@@ -154,7 +156,7 @@ struct VAxis {
   int f;
 };
 enum { FORMAL = 0, SMOOTH = 1 };
-enum { MODE_THICK = 0, MODE_SELECTIVELY_THIN = 1, MODE_THIN = 2 };
+enum { MODE_THICK = 0, MODE_SELECTIVELY_THIN = 1, MODE_THIN = 2, MODE_DENSITY_TRACING = 3 };
 enum { UNITS_TRJ = 0, UNITS_INTENSITY = 1, UNITS_TB = 2 };
 
 // Sample values along one ray, in the order the ray travels (background side
@@ -483,6 +485,36 @@ void ray_outputs_thin(const Line& ln, const DustP& du, const VAxis& va, int tran
   }
 }
 
+// Density-tracing cube of one ray (Sec. 5.11): the tracer column density per
+// unit velocity [cm^-2 per km/s] in each channel, every sample spreading its
+// column x n_H2 h over velocity with the line's Doppler profile (channel
+// average: Gaussian mass in the channel over dv); summed as the optically
+// thin integral (midpoint or Simpson).  No temperature cut, background or
+// dust.  Written to [T] and [L]; [C], [D], [B] are zero.
+void ray_outputs_density(const Line& ln, const VAxis& va, int mode,
+                         const std::vector<Sample<double>>& smp, double h, double* oT,
+                         double* oC, double* oD, double* oL, double* oB) {
+  const int K = (int)smp.size();
+  const double m = ln.mass_amu * AMU;
+  std::vector<double> f(K);
+  for (int c = 0; c < va.nchan; ++c) {
+    const double u_lo = va.v0 + c * va.dv, u_hi = u_lo + va.dv;
+    for (int k = 0; k < K; ++k) {
+      const double b = std::sqrt(2.0 * K_BOLTZ * smp[k].t_gas / m
+                                 + 2.0 * (ln.sigma_turb * 1e5) * (ln.sigma_turb * 1e5)) / 1e5;
+      const double mass = 0.5 * (std::erf((u_hi - smp[k].v_los) / b)
+                                 - std::erf((u_lo - smp[k].v_los) / b));
+      f[k] = smp[k].x_tr * smp[k].n_h2 * mass / va.dv;
+    }
+    const double col = direct_integral(mode, f, h);
+    oT[c] = col;
+    oL[c] = col;
+    oC[c] = 0.0;
+    oD[c] = 0.0;
+    oB[c] = 0.0;
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Geometry
 // ---------------------------------------------------------------------------
@@ -675,8 +707,12 @@ void oracle_ray_thin(const double* line, const double* dust, int nchan, double v
                      double* oD, double* oL, double* oB) {
   std::vector<Sample<double>> smp(K);
   for (int k = 0; k < K; ++k) smp[k] = {n_h2[k], t_gas[k], t_dust[k], v_los[k], x_tr[k]};
-  ray_outputs_thin(line_from(line), dust_from(dust), vaxis_from(nchan, v0, dv, 0), transfer,
-                   integration, units, t_bg, smp, h, oT, oC, oD, oL, oB);
+  if (transfer == MODE_DENSITY_TRACING)
+    ray_outputs_density(line_from(line), vaxis_from(nchan, v0, dv, 0), integration, smp, h, oT,
+                        oC, oD, oL, oB);
+  else
+    ray_outputs_thin(line_from(line), dust_from(dust), vaxis_from(nchan, v0, dv, 0), transfer,
+                     integration, units, t_bg, smp, h, oT, oC, oD, oL, oB);
 }
 
 // Sample list of a pixel: returns K (<= kmax), fills h and samples.
@@ -725,6 +761,9 @@ int oracle_render(const double* const* fields, int nx, int ny, int nz, double ce
     if (transfer == MODE_THICK)
       ray_outputs(ln, du, va, integration, units, t_bg, smp, h, T.data(), C.data(), D.data(),
                   L.data(), B.data());
+    else if (transfer == MODE_DENSITY_TRACING)
+      ray_outputs_density(ln, va, integration, smp, h, T.data(), C.data(), D.data(), L.data(),
+                          B.data());
     else
       ray_outputs_thin(ln, du, va, transfer, integration, units, t_bg, smp, h, T.data(),
                        C.data(), D.data(), L.data(), B.data());
