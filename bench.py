@@ -54,7 +54,7 @@ OPS_ADJ_SAMPLE = (2.5 * 165 + 60, 2.5 * 9 + 6)
 # thin: continuum and total BDF2 steps with their ReLU 2 x 5; optically thin:
 # the two Simpson sums 3).  The erf channel averages of the pairs the line
 # reaches are not counted, so the rate derived from these is a lower bound.
-OPS_THIN_PAIR = {"selectively_thin": 12, "thin": 5}
+OPS_THIN_PAIR = {"selectively_thin": 12, "thin": 5, "density_tracing": 2}
 
 
 def parse():
@@ -599,8 +599,9 @@ def gpu_arm(args):
 # batched workload: 64 uneven snapshots, BF16 storage, Kahan formal transfer
 # ---------------------------------------------------------------------------
 def thin_measure(grid, w, deq, outs, units_view, pipe_peaks, cpu=True, reps=5):
-    """Selectively thin and optically thin transfer (Sec. 4.6, 4.7), smooth
-    integration, on both views of the step's grid: each view timed with CUDA
+    """Selectively thin and optically thin transfer (Sec. 4.6, 4.7) and the
+    density-tracing cube (Sec. 5.11), smooth integration, on both views of the
+    step's grid: each view timed with CUDA
     events on the launching stream over ``reps`` warm launches (inputs larger
     than L2).  Units as the thick step (samples x channels); the oracle's rate
     in the same mode on a seeded sample of rays beside it."""
@@ -610,7 +611,7 @@ def thin_measure(grid, w, deq, outs, units_view, pipe_peaks, cpu=True, reps=5):
     res = {"workload": f"{w.name}: z view + oblique (30,45) deg, smooth integration, "
                        "no velocity subsampling (channel-averaged profile)"}
     units = float(sum(units_view))
-    for tr in ("selectively_thin", "thin"):
+    for tr in ("selectively_thin", "thin", "density_tracing"):
         ms = []
         for view, out in zip(w.views, outs):
             for _ in range(2):
@@ -630,7 +631,8 @@ def thin_measure(grid, w, deq, outs, units_view, pipe_peaks, cpu=True, reps=5):
              "frac_of_measured_fp32_lower_bound": fp32 / (pipe_peaks["fp32_ops_per_s"] / 1e12)}
         if cpu:
             rng = np.random.default_rng(5)
-            mode = {"selectively_thin": oracle.SELECTIVELY_THIN, "thin": oracle.THIN}[tr]
+            mode = {"selectively_thin": oracle.SELECTIVELY_THIN, "thin": oracle.THIN,
+                    "density_tracing": oracle.DENSITY_TRACING}[tr]
             nr, done, t0 = 64, 0.0, time.perf_counter()
             for view in w.views:
                 pix = np.stack([rng.integers(0, view.npx, nr), rng.integers(0, view.npy, nr)],

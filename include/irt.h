@@ -71,7 +71,12 @@ typedef enum {
 typedef enum { IRT_F32 = 0, IRT_F16 = 1, IRT_BF16 = 2, IRT_F64 = 3 } irt_dtype;
 
 typedef enum { IRT_FORMAL = 0, IRT_SMOOTH = 1, IRT_FORMAL_KAHAN = 2 } irt_integration;
-typedef enum { IRT_UNITS_TRJ = 0, IRT_UNITS_INTENSITY = 1 } irt_units;
+/* Output units.  TRJ: Rayleigh-Jeans temperature [K] at each channel's
+ * centre frequency; INTENSITY: erg s^-1 cm^-2 Hz^-1 sr^-1; TB: Planck
+ * brightness temperature [K] at the channel centre, with the continuum
+ * subtracted in that space ([L] = T_B([T]) - T_B([C]), [D] = T_B([C]) -
+ * T_B([B]); Sec. 4.9, 4.10).  The adjoint takes TRJ or INTENSITY. */
+typedef enum { IRT_UNITS_TRJ = 0, IRT_UNITS_INTENSITY = 1, IRT_UNITS_TB = 2 } irt_units;
 typedef enum { IRT_PREC_F32 = 0, IRT_PREC_F64 = 1 } irt_precision;
 /* Transfer modes (Sec. 4.5-4.7).  THICK: line and dust interact at every
  * fine velocity (velocity subsampling f, Simpson channel average).
@@ -86,8 +91,15 @@ typedef enum { IRT_PREC_F32 = 0, IRT_PREC_F64 = 1 } irt_precision;
 typedef enum {
   IRT_MODE_THICK = 0,
   IRT_MODE_SELECTIVELY_THIN = 1,
-  IRT_MODE_THIN = 2
+  IRT_MODE_THIN = 2,
+  IRT_MODE_DENSITY_TRACING = 3
 } irt_transfer_mode;
+/* IRT_MODE_DENSITY_TRACING (Sec. 5.11, "simple observation"): the tracer
+ * column density per unit velocity [cm^-2 per km/s], each sample spreading
+ * x n_H2 h over velocity with the line's Doppler profile (channel-averaged
+ * like the thin modes), summed as the optically thin integral (IRT_FORMAL
+ * midpoint, IRT_SMOOTH Simpson); no T_inf cut, background or dust; units
+ * ignored.  Written to out.T and out.L; out.C, out.D, out.B are zero. */
 
 /* opts.flags */
 #define IRT_FLAG_EXPLICIT_CHANNELS 1u  /* evaluate every channel explicitly (no

@@ -12,10 +12,10 @@ from . import binding as B
 _DTYPE = {torch.float32: B.IRT_F32, torch.float16: B.IRT_F16, torch.bfloat16: B.IRT_BF16,
           torch.float64: B.IRT_F64}
 _INTEGRATION = {"formal": B.IRT_FORMAL, "smooth": B.IRT_SMOOTH, "formal_kahan": B.IRT_FORMAL_KAHAN}
-_UNITS = {"trj": B.IRT_UNITS_TRJ, "intensity": B.IRT_UNITS_INTENSITY}
+_UNITS = {"trj": B.IRT_UNITS_TRJ, "intensity": B.IRT_UNITS_INTENSITY, "tb": B.IRT_UNITS_TB}
 _PREC = {"f32": B.IRT_PREC_F32, "f64": B.IRT_PREC_F64}
 _TRANSFER = {"thick": B.IRT_MODE_THICK, "selectively_thin": B.IRT_MODE_SELECTIVELY_THIN,
-             "thin": B.IRT_MODE_THIN}
+             "thin": B.IRT_MODE_THIN, "density_tracing": B.IRT_MODE_DENSITY_TRACING}
 COMPONENTS = ("T", "C", "D", "L", "B")
 
 
@@ -114,7 +114,8 @@ def forward(grid: Grid, view, vaxis, line: dict, dust: dict, *, integration="smo
             components=COMPONENTS, transfer="thick") -> dict:
     """Render one job (``irt_forward_ppv`` with njobs = 1).  Returns the cubes
     {"T","C","D","L","B"} as [nchan, npy, npx] tensors.  ``transfer`` is
-    "thick", "selectively_thin" or "thin" (Sec. 4.5-4.7)."""
+    "thick", "selectively_thin", "thin" (Sec. 4.5-4.7) or "density_tracing"
+    (Sec. 5.11: the column density per unit velocity in "T" and "L")."""
     cubes = out if out is not None else alloc_cubes(view, vaxis, precision,
                                                      components=components)
     job = make_job(grid, view, vaxis, cubes)

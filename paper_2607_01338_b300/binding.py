@@ -16,11 +16,12 @@ LIB_PATH = os.path.join(HERE, "libirt.so")
 IRT_OK, IRT_EINVAL, IRT_ENOMEM, IRT_ECUDA, IRT_EUNSUPPORTED, IRT_ETIMEOUT = range(6)
 IRT_F32, IRT_F16, IRT_BF16, IRT_F64 = range(4)
 IRT_FORMAL, IRT_SMOOTH, IRT_FORMAL_KAHAN = range(3)
-IRT_UNITS_TRJ, IRT_UNITS_INTENSITY = range(2)
+IRT_UNITS_TRJ, IRT_UNITS_INTENSITY, IRT_UNITS_TB = range(3)
 IRT_PREC_F32, IRT_PREC_F64 = range(2)
 IRT_MODE_THICK = 0
 IRT_MODE_SELECTIVELY_THIN = 1
 IRT_MODE_THIN = 2
+IRT_MODE_DENSITY_TRACING = 3
 IRT_FLAG_EXPLICIT_CHANNELS = 1
 IRT_FLAG_STATS = 2
 IRT_FLAG_AUTOTUNE = 4

@@ -213,13 +213,13 @@ irt_status check_line(const irt_line* ln, const irt_dust* du, const irt_opts* op
   if (!finite_nonneg(du->kappa_cm2_per_g_gas) || !finite_nonneg(du->mu_mass_per_h2_amu))
     return fail(IRT_EINVAL, "dust constants must be finite and >= 0");
   if (!finite_nonneg(op->t_bg_k)) return fail(IRT_EINVAL, "t_bg_k must be finite and >= 0");
-  if (op->mode < IRT_MODE_THICK || op->mode > IRT_MODE_THIN)
+  if (op->mode < IRT_MODE_THICK || op->mode > IRT_MODE_DENSITY_TRACING)
     return fail(IRT_EINVAL, "unknown transfer mode %d", op->mode);
   if (op->integration < IRT_FORMAL || op->integration > IRT_FORMAL_KAHAN)
     return fail(IRT_EINVAL, "unknown integration %d", op->integration);
   if (op->mode != IRT_MODE_THICK && op->integration == IRT_FORMAL_KAHAN)
     return fail(IRT_EUNSUPPORTED, "thin transfer modes take IRT_FORMAL or IRT_SMOOTH");
-  if (op->units != IRT_UNITS_TRJ && op->units != IRT_UNITS_INTENSITY)
+  if (op->units != IRT_UNITS_TRJ && op->units != IRT_UNITS_INTENSITY && op->units != IRT_UNITS_TB)
     return fail(IRT_EINVAL, "unknown units %d", op->units);
   if (op->precision != IRT_PREC_F32 && op->precision != IRT_PREC_F64)
     return fail(IRT_EINVAL, "unknown precision %d", op->precision);
@@ -246,7 +246,7 @@ PhysParams fold_constants(const irt_line* ln, const irt_dust* du, const irt_opts
   P.t_bg = op->t_bg_k;
   P.units = op->units;
   P.integration = op->integration;
-  P.out_scale = (op->units == IRT_UNITS_TRJ) ? 1.0 : 1.0 / k_i;
+  P.out_scale = (op->units == IRT_UNITS_INTENSITY) ? 1.0 / k_i : 1.0;
   return P;
 }
 
@@ -932,6 +932,8 @@ extern "C" irt_status irt_adjoint_ppv(const irt_job* job, const irt_line* line,
   if (st) return st;
   if (opts->mode != IRT_MODE_THICK)
     return fail(IRT_EUNSUPPORTED, "irt_adjoint_ppv: optically thick mode only");
+  if (opts->units == IRT_UNITS_TB)
+    return fail(IRT_EUNSUPPORTED, "irt_adjoint_ppv: T_RJ or intensity units only");
   if (!job->grid) return fail(IRT_EINVAL, "irt_adjoint_ppv: job without grid");
   // the cube pointers of the job are not written by the adjoint
   irt_job jb = *job;

@@ -136,25 +136,40 @@ thin_kernel(const __grid_constant__ JobTable tab, int njobs, const PhysParams P,
         sample_raw<ST>(J, rp, px, py, k, raw);
       R jl, al, b, ad;
       Rec e;
-      if constexpr (kD) {
-        line_coeffs(P, raw[0], raw[1], raw[4], h, &jl, &al, &b);
-        ad = (R)P.cad * raw[0] * h;
-        e.d0 = ad;
-        e.d1 = raw[2];
+      if constexpr (TRANSFER == IRT_MODE_DENSITY_TRACING) {
+        // tracer column x n_H2 h spread by the Doppler profile; no cut-off
+        if constexpr (kD)
+          b = sqrt((R)P.c_th * raw[1] + (R)P.two_sig2);
+        else
+          b = sqrtf(PF.c_th * raw[1] + PF.two_sig2);
+        jl = raw[4] * raw[0] * h;
+        al = (R)0;
+        ad = (R)0;
+        e.d0 = (R)0;
+        e.d1 = (R)0;
+        e.jw = jl * ((R)0.5 / (R)J.dv);   // times erf(x_hi) - erf(x_lo): x n h mass / dv
+        e.aw = (R)0;
       } else {
-        line_coeffs(PF, raw[0], raw[1], raw[4], h, &jl, &al, &b);
-        ad = PF.cad * raw[0] * h;
-        R bk0, bk1;
-        dust_source_lin(PF, raw[2], &bk0, &bk1);
-        e.d0 = ad * bk0;
-        e.d1 = ad * bk1;
+        if constexpr (kD) {
+          line_coeffs(P, raw[0], raw[1], raw[4], h, &jl, &al, &b);
+          ad = (R)P.cad * raw[0] * h;
+          e.d0 = ad;
+          e.d1 = raw[2];
+        } else {
+          line_coeffs(PF, raw[0], raw[1], raw[4], h, &jl, &al, &b);
+          ad = PF.cad * raw[0] * h;
+          R bk0, bk1;
+          dust_source_lin(PF, raw[2], &bk0, &bk1);
+          e.d0 = ad * bk0;
+          e.d1 = ad * bk1;
+        }
+        e.jw = jl * b * sq;
+        e.aw = al * b * sq;
       }
       admax = fmax(admax, ad);
-      e.jw = jl * b * sq;
-      e.aw = al * b * sq;
       e.v = raw[3];
       e.ib = (R)1 / b;
-      if constexpr (TRANSFER == IRT_MODE_THIN) {
+      if constexpr (TRANSFER == IRT_MODE_THIN || TRANSFER == IRT_MODE_DENSITY_TRACING) {
         e.X = (INTEG == M_FORMAL) ? (R)1 : simpson_weight<R>(k, K);
         e.Y = (R)0;
       } else if constexpr (INTEG == M_FORMAL) {
@@ -186,10 +201,10 @@ thin_kernel(const __grid_constant__ JobTable tab, int njobs, const PhysParams P,
     __syncwarp();
     // continuum basis (float kernels): C(u) = I_bg(u) bA + bB + u bD
     R bA = (R)1, bB = (R)0, bD = (R)0;
-    const bool basis = !kD && (TRANSFER == IRT_MODE_THIN || INTEG == M_FORMAL ||
-                               admax <= (R)0.5);
+    constexpr bool kSum = TRANSFER == IRT_MODE_THIN || TRANSFER == IRT_MODE_DENSITY_TRACING;
+    const bool basis = !kD && (kSum || INTEG == M_FORMAL || admax <= (R)0.5);
     if (basis && K >= 1) {
-      if constexpr (TRANSFER == IRT_MODE_THIN) {
+      if constexpr (kSum) {
         for (int k = 0; k < K; ++k) {
           const Rec e = rec[k];
           bB = fma(e.X, e.d0, bB);
@@ -251,7 +266,9 @@ thin_kernel(const __grid_constant__ JobTable tab, int njobs, const PhysParams P,
       }
       const bool reached = hhi >= c0 && hlo < cend;
       R ib;
-      if constexpr (kD)
+      if constexpr (TRANSFER == IRT_MODE_DENSITY_TRACING)
+        ib = (R)0;   // no background
+      else if constexpr (kD)
         ib = planck_k(P, (R)P.t_bg, uc);
       else
         ib = planck_k(PF, PF.t_bg, uc);
@@ -279,7 +296,7 @@ thin_kernel(const __grid_constant__ JobTable tab, int njobs, const PhysParams P,
         *alb = e.aw * d;
       };
       R IT = ib, IC = ib;
-      if constexpr (TRANSFER == IRT_MODE_THIN) {
+      if constexpr (kSum) {
         // direct integral of the emission (weights: 1 formal, Simpson smooth)
         R sT = (R)0, sC = (R)0;
         if (reached) {
@@ -380,7 +397,24 @@ thin_kernel(const __grid_constant__ JobTable tab, int njobs, const PhysParams P,
             s = s / (y * y);
           }
         }
-        const R vT = IT * s, vC = IC * s, vB = ib * s;
+        if constexpr (TRANSFER == IRT_MODE_DENSITY_TRACING) s = (R)1;   // cm^-2 per km/s
+        R vT = IT * s, vC = IC * s, vB = ib * s;
+        bool tb;
+        R T0, ic_kms;
+        if constexpr (kD) {
+          tb = P.units == IRT_UNITS_TB;
+          T0 = (R)P.T0;
+          ic_kms = (R)P.inv_c_kms;
+        } else {
+          tb = PF.units == IRT_UNITS_TB;
+          T0 = PF.T0;
+          ic_kms = PF.inv_c_kms;
+        }
+        if (tb && TRANSFER != IRT_MODE_DENSITY_TRACING) {   // continuum subtracted in T_B space below
+          vT = brightness_k(T0, ic_kms, uc, IT);
+          vC = brightness_k(T0, ic_kms, uc, IC);
+          vB = brightness_k(T0, ic_kms, uc, ib);
+        }
         const long long o = (long long)c * plane + pix;
         if (out[0]) out[0][o] = vT;
         if (out[1]) out[1][o] = vC;
@@ -432,6 +466,8 @@ int launch_thin(int precision, int store, int integ, int transfer, const JobTabl
   IRT_THIN_R(M_SMOOTH, IRT_MODE_SELECTIVELY_THIN)
   IRT_THIN_R(M_FORMAL, IRT_MODE_THIN)
   IRT_THIN_R(M_SMOOTH, IRT_MODE_THIN)
+  IRT_THIN_R(M_FORMAL, IRT_MODE_DENSITY_TRACING)
+  IRT_THIN_R(M_SMOOTH, IRT_MODE_DENSITY_TRACING)
 #undef IRT_THIN_R
 #undef IRT_THIN_ST
 #undef IRT_THIN

@@ -52,7 +52,7 @@ def oracle_pixels(fields64, cell_cm, view, vaxis, line, dust, pix, integration="
                   units="trj", t_bg=2.725):
     mode = {"smooth": oracle.SMOOTH, "formal": oracle.FORMAL, "formal_kahan": oracle.FORMAL}[
         integration]
-    u = {"trj": oracle.TRJ, "intensity": oracle.INTENSITY}[units]
+    u = {"trj": oracle.TRJ, "intensity": oracle.INTENSITY, "tb": oracle.TB}[units]
     return oracle.render(fields64, cell_cm, line, dust, view, vaxis, pix, integration=mode,
                          units=u, t_bg=t_bg)
 

@@ -139,3 +139,29 @@ def test_thin_modes_refuse_kahan_checkpoints_and_the_adjoint():
     finally:
         torch.cuda.synchronize()
         g.close()
+
+
+@pytest.mark.parametrize("kind", ["z", "oblique"])
+@pytest.mark.parametrize("integration", ["smooth", "formal"])
+@pytest.mark.parametrize("precision", ["f32", "f64"])
+def test_density_tracing_cube(precision, integration, kind):
+    """Sec. 5.11 density-tracing cube (column density per unit velocity)."""
+    w = workload(0)
+    fs = make_fields(w.n, w.seed)
+    view = view_of(kind, w.n, w.cell_cm)
+    if precision == "f32":
+        src, ref = to_storage(fs, np.float32)
+        tol = {}
+    else:
+        src, ref = fs, fs
+        tol = dict(rtol=1e-11, atol_frac=1e-13)
+    gpu = gpu_render(torch_fields(src), w.cell_cm, view, VA45, LINE, DUST,
+                     integration=integration, precision=precision, transfer="density_tracing")
+    pix = all_pixels(view.npx, view.npy)
+    orc = oracle.render(ref.as_tuple(), w.cell_cm, LINE, DUST, view, VA45, pix,
+                        integration=INTEG[integration], transfer=oracle.DENSITY_TRACING)
+    # the parity rule's peak is the [T] cube's peak (the column cube here)
+    assert_parity(gpu, orc, pix, **tol)
+    assert float(orc["T"].max()) > 0.0
+    for k in "CDB":
+        assert np.all(gpu[k] == 0.0)
