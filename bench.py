@@ -559,6 +559,9 @@ def gpu_arm(args):
                "sample": sample + f"; adjoint: dual-number gradient of {na} seeded z-view rays",
                "forward_rate": r, "adjoint_rate": ra, "seconds": dt + dta}
 
+    reduce_ = None
+    if rank == 0 and not args.no_thin:
+        reduce_ = reduce_measure(outs[0])
     thin = None
     if not args.no_thin and rank == 0:
         thin = thin_measure(grid, w, deq, outs, units_view, pipe_peaks,
@@ -588,7 +591,7 @@ def gpu_arm(args):
                            "parallelism": f"replicas x{ws}", "per_view_ms": view_ms,
                            "adjoint_ms": adj_ms, "units_adjoint": units_adj},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "batch": batch, "large": large,
-                "thin": thin,
+                "thin": thin, "latitude_mean": reduce_,
                 "clocks": clk, "gpu_launches": launches}
         print(json.dumps(line), flush=True)
     if ws > 1:
@@ -598,6 +601,50 @@ def gpu_arm(args):
 # ---------------------------------------------------------------------------
 # batched workload: 64 uneven snapshots, BF16 storage, Kahan formal transfer
 # ---------------------------------------------------------------------------
+def reduce_measure(cubes, reps=4):
+    """The latitude-mean reduction (Sec. 6.1, the l-v image u) of the z-view
+    cubes of the step: the five [nchan][npy][npx] float cubes in turn (5 x
+    67 MB > L2, so each launch reads its cube from HBM), replayed as one CUDA
+    graph with CUDA events around it.  Roofline: bytes read + written per launch against
+    the measured HBM copy bandwidth."""
+    import torch
+    import paper_2607_01338_b300 as irt
+    xs = [cubes[k] for k in ("T", "C", "D", "L", "B")]
+    # the launches are captured in a CUDA graph so that the host's per-call
+    # overhead (tens of microseconds against a kernel of about ten) does not
+    # leave the GPU idle between them
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        for x in xs:
+            irt.latitude_mean(x)
+    torch.cuda.current_stream().wait_stream(side)
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        keep = [irt.latitude_mean(x) for _ in range(reps) for x in xs]
+    graph.replay()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    graph.replay()
+    e1.record()
+    torch.cuda.synchronize()
+    del keep
+    ms = e0.elapsed_time(e1) / (reps * len(xs))
+    A, B, C = xs[0].shape
+    nbytes = 4 * (A * B * C + A * C)
+    pk = peaks()
+    gbs = nbytes / (ms * 1e-3) / 1e9
+    return {"workload": f"mean over b of a {A} x {B} x {C} float PPV cube (l-v image)",
+            "launch_ms": ms, "bytes_per_launch": nbytes,
+            "roofline": {"bound": "hbm", "achieved": gbs, "peak": float(pk["hbm_gbs"]),
+                         "unit": "GB/s", "frac": gbs / float(pk["hbm_gbs"]),
+                         "peak_source": "MEASURED_PEAKS.json hbm_gbs" +
+                                        (" (fallback)" if pk.get("fallback") else "")}}
+
+
 def thin_measure(grid, w, deq, outs, units_view, pipe_peaks, cpu=True, reps=5):
     """Selectively thin and optically thin transfer (Sec. 4.6, 4.7) and the
     density-tracing cube (Sec. 5.11), smooth integration, on both views of the

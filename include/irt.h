@@ -338,6 +338,19 @@ long long irt_launch_count(void);
 irt_status irt_measure_pipe_peaks(double* fp32_ops_per_s, double* mufu_ops_per_s,
                                   void* cuda_stream);
 
+/*
+ * Latitude-mean reduction (Sec. 6.1): out[a][c] = mean over b of in[a][b][c]
+ * for a C-order [A][B][C] device array (dtype IRT_F32 or IRT_F64, out the
+ * same type, [A][C], device memory, not overlapping in).  On a PPV cube
+ * [nchan][npy][npx] it is the l-v image u (b = y); on a field [nz][ny][nx]
+ * the top-down map t.  Float input is summed in float (8 interleaved partial
+ * sums), double in double.  Asynchronous on cuda_stream; the caller owns
+ * both arrays.  IRT_EINVAL for NULL arrays or extents < 1, IRT_EUNSUPPORTED
+ * for another dtype or A > 65535, IRT_ECUDA for a launch error.
+ */
+irt_status irt_mean_axis1(const void* in, int dtype, long long A, long long B, long long C,
+                          void* out, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

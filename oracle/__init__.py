@@ -241,3 +241,11 @@ def loss_grad_zview(fields, cell_cm, line, dust, vaxis, target_L, pixels=None,
                                         pix.ctypes.data_as(_ip),
                                         *[g.ctypes.data_as(_dp) for g in gs])
     return loss, gs[0], gs[1], gs[2]
+
+
+def latitude_mean(a):
+    """Latitude-mean reduction of Sec. 6.1 in FP64: out[a][c] = mean over b of
+    in[a][b][c] for an [A, B, C] array (the l-v image u of a PPV cube
+    [nchan, npy, npx]; the top-down map t of a field [nz, ny, nx])."""
+    x = np.asarray(a, dtype=np.float64)
+    return x.sum(axis=1) / x.shape[1]

@@ -125,6 +125,22 @@ def forward(grid: Grid, view, vaxis, line: dict, dust: dict, *, integration="smo
     return cubes
 
 
+def latitude_mean(x: torch.Tensor, stream=None) -> torch.Tensor:
+    """Mean over the middle axis of a [A, B, C] CUDA tensor (Sec. 6.1): the
+    l-v image u of a PPV cube [nchan, npy, npx], or the top-down map t of a
+    field [nz, ny, nx].  ``irt_mean_axis1``; float32 or float64."""
+    if x.dim() != 3 or not x.is_cuda:
+        raise ValueError("latitude_mean takes a 3-D CUDA tensor")
+    x = x.contiguous()
+    if x.dtype not in (torch.float32, torch.float64):
+        raise ValueError("latitude_mean takes float32 or float64")
+    out = torch.empty((x.shape[0], x.shape[2]), dtype=x.dtype, device=x.device)
+    dt = B.IRT_F32 if x.dtype == torch.float32 else B.IRT_F64
+    B.irt_mean_axis1(x.data_ptr(), dt, x.shape[0], x.shape[1], x.shape[2], out.data_ptr(),
+                     _stream_ptr(stream))
+    return out
+
+
 def forward_batch(jobs, line: dict, dust: dict, *, integration="smooth", units="trj",
                   t_bg=2.725, precision="f32", flags=0, outs=None, stream=None,
                   autotune=False, transfer="thick") -> list:

@@ -29,6 +29,8 @@ int dispatch_fwd_f32_formal(int store, int ni, const JobTable& jobs, int njobs,
 int dispatch_fwd_f32_kahan(int store, int ni, const JobTable& jobs, int njobs,
                            const PhysParams& P, const PhysF& PF, const FwdLaunch& L,
                            cudaStream_t s);
+int launch_mean_axis1(const void* in, int dtype, long long A, long long B, long long C,
+                      void* out, cudaStream_t s);
 int launch_thin(int precision, int store, int integ, int transfer, const JobTable& tab,
                 int njobs, const PhysParams& P, const PhysF& PF, long long total, int kmax,
                 unsigned long long* stats, cudaStream_t stream);
@@ -1032,6 +1034,25 @@ extern "C" irt_status irt_adjoint_ppv(const irt_job* job, const irt_line* line,
 }
 
 // ---------------------------------------------------------------------------
+// ---------------------------------------------------------------------------
+// Latitude-mean reductions (Sec. 6.1)
+// ---------------------------------------------------------------------------
+extern "C" irt_status irt_mean_axis1(const void* in, int dtype, long long A, long long B,
+                                     long long C, void* out, void* cuda_stream) {
+  g_err.clear();
+  if (!in || !out) return fail(IRT_EINVAL, "irt_mean_axis1: NULL array");
+  if (A < 1 || B < 1 || C < 1)
+    return fail(IRT_EINVAL, "irt_mean_axis1: extents %lld x %lld x %lld", A, B, C);
+  if (A > 65535 || (C + 127) / 128 > 2147483647LL)
+    return fail(IRT_EUNSUPPORTED, "irt_mean_axis1: A = %lld above 65535 or C too large", A);
+  if (dtype != IRT_F32 && dtype != IRT_F64)
+    return fail(IRT_EUNSUPPORTED, "irt_mean_axis1: float or double arrays only");
+  const int e = launch_mean_axis1(in, dtype, A, B, C, out, (cudaStream_t)cuda_stream);
+  ++g_launches;
+  if (e) return cuda_fail(e, "irt_mean_axis1");
+  return IRT_OK;
+}
+
 // Render without any device allocation (irt_forward_ppv_static).
 //
 // The packed cells of the grid, the per-warp sample records and the
