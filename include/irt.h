@@ -75,7 +75,10 @@ typedef enum { IRT_FORMAL = 0, IRT_SMOOTH = 1, IRT_FORMAL_KAHAN = 2 } irt_integr
  * centre frequency; INTENSITY: erg s^-1 cm^-2 Hz^-1 sr^-1; TB: Planck
  * brightness temperature [K] at the channel centre, with the continuum
  * subtracted in that space ([L] = T_B([T]) - T_B([C]), [D] = T_B([C]) -
- * T_B([B]); Sec. 4.9, 4.10).  The adjoint takes TRJ or INTENSITY. */
+ * T_B([B]); Sec. 4.9, 4.10).  The adjoint takes TRJ or INTENSITY.  The
+ * thick mode with TB renders T_RJ and converts in a second pass, so it needs
+ * the T, C and B cubes of every job (IRT_EINVAL otherwise); the graph API and
+ * irt_forward_ppv_static take TRJ or INTENSITY. */
 typedef enum { IRT_UNITS_TRJ = 0, IRT_UNITS_INTENSITY = 1, IRT_UNITS_TB = 2 } irt_units;
 typedef enum { IRT_PREC_F32 = 0, IRT_PREC_F64 = 1 } irt_precision;
 /* Transfer modes (Sec. 4.5-4.7).  THICK: line and dust interact at every

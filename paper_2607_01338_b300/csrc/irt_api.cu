@@ -31,6 +31,9 @@ int dispatch_fwd_f32_kahan(int store, int ni, const JobTable& jobs, int njobs,
                            cudaStream_t s);
 int launch_mean_axis1(const void* in, int dtype, long long A, long long B, long long C,
                       void* out, cudaStream_t s);
+int launch_tb_convert(int precision, void* T, void* C, void* B, void* L, void* D,
+                      long long plane, int nchan, double v0, double dv, double T0,
+                      double inv_c_kms, cudaStream_t s);
 int launch_thin(int precision, int store, int integ, int transfer, const JobTable& tab,
                 int njobs, const PhysParams& P, const PhysF& PF, long long total, int kmax,
                 unsigned long long* stats, cudaStream_t stream);
@@ -784,25 +787,49 @@ extern "C" irt_status irt_forward_ppv(const irt_job* jobs, int njobs, const irt_
       return fail(IRT_EUNSUPPORTED, "irt_forward_ppv: IRT_FLAG_SAVE_CHECKPOINTS needs one "
                                     "z-view job, smooth integration, float precision");
   }
-  const PhysParams P = fold_constants(line, dust, opts);
-  const PhysF PF = to_float(P);
   cudaStream_t s = (cudaStream_t)cuda_stream;
   if (opts->mode != IRT_MODE_THICK) {
     if (opts->flags & IRT_FLAG_SAVE_CHECKPOINTS)
       return fail(IRT_EUNSUPPORTED, "irt_forward_ppv: checkpoints belong to the thick mode");
-    return run_thin(jobs, njobs, P, PF, opts, s);
+    const PhysParams P = fold_constants(line, dust, opts);
+    return run_thin(jobs, njobs, P, to_float(P), opts, s);
   }
+  // T_B output of the thick mode: rendered in T_RJ, then converted in place
+  // by a separate pass (which needs the [T], [C] and [B] cubes)
+  const bool tb = opts->units == IRT_UNITS_TB;
+  irt_opts o = *opts;
+  if (tb) {
+    for (int j = 0; j < njobs; ++j)
+      if (!jobs[j].out.T || !jobs[j].out.C || !jobs[j].out.B)
+        return fail(IRT_EINVAL, "irt_forward_ppv: IRT_UNITS_TB needs the T, C and B cubes of "
+                                "every job");
+    o.units = IRT_UNITS_TRJ;
+  }
+  const PhysParams P = fold_constants(line, dust, &o);
+  const PhysF PF = to_float(P);
   Tuned tp;
-  if (opts->precision != IRT_PREC_F64) {
-    const unsigned long long sig = job_signature(jobs, njobs, opts);
-    if (!lookup_tuned(sig, &tp) && (opts->flags & IRT_FLAG_AUTOTUNE)) {
-      st = autotune(jobs, njobs, P, PF, opts, s, &tp);
+  if (o.precision != IRT_PREC_F64) {
+    const unsigned long long sig = job_signature(jobs, njobs, &o);
+    if (!lookup_tuned(sig, &tp) && (o.flags & IRT_FLAG_AUTOTUNE)) {
+      st = autotune(jobs, njobs, P, PF, &o, s, &tp);
       if (st) return st;
       store_tuned(sig, tp);
     }
     forced_plan(&tp);
   }
-  return run_forward(jobs, njobs, P, PF, opts, tp, s);
+  st = run_forward(jobs, njobs, P, PF, &o, tp, s);
+  if (st || !tb) return st;
+  for (int j = 0; j < njobs; ++j) {
+    const irt_job& jb = jobs[j];
+    const int e = launch_tb_convert(o.precision == IRT_PREC_F64 ? 1 : 0, jb.out.T, jb.out.C,
+                                    jb.out.B, jb.out.L, jb.out.D,
+                                    (long long)jb.view.npx * jb.view.npy, jb.vaxis.nchan,
+                                    jb.vaxis.v_first_edge_kms, jb.vaxis.dv_kms, P.T0, P.inv_c_kms,
+                                    s);
+    ++g_launches;
+    if (e) return cuda_fail(e, "irt_forward_ppv: T_B conversion");
+  }
+  return IRT_OK;
 }
 
 // ---------------------------------------------------------------------------
@@ -825,6 +852,8 @@ extern "C" irt_status irt_forward_graph_create(const irt_job* jobs, int njobs,
   if (st) return st;
   if (opts->mode != IRT_MODE_THICK)
     return fail(IRT_EUNSUPPORTED, "irt_forward_graph_create: optically thick mode only");
+  if (opts->units == IRT_UNITS_TB)
+    return fail(IRT_EUNSUPPORTED, "irt_forward_graph_create: T_RJ or intensity units only");
   for (int j = 0; j < njobs; ++j) {
     st = check_job(jobs[j], opts->precision);
     if (st) return st;
@@ -1149,6 +1178,8 @@ extern "C" irt_status irt_forward_ppv_static(const irt_grid_desc* desc, const ir
     return fail(IRT_EUNSUPPORTED, "irt_forward_ppv_static: no checkpoints (no grid keeps them)");
   if (opts->mode != IRT_MODE_THICK)
     return fail(IRT_EUNSUPPORTED, "irt_forward_ppv_static: optically thick mode only");
+  if (opts->units == IRT_UNITS_TB)
+    return fail(IRT_EUNSUPPORTED, "irt_forward_ppv_static: T_RJ or intensity units only");
 
   // a grid descriptor on the host stack pointing into the static array
   irt_grid g;

@@ -331,22 +331,6 @@ __device__ __forceinline__ float planck_k(const PhysF& P, float T, float u) {
   return P.T0 * y * y * y / expm1f(P.T0 * y / T);
 }
 
-// Planck brightness temperature [K] of an intensity I in K units at velocity
-// u (Planck's law in K units solved for T: T0 y / ln(1 + T0 y^3 / I), y =
-// nu(u) / nu_ul); 0 for a non-positive intensity.
-__device__ __forceinline__ float brightness_k(float T0, float inv_c_kms, float u, float I) {
-  if (!(I > 0.0f)) return 0.0f;
-  const float y = 1.0f - u * inv_c_kms;
-  const float t0y = T0 * y;
-  return t0y / log1pf(t0y * y * y / I);
-}
-__device__ __forceinline__ double brightness_k(double T0, double inv_c_kms, double u, double I) {
-  if (!(I > 0.0)) return 0.0;
-  const double y = 1.0 - u * inv_c_kms;
-  const double t0y = T0 * y;
-  return t0y / log1p(t0y * y * y / I);
-}
-
 // ---------------------------------------------------------------------------
 // per-sample records in shared memory
 // ---------------------------------------------------------------------------

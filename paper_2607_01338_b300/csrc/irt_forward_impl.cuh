@@ -1010,12 +1010,7 @@ __device__ void render_ray(const JobDev& J, const PhysParams& PD, const PhysF& P
       const R y = (R)1 - uc * (R)P.inv_c_kms;
       s = s / (y * y);
     }
-    R vT = ibar * s, vC = ic * s, vB = ib * s;
-    if (P.units == IRT_UNITS_TB) {   // continuum subtracted in T_B space below
-      vT = brightness_k((R)P.T0, (R)P.inv_c_kms, uc, ibar);
-      vC = brightness_k((R)P.T0, (R)P.inv_c_kms, uc, ic);
-      vB = brightness_k((R)P.T0, (R)P.inv_c_kms, uc, ib);
-    }
+    const R vT = ibar * s, vC = ic * s, vB = ib * s;
     const long long o = (long long)c * plane + pix;
     if (out[0]) out[0][o] = vT;
     if (out[1]) out[1][o] = vC;

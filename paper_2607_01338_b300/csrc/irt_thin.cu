@@ -32,6 +32,7 @@
 // with non-negative sources non-negative); rays beyond it run the
 // continuum per channel.
 #include "irt_forward_impl.cuh"
+#include "irt_units.cuh"
 
 namespace irt {
 namespace dev {
