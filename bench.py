@@ -559,9 +559,10 @@ def gpu_arm(args):
                "sample": sample + f"; adjoint: dual-number gradient of {na} seeded z-view rays",
                "forward_rate": r, "adjoint_rate": ra, "seconds": dt + dta}
 
-    reduce_ = None
+    reduce_ = beam = None
     if rank == 0 and not args.no_thin:
         reduce_ = reduce_measure(outs[0])
+        beam = beam_measure(outs[0])
     thin = None
     if not args.no_thin and rank == 0:
         thin = thin_measure(grid, w, deq, outs, units_view, pipe_peaks,
@@ -591,7 +592,7 @@ def gpu_arm(args):
                            "parallelism": f"replicas x{ws}", "per_view_ms": view_ms,
                            "adjoint_ms": adj_ms, "units_adjoint": units_adj},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "batch": batch, "large": large,
-                "thin": thin, "latitude_mean": reduce_,
+                "thin": thin, "latitude_mean": reduce_, "beam": beam,
                 "clocks": clk, "gpu_launches": launches}
         print(json.dumps(line), flush=True)
     if ws > 1:
@@ -643,6 +644,44 @@ def reduce_measure(cubes, reps=4):
                          "unit": "GB/s", "frac": gbs / float(pk["hbm_gbs"]),
                          "peak_source": "MEASURED_PEAKS.json hbm_gbs" +
                                         (" (fallback)" if pk.get("fallback") else "")}}
+
+
+def beam_measure(cubes, fwhm_px=3.0, reps=2):
+    """Gaussian beam convolution (Sec. 4.11) of the five z-view cubes in turn
+    (FWHM 3 pixels), replayed as one CUDA graph.  Algorithmic bytes per call:
+    two passes, each reading and writing the cube once."""
+    import torch
+    import paper_2607_01338_b300 as irt
+    xs = [cubes[k] for k in ("T", "C", "D", "L", "B")]
+    outs = [torch.empty_like(x) for x in xs]
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        for x, o in zip(xs, outs):
+            irt.beam_convolve(x, fwhm_px, out=o)
+    torch.cuda.current_stream().wait_stream(side)
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        for _ in range(reps):
+            for x, o in zip(xs, outs):
+                irt.beam_convolve(x, fwhm_px, out=o)
+    graph.replay()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    graph.replay()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / (reps * len(xs))
+    nbytes = 4 * 4 * xs[0].numel()
+    pk = peaks()
+    gbs = nbytes / (ms * 1e-3) / 1e9
+    return {"workload": f"FWHM {fwhm_px} px Gaussian beam on a {tuple(xs[0].shape)} float cube",
+            "call_ms": ms, "bytes_per_call": nbytes,
+            "roofline": {"bound": "hbm", "achieved": gbs, "peak": float(pk["hbm_gbs"]),
+                         "unit": "GB/s", "frac": gbs / float(pk["hbm_gbs"])}}
 
 
 def thin_measure(grid, w, deq, outs, units_view, pipe_peaks, cpu=True, reps=5):

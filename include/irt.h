@@ -354,6 +354,20 @@ irt_status irt_measure_pipe_peaks(double* fp32_ops_per_s, double* mufu_ops_per_s
 irt_status irt_mean_axis1(const void* in, int dtype, long long A, long long B, long long C,
                           void* out, void* cuda_stream);
 
+/*
+ * Gaussian beam convolution (Sec. 4.11) of a [nchan][npy][npx] device cube
+ * (dtype IRT_F32 or IRT_F64): each channel image convolved with a separable
+ * Gaussian of FWHM fwhm_px pixels (the paper's 30 arcsec divided by the
+ * map's angular pixel size); sigma = FWHM / (2 sqrt(2 ln 2)), taps out to
+ * ceil(4 sigma) normalised to unit sum, the sky outside the image zero.
+ * scratch is a caller-owned cube of the same size (the pass along x lands
+ * there); out may equal in.  Asynchronous on cuda_stream.  IRT_EINVAL for
+ * NULL arrays, bad extents, FWHM <= 0 or a scratch aliasing in/out;
+ * IRT_EUNSUPPORTED for another dtype or more than 64 taps a side.
+ */
+irt_status irt_beam_convolve(const void* in, int dtype, long long nchan, int npy, int npx,
+                             double fwhm_px, void* scratch, void* out, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -141,6 +141,20 @@ def latitude_mean(x: torch.Tensor, stream=None) -> torch.Tensor:
     return out
 
 
+def beam_convolve(cube: torch.Tensor, fwhm_px: float, out=None, stream=None) -> torch.Tensor:
+    """Gaussian beam convolution of a [nchan, npy, npx] CUDA cube (Sec. 4.11)
+    with the beam FWHM given in pixels (``irt_beam_convolve``)."""
+    if cube.dim() != 3 or not cube.is_cuda or cube.dtype not in (torch.float32, torch.float64):
+        raise ValueError("beam_convolve takes a 3-D float32/float64 CUDA tensor")
+    cube = cube.contiguous()
+    scratch = torch.empty_like(cube)
+    out = torch.empty_like(cube) if out is None else out
+    dt = B.IRT_F32 if cube.dtype == torch.float32 else B.IRT_F64
+    B.irt_beam_convolve(cube.data_ptr(), dt, cube.shape[0], cube.shape[1], cube.shape[2],
+                        float(fwhm_px), scratch.data_ptr(), out.data_ptr(), _stream_ptr(stream))
+    return out
+
+
 def forward_batch(jobs, line: dict, dust: dict, *, integration="smooth", units="trj",
                   t_bg=2.725, precision="f32", flags=0, outs=None, stream=None,
                   autotune=False, transfer="thick") -> list:

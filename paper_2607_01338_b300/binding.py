@@ -34,7 +34,8 @@ STATUS_NAMES = {0: "IRT_OK", 1: "IRT_EINVAL", 2: "IRT_ENOMEM", 3: "IRT_ECUDA",
 EXPORTED = ("irt_create_grid", "irt_forward_ppv", "irt_adjoint_ppv", "irt_destroy",
             "irt_grid_stats", "irt_forward_ppv_static", "irt_forward_graph_create",
             "irt_forward_graph_launch", "irt_forward_graph_destroy", "irt_tuned_plan",
-            "irt_last_error", "irt_launch_count", "irt_measure_pipe_peaks", "irt_mean_axis1")
+            "irt_last_error", "irt_launch_count", "irt_measure_pipe_peaks", "irt_mean_axis1",
+            "irt_beam_convolve")
 
 
 class irt_grid_desc(ctypes.Structure):
@@ -123,6 +124,10 @@ def _load():
     L.irt_forward_graph_destroy.argtypes = [ctypes.c_void_p]
     L.irt_tuned_plan.restype = ctypes.c_int
     L.irt_tuned_plan.argtypes = [P(irt_job), ctypes.c_int, P(irt_opts), P(ctypes.c_int)]
+    L.irt_beam_convolve.restype = ctypes.c_int
+    L.irt_beam_convolve.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_longlong,
+                                    ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                    ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
     L.irt_mean_axis1.restype = ctypes.c_int
     L.irt_mean_axis1.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_longlong,
                                  ctypes.c_longlong, ctypes.c_longlong, ctypes.c_void_p,
@@ -223,6 +228,14 @@ def irt_mean_axis1(inp: int, dtype: int, A: int, B: int, C: int, out: int,
     """out[a][c] = mean over b of in[a][b][c] (device pointers)."""
     _check(lib.irt_mean_axis1(ctypes.c_void_p(inp), dtype, A, B, C, ctypes.c_void_p(out),
                               ctypes.c_void_p(stream)))
+
+
+def irt_beam_convolve(inp: int, dtype: int, nchan: int, npy: int, npx: int, fwhm_px: float,
+                      scratch: int, out: int, stream: int = 0) -> None:
+    """Gaussian beam convolution of a device cube (scratch: same-size buffer)."""
+    _check(lib.irt_beam_convolve(ctypes.c_void_p(inp), dtype, nchan, npy, npx, fwhm_px,
+                                 ctypes.c_void_p(scratch), ctypes.c_void_p(out),
+                                 ctypes.c_void_p(stream)))
 
 
 def irt_measure_pipe_peaks(stream: int = 0) -> dict:

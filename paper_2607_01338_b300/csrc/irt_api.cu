@@ -31,6 +31,8 @@ int dispatch_fwd_f32_kahan(int store, int ni, const JobTable& jobs, int njobs,
                            cudaStream_t s);
 int launch_mean_axis1(const void* in, int dtype, long long A, long long B, long long C,
                       void* out, cudaStream_t s);
+int launch_beam(const void* in, int dtype, long long nchan, int npy, int npx, double fwhm_px,
+                void* scratch, void* out, cudaStream_t s);
 int launch_tb_convert(int precision, void* T, void* C, void* B, void* L, void* D,
                       long long plane, int nchan, double v0, double dv, double T0,
                       double inv_c_kms, cudaStream_t s);
@@ -1079,6 +1081,28 @@ extern "C" irt_status irt_mean_axis1(const void* in, int dtype, long long A, lon
   const int e = launch_mean_axis1(in, dtype, A, B, C, out, (cudaStream_t)cuda_stream);
   ++g_launches;
   if (e) return cuda_fail(e, "irt_mean_axis1");
+  return IRT_OK;
+}
+
+extern "C" irt_status irt_beam_convolve(const void* in, int dtype, long long nchan, int npy,
+                                        int npx, double fwhm_px, void* scratch, void* out,
+                                        void* cuda_stream) {
+  g_err.clear();
+  if (!in || !scratch || !out) return fail(IRT_EINVAL, "irt_beam_convolve: NULL array");
+  if (nchan < 1 || npy < 1 || npx < 1)
+    return fail(IRT_EINVAL, "irt_beam_convolve: extents %lld x %d x %d", nchan, npy, npx);
+  if (!finite_pos(fwhm_px)) return fail(IRT_EINVAL, "irt_beam_convolve: FWHM must be > 0");
+  if (dtype != IRT_F32 && dtype != IRT_F64)
+    return fail(IRT_EUNSUPPORTED, "irt_beam_convolve: float or double cubes only");
+  if (in == scratch || out == scratch)
+    return fail(IRT_EINVAL, "irt_beam_convolve: the scratch cube must be a separate buffer");
+  const int e = launch_beam(in, dtype, nchan, npy, npx, fwhm_px, scratch, out,
+                            (cudaStream_t)cuda_stream);
+  g_launches += 2;
+  if (e == (int)cudaErrorInvalidValue)
+    return fail(IRT_EUNSUPPORTED, "irt_beam_convolve: FWHM %.3g px needs more than 64 taps a "
+                                  "side", fwhm_px);
+  if (e) return cuda_fail(e, "irt_beam_convolve");
   return IRT_OK;
 }
 
