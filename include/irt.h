@@ -363,7 +363,8 @@ irt_status irt_mean_axis1(const void* in, int dtype, long long A, long long B, l
  * scratch is a caller-owned cube of the same size (the pass along x lands
  * there); out may equal in.  Asynchronous on cuda_stream.  IRT_EINVAL for
  * NULL arrays, bad extents, FWHM <= 0 or a scratch aliasing in/out;
- * IRT_EUNSUPPORTED for another dtype or more than 64 taps a side.
+ * IRT_EUNSUPPORTED for another dtype, more than 64 taps a side or more than
+ * 65535 channels.
  */
 irt_status irt_beam_convolve(const void* in, int dtype, long long nchan, int npy, int npx,
                              double fwhm_px, void* scratch, void* out, void* cuda_stream);

@@ -1096,6 +1096,8 @@ extern "C" irt_status irt_beam_convolve(const void* in, int dtype, long long nch
     return fail(IRT_EUNSUPPORTED, "irt_beam_convolve: float or double cubes only");
   if (in == scratch || out == scratch)
     return fail(IRT_EINVAL, "irt_beam_convolve: the scratch cube must be a separate buffer");
+  if (nchan > 65535)
+    return fail(IRT_EUNSUPPORTED, "irt_beam_convolve: more than 65535 channels");
   const int e = launch_beam(in, dtype, nchan, npy, npx, fwhm_px, scratch, out,
                             (cudaStream_t)cuda_stream);
   g_launches += 2;

@@ -3,7 +3,10 @@
 // FWHM / (2 sqrt(2 ln 2)), taps out to ceil(4 sigma), normalised to unit sum),
 // the sky outside the image taken as zero.  Two passes, along x into the
 // caller's scratch cube and along y into the output: each reads and writes
-// the cube once (HBM bound; the taps' neighbouring reads hit L1).
+// the cube once (HBM bound).  Both passes stage a tile with its halo in
+// shared memory (zero outside the image): the x pass 8 rows by 256 columns
+// plus 2R, the y pass 32 rows plus 2R by 128 columns, so each input element
+// is read (tile + 2R) / tile times from the memory system instead of 2R + 1.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -22,29 +25,71 @@ struct BeamTaps {
   double wd[2 * kBeamMaxR + 1];
 };
 
-// One block per image row (row = channel * npy + y), threads over x.
-template <typename T, bool ALONG_X>
+constexpr int kBeamXW = 256;   // output columns of an x-pass tile
+constexpr int kBeamXH = 8;     // rows of an x-pass tile
+
+// x pass, tiled: blockIdx.x = column tile, blockIdx.y = row tile, blockIdx.z
+// = channel.
+template <typename T>
 __global__ void __launch_bounds__(256)
-beam_pass(const T* __restrict__ in, T* __restrict__ out, int npy, int npx,
-          const __grid_constant__ BeamTaps taps) {
-  const long long row = blockIdx.x;
-  const int y = (int)(row % npy);
+beam_pass_x_tiled(const T* __restrict__ in, T* __restrict__ out, int npy, int npx,
+                  const __grid_constant__ BeamTaps taps) {
+  extern __shared__ __align__(16) unsigned char beam_smem_x[];
+  T* tile = reinterpret_cast<T*>(beam_smem_x);
   const int R = taps.R;
-  const T* rin = in + row * npx;
-  T* rout = out + row * npx;
-  for (int x = threadIdx.x; x < npx; x += blockDim.x) {
-    T acc = (T)0;
-    if constexpr (ALONG_X) {
-      const int lo = max(-R, -x), hi = min(R, npx - 1 - x);
-      for (int d = lo; d <= hi; ++d)
-        acc += (sizeof(T) == 4 ? (T)taps.wf[d + R] : (T)taps.wd[d + R]) * rin[x + d];
-    } else {
-      const int lo = max(-R, -y), hi = min(R, npy - 1 - y);
-      for (int d = lo; d <= hi; ++d)
-        acc += (sizeof(T) == 4 ? (T)taps.wf[d + R] : (T)taps.wd[d + R]) *
-               rin[(long long)d * npx + x];
+  const int W = kBeamXW + 2 * R;
+  const int x0 = blockIdx.x * kBeamXW, y0 = blockIdx.y * kBeamXH;
+  const long long img = (long long)blockIdx.z * npy * npx;
+  for (int i = threadIdx.x; i < kBeamXH * W; i += blockDim.x) {
+    const int r = i / W, cx = i - r * W;
+    const int y = y0 + r, x = x0 - R + cx;
+    tile[i] = (y < npy && x >= 0 && x < npx) ? in[img + (long long)y * npx + x] : (T)0;
+  }
+  __syncthreads();
+  for (int o = threadIdx.x; o < kBeamXH * kBeamXW; o += blockDim.x) {
+    const int ty = o / kBeamXW, cx = o - ty * kBeamXW;
+    const int y = y0 + ty, x = x0 + cx;
+    if (y < npy && x < npx) {
+      T acc = (T)0;
+      const T* row = tile + ty * W + cx + R;
+      for (int d = -R; d <= R; ++d)
+        acc += (sizeof(T) == 4 ? (T)taps.wf[d + R] : (T)taps.wd[d + R]) * row[d];
+      out[img + (long long)y * npx + x] = acc;
     }
-    rout[x] = acc;
+  }
+}
+
+constexpr int kBeamTX = 128;   // columns of a y-pass tile
+constexpr int kBeamTY = 32;    // output rows of a y-pass tile
+
+// y pass, tiled: blockIdx.x = column tile, blockIdx.y = row tile, blockIdx.z
+// = channel.
+template <typename T>
+__global__ void __launch_bounds__(256)
+beam_pass_y_tiled(const T* __restrict__ in, T* __restrict__ out, int npy, int npx,
+                  const __grid_constant__ BeamTaps taps) {
+  extern __shared__ __align__(16) unsigned char beam_smem[];
+  T* tile = reinterpret_cast<T*>(beam_smem);
+  const int R = taps.R;
+  const int x0 = blockIdx.x * kBeamTX, y0 = blockIdx.y * kBeamTY;
+  const long long img = (long long)blockIdx.z * npy * npx;
+  const int rows = kBeamTY + 2 * R;
+  for (int i = threadIdx.x; i < rows * kBeamTX; i += blockDim.x) {
+    const int r = i / kBeamTX, cx = i - r * kBeamTX;
+    const int y = y0 - R + r, x = x0 + cx;
+    tile[i] = (y >= 0 && y < npy && x < npx) ? in[img + (long long)y * npx + x] : (T)0;
+  }
+  __syncthreads();
+  for (int o = threadIdx.x; o < kBeamTY * kBeamTX; o += blockDim.x) {
+    const int ty = o / kBeamTX, cx = o - ty * kBeamTX;
+    const int y = y0 + ty, x = x0 + cx;
+    if (y < npy && x < npx) {
+      T acc = (T)0;
+      for (int d = -R; d <= R; ++d)
+        acc += (sizeof(T) == 4 ? (T)taps.wf[d + R] : (T)taps.wd[d + R]) *
+               tile[(ty + R + d) * kBeamTX + cx];
+      out[img + (long long)y * npx + x] = acc;
+    }
   }
 }
 
@@ -52,7 +97,7 @@ beam_pass(const T* __restrict__ in, T* __restrict__ out, int npy, int npx,
 
 // Launcher (arguments validated by irt_beam_convolve): returns a cudaError_t,
 // or cudaErrorInvalidValue when the beam needs more than kBeamMaxR taps a side
-// (or the cube has more than 2^31 rows).
+// (or the cube has more than 65535 channels).
 int launch_beam(const void* in, int dtype, long long nchan, int npy, int npx, double fwhm_px,
                 void* scratch, void* out, cudaStream_t s) {
   dev::BeamTaps t;
@@ -68,20 +113,30 @@ int launch_beam(const void* in, int dtype, long long nchan, int npy, int npx, do
     t.wd[k] /= sum;
     t.wf[k] = (float)t.wd[k];
   }
-  const long long rows = nchan * npy;
-  if (rows > 2147483647LL) return (int)cudaErrorInvalidValue;
-  const int blocks = (int)rows;
-  const int threads = npx >= 256 ? 256 : ((npx + 31) / 32) * 32;
+  if (nchan > 65535) return (int)cudaErrorInvalidValue;
+  const dim3 tgrid((unsigned)((npx + dev::kBeamTX - 1) / dev::kBeamTX),
+                   (unsigned)((npy + dev::kBeamTY - 1) / dev::kBeamTY), (unsigned)nchan);
+  const size_t es = dtype == IRT_F32 ? 4 : 8;
+  const size_t smem = (size_t)(dev::kBeamTY + 2 * t.R) * dev::kBeamTX * es;
+  const dim3 xgrid((unsigned)((npx + dev::kBeamXW - 1) / dev::kBeamXW),
+                   (unsigned)((npy + dev::kBeamXH - 1) / dev::kBeamXH), (unsigned)nchan);
+  const size_t xsmem = (size_t)dev::kBeamXH * (dev::kBeamXW + 2 * t.R) * es;
   if (dtype == IRT_F32) {
-    dev::beam_pass<float, true><<<blocks, threads, 0, s>>>(static_cast<const float*>(in),
+    cudaError_t e = cudaFuncSetAttribute(dev::beam_pass_y_tiled<float>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return (int)e;
+    dev::beam_pass_x_tiled<float><<<xgrid, 256, xsmem, s>>>(static_cast<const float*>(in),
         static_cast<float*>(scratch), npy, npx, t);
-    dev::beam_pass<float, false><<<blocks, threads, 0, s>>>(static_cast<const float*>(scratch),
+    dev::beam_pass_y_tiled<float><<<tgrid, 256, smem, s>>>(static_cast<const float*>(scratch),
         static_cast<float*>(out), npy, npx, t);
   } else {
-    dev::beam_pass<double, true><<<blocks, threads, 0, s>>>(static_cast<const double*>(in),
-        static_cast<double*>(scratch), npy, npx, t);
-    dev::beam_pass<double, false><<<blocks, threads, 0, s>>>(static_cast<const double*>(scratch),
-        static_cast<double*>(out), npy, npx, t);
+    cudaError_t e = cudaFuncSetAttribute(dev::beam_pass_y_tiled<double>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return (int)e;
+    dev::beam_pass_x_tiled<double><<<xgrid, 256, xsmem, s>>>(
+        static_cast<const double*>(in), static_cast<double*>(scratch), npy, npx, t);
+    dev::beam_pass_y_tiled<double><<<tgrid, 256, smem, s>>>(
+        static_cast<const double*>(scratch), static_cast<double*>(out), npy, npx, t);
   }
   return (int)cudaGetLastError();
 }
