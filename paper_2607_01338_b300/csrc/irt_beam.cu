@@ -11,6 +11,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <type_traits>
 
 #include "irt_internal.h"
 
@@ -30,13 +31,24 @@ constexpr int kBeamXH = 8;     // rows of an x-pass tile
 
 // x pass, tiled: blockIdx.x = column tile, blockIdx.y = row tile, blockIdx.z
 // = channel.
+// Weight of tap k (k = d + R).
 template <typename T>
+__device__ __forceinline__ T tap(const BeamTaps& t, int k) {
+  if constexpr (sizeof(T) == 4)
+    return t.wf[k];
+  else
+    return t.wd[k];
+}
+
+// RC > 0: the tap count a side fixed at compile time (the loop unrolls);
+// RC = 0: taken from taps.R at run time.
+template <typename T, int RC>
 __global__ void __launch_bounds__(256)
 beam_pass_x_tiled(const T* __restrict__ in, T* __restrict__ out, int npy, int npx,
                   const __grid_constant__ BeamTaps taps) {
   extern __shared__ __align__(16) unsigned char beam_smem_x[];
   T* tile = reinterpret_cast<T*>(beam_smem_x);
-  const int R = taps.R;
+  const int R = RC > 0 ? RC : taps.R;
   const int W = kBeamXW + 2 * R;
   const int x0 = blockIdx.x * kBeamXW, y0 = blockIdx.y * kBeamXH;
   const long long img = (long long)blockIdx.z * npy * npx;
@@ -51,9 +63,13 @@ beam_pass_x_tiled(const T* __restrict__ in, T* __restrict__ out, int npy, int np
     const int y = y0 + ty, x = x0 + cx;
     if (y < npy && x < npx) {
       T acc = (T)0;
-      const T* row = tile + ty * W + cx + R;
-      for (int d = -R; d <= R; ++d)
-        acc += (sizeof(T) == 4 ? (T)taps.wf[d + R] : (T)taps.wd[d + R]) * row[d];
+      const T* row = tile + ty * W + cx;
+      if constexpr (RC > 0) {
+#pragma unroll
+        for (int k = 0; k <= 2 * RC; ++k) acc += tap<T>(taps, k) * row[k];
+      } else {
+        for (int k = 0; k <= 2 * R; ++k) acc += tap<T>(taps, k) * row[k];
+      }
       out[img + (long long)y * npx + x] = acc;
     }
   }
@@ -64,13 +80,13 @@ constexpr int kBeamTY = 32;    // output rows of a y-pass tile
 
 // y pass, tiled: blockIdx.x = column tile, blockIdx.y = row tile, blockIdx.z
 // = channel.
-template <typename T>
+template <typename T, int RC>
 __global__ void __launch_bounds__(256)
 beam_pass_y_tiled(const T* __restrict__ in, T* __restrict__ out, int npy, int npx,
                   const __grid_constant__ BeamTaps taps) {
   extern __shared__ __align__(16) unsigned char beam_smem[];
   T* tile = reinterpret_cast<T*>(beam_smem);
-  const int R = taps.R;
+  const int R = RC > 0 ? RC : taps.R;
   const int x0 = blockIdx.x * kBeamTX, y0 = blockIdx.y * kBeamTY;
   const long long img = (long long)blockIdx.z * npy * npx;
   const int rows = kBeamTY + 2 * R;
@@ -85,9 +101,13 @@ beam_pass_y_tiled(const T* __restrict__ in, T* __restrict__ out, int npy, int np
     const int y = y0 + ty, x = x0 + cx;
     if (y < npy && x < npx) {
       T acc = (T)0;
-      for (int d = -R; d <= R; ++d)
-        acc += (sizeof(T) == 4 ? (T)taps.wf[d + R] : (T)taps.wd[d + R]) *
-               tile[(ty + R + d) * kBeamTX + cx];
+      const T* col = tile + ty * kBeamTX + cx;
+      if constexpr (RC > 0) {
+#pragma unroll
+        for (int k = 0; k <= 2 * RC; ++k) acc += tap<T>(taps, k) * col[k * kBeamTX];
+      } else {
+        for (int k = 0; k <= 2 * R; ++k) acc += tap<T>(taps, k) * col[k * kBeamTX];
+      }
       out[img + (long long)y * npx + x] = acc;
     }
   }
@@ -121,23 +141,31 @@ int launch_beam(const void* in, int dtype, long long nchan, int npy, int npx, do
   const dim3 xgrid((unsigned)((npx + dev::kBeamXW - 1) / dev::kBeamXW),
                    (unsigned)((npy + dev::kBeamXH - 1) / dev::kBeamXH), (unsigned)nchan);
   const size_t xsmem = (size_t)dev::kBeamXH * (dev::kBeamXW + 2 * t.R) * es;
-  if (dtype == IRT_F32) {
-    cudaError_t e = cudaFuncSetAttribute(dev::beam_pass_y_tiled<float>,
+  auto run = [&](auto tag, auto rc) -> int {
+    using T = decltype(tag);
+    constexpr int RC = decltype(rc)::value;
+    cudaError_t e = cudaFuncSetAttribute(dev::beam_pass_y_tiled<T, RC>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return (int)e;
-    dev::beam_pass_x_tiled<float><<<xgrid, 256, xsmem, s>>>(static_cast<const float*>(in),
-        static_cast<float*>(scratch), npy, npx, t);
-    dev::beam_pass_y_tiled<float><<<tgrid, 256, smem, s>>>(static_cast<const float*>(scratch),
-        static_cast<float*>(out), npy, npx, t);
-  } else {
-    cudaError_t e = cudaFuncSetAttribute(dev::beam_pass_y_tiled<double>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return (int)e;
-    dev::beam_pass_x_tiled<double><<<xgrid, 256, xsmem, s>>>(
-        static_cast<const double*>(in), static_cast<double*>(scratch), npy, npx, t);
-    dev::beam_pass_y_tiled<double><<<tgrid, 256, smem, s>>>(
-        static_cast<const double*>(scratch), static_cast<double*>(out), npy, npx, t);
-  }
+    dev::beam_pass_x_tiled<T, RC><<<xgrid, 256, xsmem, s>>>(static_cast<const T*>(in),
+        static_cast<T*>(scratch), npy, npx, t);
+    dev::beam_pass_y_tiled<T, RC><<<tgrid, 256, smem, s>>>(static_cast<const T*>(scratch),
+        static_cast<T*>(out), npy, npx, t);
+    return 0;
+  };
+  auto by_r = [&](auto tag) -> int {
+    switch (t.R) {
+#define IRT_BEAM_R(N) \
+      case N: return run(tag, std::integral_constant<int, N>{});
+      IRT_BEAM_R(1) IRT_BEAM_R(2) IRT_BEAM_R(3) IRT_BEAM_R(4) IRT_BEAM_R(5) IRT_BEAM_R(6)
+      IRT_BEAM_R(7) IRT_BEAM_R(8) IRT_BEAM_R(9) IRT_BEAM_R(10) IRT_BEAM_R(11) IRT_BEAM_R(12)
+      IRT_BEAM_R(13) IRT_BEAM_R(14) IRT_BEAM_R(15) IRT_BEAM_R(16)
+#undef IRT_BEAM_R
+      default: return run(tag, std::integral_constant<int, 0>{});
+    }
+  };
+  const int e = dtype == IRT_F32 ? by_r(float{}) : by_r(double{});
+  if (e) return e;
   return (int)cudaGetLastError();
 }
 
