@@ -134,3 +134,35 @@ def test_product_path_has_no_oracle_or_fallback():
                 text = open(os.path.join(dirpath, fn)).read()
                 assert "import oracle" not in text and "from oracle" not in text, fn
                 assert "irt_oracle" not in text, fn
+
+
+def test_post_processing_calls_validate_before_any_launch(B):
+    """irt_mean_axis1 and irt_beam_convolve refuse bad arguments on the host
+    (no device needed)."""
+    L = B.lib
+    assert L.irt_mean_axis1(None, B.IRT_F32, 2, 3, 4, None, None) == B.IRT_EINVAL
+    assert L.irt_mean_axis1(1, B.IRT_F32, 0, 3, 4, 1, None) == B.IRT_EINVAL
+    assert L.irt_mean_axis1(1, B.IRT_F16, 2, 3, 4, 1, None) == B.IRT_EUNSUPPORTED
+    assert L.irt_mean_axis1(1, B.IRT_F32, 70000, 3, 4, 1, None) == B.IRT_EUNSUPPORTED
+    assert L.irt_beam_convolve(None, B.IRT_F32, 1, 4, 4, 2.0, 1, 2, None) == B.IRT_EINVAL
+    assert L.irt_beam_convolve(1, B.IRT_F32, 1, 4, 4, 0.0, 2, 3, None) == B.IRT_EINVAL
+    assert b"FWHM" in L.irt_last_error()
+    assert L.irt_beam_convolve(1, B.IRT_F32, 1, 4, 4, 2.0, 1, 3, None) == B.IRT_EINVAL
+    assert b"scratch" in L.irt_last_error()
+    assert L.irt_beam_convolve(1, B.IRT_BF16, 1, 4, 4, 2.0, 2, 3, None) == B.IRT_EUNSUPPORTED
+
+
+def test_thin_and_tb_options_validate_before_any_launch(B):
+    """Transfer modes and units outside the enums, and Kahan with a thin
+    mode, are refused before the jobs are looked at."""
+    L = B.lib
+    line = _line(B)
+    dust = B.irt_dust(0.01, 2.8)
+    job = B.irt_job(None, B.irt_view(0, 0, 4, 4, 1.0, 0), B.irt_vaxis(4, -2.0, 1.0, 1),
+                    B.irt_cubes(1, None, None, None, None))
+    for opts, code in ((B.irt_opts(9, 1, 0, 2.725, 0, 0), B.IRT_EINVAL),
+                       (B.irt_opts(B.IRT_MODE_THIN, B.IRT_FORMAL_KAHAN, 0, 2.725, 0, 0),
+                        B.IRT_EUNSUPPORTED),
+                       (B.irt_opts(0, 1, 7, 2.725, 0, 0), B.IRT_EINVAL)):
+        assert L.irt_forward_ppv(ctypes.byref(job), 1, ctypes.byref(line), ctypes.byref(dust),
+                                 ctypes.byref(opts), None) == code
