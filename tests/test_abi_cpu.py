@@ -166,3 +166,23 @@ def test_thin_and_tb_options_validate_before_any_launch(B):
                        (B.irt_opts(0, 1, 7, 2.725, 0, 0), B.IRT_EINVAL)):
         assert L.irt_forward_ppv(ctypes.byref(job), 1, ctypes.byref(line), ctypes.byref(dust),
                                  ctypes.byref(opts), None) == code
+
+
+def test_static_entry_takes_the_thick_mode_and_rj_or_intensity_units(B):
+    """The allocation-free entry refuses the thin modes and T_B output before
+    any CUDA call."""
+    L = B.lib
+    line = _line(B)
+    dust = B.irt_dust(0.01, 2.8)
+    f = B.irt_fields(1, 2, 3, 4, 5)
+    desc = B.irt_grid_desc(4, 4, 4, 1.0, (ctypes.c_int * 5)(0, 0, 0, 0, 0))
+    view = B.irt_view(0, 0, 4, 4, 1.0, 0)
+    vaxis = B.irt_vaxis(4, -2.0, 1.0, 1)
+    cubes = B.irt_cubes(1, None, None, None, None)
+    for opts, word in ((B.irt_opts(B.IRT_MODE_THIN, 1, 0, 2.725, 0, 0), b"thick"),
+                       (B.irt_opts(0, 1, B.IRT_UNITS_TB, 2.725, 0, 0), b"intensity")):
+        assert L.irt_forward_ppv_static(ctypes.byref(desc), ctypes.byref(f), ctypes.byref(view),
+                                        ctypes.byref(vaxis), ctypes.byref(cubes),
+                                        ctypes.byref(line), ctypes.byref(dust),
+                                        ctypes.byref(opts), None) == B.IRT_EUNSUPPORTED
+        assert word in L.irt_last_error()
