@@ -38,7 +38,7 @@ int launch_tb_convert(int precision, void* T, void* C, void* B, void* L, void* D
                       double inv_c_kms, cudaStream_t s);
 int launch_thin(int precision, int store, int integ, int transfer, const JobTable& tab,
                 int njobs, const PhysParams& P, const PhysF& PF, long long total, int kmax,
-                unsigned long long* stats, cudaStream_t stream);
+                int nchan_max, unsigned long long* stats, cudaStream_t stream);
 int launch_adjoint(int store, int ni, const JobTable& tab, const PhysF& PF, const AdjArgs& A,
                    long long total_items, unsigned long long* queue, int blocks, int kmax,
                    int nfw, int nchan, cudaStream_t stream, int* per_warp_smem);
@@ -699,8 +699,9 @@ irt_status run_thin(const irt_job* jobs, int njobs, const PhysParams& P, const P
     JobTable tab;
     std::memset(&tab, 0, sizeof tab);
     long long total = 0;
-    int kmax = 1;
+    int kmax = 1, nchan_max = 1;
     for (int t = 0; t < nb; ++t) {
+      nchan_max = std::max(nchan_max, jobs[base + t].vaxis.nchan);
       const Plan pl = plan_job(jobs[base + t], prec, 0);
       tab.j[t] = make_jobdev(jobs[base + t], pl);
       tab.j[t].item_begin = total;
@@ -711,7 +712,7 @@ irt_status run_thin(const irt_job* jobs, int njobs, const PhysParams& P, const P
     unsigned long long* stats =
         (opts->flags & IRT_FLAG_STATS) ? jobs[base].grid->ctl + 1 : nullptr;
     const int e = launch_thin(prec == IRT_PREC_F64 ? 1 : 0, store, integ, opts->mode, tab, nb, P,
-                              PF, total, kmax, stats, s);
+                              PF, total, kmax, nchan_max, stats, s);
     ++g_launches;
     if (e == (int)cudaErrorInvalidValue)
       return fail(IRT_EUNSUPPORTED, "irt_forward_ppv: thin-mode rays of %d samples exceed the "

@@ -92,14 +92,21 @@ __device__ __forceinline__ R simpson_weight(int k, int K) {
 template <typename R, int ST, int INTEG, int TRANSFER>
 __global__ void __launch_bounds__(kThinWarps * 32, 4)
 thin_kernel(const __grid_constant__ JobTable tab, int njobs, const PhysParams P, const PhysF PF,
-            long long total, int kmax, int warps, unsigned long long* stats) {
+            long long total, int kmax, int warps, long long per_warp_bytes, int nchunk_max,
+            unsigned long long* stats) {
   constexpr bool kD = sizeof(R) == 8;
   using Rec = ThinRec<R>;
   extern __shared__ __align__(16) unsigned char smem[];
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
   if (warp >= warps) return;
-  Rec* rec = reinterpret_cast<Rec*>(smem) + (size_t)warp * kmax;
+  unsigned char* wbase = smem + (size_t)warp * (size_t)per_warp_bytes;
+  Rec* rec = reinterpret_cast<Rec*>(wbase);
+  // optically thin / density tracing (float): per 31-channel block, a bit per
+  // sample whose line reaches it, 32 samples a word ([block][chunk])
+  unsigned* masks = reinterpret_cast<unsigned*>(wbase + (size_t)kmax * sizeof(Rec));
+  constexpr bool kMask =
+      !kD && (TRANSFER == IRT_MODE_THIN || TRANSFER == IRT_MODE_DENSITY_TRACING);
   const long long nw = (long long)gridDim.x * warps;
   for (long long item = (long long)blockIdx.x * warps + warp; item < total; item += nw) {
     int jj = 0;
@@ -129,7 +136,11 @@ thin_kernel(const __grid_constant__ JobTable tab, int njobs, const PhysParams P,
     int hlo = 1 << 30, hhi = -1;   // channels any sample's line reaches
     const R v0r = (R)J.v0, inv_dv = (R)(1.0 / J.dv);
     R admax = (R)0;
-    for (int k = lane; k < K; k += 32) {
+    const int nblk = (J.nchan + 30) / 31;
+    const int nchunk = (K + 31) / 32;
+    // record of sample k (lanes over samples); the channel blocks its line
+    // reaches go to blo_k .. bhi_k
+    auto record = [&](int k, int& blo_k, int& bhi_k) {
       R raw[5];
       if constexpr (kD)
         sample_raw<ST>(J, g, px, py, k, raw);
@@ -188,9 +199,28 @@ thin_kernel(const __grid_constant__ JobTable tab, int njobs, const PhysParams P,
         const R clo = floor((raw[3] - w - v0r) * inv_dv) - (R)1;
         const R chi = floor((raw[3] + w - v0r) * inv_dv) + (R)1;
         if (chi >= (R)0 && clo <= (R)(J.nchan - 1)) {
-          hlo = min(hlo, (int)fmax(clo, (R)0));
-          hhi = max(hhi, (int)fmin(chi, (R)(J.nchan - 1)));
+          const int ci_lo = (int)fmax(clo, (R)0), ci_hi = (int)fmin(chi, (R)(J.nchan - 1));
+          hlo = min(hlo, ci_lo);
+          hhi = max(hhi, ci_hi);
+          blo_k = ci_lo / 31;
+          bhi_k = ci_hi / 31;
         }
+      }
+    };
+    if constexpr (kMask) {
+      for (int k0 = 0; k0 < K; k0 += 32) {
+        const int k = k0 + lane;
+        int blo_k = 1 << 30, bhi_k = -1;
+        if (k < K) record(k, blo_k, bhi_k);
+        for (int bb = 0; bb < nblk; ++bb) {
+          const unsigned m = __ballot_sync(0xffffffffu, bb >= blo_k && bb <= bhi_k);
+          if (lane == 0) masks[bb * nchunk + (k0 >> 5)] = m;
+        }
+      }
+    } else {
+      for (int k = lane; k < K; k += 32) {
+        int blo_k = 1 << 30, bhi_k = -1;   // unused without masks
+        record(k, blo_k, bhi_k);
       }
     }
 #pragma unroll
@@ -300,7 +330,25 @@ thin_kernel(const __grid_constant__ JobTable tab, int njobs, const PhysParams P,
       if constexpr (kSum) {
         // direct integral of the emission (weights: 1 formal, Simpson smooth)
         R sT = (R)0, sC = (R)0;
-        if (reached) {
+        if (kMask && reached && basis) {
+          // the line from the samples that reach this block, the dust from
+          // the continuum basis
+          R sL = (R)0;
+          const unsigned* mb = masks + (c0 / 31) * nchunk;
+          for (int ch = 0; ch < nchunk; ++ch) {
+            unsigned m = mb[ch];
+            while (m) {
+              const int k = (ch << 5) + __ffs(m) - 1;
+              m &= m - 1;
+              const Rec e = rec[k];
+              R jlb, alb;
+              line(e, &jlb, &alb);
+              sL = fma(e.X, jlb, sL);
+            }
+          }
+          sC = fma(uc, bD, bB);
+          sT = sC + sL;
+        } else if (reached) {
           for (int k = 0; k < K; ++k) {
             const Rec e = rec[k];
             R jlb, alb;
@@ -434,9 +482,14 @@ thin_kernel(const __grid_constant__ JobTable tab, int njobs, const PhysParams P,
 // storage, integration (M_FORMAL or M_SMOOTH), transfer mode.
 int launch_thin(int precision, int store, int integ, int transfer, const JobTable& tab,
                 int njobs, const PhysParams& P, const PhysF& PF, long long total, int kmax,
-                unsigned long long* stats, cudaStream_t stream) {
+                int nchan_max, unsigned long long* stats, cudaStream_t stream) {
   const size_t rec_bytes = precision ? sizeof(dev::ThinRec<double>) : sizeof(dev::ThinRec<float>);
-  const size_t per_warp = rec_bytes * (size_t)kmax;
+  const int nchunk_max = (kmax + 31) / 32;
+  // sample masks: the float optically thin and density-tracing kernels only
+  const bool masks = !precision && (transfer == IRT_MODE_THIN ||
+                                    transfer == IRT_MODE_DENSITY_TRACING);
+  const size_t mask_bytes = masks ? (size_t)4 * ((nchan_max + 30) / 31) * nchunk_max : 0;
+  const size_t per_warp = (rec_bytes * (size_t)kmax + mask_bytes + 15) & ~(size_t)15;
   const size_t budget = 200 * 1024;
   if (per_warp > budget) return (int)cudaErrorInvalidValue;
   const int warps = (int)std::max<size_t>(1, std::min<size_t>(dev::kThinWarps, budget / per_warp));
@@ -457,7 +510,8 @@ int launch_thin(int precision, int store, int integ, int transfer, const JobTabl
     const int blocks = (int)std::max<long long>(                                               \
         1, std::min<long long>(need, (long long)std::max(per_sm, 1) * sms));                   \
     kern<<<blocks, dev::kThinWarps * 32, smem, stream>>>(tab, njobs, P, PF, total, kmax,        \
-                                                         warps, stats);                        \
+                                                         warps, (long long)per_warp,           \
+                                                         nchunk_max, stats);                   \
     return (int)cudaGetLastError();                                                            \
   }
 #define IRT_THIN_ST(R_, IN_, TR_) \
