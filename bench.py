@@ -35,20 +35,21 @@ if ROOT not in sys.path:
 
 METRIC = "PPV cell-channel updates/s (fwd and adjoint) at stated error vs FP64 oracle"
 UNIT = "cell-channel updates/s"
-#: algorithmic FP32 / MUFU lane-operations of the smooth integrator (see
-#: the design doc): per (sample, 32-velocity block) pair where the line is
-#: evaluated, per pair integrated without the line, per sample (records and
-#: the three continuum basis recurrences)
+#: algorithmic FP32 / MUFU lane-operations of the smooth integrator: per
+#: (sample, 32-velocity block) pair where the line is evaluated, per pair
+#: integrated without the line, per sample (records and the three continuum
+#: basis recurrences)
 OPS_LINE = (10, 2)
 OPS_DUST = (5, 0)
 OPS_SAMPLE = (165, 9)
-#: adjoint: the forward is run 2.5 times (initial pass with checkpoints, then
-#: each 32-sample segment again in two 16-sample sub-segments) plus the reverse
-#: step (about 12 FP32 per block pair, 30 FP32 + 3 MUFU per line slot) and the
-#: per-sample chain rule
-OPS_ADJ_LINE = (2.5 * 10 + 12 + 30, 2.5 * 2 + 3)
-OPS_ADJ_DUST = (2.5 * 5 + 12, 0)
-OPS_ADJ_SAMPLE = (2.5 * 165 + 60, 2.5 * 9 + 6)
+#: adjoint: the forward once more (each 32-sample segment recomputed from the
+#: checkpoint the forward render saved, keeping its pre-ReLU values) plus the
+#: reverse step (about 12 FP32 per block pair, 30 FP32 + 3 MUFU per line slot)
+#: and the per-sample chain rule
+ADJ_FWD = 1.0
+OPS_ADJ_LINE = (ADJ_FWD * 10 + 12 + 30, ADJ_FWD * 2 + 3)
+OPS_ADJ_DUST = (ADJ_FWD * 5 + 12, 0)
+OPS_ADJ_SAMPLE = (ADJ_FWD * 165 + 60, ADJ_FWD * 9 + 6)
 # Thin transfer modes (Sec. 4.6, 4.7), smooth integration: FP32 operations per
 # (sample, channel) pair of the recurrences alone (dust source 2; selectively
 # thin: continuum and total BDF2 steps with their ReLU 2 x 5; optically thin:
@@ -430,8 +431,7 @@ def gpu_arm(args):
     kname = ("adjoint: adj_kernel<9,F32> + deferred-ray pass adj_kernel<17,F32> (z view)"
              if is_adj else f"fwd_kernel<float,17,F32,smooth> ({['z', 'oblique'][dom]} view)")
     # DRAM bytes per launch of the dominant kernel from one ncu capture of
-    # this workload (profiles/step_256cube_launches_and_dram.md); other sizes
-    # have no capture
+    # this workload (the committed step profile); other sizes have no capture
     traffic = None
     if nx == 256 and is_adj:
         traffic = 1.365e9 + 1.581e9 + 66.56e3
