@@ -686,7 +686,7 @@ def beam_measure(cubes, fwhm_px=3.0, reps=2):
 
 def thin_measure(grid, w, deq, outs, units_view, pipe_peaks, cpu=True, reps=5):
     """Selectively thin and optically thin transfer (Sec. 4.6, 4.7) and the
-    density-tracing cube (Sec. 5.11), smooth integration, on both views of the
+    density-tracing cube (Sec. 5.10), smooth integration, on both views of the
     step's grid: each view timed with CUDA
     events on the launching stream over ``reps`` warm launches (inputs larger
     than L2).  Units as the thick step (samples x channels); the oracle's rate

@@ -97,7 +97,7 @@ typedef enum {
   IRT_MODE_THIN = 2,
   IRT_MODE_DENSITY_TRACING = 3
 } irt_transfer_mode;
-/* IRT_MODE_DENSITY_TRACING (Sec. 5.11, "simple observation"): the tracer
+/* IRT_MODE_DENSITY_TRACING (Sec. 5.10, "simple observation"): the tracer
  * column density per unit velocity [cm^-2 per km/s], each sample spreading
  * x n_H2 h over velocity with the line's Doppler profile (channel-averaged
  * like the thin modes), summed as the optically thin integral (IRT_FORMAL
@@ -188,13 +188,23 @@ typedef struct {
 
 /*
  * irt_create_grid - copy the five fields (device pointers, layout above) into
- * a grid owned by the library, in a cell-interleaved layout.  Storage: all
+ * a grid owned by the library, in a cell-interleaved layout.  The grid is the
+ * library's form of the paper's physical tensor (Sec. 2.2: velocity,
+ * density, gas and dust temperature and abundances sampled on a regular
+ * lattice; Sec. 2.3 for the gas temperature): here a Cartesian lattice of
+ * cubic cells, or the paper's observer-centred [r][b][l] tensor read with
+ * its radial axis as z (see irt_view).  Storage: all
  * 16-bit fields stay 16-bit (fp16/bf16 per field); otherwise fields are kept
  * as float, or as double when any field is IRT_F64.  Later edits to the
  * caller's buffers do not affect the grid.  On success *out is a new handle
  * to release with irt_destroy.  IRT_EINVAL for non-positive sizes, a
  * non-positive or non-finite cell size, NULL pointers or an unknown dtype;
  * IRT_ENOMEM if the device allocation fails.
+ *
+ * Every device allocation of the library (grids, scratch, graphs) fails with
+ * IRT_ENOMEM, without calling the CUDA runtime, while the environment
+ * variable IRT_FAIL_ALLOC is set to a non-empty value other than "0" (read on
+ * every call): host-side fault injection for tests of the IRT_ENOMEM paths.
  */
 irt_status irt_create_grid(const irt_grid_desc* desc, const irt_fields* fields,
                            void* cuda_stream, irt_grid** out);
@@ -289,9 +299,13 @@ irt_status irt_adjoint_ppv(const irt_job* job, const irt_line* line, const irt_d
  * warps the launch keeps resident: each holds the records of its longest
  * ray).  A grid needing more than 32 MiB of packed cells (32, 16 or
  * 64 bytes per cell for float, 16-bit or double storage; e.g. 1,048,576 float
- * cells) is rejected with IRT_EINVAL and a message giving both sizes.  The
- * call issues no cudaMalloc/cudaFree.  IRT_FLAG_SAVE_CHECKPOINTS gives
- * IRT_EUNSUPPORTED (no grid keeps them).  The first call on a device looks up the
+ * cells) is rejected with IRT_EINVAL and a message giving both sizes, and so
+ * is a view whose longest ray needs more than the 16 MiB of records for one
+ * block of 4 warps (48 bytes a sample in float precision, 64 in double:
+ * rays of at most 87,381 or 65,536 samples); both checks come before any
+ * CUDA call.  The call issues no cudaMalloc/cudaFree.
+ * IRT_FLAG_SAVE_CHECKPOINTS and IRT_FLAG_STATS give IRT_EUNSUPPORTED (no grid
+ * keeps checkpoints or work counters).  The first call on a device looks up the
  * array's device address (cudaGetSymbolAddress); make that first call before
  * any stream capture.  All calls share the array and it keeps the last call's
  * contents (the counter is cleared by each call): calls whose kernels overlap

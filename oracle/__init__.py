@@ -90,7 +90,7 @@ LINE_KEYS = ("nu_ul_hz", "a_ul_s", "e_u_k", "b0_hz", "g_u", "g_l", "mass_amu", "
 DUST_KEYS = ("kappa_cm2_per_g_gas", "mu_mass_per_h2_amu")
 FORMAL, SMOOTH = 0, 1
 THICK, SELECTIVELY_THIN, THIN = 0, 1, 2   # transfer modes (Sec. 4.5-4.7)
-DENSITY_TRACING = 3                        # column density per unit velocity (Sec. 5.11)
+DENSITY_TRACING = 3                        # column density per unit velocity (Sec. 5.10)
 TRJ, INTENSITY, TB = 0, 1, 2   # output units (Sec. 4.9)
 
 

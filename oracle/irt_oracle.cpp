@@ -18,7 +18,7 @@
 //   Sec. 4.8  formal step and smooth (TR first step, BDF2, ReLU) integration
 //   Sec. 4.9  Rayleigh-Jeans and Planck brightness temperature;  Sec. 4.10
 //             continuum subtraction (in intensity / T_RJ space, or in T_B space)
-//   Sec. 5.11 density tracing ("simple observation"): tracer column density
+//   Sec. 5.10 density tracing ("simple observation"): tracer column density
 //             per unit velocity
 //   Sec. 4.6  selectively thin transfer (channel-averaged profile by erf, the
 //             line sees the continuum only), Sec. 4.7 optically thin transfer
@@ -485,7 +485,7 @@ void ray_outputs_thin(const Line& ln, const DustP& du, const VAxis& va, int tran
   }
 }
 
-// Density-tracing cube of one ray (Sec. 5.11): the tracer column density per
+// Density-tracing cube of one ray (Sec. 5.10): the tracer column density per
 // unit velocity [cm^-2 per km/s] in each channel, every sample spreading its
 // column x n_H2 h over velocity with the line's Doppler profile (channel
 // average: Gaussian mass in the channel over dv); summed as the optically

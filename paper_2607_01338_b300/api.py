@@ -115,7 +115,7 @@ def forward(grid: Grid, view, vaxis, line: dict, dust: dict, *, integration="smo
     """Render one job (``irt_forward_ppv`` with njobs = 1).  Returns the cubes
     {"T","C","D","L","B"} as [nchan, npy, npx] tensors.  ``transfer`` is
     "thick", "selectively_thin", "thin" (Sec. 4.5-4.7) or "density_tracing"
-    (Sec. 5.11: the column density per unit velocity in "T" and "L")."""
+    (Sec. 5.10: the column density per unit velocity in "T" and "L")."""
     cubes = out if out is not None else alloc_cubes(view, vaxis, precision,
                                                      components=components)
     job = make_job(grid, view, vaxis, cubes)

@@ -66,6 +66,20 @@ irt_status cuda_fail(int e, const char* where) {
   return fail(IRT_ECUDA, "%s: %s", where, cudaGetErrorString((cudaError_t)e));
 }
 
+// Every device allocation of the library goes through here.  Host-side fault
+// injection for tests: with IRT_FAIL_ALLOC set to a non-empty value other
+// than "0" in the environment (read on every call), the allocation fails
+// without calling the CUDA runtime, so that the IRT_ENOMEM paths can be
+// exercised without exhausting a shared GPU.
+cudaError_t dev_malloc(void** p, size_t bytes) {
+  const char* e = std::getenv("IRT_FAIL_ALLOC");
+  if (e && *e && std::strcmp(e, "0") != 0) {
+    *p = nullptr;
+    return cudaErrorMemoryAllocation;
+  }
+  return cudaMalloc(p, bytes);
+}
+
 bool finite_pos(double x) { return std::isfinite(x) && x > 0.0; }
 bool finite_nonneg(double x) { return std::isfinite(x) && x >= 0.0; }
 
@@ -152,12 +166,12 @@ irt_status irt_create_grid(const irt_grid_desc* desc, const irt_fields* fields,
   g->ck_bytes = 0;
   g->ck_sig = 0;
   cudaGetDevice(&g->device);
-  if (cudaMalloc(&g->cells, g->cell_bytes) != cudaSuccess) {
+  if (dev_malloc(&g->cells, g->cell_bytes) != cudaSuccess) {
     cudaGetLastError();
     delete g;
     return fail(IRT_ENOMEM, "irt_create_grid: cannot allocate %zu bytes", cb * (size_t)ncell);
   }
-  if (cudaMalloc((void**)&g->ctl, 64) != cudaSuccess) {
+  if (dev_malloc((void**)&g->ctl, 64) != cudaSuccess) {
     cudaGetLastError();
     cudaFree(g->cells);
     delete g;
@@ -550,7 +564,7 @@ irt_status grow(unsigned char** p, size_t* have, size_t need, cudaStream_t s, co
   if (*p) cudaFree(*p);
   *p = nullptr;
   *have = 0;
-  if (cudaMalloc((void**)p, need) != cudaSuccess) {
+  if (dev_malloc((void**)p, need) != cudaSuccess) {
     cudaGetLastError();
     return fail(IRT_ENOMEM, "%s: cannot allocate %zu bytes of scratch", what, need);
   }
@@ -711,12 +725,19 @@ irt_status run_thin(const irt_job* jobs, int njobs, const PhysParams& P, const P
     }
     unsigned long long* stats =
         (opts->flags & IRT_FLAG_STATS) ? jobs[base].grid->ctl + 1 : nullptr;
+    {
+      size_t rec_b = 0, mask_b = 0;
+      const size_t need = thin_smem_per_warp(prec == IRT_PREC_F64 ? 1 : 0, opts->mode, kmax,
+                                             nchan_max, &rec_b, &mask_b);
+      if (need > kThinSmemBudget)
+        return fail(IRT_EUNSUPPORTED,
+                    "irt_forward_ppv: thin-mode rays of %d samples with %d channels need %zu "
+                    "bytes of shared memory per warp (records %zu + sample masks %zu); the "
+                    "budget is %zu", kmax, nchan_max, need, rec_b, mask_b, kThinSmemBudget);
+    }
     const int e = launch_thin(prec == IRT_PREC_F64 ? 1 : 0, store, integ, opts->mode, tab, nb, P,
                               PF, total, kmax, nchan_max, stats, s);
     ++g_launches;
-    if (e == (int)cudaErrorInvalidValue)
-      return fail(IRT_EUNSUPPORTED, "irt_forward_ppv: thin-mode rays of %d samples exceed the "
-                                    "shared-memory record buffer", kmax);
     if (e) return cuda_fail(e, "irt_forward_ppv: thin-mode kernel");
   }
   return IRT_OK;
@@ -885,7 +906,7 @@ extern "C" irt_status irt_forward_graph_create(const irt_job* jobs, int njobs,
     for (int j = 0; j < njobs; ++j) plans[j] = plan_job(jobs[j], opts->precision, 0);
     sc.bytes = fwd_scratch_need(plans, opts->precision);
   }
-  if (cudaMalloc((void**)&sc.p, sc.bytes) != cudaSuccess) {
+  if (dev_malloc((void**)&sc.p, sc.bytes) != cudaSuccess) {
     cudaGetLastError();
     cudaStreamDestroy(cs);
     return fail(IRT_ENOMEM, "irt_forward_graph_create: cannot allocate %zu bytes of scratch",
@@ -1203,6 +1224,9 @@ extern "C" irt_status irt_forward_ppv_static(const irt_grid_desc* desc, const ir
   if (st) return st;
   if (opts->flags & IRT_FLAG_SAVE_CHECKPOINTS)
     return fail(IRT_EUNSUPPORTED, "irt_forward_ppv_static: no checkpoints (no grid keeps them)");
+  if (opts->flags & IRT_FLAG_STATS)
+    return fail(IRT_EUNSUPPORTED, "irt_forward_ppv_static: no work counters (no grid keeps "
+                                  "them for irt_grid_stats)");
   if (opts->mode != IRT_MODE_THICK)
     return fail(IRT_EUNSUPPORTED, "irt_forward_ppv_static: optically thick mode only");
   if (opts->units == IRT_UNITS_TB)
@@ -1224,6 +1248,21 @@ extern "C" irt_status irt_forward_ppv_static(const irt_grid_desc* desc, const ir
   job.out = *out;
   st = check_job(job, opts->precision);
   if (st) return st;
+  // the record area must hold one block of warps, each with the records of
+  // the longest ray (checked here so that no kernel of the call runs)
+  const Plan p = plan_job(job, opts->precision, 0);
+  {
+    const size_t rec = opts->precision == IRT_PREC_F64 ? kRecBytesF64 : kRecBytesF32;
+    const size_t stride = ((size_t)p.kmax * rec + 255) & ~(size_t)255;
+    const size_t rec_need = stride * kWarpsPerBlock;
+    if (rec_need > kStaticRecBytes)
+      return fail(IRT_EINVAL,
+                  "irt_forward_ppv_static: rays of up to %d samples need %zu bytes of sample "
+                  "records (%d warps x %zu B); the static scratch holds %zu bytes (rays of at most "
+                  "%zu samples)",
+                  p.kmax, rec_need, kWarpsPerBlock, stride, kStaticRecBytes,
+                  (kStaticRecBytes / kWarpsPerBlock) / rec);
+  }
 
   void* base = nullptr;
   st = static_scratch_base(&base);
@@ -1240,7 +1279,6 @@ extern "C" irt_status irt_forward_ppv_static(const irt_grid_desc* desc, const ir
   if (e) return cuda_fail(e, "irt_forward_ppv_static: pack kernel");
 
   const PhysParams P = fold_constants(line, dust, opts);
-  const Plan p = plan_job(job, opts->precision, 0);
   JobTable tab;
   std::memset(&tab, 0, sizeof tab);
   tab.j[0] = make_jobdev(job, p);
@@ -1254,7 +1292,7 @@ extern "C" irt_status irt_forward_ppv_static(const irt_grid_desc* desc, const ir
   L.fwmax = 32 * p.ni;
   L.cwmax = p.cw;
   L.flags = opts->flags;
-  L.stats = (opts->flags & IRT_FLAG_STATS) ? g.ctl + 1 : nullptr;
+  L.stats = nullptr;
   L.rscr = recs;
   L.rbytes = kStaticRecBytes;
   e = dispatch(opts->precision, opts->integration, store, p.ni, tab, 1, P, to_float(P), L, s);

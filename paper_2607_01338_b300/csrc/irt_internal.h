@@ -131,6 +131,11 @@ struct FwdLaunch {
   size_t rbytes;               // size of rscr; bounds the resident warps
 };
 
+// Shared memory per warp the thin-mode kernel may use (records and masks).
+constexpr size_t kThinSmemBudget = 200 * 1024;
+size_t thin_smem_per_warp(int precision, int transfer, int kmax, int nchan_max,
+                          size_t* record_bytes, size_t* mask_bytes);
+
 int launch_pack(int store, const void* const* src, const int* dtypes, const double* scale,
                 void* cells, long long ncell, void* stream);
 

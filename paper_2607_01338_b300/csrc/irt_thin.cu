@@ -480,17 +480,28 @@ thin_kernel(const __grid_constant__ JobTable tab, int njobs, const PhysParams P,
 
 // Host launcher of the thin modes: precision (0 float, 1 double), field
 // storage, integration (M_FORMAL or M_SMOOTH), transfer mode.
-int launch_thin(int precision, int store, int integ, int transfer, const JobTable& tab,
-                int njobs, const PhysParams& P, const PhysF& PF, long long total, int kmax,
-                int nchan_max, unsigned long long* stats, cudaStream_t stream) {
+// Shared memory one warp of the thin kernel needs: the records of the longest
+// ray plus, for the float optically thin and density-tracing kernels, the
+// per-block sample masks (one bit per sample and 31-channel block).
+size_t thin_smem_per_warp(int precision, int transfer, int kmax, int nchan_max,
+                          size_t* record_bytes, size_t* mask_bytes_out) {
   const size_t rec_bytes = precision ? sizeof(dev::ThinRec<double>) : sizeof(dev::ThinRec<float>);
   const int nchunk_max = (kmax + 31) / 32;
-  // sample masks: the float optically thin and density-tracing kernels only
   const bool masks = !precision && (transfer == IRT_MODE_THIN ||
                                     transfer == IRT_MODE_DENSITY_TRACING);
   const size_t mask_bytes = masks ? (size_t)4 * ((nchan_max + 30) / 31) * nchunk_max : 0;
-  const size_t per_warp = (rec_bytes * (size_t)kmax + mask_bytes + 15) & ~(size_t)15;
-  const size_t budget = 200 * 1024;
+  if (record_bytes) *record_bytes = rec_bytes * (size_t)kmax;
+  if (mask_bytes_out) *mask_bytes_out = mask_bytes;
+  return (rec_bytes * (size_t)kmax + mask_bytes + 15) & ~(size_t)15;
+}
+
+int launch_thin(int precision, int store, int integ, int transfer, const JobTable& tab,
+                int njobs, const PhysParams& P, const PhysF& PF, long long total, int kmax,
+                int nchan_max, unsigned long long* stats, cudaStream_t stream) {
+  const int nchunk_max = (kmax + 31) / 32;
+  const size_t per_warp = thin_smem_per_warp(precision, transfer, kmax, nchan_max, nullptr,
+                                             nullptr);
+  const size_t budget = kThinSmemBudget;
   if (per_warp > budget) return (int)cudaErrorInvalidValue;
   const int warps = (int)std::max<size_t>(1, std::min<size_t>(dev::kThinWarps, budget / per_warp));
   const size_t smem = per_warp * warps;

@@ -186,3 +186,60 @@ def test_static_entry_takes_the_thick_mode_and_rj_or_intensity_units(B):
                                         ctypes.byref(line), ctypes.byref(dust),
                                         ctypes.byref(opts), None) == B.IRT_EUNSUPPORTED
         assert word in L.irt_last_error()
+
+
+def test_static_entry_refuses_long_rays_and_stats_before_any_cuda_call(B):
+    """Rays longer than the static record area holds for one block of warps
+    are refused with IRT_EINVAL before any launch (a 2 x 2 x 262144 z-view
+    grid is within the cell limit but its rays have 262144 samples), and so is
+    IRT_FLAG_STATS (no grid keeps the counters)."""
+    L = B.lib
+    line = _line(B)
+    dust = B.irt_dust(0.01, 2.8)
+    f = B.irt_fields(1, 2, 3, 4, 5)
+    vaxis = B.irt_vaxis(4, -2.0, 1.0, 1)
+    cubes = B.irt_cubes(1, None, None, None, None)
+    opts = B.irt_opts(0, 1, 0, 2.725, 0, 0)
+    desc = B.irt_grid_desc(2, 2, 262144, 1.0, (ctypes.c_int * 5)(0, 0, 0, 0, 0))
+    view = B.irt_view(0, 0, 2, 2, 1.0, 0)
+    args = (ctypes.byref(desc), ctypes.byref(f), ctypes.byref(view), ctypes.byref(vaxis),
+            ctypes.byref(cubes), ctypes.byref(line), ctypes.byref(dust))
+    assert L.irt_forward_ppv_static(*args, ctypes.byref(opts), None) == B.IRT_EINVAL
+    msg = L.irt_last_error()
+    assert b"262144 samples" in msg and b"87381 samples" in msg
+    stats = B.irt_opts(0, 1, 0, 2.725, 0, B.IRT_FLAG_STATS)
+    desc4 = B.irt_grid_desc(4, 4, 4, 1.0, (ctypes.c_int * 5)(0, 0, 0, 0, 0))
+    view4 = B.irt_view(0, 0, 4, 4, 1.0, 0)
+    assert L.irt_forward_ppv_static(ctypes.byref(desc4), ctypes.byref(f), ctypes.byref(view4),
+                                    ctypes.byref(vaxis), ctypes.byref(cubes), ctypes.byref(line),
+                                    ctypes.byref(dust), ctypes.byref(stats),
+                                    None) == B.IRT_EUNSUPPORTED
+    assert b"counters" in L.irt_last_error()
+
+
+def test_forced_allocation_failure_reports_enomem(B, monkeypatch):
+    """Host-side fault injection: with IRT_FAIL_ALLOC set, irt_create_grid
+    fails with IRT_ENOMEM, returns no handle and names the allocation; with it
+    cleared (or "0") the same call gets past the allocation."""
+    L = B.lib
+    f = B.irt_fields(1, 2, 3, 4, 5)
+    desc = B.irt_grid_desc(8, 8, 8, 1.0, (ctypes.c_int * 5)(0, 0, 0, 0, 0))
+    out = ctypes.c_void_p(12345)
+    monkeypatch.setenv("IRT_FAIL_ALLOC", "1")
+    assert L.irt_create_grid(ctypes.byref(desc), ctypes.byref(f), None,
+                             ctypes.byref(out)) == B.IRT_ENOMEM
+    assert out.value is None
+    assert b"allocate" in L.irt_last_error()
+    monkeypatch.setenv("IRT_FAIL_ALLOC", "0")
+    if not _has_gpu():
+        # without a device the real allocation fails too, with the same code
+        assert L.irt_create_grid(ctypes.byref(desc), ctypes.byref(f), None,
+                                 ctypes.byref(out)) == B.IRT_ENOMEM
+
+
+def _has_gpu():
+    try:
+        import torch
+        return torch.cuda.is_available()
+    except Exception:
+        return False

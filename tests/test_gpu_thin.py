@@ -145,7 +145,7 @@ def test_thin_modes_refuse_kahan_checkpoints_and_the_adjoint():
 @pytest.mark.parametrize("integration", ["smooth", "formal"])
 @pytest.mark.parametrize("precision", ["f32", "f64"])
 def test_density_tracing_cube(precision, integration, kind):
-    """Sec. 5.11 density-tracing cube (column density per unit velocity)."""
+    """Sec. 5.10 density-tracing cube (column density per unit velocity)."""
     w = workload(0)
     fs = make_fields(w.n, w.seed)
     view = view_of(kind, w.n, w.cell_cm)

@@ -1,4 +1,4 @@
-"""Pins of the oracle's density-tracing cube (Sec. 5.11, "simple
+"""Pins of the oracle's density-tracing cube (Sec. 5.10, "simple
 observation": tracer column density per unit velocity): the channel sum is
 the column density, a cold cell puts its whole column in its own channel,
 linearity, and the Gaussian spread.  All run on CPU."""
