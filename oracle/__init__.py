@@ -78,6 +78,30 @@ def lib():
                                                   ctypes.c_double, _dp, ctypes.c_int, _ip,
                                                   _dp, _dp, _dp])
             L.oracle_num_threads.restype = ctypes.c_int
+            L.oracle_render_levels.restype = ctypes.c_int
+            L.oracle_render_levels.argtypes = ([ctypes.POINTER(_dp), _dp, ctypes.c_int,
+                                                ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                                _dp, _dp, _dp, ctypes.c_int, ctypes.c_double,
+                                                ctypes.c_double, ctypes.c_int, ctypes.c_int,
+                                                ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                                ctypes.c_int, _ip] + [_dp] * 5
+                                               + [ctypes.c_void_p, ctypes.c_int])
+            L.oracle_ot_populations.restype = None
+            L.oracle_ot_populations.argtypes = [ctypes.POINTER(OracleLevelModel),
+                                                ctypes.c_double, ctypes.c_double,
+                                                ctypes.c_double, _dp]
+            L.oracle_ot_table_build.restype = ctypes.c_void_p
+            L.oracle_ot_table_build.argtypes = [ctypes.POINTER(OracleLevelModel), _ip, _dp, _dp,
+                                                ctypes.c_int, _ip]
+            L.oracle_ot_table_values.restype = None
+            L.oracle_ot_table_values.argtypes = [ctypes.c_void_p, _dp]
+            L.oracle_ot_lookup.restype = None
+            L.oracle_ot_lookup.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_double,
+                                           ctypes.c_double, ctypes.c_double, _dp]
+            L.oracle_ot_table_from_values.restype = ctypes.c_void_p
+            L.oracle_ot_table_from_values.argtypes = [_ip, _dp, _dp, ctypes.c_int, _dp, _dp]
+            L.oracle_ot_table_free.restype = None
+            L.oracle_ot_table_free.argtypes = [ctypes.c_void_p]
             _lib = L
     return _lib
 
@@ -85,6 +109,95 @@ def lib():
 # --------------------------------------------------------------------------
 # argument packing
 # --------------------------------------------------------------------------
+class OracleLevelModel(ctypes.Structure):
+    """Layout of LevelModel in irt_oracle.cpp (pointers into numpy arrays)."""
+    _fields_ = [("nlev", ctypes.c_int), ("energy_k", _dp), ("g", _dp),
+                ("nrad", ctypes.c_int), ("rad_up", _ip), ("rad_lo", _ip), ("a_ul", _dp),
+                ("nu", _dp), ("npartner", ctypes.c_int), ("partner", _ip),
+                ("ntemp", ctypes.c_int), ("coll_temp", _dp), ("ncoll", ctypes.c_int),
+                ("coll_up", _ip), ("coll_lo", _ip), ("k_ul", _dp), ("t_rad", ctypes.c_double),
+                ("ortho_para", ctypes.c_double), ("x_he", ctypes.c_double)]
+
+
+def _level_model(model: dict):
+    """(keep-alive arrays, OracleLevelModel) from a level-model dict."""
+    d = lambda k: np.ascontiguousarray(np.asarray(model[k], dtype=np.float64))  # noqa: E731
+    i = lambda k: np.ascontiguousarray(np.asarray(model[k], dtype=np.int32))    # noqa: E731
+    keep = dict(energy_k=d("energy_k"), g=d("g"), rad_up=i("rad_up"), rad_lo=i("rad_lo"),
+                a_ul=d("a_ul_s"), nu=d("nu_hz"), partner=i("partner"),
+                coll_temp=d("coll_temp_k"), coll_up=i("coll_up"), coll_lo=i("coll_lo"),
+                k_ul=d("k_ul_cm3_s"))
+    ntemp = keep["coll_temp"].shape[-1]
+    ncoll = keep["coll_up"].shape[-1]
+    m = OracleLevelModel(int(model["nlev"]), keep["energy_k"].ctypes.data_as(_dp),
+                         keep["g"].ctypes.data_as(_dp), len(keep["rad_up"]),
+                         keep["rad_up"].ctypes.data_as(_ip), keep["rad_lo"].ctypes.data_as(_ip),
+                         keep["a_ul"].ctypes.data_as(_dp), keep["nu"].ctypes.data_as(_dp),
+                         len(keep["partner"]), keep["partner"].ctypes.data_as(_ip), ntemp,
+                         keep["coll_temp"].ctypes.data_as(_dp), ncoll,
+                         keep["coll_up"].ctypes.data_as(_ip), keep["coll_lo"].ctypes.data_as(_ip),
+                         keep["k_ul"].ctypes.data_as(_dp), float(model["t_rad_k"]),
+                         float(model["ortho_para"]), float(model["x_he"]))
+    return keep, m
+
+
+def ot_populations(model: dict, n_h: float, chi: float, T: float) -> np.ndarray:
+    """Fractional level populations n_i / N of the OT level balance at total
+    H density n_h [cm^-3], H2 abundance chi and gas temperature T (Sec. 3.5)."""
+    keep, m = _level_model(model)
+    f = np.zeros(int(model["nlev"]))
+    lib().oracle_ot_populations(ctypes.byref(m), n_h, chi, T, f.ctypes.data_as(_dp))
+    return f
+
+
+class OTTable:
+    """Coefficient grid of Sec. 4.2 over (log10 n_H, chi, log10 T) for the
+    radiative transitions ``lines`` of ``model``; values per tracer molecule
+    [cgs]: j = (h nu / 4 pi) A f_u, alpha = (h nu / 4 pi)(f_l B_lu - f_u B_ul)."""
+
+    def __init__(self, model: dict, axes: dict, lines, values=None):
+        self.axes = dict(axes)
+        self.n = (int(axes["n_n"]), int(axes["n_chi"]), int(axes["n_t"]))
+        n = np.array(self.n, dtype=np.int32)
+        lo = np.array([axes["log10_nh_min"], axes["chi_min"], axes["log10_t_min"]])
+        hi = np.array([axes["log10_nh_max"], axes["chi_max"], axes["log10_t_max"]])
+        ln = np.ascontiguousarray(np.asarray(lines, dtype=np.int32))
+        self.nlines = len(ln)
+        if values is not None:
+            # a table with given content [nlines, n_n, n_chi, n_t, 2]
+            v = np.ascontiguousarray(np.asarray(values, dtype=np.float64))
+            assert v.shape == (self.nlines,) + self.n + (2,)
+            nu = np.ascontiguousarray(np.asarray(model["nu_hz"], dtype=np.float64)[ln])
+            self.ptr = lib().oracle_ot_table_from_values(
+                n.ctypes.data_as(_ip), lo.ctypes.data_as(_dp), hi.ctypes.data_as(_dp),
+                self.nlines, nu.ctypes.data_as(_dp), v.ctypes.data_as(_dp))
+            return
+        keep, m = _level_model(model)
+        self.ptr = lib().oracle_ot_table_build(ctypes.byref(m), n.ctypes.data_as(_ip),
+                                               lo.ctypes.data_as(_dp), hi.ctypes.data_as(_dp),
+                                               self.nlines, ln.ctypes.data_as(_ip))
+
+    def values(self) -> np.ndarray:
+        """[nlines, n_n, n_chi, n_t, 2] array of (j, alpha) per molecule."""
+        out = np.zeros((self.nlines,) + self.n + (2,))
+        lib().oracle_ot_table_values(self.ptr, out.ctypes.data_as(_dp))
+        return out
+
+    def lookup(self, line: int, n_h: float, chi: float, T: float):
+        out = np.zeros(2)
+        lib().oracle_ot_lookup(self.ptr, line, n_h, chi, T, out.ctypes.data_as(_dp))
+        return float(out[0]), float(out[1])
+
+    def close(self):
+        if getattr(self, "ptr", None):
+            lib().oracle_ot_table_free(self.ptr)
+            self.ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 LINE_KEYS = ("nu_ul_hz", "a_ul_s", "e_u_k", "b0_hz", "g_u", "g_l", "mass_amu", "t_inf_k",
              "sigma_turb_kms")
 DUST_KEYS = ("kappa_cm2_per_g_gas", "mu_mass_per_h2_amu")
@@ -192,9 +305,12 @@ def ray_thin(line, dust, vaxis, samples, h, transfer=SELECTIVELY_THIN, integrati
 
 
 def render(fields, cell_cm, line, dust, view, vaxis, pixels, integration=SMOOTH, units=TRJ,
-           t_bg=2.725, transfer=THICK):
+           t_bg=2.725, transfer=THICK, levels=None, line_index=0, chi=None):
     """Render the pixels ``pixels`` (int array [npix, 2] of (px, py)).
-    Returns dict of [npix, nchan] float64 arrays T, C, D, L, B."""
+    Returns dict of [npix, nchan] float64 arrays T, C, D, L, B.  ``levels``:
+    an OTTable whose line ``line_index`` gives the line coefficients (OT level
+    balance, Sec. 4.2-4.3) instead of LTE; ``chi``: H2 abundance per H nucleus
+    [z][y][x] (default 0.5 everywhere)."""
     nz, ny, nx = np.asarray(fields[0]).shape
     arrs, ptrs = _fields(fields)
     kl, pl = _line(line)
@@ -204,9 +320,13 @@ def render(fields, cell_cm, line, dust, view, vaxis, pixels, integration=SMOOTH,
     npix = pix.shape[0]
     nch = vaxis.nchan
     outs = [np.zeros((npix, nch)) for _ in range(5)]
-    lib().oracle_render(ptrs, nx, ny, nz, cell_cm, pl, pd, pv, nch, vaxis.v_first_edge_kms,
-                        vaxis.dv_kms, vaxis.subsample_f, transfer, integration, units, t_bg, npix,
-                        pix.ctypes.data_as(_ip), *[o.ctypes.data_as(_dp) for o in outs])
+    chi_a = None if chi is None else np.ascontiguousarray(np.asarray(chi, dtype=np.float64))
+    lib().oracle_render_levels(ptrs, None if chi_a is None else chi_a.ctypes.data_as(_dp),
+                               nx, ny, nz, cell_cm, pl, pd, pv, nch, vaxis.v_first_edge_kms,
+                               vaxis.dv_kms, vaxis.subsample_f, transfer, integration, units,
+                               t_bg, npix, pix.ctypes.data_as(_ip),
+                               *[o.ctypes.data_as(_dp) for o in outs],
+                               None if levels is None else levels.ptr, int(line_index))
     return dict(zip("TCDLB", outs))
 
 

@@ -57,6 +57,7 @@
 #include <cmath>
 #include <cstdint>
 #include <cstring>
+#include <type_traits>
 #include <vector>
 
 #ifdef _OPENMP
@@ -164,6 +165,7 @@ enum { UNITS_TRJ = 0, UNITS_INTENSITY = 1, UNITS_TB = 2 };
 template <class S>
 struct Sample {
   S n_h2, t_gas, t_dust, v_los, x_tr;
+  S chi = S(0.5);   // H2 abundance per H nucleus (0.5: fully molecular); OT balance only
 };
 
 // ---------------------------------------------------------------------------
@@ -235,6 +237,214 @@ void line_coefficients(const Line& ln, const Sample<S>& s, S* jL, S* aL) {
   *aL = (H_PLANCK * nu / (4.0 * PI)) * (n_l * B_lu - n_u * B_ul);
 }
 
+// ---------------------------------------------------------------------------
+// Optically thin (OT) level balance (Sec. 3.4-3.6) and its coefficient grid
+// (Sec. 4.2).  The level system of Sec. 3.5: for every level i but the
+// ground state, what flows in equals what flows out,
+//   sum_{j != i} [ n_j (C_ji + A_ji + B_ji J_ji) - n_i (C_ij + A_ij + B_ij J_ij) ] = 0,
+// with A_ij = 0 for i < j, J the Planck intensity of a blackbody at the fixed
+// background temperature T-bar at the transition frequency (the OT
+// assumption), C_ij = sum over partners of K_ij n_partner, the excitation
+// rates from the de-excitation rates by detailed balance at the gas
+// temperature (Sec. 3.6), and the ground-state row replaced by sum_i n_i = N.
+// ---------------------------------------------------------------------------
+enum { PARTNER_H2 = 0, PARTNER_PH2 = 1, PARTNER_OH2 = 2, PARTNER_H = 3, PARTNER_HE = 4 };
+
+// Caller's level model (energies, weights, radiative and collisional data),
+// the layout of the ctypes structure OracleLevelModel.
+struct LevelModel {
+  int nlev;
+  const double* energy_k;   // [nlev] E_i / k [K]
+  const double* g;          // [nlev]
+  int nrad;
+  const int* rad_up;        // [nrad]
+  const int* rad_lo;
+  const double* a_ul;       // [nrad] Einstein A [1/s]
+  const double* nu;         // [nrad] [Hz]
+  int npartner;
+  const int* partner;       // [npartner] PARTNER_*
+  int ntemp;
+  const double* coll_temp;  // [npartner][ntemp] ascending [K]
+  int ncoll;
+  const int* coll_up;       // [npartner][ncoll]
+  const int* coll_lo;
+  const double* k_ul;       // [npartner][ncoll][ntemp] de-excitation [cm^3/s]
+  double t_rad;             // T-bar [K]
+  double ortho_para;        // ortho-H2 / para-H2
+  double x_he;              // He per H nucleus
+};
+
+// Number density of a collision partner [cm^-3] for total H nucleus density
+// n_h and H2 abundance chi (H2 molecules per H nucleus; the rest of the H is
+// atomic, Sec. 4.2).
+double partner_density(const LevelModel& m, int kind, double n_h, double chi) {
+  const double n_h2 = chi * n_h;
+  switch (kind) {
+    case PARTNER_H2: return n_h2;
+    case PARTNER_PH2: return n_h2 / (1.0 + m.ortho_para);
+    case PARTNER_OH2: return n_h2 * m.ortho_para / (1.0 + m.ortho_para);
+    case PARTNER_H: return std::max(0.0, n_h * (1.0 - 2.0 * chi));
+    case PARTNER_HE: return m.x_he * n_h;
+  }
+  return 0.0;
+}
+
+// Rate coefficient of partner p, collisional transition c at temperature T:
+// linear interpolation between the tabulated temperatures, the end values
+// held beyond them.
+double rate_coefficient(const LevelModel& m, int p, int c, double T) {
+  const double* tt = m.coll_temp + (int64_t)p * m.ntemp;
+  const double* kk = m.k_ul + ((int64_t)p * m.ncoll + c) * m.ntemp;
+  if (m.ntemp == 1 || T <= tt[0]) return kk[0];
+  if (T >= tt[m.ntemp - 1]) return kk[m.ntemp - 1];
+  int i = 0;
+  while (T > tt[i + 1]) ++i;
+  const double w = (T - tt[i]) / (tt[i + 1] - tt[i]);
+  return kk[i] + w * (kk[i + 1] - kk[i]);
+}
+
+// Solve A x = b (n x n, row major) by Gaussian elimination with partial
+// pivoting; A and b are overwritten.
+void gauss_solve(int n, std::vector<double>& A, std::vector<double>& b, double* x) {
+  for (int k = 0; k < n; ++k) {
+    int p = k;
+    for (int i = k + 1; i < n; ++i)
+      if (std::fabs(A[(int64_t)i * n + k]) > std::fabs(A[(int64_t)p * n + k])) p = i;
+    if (p != k) {
+      for (int j = 0; j < n; ++j) std::swap(A[(int64_t)k * n + j], A[(int64_t)p * n + j]);
+      std::swap(b[k], b[p]);
+    }
+    for (int i = k + 1; i < n; ++i) {
+      const double f = A[(int64_t)i * n + k] / A[(int64_t)k * n + k];
+      if (f == 0.0) continue;
+      for (int j = k; j < n; ++j) A[(int64_t)i * n + j] -= f * A[(int64_t)k * n + j];
+      b[i] -= f * b[k];
+    }
+  }
+  for (int i = n - 1; i >= 0; --i) {
+    double acc = b[i];
+    for (int j = i + 1; j < n; ++j) acc -= A[(int64_t)i * n + j] * x[j];
+    x[i] = acc / A[(int64_t)i * n + i];
+  }
+}
+
+// Fractional level populations n_i / N of the OT balance at total H density
+// n_h [cm^-3], H2 abundance chi and gas temperature T [K].
+void ot_populations(const LevelModel& m, double n_h, double chi, double T, double* f) {
+  const int n = m.nlev;
+  // R[i][j]: rate i -> j per molecule in level i [1/s]
+  std::vector<double> R((size_t)n * n, 0.0);
+  for (int p = 0; p < m.npartner; ++p) {
+    const double np = partner_density(m, m.partner[p], n_h, chi);
+    for (int c = 0; c < m.ncoll; ++c) {
+      const int u = m.coll_up[(int64_t)p * m.ncoll + c];
+      const int l = m.coll_lo[(int64_t)p * m.ncoll + c];
+      const double cul = rate_coefficient(m, p, c, T) * np;
+      R[(size_t)u * n + l] += cul;
+      // detailed balance (Sec. 3.6): K_lu = K_ul (g_u / g_l) exp(-(E_u - E_l) / kT)
+      R[(size_t)l * n + u] += cul * (m.g[u] / m.g[l]) * std::exp(-(m.energy_k[u] - m.energy_k[l]) / T);
+    }
+  }
+  for (int r = 0; r < m.nrad; ++r) {
+    const int u = m.rad_up[r], l = m.rad_lo[r];
+    const double nu = m.nu[r];
+    // Einstein B relations (Sec. 3.6) and the background J = B_nu(T-bar)
+    const double B_ul = C_LIGHT * C_LIGHT * m.a_ul[r] / (2.0 * H_PLANCK * nu * nu * nu);
+    const double B_lu = (m.g[u] / m.g[l]) * B_ul;
+    const double J = planck(nu, m.t_rad);
+    R[(size_t)u * n + l] += m.a_ul[r] + B_ul * J;
+    R[(size_t)l * n + u] += B_lu * J;
+  }
+  std::vector<double> M((size_t)n * n, 0.0), b(n, 0.0);
+  for (int i = 1; i < n; ++i) {
+    double out = 0.0;
+    for (int j = 0; j < n; ++j) {
+      if (j == i) continue;
+      M[(size_t)i * n + j] = R[(size_t)j * n + i];   // inflow from j
+      out += R[(size_t)i * n + j];
+    }
+    M[(size_t)i * n + i] = -out;
+  }
+  for (int j = 0; j < n; ++j) M[j] = 1.0;   // conservation row
+  b[0] = 1.0;
+  gauss_solve(n, M, b, f);
+}
+
+// Coefficient grid of Sec. 4.2 over (log10 n_H, chi, log10 T), uniform
+// nodes per axis; per node and line, the frequency-integrated line emission
+// and absorption coefficients per tracer molecule [cgs], j = (h nu / 4 pi)
+// A f_u and alpha = (h nu / 4 pi)(f_l B_lu - f_u B_ul).
+struct OTTable {
+  int n[3];
+  double lo[3], hi[3];
+  int nlines;
+  std::vector<double> nu;     // [nlines]
+  std::vector<double> v;      // [nlines][n0][n1][n2][2]
+};
+
+double axis_value(const OTTable& t, int a, int i) {
+  return t.lo[a] + (t.hi[a] - t.lo[a]) * i / (t.n[a] - 1);
+}
+
+// Trilinear interpolation of the grid at (log10 n_H, chi, log10 T) with the
+// cell index clamped to the grid, so that outside the bounds the value
+// continues linearly from the edge cell (Sec. 4.2).
+void ot_lookup(const OTTable& t, int line, double n_h, double chi, double T, double* jt,
+               double* at) {
+  const double x[3] = {std::log10(n_h), chi, std::log10(T)};
+  int i0[3];
+  double w[3];
+  for (int a = 0; a < 3; ++a) {
+    const double u = (x[a] - t.lo[a]) / (t.hi[a] - t.lo[a]) * (t.n[a] - 1);
+    int i = (int)std::floor(u);
+    i = std::min(std::max(i, 0), t.n[a] - 2);
+    i0[a] = i;
+    w[a] = u - i;
+  }
+  double acc[2] = {0.0, 0.0};
+  for (int c = 0; c < 8; ++c) {
+    const int a0 = i0[0] + (c & 1), a1 = i0[1] + ((c >> 1) & 1), a2 = i0[2] + ((c >> 2) & 1);
+    const double wc = ((c & 1) ? w[0] : 1.0 - w[0]) * ((c & 2) ? w[1] : 1.0 - w[1]) *
+                      ((c & 4) ? w[2] : 1.0 - w[2]);
+    const int64_t idx = ((((int64_t)line * t.n[0] + a0) * t.n[1] + a1) * t.n[2] + a2) * 2;
+    acc[0] += wc * t.v[idx];
+    acc[1] += wc * t.v[idx + 1];
+  }
+  *jt = acc[0];
+  *at = acc[1];
+}
+
+struct OTLine {
+  const OTTable* t;
+  int line;
+};
+
+// Line coefficients of a sample: LTE (ot == nullptr), or the OT grid looked
+// up at n_H = n_H2 / chi, with the tracer density N = x n_H2 (Sec. 4.3: the
+// per-molecule coefficients times the tracer density).  Zero above T_inf.
+template <class S>
+void line_coeffs_for(const Line& ln, const OTLine* ot, const Sample<S>& s, S* jL, S* aL) {
+  if (!ot) {
+    line_coefficients(ln, s, jL, aL);
+    return;
+  }
+  if constexpr (std::is_same<S, double>::value) {
+    if (s.t_gas > ln.t_inf || s.t_gas <= 0.0 || s.n_h2 <= 0.0 || s.chi <= 0.0 || s.x_tr <= 0.0) {
+      *jL = 0.0;
+      *aL = 0.0;
+      return;
+    }
+    double jt, at;
+    ot_lookup(*ot->t, ot->line, s.n_h2 / s.chi, s.chi, s.t_gas, &jt, &at);
+    const double N = s.x_tr * s.n_h2;
+    *jL = N * jt;
+    *aL = N * at;
+  } else {
+    *jL = S(0.0);   // not reached: the gradient oracle takes LTE only
+    *aL = S(0.0);
+  }
+}
+
 // Gaussian Doppler profile per unit frequency (Sec. 3.3), evaluated at the
 // observed velocity u for a cell moving at v_los.  The width adds the 1-D
 // microturbulent dispersion to the thermal one: b^2 = 2kT/m + 2 sigma^2.
@@ -295,14 +505,14 @@ S integrate(int mode, const std::vector<S>& j, const std::vector<S>& a, double h
 template <class S>
 void ray_outputs(const Line& ln, const DustP& du, const VAxis& va, int mode, int units,
                  double t_bg, const std::vector<Sample<S>>& smp, double h,
-                 S* oT, S* oC, S* oD, S* oL, S* oB) {
+                 S* oT, S* oC, S* oD, S* oL, S* oB, const OTLine* ot = nullptr) {
   const int K = (int)smp.size();
   const int nch = va.nchan;
   const int f = va.f;
   // per-sample frequency-independent coefficients
   std::vector<S> jL(K), aL(K), aD(K);
   for (int k = 0; k < K; ++k) {
-    line_coefficients(ln, smp[k], &jL[k], &aL[k]);
+    line_coeffs_for(ln, ot, smp[k], &jL[k], &aL[k]);
     aD[k] = dust_alpha(du, smp[k]);
   }
   // fine velocity grid (Sec. 4.5, Table 4)
@@ -431,11 +641,12 @@ double direct_integral(int mode, const std::vector<double>& f, double h) {
 // fine velocities: every channel is solved at its own averaged coefficients).
 void ray_outputs_thin(const Line& ln, const DustP& du, const VAxis& va, int transfer, int mode,
                       int units, double t_bg, const std::vector<Sample<double>>& smp, double h,
-                      double* oT, double* oC, double* oD, double* oL, double* oB) {
+                      double* oT, double* oC, double* oD, double* oL, double* oB,
+                      const OTLine* ot = nullptr) {
   const int K = (int)smp.size();
   std::vector<double> jL(K), aL(K), aD(K);
   for (int k = 0; k < K; ++k) {
-    line_coefficients(ln, smp[k], &jL[k], &aL[k]);
+    line_coeffs_for(ln, ot, smp[k], &jL[k], &aL[k]);
     aD[k] = dust_alpha(du, smp[k]);
   }
   std::vector<double> jLb(K), aLb(K), jD(K), jT(K), aT(K);
@@ -522,8 +733,12 @@ struct Grid {
   const double* f[5];  // n_h2, t_gas, t_dust, v_los, x_tr, each [z][y][x]
   int nx, ny, nz;
   double dx;
+  const double* chi = nullptr;   // H2 abundance per H nucleus, or nullptr (0.5)
   double at(int q, int x, int y, int z) const {
     return f[q][((int64_t)z * ny + y) * nx + x];
+  }
+  double at_field(const double* a, int x, int y, int z) const {
+    return a[((int64_t)z * ny + y) * nx + x];
   }
 };
 
@@ -566,7 +781,7 @@ bool ray_chord(const Grid& g, const ViewP& v, int px, int py, double o[3], doubl
 
 // Trilinear interpolation of the raw field q at position r [cm], cell-centred
 // values, indices clamped to the grid (edge extension).
-double trilinear(const Grid& g, int q, const double r[3]) {
+double trilinear_field(const Grid& g, const double* field, const double r[3]) {
   const int n[3] = {g.nx, g.ny, g.nz};
   int i0[3], i1[3];
   double w[3];
@@ -586,10 +801,12 @@ double trilinear(const Grid& g, int q, const double r[3]) {
     const double wx = (c & 1) ? w[0] : 1.0 - w[0];
     const double wy = (c & 2) ? w[1] : 1.0 - w[1];
     const double wz = (c & 4) ? w[2] : 1.0 - w[2];
-    acc += wx * wy * wz * g.at(q, ix, iy, iz);
+    acc += wx * wy * wz * g.at_field(field, ix, iy, iz);
   }
   return acc;
 }
+
+double trilinear(const Grid& g, int q, const double r[3]) { return trilinear_field(g, g.f[q], r); }
 
 // Samples of one ray.  z view: the cells (px, py, k) for k = 0..nz-1 with
 // h = dx.  Oblique: K = ceil(chord/dx) midpoint samples of a uniform split.
@@ -605,6 +822,7 @@ void ray_samples(const Grid& g, const ViewP& v, int px, int py,
       s.t_dust = g.at(2, px, py, k);
       s.v_los = g.at(3, px, py, k);
       s.x_tr = g.at(4, px, py, k);
+      if (g.chi) s.chi = g.at_field(g.chi, px, py, k);
       smp->push_back(s);
     }
     return;
@@ -627,6 +845,7 @@ void ray_samples(const Grid& g, const ViewP& v, int px, int py,
     s.t_dust = trilinear(g, 2, r);
     s.v_los = trilinear(g, 3, r);
     s.x_tr = trilinear(g, 4, r);
+    if (g.chi) s.chi = trilinear_field(g, g.chi, r);
     smp->push_back(s);
   }
 }
@@ -740,14 +959,38 @@ int oracle_ray_samples(const double* const* fields, int nx, int ny, int nz, doub
 
 // Render a list of pixels.  pix[2*i], pix[2*i+1] = (px, py); outputs are
 // [npix][nchan] per component (NULL = not wanted).
+int oracle_render_levels(const double* const* fields, const double* chi, int nx, int ny, int nz,
+                         double cell_cm, const double* line, const double* dust,
+                         const double* view, int nchan, double v0, double dv, int f,
+                         int transfer, int integration, int units, double t_bg, int npix,
+                         const int* pix, double* oT, double* oC, double* oD, double* oL,
+                         double* oB, const void* ot_table, int ot_line);
+
 int oracle_render(const double* const* fields, int nx, int ny, int nz, double cell_cm,
                   const double* line, const double* dust, const double* view, int nchan,
                   double v0, double dv, int f, int transfer, int integration, int units,
                   double t_bg, int npix, const int* pix, double* oT, double* oC, double* oD,
                   double* oL, double* oB) {
+  return oracle_render_levels(fields, nullptr, nx, ny, nz, cell_cm, line, dust, view, nchan, v0,
+                              dv, f, transfer, integration, units, t_bg, npix, pix, oT, oC, oD,
+                              oL, oB, nullptr, 0);
+}
+
+// oracle_render with the line coefficients of an OT grid (ot_table from
+// oracle_ot_table_build, line index ot_line; NULL = LTE) and an optional H2
+// abundance field chi [z][y][x] (NULL = 0.5 everywhere).
+int oracle_render_levels(const double* const* fields, const double* chi, int nx, int ny, int nz,
+                         double cell_cm, const double* line, const double* dust,
+                         const double* view, int nchan, double v0, double dv, int f,
+                         int transfer, int integration, int units, double t_bg, int npix,
+                         const int* pix, double* oT, double* oC, double* oD, double* oL,
+                         double* oB, const void* ot_table, int ot_line) {
   Grid g;
   for (int q = 0; q < 5; ++q) g.f[q] = fields[q];
   g.nx = nx; g.ny = ny; g.nz = nz; g.dx = cell_cm;
+  g.chi = chi;
+  OTLine otl{static_cast<const OTTable*>(ot_table), ot_line};
+  const OTLine* ot = ot_table ? &otl : nullptr;
   const ViewP v{view[0], view[1], (int)view[2], (int)view[3], view[4], (int)view[5]};
   const Line ln = line_from(line);
   const DustP du = dust_from(dust);
@@ -760,13 +1003,13 @@ int oracle_render(const double* const* fields, int nx, int ny, int nz, double ce
     std::vector<double> T(nchan), C(nchan), D(nchan), L(nchan), B(nchan);
     if (transfer == MODE_THICK)
       ray_outputs(ln, du, va, integration, units, t_bg, smp, h, T.data(), C.data(), D.data(),
-                  L.data(), B.data());
+                  L.data(), B.data(), ot);
     else if (transfer == MODE_DENSITY_TRACING)
       ray_outputs_density(ln, va, integration, smp, h, T.data(), C.data(), D.data(), L.data(),
                           B.data());
     else
       ray_outputs_thin(ln, du, va, transfer, integration, units, t_bg, smp, h, T.data(),
-                       C.data(), D.data(), L.data(), B.data());
+                       C.data(), D.data(), L.data(), B.data(), ot);
     const int64_t off = (int64_t)i * nchan;
     for (int c = 0; c < nchan; ++c) {
       if (oT) oT[off + c] = T[c];
@@ -839,5 +1082,82 @@ double oracle_loss_grad_zview(const double* const* fields, int nx, int ny, int n
   }
   return loss;
 }
+
+// ---------------------------------------------------------------------------
+// OT level balance and its grid (Sec. 3.4-3.6, 4.2)
+// ---------------------------------------------------------------------------
+// Fractional populations n_i / N at (n_H, chi, T); f_out[nlev].
+void oracle_ot_populations(const LevelModel* m, double n_h, double chi, double T, double* f_out) {
+  ot_populations(*m, n_h, chi, T, f_out);
+}
+
+// Build the grid: axes n[3] nodes, lo[3], hi[3] (log10 n_H, chi, log10 T);
+// lines[nlines] = radiative transition indices of the model.  Returns an
+// opaque table (oracle_ot_table_free releases it).
+void* oracle_ot_table_build(const LevelModel* m, const int* n, const double* lo,
+                            const double* hi, int nlines, const int* lines) {
+  OTTable* t = new OTTable();
+  for (int a = 0; a < 3; ++a) {
+    t->n[a] = n[a];
+    t->lo[a] = lo[a];
+    t->hi[a] = hi[a];
+  }
+  t->nlines = nlines;
+  for (int q = 0; q < nlines; ++q) t->nu.push_back(m->nu[lines[q]]);
+  const int64_t nodes = (int64_t)n[0] * n[1] * n[2];
+  t->v.assign((size_t)nlines * nodes * 2, 0.0);
+#pragma omp parallel for schedule(dynamic, 64)
+  for (int64_t node = 0; node < nodes; ++node) {
+    const int i2 = (int)(node % n[2]);
+    const int i1 = (int)((node / n[2]) % n[1]);
+    const int i0 = (int)(node / ((int64_t)n[2] * n[1]));
+    const double n_h = std::pow(10.0, axis_value(*t, 0, i0));
+    const double chi = axis_value(*t, 1, i1);
+    const double T = std::pow(10.0, axis_value(*t, 2, i2));
+    std::vector<double> f(m->nlev);
+    ot_populations(*m, n_h, chi, T, f.data());
+    for (int q = 0; q < nlines; ++q) {
+      const int r = lines[q];
+      const int u = m->rad_up[r], l = m->rad_lo[r];
+      const double nu = m->nu[r];
+      const double B_ul = C_LIGHT * C_LIGHT * m->a_ul[r] / (2.0 * H_PLANCK * nu * nu * nu);
+      const double B_lu = (m->g[u] / m->g[l]) * B_ul;
+      const double hn = H_PLANCK * nu / (4.0 * PI);
+      const int64_t idx = ((int64_t)q * nodes + node) * 2;
+      t->v[idx] = hn * m->a_ul[r] * f[u];
+      t->v[idx + 1] = hn * (f[l] * B_lu - f[u] * B_ul);
+    }
+  }
+  return t;
+}
+
+// A grid holding given values [nlines][n0][n1][n2][2] (for checks of the
+// lookup on tables with known content); nu_hz[nlines].
+void* oracle_ot_table_from_values(const int* n, const double* lo, const double* hi, int nlines,
+                                  const double* nu_hz, const double* values) {
+  OTTable* t = new OTTable();
+  for (int a = 0; a < 3; ++a) {
+    t->n[a] = n[a];
+    t->lo[a] = lo[a];
+    t->hi[a] = hi[a];
+  }
+  t->nlines = nlines;
+  t->nu.assign(nu_hz, nu_hz + nlines);
+  const size_t cnt = (size_t)nlines * n[0] * n[1] * n[2] * 2;
+  t->v.assign(values, values + cnt);
+  return t;
+}
+
+// Copy of the grid values [nlines][n0][n1][n2][2] (j, alpha per molecule).
+void oracle_ot_table_values(const void* t, double* out) {
+  const OTTable* tt = static_cast<const OTTable*>(t);
+  std::copy(tt->v.begin(), tt->v.end(), out);
+}
+
+void oracle_ot_lookup(const void* t, int line, double n_h, double chi, double T, double* out) {
+  ot_lookup(*static_cast<const OTTable*>(t), line, n_h, chi, T, &out[0], &out[1]);
+}
+
+void oracle_ot_table_free(void* t) { delete static_cast<OTTable*>(t); }
 
 }  // extern "C"

@@ -1,6 +1,8 @@
 """Adjoint (reverse sweep) of the CUDA path against the FP64 oracle:
 dual-number gradients on a 16^3 grid and FP64 central differences on 200
-random cells of the 128^3 workload, tolerance 1e-3 relative."""
+random cells of the 128^3 workload, tolerance 1e-3 relative per cell (with
+an absolute floor at the float32 rounding level of the largest gradient, and,
+against finite differences, the rounding error of the difference itself)."""
 import math
 
 import numpy as np
@@ -46,10 +48,32 @@ def _gpu_loss_grads(f32, dx, view, va, target_L, integration="smooth", save=Fals
     return loss, out
 
 
-def _cmp(got, ref, rtol=GRAD_RTOL, floor=1e-3):
-    """Elementwise |got - ref| <= rtol |ref| + floor * max|ref|."""
-    allow = rtol * np.abs(ref) + floor * np.abs(ref).max()
+#: absolute floor of the gradient comparisons, as a fraction of the largest
+#: gradient: the float32 rounding level (unit roundoff 2^-24 = 6e-8) of the
+#: largest per-cell gradient, so that exact zeros of the reference compare.
+#: Everything above it is held to 1e-3 relative per cell.
+GRAD_FLOOR = 1e-7
+U64 = 2.0 ** -53
+
+
+def _cmp(got, ref, rtol=GRAD_RTOL, floor=None):
+    """Elementwise |got - ref| <= rtol |ref| + GRAD_FLOOR max|ref| (+ ``floor``,
+    an array of per-cell allowances for the error of the reference itself)."""
+    allow = rtol * np.abs(ref) + GRAD_FLOOR * np.abs(ref).max()
+    if floor is not None:
+        allow = allow + floor
     return float((np.abs(got - ref) / allow).max())
+
+
+def fd_rounding_floor(L_plus, target, K, eps, nvox):
+    """Rounding error of an FP64 central difference of a ray's squared-error
+    loss: each K-step recurrence leaves [L]_c with a relative error of at most
+    about K u (u = 2^-53), which moves sum_c ([L]_c - t_c)^2 by
+    2 sum_c |[L]_c - t_c| |[L]_c| K u; two such sums are differenced and
+    divided by 2 eps.  The truncation error of the central difference (eps^2
+    times the third derivative over 6, at eps = 1e-6 relative) is far below."""
+    return (2.0 * 2.0 * np.sum(np.abs(L_plus - target) * np.abs(L_plus)) * K * U64
+            / (2.0 * eps) / nvox)
 
 
 def crop_fields(fs, n, seed=0):
@@ -130,7 +154,7 @@ def test_adjoint_matches_fp64_finite_differences_128cube():
     fields = [a.copy() for a in deq.as_tuple()]
     worst = {}
     for q, g, name in ((0, gn, "n"), (1, gt, "T"), (3, gv, "v")):
-        fd, got = [], []
+        fd, got, fl = [], [], []
         for (z, y, x) in cells:
             v0 = fields[q][z, y, x]
             eps = 1e-6 * max(abs(v0), 1.0)
@@ -139,10 +163,12 @@ def test_adjoint_matches_fp64_finite_differences_128cube():
                 fields[q][z, y, x] = v0 + sgn * eps
                 Lr = oracle.render(fields, w.cell_cm, LINE, DUST, view, va, [(x, y)])["L"][0]
                 vals.append(np.sum((Lr - target[:, y, x]) ** 2))
+                if sgn == 1:
+                    fl.append(fd_rounding_floor(Lr, target[:, y, x], w.n, eps, nvox))
             fields[q][z, y, x] = v0
             fd.append((vals[0] - vals[1]) / (2 * eps) / nvox)
             got.append(g[z, y, x])
-        worst[name] = _cmp(np.array(got), np.array(fd))
+        worst[name] = _cmp(np.array(got), np.array(fd), floor=np.array(fl))
     assert all(v <= 1.0 for v in worst.values()), worst
 
 

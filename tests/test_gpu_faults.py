@@ -39,7 +39,7 @@ def test_create_grid_enomem_then_recovers(monkeypatch):
     monkeypatch.setenv("IRT_FAIL_ALLOC", "1")
     with pytest.raises(IrtError) as ei:
         irt.Grid(*tf, 0.1 * PC)
-    assert ei.value.args[0] == IRT_ENOMEM
+    assert ei.value.status == IRT_ENOMEM
     monkeypatch.delenv("IRT_FAIL_ALLOC")
     g = irt.Grid(*tf, 0.1 * PC)
     g.close()
@@ -75,7 +75,7 @@ def test_forward_scratch_growth_enomem_then_recovers(monkeypatch):
     monkeypatch.setenv("IRT_FAIL_ALLOC", "1")
     with pytest.raises(IrtError) as ei:
         irt.forward(g, view, va, LINE_13CO_21, DUST, out=out, stream=s)
-    assert ei.value.args[0] == IRT_ENOMEM
+    assert ei.value.status == IRT_ENOMEM
     torch.cuda.synchronize()
     assert all(bool((out[k] == -7.0).all()) for k in COMP), "a failed call wrote output"
     monkeypatch.delenv("IRT_FAIL_ALLOC")
@@ -98,7 +98,7 @@ def test_graph_create_enomem(monkeypatch):
     monkeypatch.setenv("IRT_FAIL_ALLOC", "1")
     with pytest.raises(IrtError) as ei:
         irt.ForwardGraph([(g, view, va)], LINE_13CO_21, DUST)
-    assert ei.value.args[0] == IRT_ENOMEM
+    assert ei.value.status == IRT_ENOMEM
     monkeypatch.delenv("IRT_FAIL_ALLOC")
     gr = irt.ForwardGraph([(g, view, va)], LINE_13CO_21, DUST)
     outs = gr.launch()

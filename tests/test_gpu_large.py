@@ -14,6 +14,7 @@ pytestmark = pytest.mark.gpu
 import oracle  # noqa: E402
 from synth import DUST, LINE_13CO_21, View, make_fields_torch, workload  # noqa: E402
 from tests.gpu_helpers import compare  # noqa: E402
+from tests.test_gpu_adjoint import GRAD_FLOOR, fd_rounding_floor  # noqa: E402
 
 LINE = dict(LINE_13CO_21)
 #: stored value x scale = physical value (density in 1e4 cm^-3, abundance in 1e-6)
@@ -85,7 +86,7 @@ def test_512cube_fp16_adjoint_against_central_differences(big):
     one = View(0.0, 0.0, 1, 1, w.cell_cm, 0)
     pix0 = np.zeros((1, 2), dtype=int)
     for q, grad in ((0, gn), (1, gt), (3, gv)):
-        fd, got = [], []
+        fd, got, fl = [], [], []
         for (z, y, x) in cells:
             col = _columns(h, [(int(x), int(y))])
             v0 = col[q][z, 0, 0]
@@ -95,9 +96,13 @@ def test_512cube_fp16_adjoint_against_central_differences(big):
                 col[q][z, 0, 0] = v0 + sgn * eps
                 Lr = oracle.render(col, w.cell_cm, LINE, DUST, one, va, pix0)["L"][0]
                 vals.append(np.sum(Lr * Lr))
+                if sgn == 1.0:
+                    fl.append(fd_rounding_floor(Lr, 0.0, w.n, eps, ntot))
             col[q][z, 0, 0] = v0
             fd.append((vals[0] - vals[1]) / (2.0 * eps) / ntot)
             got.append(float(grad[z, y, x]))
-        fd, got = np.array(fd), np.array(got)
-        allow = 1e-3 * np.abs(fd) + 1e-3 * np.abs(fd).max()
+        fd, got, fl = np.array(fd), np.array(got), np.array(fl)
+        # 1e-3 relative per cell; floors: the float32 rounding level of the
+        # largest gradient and the FP64 rounding of the central difference
+        allow = 1e-3 * np.abs(fd) + GRAD_FLOOR * np.abs(fd).max() + fl
         assert np.all(np.abs(got - fd) <= allow), (q, np.max(np.abs(got - fd) / allow))
