@@ -40,7 +40,11 @@
  *     pixel e_p with e_t = (cos t cos p, cos t sin p, -sin t), e_p = (-sin p,
  *     cos p, 0); the chord through the box is split into K = ceil(chord/dx)
  *     equal steps sampled at their midpoints with trilinear interpolation of
- *     cell-centred values (indices clamped at the faces).
+ *     cell-centred values (indices clamped at the faces).  view.trilinear = 2
+ *     is the radial view of an observer-centred spherical tensor (Sec. 2.2)
+ *     stored [r][b][l] as [z][y][x]: pixel (x, y) = (l, b), the ray runs
+ *     from the far end r = nz - 1 (background) to the observer at r = 0, one
+ *     sample per cell with step cell_cm = the radial spacing.
  *
  * All entry points are asynchronous on the given CUDA stream (NULL = legacy
  * default stream) and never throw.  A status other than IRT_OK means that no
@@ -152,9 +156,10 @@ typedef struct {
 
 typedef struct {
   double theta_rad, phi_rad;
-  int npx, npy;        /* image size (z view: must equal nx, ny) */
+  int npx, npy;        /* image size (z and radial views: must equal nx, ny) */
   double pixel_cm;     /* pixel pitch (oblique views) */
-  int trilinear;       /* 0: z view (cell exact), 1: oblique trilinear view */
+  int trilinear;       /* 0: z view (cell exact), 1: oblique trilinear view,
+                          2: radial view of an [r][b][l] tensor (cell exact) */
 } irt_view;
 
 typedef struct {
@@ -266,7 +271,8 @@ irt_status irt_tuned_plan(const irt_job* jobs, int njobs, const irt_opts* opts, 
 
 /*
  * irt_adjoint_ppv - gradients of a scalar loss with respect to n_H2, T_gas
- * and v_los of every cell for one z-view job (Sec. 4.8 run in reverse), given
+ * and v_los of every cell for one z- or radial-view job (Sec. 4.8 run in
+ * reverse), given
  * the cotangents dLoss/d[T], d[C], d[D], d[L], d[B] (float cubes
  * [nchan][npy][npx], NULL = zero).  grad_* are float [nz][ny][nx], written
  * completely (overwritten, not accumulated).  The forward transfer state is
@@ -318,6 +324,141 @@ irt_status irt_forward_ppv_static(const irt_grid_desc* desc, const irt_fields* f
                                   const irt_cubes* out, const irt_line* line,
                                   const irt_dust* dust, const irt_opts* opts,
                                   void* cuda_stream);
+
+/*
+ * Non-LTE level populations by the optically thin (OT) level balance
+ * (Sec. 3.4-3.6) through a precomputed coefficient grid (Sec. 4.2, 4.3).
+ *
+ * irt_level_model describes the tracer molecule as a molecular data file
+ * does (Sec. 4.1): nlev levels (2..64) with energies E_i / k [K] and weights
+ * g_i; nrad radiative transitions (rad_up > rad_lo, Einstein A [1/s],
+ * frequency [Hz]); npartner collision partners (irt_partner kinds, at most
+ * 5), each with ncoll de-excitation transitions (coll_up > coll_lo, indices
+ * [partner][c]) and rate coefficients k_ul_cm3_s [partner][c][t] [cm^3/s]
+ * tabulated at coll_temp_k [partner][t] (ntemp ascending temperatures; linear
+ * interpolation in T, end values held beyond); the excitation rates follow
+ * by detailed balance at the gas temperature (Sec. 3.6).  t_rad_k is the
+ * blackbody background T-bar of the balance (0 = pure OT), ortho_para the
+ * ortho-/para-H2 ratio, x_he the He abundance per H nucleus.  Partner
+ * densities at total H density n_H and H2 abundance chi (H2 per H nucleus):
+ * H2 chi n_H, para/ortho H2 split by ortho_para, H (1 - 2 chi) n_H, He
+ * x_he n_H.  All arrays are host memory, read during the call.
+ *
+ * irt_ot_axes: the grid nodes, uniform in log10 n_H [cm^-3], in chi and in
+ * log10 T [K] (each axis >= 2 nodes; the paper's grid is 128 x 64 x 64).
+ */
+typedef enum {
+  IRT_PARTNER_H2 = 0, IRT_PARTNER_PH2 = 1, IRT_PARTNER_OH2 = 2, IRT_PARTNER_H = 3,
+  IRT_PARTNER_HE = 4
+} irt_partner;
+
+typedef struct {
+  int nlev;
+  const double* energy_k;
+  const double* g;
+  int nrad;
+  const int* rad_up;
+  const int* rad_lo;
+  const double* a_ul_s;
+  const double* nu_hz;
+  int npartner;
+  const int* partner;
+  int ntemp;
+  const double* coll_temp_k;
+  int ncoll;
+  const int* coll_up;
+  const int* coll_lo;
+  const double* k_ul_cm3_s;
+  double t_rad_k;
+  double ortho_para;
+  double x_he;
+} irt_level_model;
+
+typedef struct {
+  int n_n, n_chi, n_t;
+  double log10_nh_min, log10_nh_max;
+  double chi_min, chi_max;
+  double log10_t_min, log10_t_max;
+} irt_ot_axes;
+
+typedef struct irt_ot_table irt_ot_table;   /* opaque */
+
+/*
+ * irt_create_ot_table - solve the OT level system at every grid node (one
+ * FP64 solve per node on the device, Sec. 4.2) and keep, for each of the
+ * nlines (1..8) radiative transitions lines[] of the model, the
+ * frequency-integrated line emission and absorption coefficients per tracer
+ * molecule, j = (h nu / 4 pi) A f_u and alpha = (h nu / 4 pi)(f_l B_lu -
+ * f_u B_ul) (Sec. 3.3, 3.6).  Asynchronous on cuda_stream (the model is
+ * copied before the call returns).  IRT_EINVAL for NULL arguments, level or
+ * transition indices out of range, non-positive weights, frequencies, A or
+ * temperatures, negative rates, unknown partners, axes with fewer than 2
+ * nodes or empty ranges, chi outside [0, 0.5]; IRT_EUNSUPPORTED beyond 64
+ * levels, 5 partners or 8 lines; IRT_ENOMEM.
+ */
+irt_status irt_create_ot_table(const irt_level_model* model, const irt_ot_axes* axes,
+                               const int* lines, int nlines, void* cuda_stream,
+                               irt_ot_table** out);
+
+/* irt_ot_table_values - copy the grid to host memory, synchronously:
+ * out[nlines][n_n][n_chi][n_t][2] = (j, alpha) per tracer molecule [cgs]. */
+irt_status irt_ot_table_values(const irt_ot_table* table, double* out);
+
+/* irt_destroy_ot_table - free a grid (NULL is a no-op); no launch may still
+ * use it. */
+irt_status irt_destroy_ot_table(irt_ot_table* table);
+
+/*
+ * irt_grid_set_h2_fraction - the H2 abundance chi (H2 molecules per H
+ * nucleus, device array [z][y][x] of dtype IRT_F32/F16/BF16/F64) of every
+ * cell, kept in the grid beside the five fields (in the grid's storage
+ * precision, fp16 for 16-bit grids).  Used only by irt_forward_ppv_ot; a grid
+ * whose abundance was never set is fully molecular (chi = 0.5).  Asynchronous
+ * on cuda_stream.  IRT_EINVAL for NULL arguments or an unknown dtype.
+ */
+irt_status irt_grid_set_h2_fraction(irt_grid* grid, const void* chi, int dtype,
+                                    void* cuda_stream);
+
+/*
+ * irt_forward_ppv_ot - irt_forward_ppv with the line coefficients of the OT
+ * level balance: each sample looks up line line_index of the grid at
+ * (log10 n_H, chi, log10 T) by trilinear interpolation, the cell index
+ * clamped to the grid so that beyond its bounds the edge cell continues
+ * linearly (Sec. 4.2), with n_H = n_H2 / chi, and multiplies by the tracer
+ * density x n_H2 (Sec. 4.3).  line supplies the profile (mass, sigma_turb),
+ * T_inf and the frequency, which must equal the grid line's to 1e-12
+ * relative; its a_ul_s, e_u_k, b0_hz, g_u and g_l are not used.  A sample with
+ * n_H2, chi or x not positive, or T outside (0, T_inf], has no line.  Modes,
+ * precisions, units and errors as irt_forward_ppv; IRT_EINVAL for a NULL
+ * table, a line index out of range or a frequency mismatch;
+ * IRT_EUNSUPPORTED for IRT_FLAG_SAVE_CHECKPOINTS (the adjoint takes LTE
+ * populations only).
+ */
+irt_status irt_forward_ppv_ot(const irt_job* jobs, int njobs, const irt_ot_table* table,
+                              int line_index, const irt_line* line, const irt_dust* dust,
+                              const irt_opts* opts, void* cuda_stream);
+
+/*
+ * irt_forward_ppv_lines - render nlines (1..4) spectral lines of one job in
+ * one persistent launch (Sec. 4.1: one or several lines; Sec. 3.2: each line
+ * with its own dust opacity): line q takes its constants lines[q], its dust
+ * dusts[q] and writes the cubes outs[q] (job->out is not used).  Each ray's
+ * field samples are taken once (cell loads, trilinear blends) and kept for
+ * the ray's other lines; the per-sample physics, the transfer and the
+ * epilogue run per line.  With table != NULL the lines take their
+ * coefficients from the OT grid, line q from grid line table_lines[q] (as
+ * irt_forward_ppv_ot).  Each line's cubes equal those of a single-line
+ * irt_forward_ppv (or irt_forward_ppv_ot) call with the same arguments.
+ * Thick mode, float precision, float or 16-bit storage; units as
+ * irt_forward_ppv (T_B by a conversion pass per line).  IRT_EINVAL as
+ * irt_forward_ppv per line, and for a NULL table_lines or a frequency
+ * mismatch with the table; IRT_EUNSUPPORTED for other modes, precisions or
+ * storage, more than 4 lines or IRT_FLAG_SAVE_CHECKPOINTS.
+ */
+irt_status irt_forward_ppv_lines(const irt_job* job, int nlines, const irt_line* lines,
+                                 const irt_dust* dusts, const irt_cubes* outs,
+                                 const irt_ot_table* table, const int* table_lines,
+                                 const irt_opts* opts, void* cuda_stream);
 
 /* irt_destroy - free the grid and everything it owns (NULL is a no-op).  The
  * caller must make sure no launch using the grid is still running. */

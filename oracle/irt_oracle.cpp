@@ -813,16 +813,20 @@ double trilinear(const Grid& g, int q, const double r[3]) { return trilinear_fie
 void ray_samples(const Grid& g, const ViewP& v, int px, int py,
                  std::vector<Sample<double>>* smp, double* h) {
   smp->clear();
-  if (!v.trilinear) {
+  if (v.trilinear == 0 || v.trilinear == 2) {
+    // z view: cells k = 0 .. nz-1 of the column; radial view of an
+    // observer-centred [r][b][l] tensor (Sec. 2.2): the column read from the
+    // far end of the radial axis (r = nz-1) to the observer (r = 0)
     *h = g.dx;
     for (int k = 0; k < g.nz; ++k) {
+      const int z = (v.trilinear == 2) ? g.nz - 1 - k : k;
       Sample<double> s;
-      s.n_h2 = g.at(0, px, py, k);
-      s.t_gas = g.at(1, px, py, k);
-      s.t_dust = g.at(2, px, py, k);
-      s.v_los = g.at(3, px, py, k);
-      s.x_tr = g.at(4, px, py, k);
-      if (g.chi) s.chi = g.at_field(g.chi, px, py, k);
+      s.n_h2 = g.at(0, px, py, z);
+      s.t_gas = g.at(1, px, py, z);
+      s.t_dust = g.at(2, px, py, z);
+      s.v_los = g.at(3, px, py, z);
+      s.x_tr = g.at(4, px, py, z);
+      if (g.chi) s.chi = g.at_field(g.chi, px, py, z);
       smp->push_back(s);
     }
     return;

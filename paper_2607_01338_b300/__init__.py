@@ -12,8 +12,9 @@ import importlib
 
 _BINDING = ("irt_create_grid", "irt_forward_ppv", "irt_adjoint_ppv", "irt_destroy",
             "irt_grid_stats", "irt_launch_count", "IrtError", "LIB_PATH")
-_API = ("COMPONENTS", "Grid", "RenderConfig", "RenderPPV", "ForwardGraph", "adjoint",
-        "alloc_cubes", "beam_convolve", "forward", "forward_batch", "latitude_mean",
+_API = ("COMPONENTS", "Grid", "LevelTable", "RenderConfig", "RenderPPV", "ForwardGraph", "adjoint",
+        "alloc_cubes", "beam_convolve", "forward", "forward_batch", "forward_lines",
+        "latitude_mean",
         "render_ppv")
 
 __all__ = list(_BINDING + _API)

@@ -55,12 +55,76 @@ class Grid:
         self.cell_cm = float(cell_cm)
         self.dtypes = tuple(t.dtype for t in ts)
 
+    def set_h2_fraction(self, chi: torch.Tensor, stream=None):
+        """H2 abundance per H nucleus of every cell ([nz, ny, nx] CUDA tensor),
+        read by the optically thin level balance (``irt_grid_set_h2_fraction``;
+        default 0.5, fully molecular)."""
+        if not chi.is_cuda or tuple(chi.shape) != self.shape or chi.dtype not in _DTYPE:
+            raise ValueError("chi must be a CUDA tensor of the grid's shape")
+        chi = chi.contiguous()
+        B.irt_grid_set_h2_fraction(self.handle, chi.data_ptr(), _DTYPE[chi.dtype],
+                                   _stream_ptr(stream))
+        self._chi = chi   # read on the stream
+
     def close(self):
         if getattr(self, "handle", None):
             torch.cuda.synchronize()
             B.irt_destroy(self.handle)
             self.handle = None
             self._keep = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class LevelTable:
+    """Optically thin level-balance grid (``irt_create_ot_table``, Sec. 4.2)
+    of the radiative transitions ``lines`` of a level model (a dict of
+    arrays: nlev, energy_k, g, rad_up, rad_lo, a_ul_s, nu_hz, partner,
+    coll_temp_k [partner, t], coll_up / coll_lo [partner, c], k_ul_cm3_s
+    [partner, c, t], t_rad_k, ortho_para, x_he) on the grid ``axes`` (n_n,
+    n_chi, n_t and the log10 n_H, chi, log10 T ranges)."""
+
+    def __init__(self, model: dict, axes: dict, lines, stream=None):
+        import numpy as np
+        d = lambda k: np.ascontiguousarray(np.asarray(model[k], dtype=np.float64))  # noqa: E731
+        i = lambda k: np.ascontiguousarray(np.asarray(model[k], dtype=np.int32))    # noqa: E731
+        keep = dict(energy_k=d("energy_k"), g=d("g"), rad_up=i("rad_up"), rad_lo=i("rad_lo"),
+                    a=d("a_ul_s"), nu=d("nu_hz"), partner=i("partner"),
+                    ct=d("coll_temp_k"), cu=i("coll_up"), cl=i("coll_lo"), k=d("k_ul_cm3_s"))
+        dp = lambda a: a.ctypes.data_as(B._DP)   # noqa: E731
+        ip = lambda a: a.ctypes.data_as(B._IP)   # noqa: E731
+        m = B.irt_level_model(int(model["nlev"]), dp(keep["energy_k"]), dp(keep["g"]),
+                              len(keep["rad_up"]), ip(keep["rad_up"]), ip(keep["rad_lo"]),
+                              dp(keep["a"]), dp(keep["nu"]), len(keep["partner"]),
+                              ip(keep["partner"]), int(keep["ct"].shape[-1]), dp(keep["ct"]),
+                              int(keep["cu"].shape[-1]), ip(keep["cu"]), ip(keep["cl"]),
+                              dp(keep["k"]), float(model["t_rad_k"]),
+                              float(model["ortho_para"]), float(model["x_he"]))
+        ax = B.irt_ot_axes(int(axes["n_n"]), int(axes["n_chi"]), int(axes["n_t"]),
+                           float(axes["log10_nh_min"]), float(axes["log10_nh_max"]),
+                           float(axes["chi_min"]), float(axes["chi_max"]),
+                           float(axes["log10_t_min"]), float(axes["log10_t_max"]))
+        self.shape = (len(lines), int(axes["n_n"]), int(axes["n_chi"]), int(axes["n_t"]), 2)
+        self.nu_hz = [float(model["nu_hz"][q]) for q in lines]
+        self.handle = B.irt_create_ot_table(m, ax, list(lines), _stream_ptr(stream))
+
+    def values(self):
+        """The grid, [nlines, n_n, n_chi, n_t, 2] float64 numpy array of (j,
+        alpha) per tracer molecule [cgs] (synchronous)."""
+        import numpy as np
+        out = np.zeros(self.shape)
+        B.irt_ot_table_values(self.handle, out.ctypes.data)
+        return out
+
+    def close(self):
+        if getattr(self, "handle", None):
+            torch.cuda.synchronize()
+            B.irt_destroy_ot_table(self.handle)
+            self.handle = None
 
     def __del__(self):
         try:
@@ -111,18 +175,44 @@ def make_job(grid: Grid, view, vaxis, cubes: dict) -> B.irt_job:
 
 def forward(grid: Grid, view, vaxis, line: dict, dust: dict, *, integration="smooth",
             units="trj", t_bg=2.725, precision="f32", flags=0, out=None, stream=None,
-            components=COMPONENTS, transfer="thick") -> dict:
+            components=COMPONENTS, transfer="thick", levels: LevelTable = None,
+            line_index: int = 0) -> dict:
     """Render one job (``irt_forward_ppv`` with njobs = 1).  Returns the cubes
     {"T","C","D","L","B"} as [nchan, npy, npx] tensors.  ``transfer`` is
     "thick", "selectively_thin", "thin" (Sec. 4.5-4.7) or "density_tracing"
-    (Sec. 5.10: the column density per unit velocity in "T" and "L")."""
+    (Sec. 5.10: the column density per unit velocity in "T" and "L").
+    ``levels``: a LevelTable whose line ``line_index`` gives the level
+    populations (optically thin balance, ``irt_forward_ppv_ot``) instead of
+    LTE."""
     cubes = out if out is not None else alloc_cubes(view, vaxis, precision,
                                                      components=components)
     job = make_job(grid, view, vaxis, cubes)
-    B.irt_forward_ppv([job], line_struct(line), dust_struct(dust),
-                      opts_struct(integration, units, t_bg, precision, flags, transfer),
-                      _stream_ptr(stream))
+    opts = opts_struct(integration, units, t_bg, precision, flags, transfer)
+    if levels is not None:
+        B.irt_forward_ppv_ot([job], levels.handle, line_index, line_struct(line),
+                             dust_struct(dust), opts, _stream_ptr(stream))
+    else:
+        B.irt_forward_ppv([job], line_struct(line), dust_struct(dust), opts, _stream_ptr(stream))
     return cubes
+
+
+def forward_lines(grid: Grid, view, vaxis, lines, dusts, *, integration="smooth", units="trj",
+                  t_bg=2.725, flags=0, outs=None, stream=None, levels: LevelTable = None,
+                  line_indices=None) -> list:
+    """Render several lines of one job in one launch (``irt_forward_ppv_lines``):
+    ``lines`` and ``dusts`` are sequences of line and dust dicts (one dust
+    per line: its own opacity); returns one cube dict per line.  With
+    ``levels`` (a LevelTable) line q takes grid line ``line_indices[q]``."""
+    if outs is None:
+        outs = [alloc_cubes(view, vaxis) for _ in lines]
+    job = make_job(grid, view, vaxis, {k: None for k in COMPONENTS})
+    B.irt_forward_ppv_lines(job, [line_struct(x) for x in lines], [dust_struct(d) for d in dusts],
+                            [_cubes_struct(o) for o in outs],
+                            None if levels is None else levels.handle,
+                            None if levels is None else list(line_indices),
+                            opts_struct(integration, units, t_bg, "f32", flags),
+                            _stream_ptr(stream))
+    return outs
 
 
 def latitude_mean(x: torch.Tensor, stream=None) -> torch.Tensor:

@@ -35,7 +35,10 @@ EXPORTED = ("irt_create_grid", "irt_forward_ppv", "irt_adjoint_ppv", "irt_destro
             "irt_grid_stats", "irt_forward_ppv_static", "irt_forward_graph_create",
             "irt_forward_graph_launch", "irt_forward_graph_destroy", "irt_tuned_plan",
             "irt_last_error", "irt_launch_count", "irt_measure_pipe_peaks", "irt_mean_axis1",
-            "irt_beam_convolve")
+            "irt_beam_convolve", "irt_create_ot_table", "irt_ot_table_values",
+            "irt_destroy_ot_table", "irt_grid_set_h2_fraction", "irt_forward_ppv_ot",
+            "irt_forward_ppv_lines")
+IRT_PARTNER_H2, IRT_PARTNER_PH2, IRT_PARTNER_OH2, IRT_PARTNER_H, IRT_PARTNER_HE = range(5)
 
 
 class irt_grid_desc(ctypes.Structure):
@@ -85,6 +88,26 @@ class irt_cubes(ctypes.Structure):
 class irt_job(ctypes.Structure):
     _fields_ = [("grid", ctypes.c_void_p), ("view", irt_view), ("vaxis", irt_vaxis),
                 ("out", irt_cubes)]
+
+
+_DP = ctypes.POINTER(ctypes.c_double)
+_IP = ctypes.POINTER(ctypes.c_int)
+
+
+class irt_level_model(ctypes.Structure):
+    _fields_ = [("nlev", ctypes.c_int), ("energy_k", _DP), ("g", _DP), ("nrad", ctypes.c_int),
+                ("rad_up", _IP), ("rad_lo", _IP), ("a_ul_s", _DP), ("nu_hz", _DP),
+                ("npartner", ctypes.c_int), ("partner", _IP), ("ntemp", ctypes.c_int),
+                ("coll_temp_k", _DP), ("ncoll", ctypes.c_int), ("coll_up", _IP),
+                ("coll_lo", _IP), ("k_ul_cm3_s", _DP), ("t_rad_k", ctypes.c_double),
+                ("ortho_para", ctypes.c_double), ("x_he", ctypes.c_double)]
+
+
+class irt_ot_axes(ctypes.Structure):
+    _fields_ = [("n_n", ctypes.c_int), ("n_chi", ctypes.c_int), ("n_t", ctypes.c_int),
+                ("log10_nh_min", ctypes.c_double), ("log10_nh_max", ctypes.c_double),
+                ("chi_min", ctypes.c_double), ("chi_max", ctypes.c_double),
+                ("log10_t_min", ctypes.c_double), ("log10_t_max", ctypes.c_double)]
 
 
 class IrtError(RuntimeError):
@@ -140,6 +163,23 @@ def _load():
     L.irt_last_error.argtypes = []
     L.irt_launch_count.restype = ctypes.c_longlong
     L.irt_launch_count.argtypes = []
+    L.irt_create_ot_table.restype = ctypes.c_int
+    L.irt_create_ot_table.argtypes = [P(irt_level_model), P(irt_ot_axes), _IP, ctypes.c_int,
+                                      ctypes.c_void_p, P(ctypes.c_void_p)]
+    L.irt_ot_table_values.restype = ctypes.c_int
+    L.irt_ot_table_values.argtypes = [ctypes.c_void_p, _DP]
+    L.irt_destroy_ot_table.restype = ctypes.c_int
+    L.irt_destroy_ot_table.argtypes = [ctypes.c_void_p]
+    L.irt_grid_set_h2_fraction.restype = ctypes.c_int
+    L.irt_grid_set_h2_fraction.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                                           ctypes.c_void_p]
+    L.irt_forward_ppv_lines.restype = ctypes.c_int
+    L.irt_forward_ppv_lines.argtypes = [P(irt_job), ctypes.c_int, P(irt_line), P(irt_dust),
+                                        P(irt_cubes), ctypes.c_void_p, _IP, P(irt_opts),
+                                        ctypes.c_void_p]
+    L.irt_forward_ppv_ot.restype = ctypes.c_int
+    L.irt_forward_ppv_ot.argtypes = [P(irt_job), ctypes.c_int, ctypes.c_void_p, ctypes.c_int,
+                                     P(irt_line), P(irt_dust), P(irt_opts), ctypes.c_void_p]
     return L
 
 
@@ -243,3 +283,49 @@ def irt_measure_pipe_peaks(stream: int = 0) -> dict:
     a, b = ctypes.c_double(), ctypes.c_double()
     _check(lib.irt_measure_pipe_peaks(ctypes.byref(a), ctypes.byref(b), ctypes.c_void_p(stream)))
     return {"fp32_ops_per_s": a.value, "mufu_ops_per_s": b.value}
+
+
+def irt_create_ot_table(model: irt_level_model, axes: irt_ot_axes, lines, stream: int) -> int:
+    """Optically thin level-balance grid of the model's radiative transitions
+    ``lines`` (Sec. 4.2); returns the table handle."""
+    arr = (ctypes.c_int * len(lines))(*[int(x) for x in lines])
+    h = ctypes.c_void_p()
+    _check(lib.irt_create_ot_table(ctypes.byref(model), ctypes.byref(axes), arr, len(lines),
+                                   ctypes.c_void_p(stream), ctypes.byref(h)))
+    return h.value
+
+
+def irt_ot_table_values(handle: int, out_ptr: int) -> None:
+    _check(lib.irt_ot_table_values(ctypes.c_void_p(handle), ctypes.cast(out_ptr, _DP)))
+
+
+def irt_destroy_ot_table(handle: int) -> None:
+    _check(lib.irt_destroy_ot_table(ctypes.c_void_p(handle)))
+
+
+def irt_grid_set_h2_fraction(grid: int, chi: int, dtype: int, stream: int) -> None:
+    _check(lib.irt_grid_set_h2_fraction(ctypes.c_void_p(grid), ctypes.c_void_p(chi), dtype,
+                                        ctypes.c_void_p(stream)))
+
+
+def irt_forward_ppv_ot(jobs, table: int, line_index: int, line: irt_line, dust: irt_dust,
+                       opts: irt_opts, stream: int) -> None:
+    arr = (irt_job * len(jobs))(*jobs)
+    _check(lib.irt_forward_ppv_ot(arr, len(jobs), ctypes.c_void_p(table), int(line_index),
+                                  ctypes.byref(line), ctypes.byref(dust), ctypes.byref(opts),
+                                  ctypes.c_void_p(stream)))
+
+
+def irt_forward_ppv_lines(job: irt_job, lines, dusts, outs, table, table_lines,
+                          opts: irt_opts, stream: int) -> None:
+    """Several lines of one job in one launch (``lines``, ``dusts``,
+    ``outs``: sequences of irt_line, irt_dust, irt_cubes); ``table`` an OT
+    table handle or None with ``table_lines`` its line indices."""
+    n = len(lines)
+    la = (irt_line * n)(*lines)
+    da = (irt_dust * n)(*dusts)
+    oa = (irt_cubes * n)(*outs)
+    ta = None if table_lines is None else (ctypes.c_int * n)(*[int(x) for x in table_lines])
+    _check(lib.irt_forward_ppv_lines(ctypes.byref(job), n, la, da, oa,
+                                     ctypes.c_void_p(table) if table else None, ta,
+                                     ctypes.byref(opts), ctypes.c_void_p(stream)))

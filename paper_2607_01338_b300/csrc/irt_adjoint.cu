@@ -380,6 +380,7 @@ struct AdjRayArgs {
   float* grad[3];          // n_H2, T_gas, v_los
   int ck_nb;               // rows of a saved checkpoint
   int npx, nx, ny;         // image width, grid extent in x and y
+  int nz, zrev;            // grid extent in z; radial view: sample n is cell nz - 1 - n
   float cad_h;             // cad * cell size: d(h alpha_D) / d n_H2
   float T0, inv_c_kms, t_bg;   // background Planck function (K units)
 };
@@ -524,7 +525,8 @@ __device__ __noinline__ void adj_ray(const AdjRayArgs* __restrict__ Ap, const Re
           const float gvv = g5[3 * kPStride], gb = g5[4 * kPStride];
           const float gn = fmaf(gjl, cf[0], fmaf(gal, cf[1], gad * A.cad_h));
           const float gt = fmaf(gjl, cf[2], fmaf(gal, cf[3], gb * cf[4]));
-          const long long idx = ((long long)n * A.ny + py) * A.nx + px;
+          const int zc = A.zrev ? A.nz - 1 - n : n;
+          const long long idx = ((long long)zc * A.ny + py) * A.nx + px;
           A.grad[0][idx] = gn;
           A.grad[1][idx] = gt;
           A.grad[2][idx] = gvv;
@@ -620,6 +622,8 @@ adj_kernel(const __grid_constant__ JobTable tab, const PhysF PF, const AdjArgs A
     RA->npx = J.npx;
     RA->nx = J.nx;
     RA->ny = J.ny;
+    RA->nz = J.nz;
+    RA->zrev = J.zrev;
     RA->cad_h = PF.cad * (float)J.dx;
     RA->T0 = PF.T0;
     RA->inv_c_kms = PF.inv_c_kms;
@@ -654,9 +658,10 @@ adj_kernel(const __grid_constant__ JobTable tab, const PhysF PF, const AdjArgs A
     for (int k0 = 0; k0 < K; k0 += 32) {
       const int k = k0 + lane;
       if (k < K) {
-        float raw[5];
+        float raw[6];
         sample_raw<ST>(J, rp, px, py, k, raw);
-        const float ad = make_record<M_SMOOTH>(PF, raw, h, G, nfw, &rec[k]);
+        raw[5] = 0.5f;   // H2 abundance: unused (the adjoint takes LTE populations)
+        const float ad = make_record<M_SMOOTH, false>(PF, raw, h, G, nfw, &rec[k]);
         float bk0, bk1;
         dust_source_lin(PF, raw[2], &bk0, &bk1);
         rec[k].pad[0] = 2.0f * bk0;
@@ -747,7 +752,7 @@ adj_kernel(const __grid_constant__ JobTable tab, const PhysF PF, const AdjArgs A
       // is outside what this kernel integrates (NaN marks it)
       const float val = (K <= 1) ? 0.0f : __int_as_float(0x7fc00000);
       for (int k = lane; k < K; k += 32) {
-        const long long idx = ((long long)k * J.ny + py) * J.nx + px;
+        const long long idx = ((long long)zcell(J, k) * J.ny + py) * J.nx + px;
         A.grad[0][idx] = val;
         A.grad[1][idx] = val;
         A.grad[2][idx] = val;

@@ -45,6 +45,24 @@ int launch_adjoint(int store, int ni, const JobTable& tab, const PhysF& PF, cons
 int adjoint_blocks_per_sm(int store, int ni, size_t smem);
 int dispatch_fwd_f64(int mode, int store, int ni, const JobTable& jobs, int njobs,
                      const PhysParams& P, const PhysF& PF, const FwdLaunch& L, cudaStream_t s);
+int dispatch_fwd_ml_smooth(int store, int ni, const JobTable& jobs, int njobs,
+                           const PhysParams& P, const PhysF& PF, const FwdLaunch& L,
+                           cudaStream_t s);
+int dispatch_fwd_ml_formal(int store, int ni, const JobTable& jobs, int njobs,
+                           const PhysParams& P, const PhysF& PF, const FwdLaunch& L,
+                           cudaStream_t s);
+int dispatch_fwd_ml_kahan(int store, int ni, const JobTable& jobs, int njobs,
+                          const PhysParams& P, const PhysF& PF, const FwdLaunch& L,
+                          cudaStream_t s);
+int dispatch_fwd_ot_smooth(int precision, int store, int ni, const JobTable& jobs, int njobs,
+                           const PhysParams& P, const PhysF& PF, const FwdLaunch& L,
+                           cudaStream_t s);
+int dispatch_fwd_ot_formal(int precision, int store, int ni, const JobTable& jobs, int njobs,
+                           const PhysParams& P, const PhysF& PF, const FwdLaunch& L,
+                           cudaStream_t s);
+int dispatch_fwd_ot_kahan(int precision, int store, int ni, const JobTable& jobs, int njobs,
+                          const PhysParams& P, const PhysF& PF, const FwdLaunch& L,
+                          cudaStream_t s);
 
 namespace {
 
@@ -249,6 +267,7 @@ irt_status check_line(const irt_line* ln, const irt_dust* du, const irt_opts* op
 
 PhysParams fold_constants(const irt_line* ln, const irt_dust* du, const irt_opts* op) {
   PhysParams P;
+  std::memset(&P, 0, sizeof P);   // no padding bytes of unknown value (the struct is hashed)
   const double nu = ln->nu_ul_hz;
   P.T0 = kH * nu / kK;
   P.e_u = ln->e_u_k;
@@ -273,6 +292,7 @@ PhysParams fold_constants(const irt_line* ln, const irt_dust* du, const irt_opts
 
 PhysF to_float(const PhysParams& P) {
   PhysF F;
+  std::memset(&F, 0, sizeof F);
   F.T0 = (float)P.T0;
   F.e_u = (float)P.e_u;
   F.e_l = (float)P.e_l;
@@ -306,19 +326,19 @@ irt_status check_job(const irt_job& jb, int precision) {
       return fail(IRT_EUNSUPPORTED, "%lld fine velocities (2 f nchan + 1) exceed 32000", nfw);
   }
   const irt_view& vw = jb.view;
-  if (vw.trilinear == 0) {
+  if (vw.trilinear == 0 || vw.trilinear == 2) {
     if (vw.theta_rad != 0.0 || vw.phi_rad != 0.0)
-      return fail(IRT_EINVAL, "z view (trilinear = 0) needs theta = phi = 0");
+      return fail(IRT_EINVAL, "z and radial views (trilinear = 0, 2) need theta = phi = 0");
     if (vw.npx != g->nx || vw.npy != g->ny)
-      return fail(IRT_EINVAL, "z view image %d x %d differs from grid %d x %d", vw.npx, vw.npy,
-                  g->nx, g->ny);
+      return fail(IRT_EINVAL, "z or radial view image %d x %d differs from grid %d x %d", vw.npx,
+                  vw.npy, g->nx, g->ny);
   } else if (vw.trilinear == 1) {
     if (vw.npx < 1 || vw.npy < 1) return fail(IRT_EINVAL, "view npx/npy < 1");
     if (!finite_pos(vw.pixel_cm)) return fail(IRT_EINVAL, "view pixel_cm must be > 0");
     if (!std::isfinite(vw.theta_rad) || !std::isfinite(vw.phi_rad))
       return fail(IRT_EINVAL, "view angles not finite");
   } else {
-    return fail(IRT_EINVAL, "view.trilinear must be 0 or 1");
+    return fail(IRT_EINVAL, "view.trilinear must be 0 (z), 1 (oblique) or 2 (radial)");
   }
   const void* o[5] = {jb.out.T, jb.out.C, jb.out.D, jb.out.L, jb.out.B};
   bool any = false;
@@ -363,7 +383,7 @@ Plan plan_job(const irt_job& jb, int precision, int force_ni) {
   p.nwin = (nch + p.cw - 1) / p.cw;
   p.nfw = fine_of(p.cw);
   const irt_grid* g = jb.grid;
-  if (jb.view.trilinear == 0) {
+  if (jb.view.trilinear != 1) {   // z and radial views: one sample per cell
     p.kmax = g->nz;
   } else {
     const double diag = std::sqrt((double)g->nx * g->nx + (double)g->ny * g->ny +
@@ -385,7 +405,8 @@ JobDev make_jobdev(const irt_job& jb, const Plan& p) {
   for (int q = 0; q < 5; ++q) d.scale[q] = g->store == ST_H16 ? (float)g->scale[q] : 1.0f;
   d.nx = g->nx; d.ny = g->ny; d.nz = g->nz;
   d.dx = g->dx;
-  d.zview = jb.view.trilinear == 0;
+  d.zview = jb.view.trilinear == 0 || jb.view.trilinear == 2;
+  d.zrev = jb.view.trilinear == 2;
   d.theta = jb.view.theta_rad;
   d.phi = jb.view.phi_rad;
   {
@@ -433,6 +454,12 @@ JobDev make_jobdev(const irt_job& jb, const Plan& p) {
 
 int dispatch(int precision, int mode, int store, int ni, const JobTable& jobs, int njobs,
              const PhysParams& P, const PhysF& PF, const FwdLaunch& L, cudaStream_t s) {
+  if (P.ot_tab) {
+    // optically thin level balance: kernel instances of their own
+    if (mode == M_SMOOTH) return dispatch_fwd_ot_smooth(precision, store, ni, jobs, njobs, P, PF, L, s);
+    if (mode == M_FORMAL) return dispatch_fwd_ot_formal(precision, store, ni, jobs, njobs, P, PF, L, s);
+    return dispatch_fwd_ot_kahan(precision, store, ni, jobs, njobs, P, PF, L, s);
+  }
   if (precision == IRT_PREC_F64) return dispatch_fwd_f64(mode, store, ni, jobs, njobs, P, PF, L, s);
   if (mode == M_SMOOTH) return dispatch_fwd_f32_smooth(store, ni, jobs, njobs, P, PF, L, s);
   if (mode == M_FORMAL) return dispatch_fwd_f32_formal(store, ni, jobs, njobs, P, PF, L, s);
@@ -441,14 +468,16 @@ int dispatch(int precision, int mode, int store, int ni, const JobTable& jobs, i
 
 // Record scratch a forward launch over these plans wants: every warp that can
 // be resident on the device holds the records of its longest ray.
-size_t fwd_scratch_need(const std::vector<Plan>& plans, int precision) {
+size_t fwd_scratch_need(const std::vector<Plan>& plans, int precision, bool lines = false) {
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   int kmax = 1;
   for (const Plan& p : plans) kmax = std::max(kmax, p.kmax);
   const size_t rec = precision == IRT_PREC_F64 ? kRecBytesF64 : kRecBytesF32;
-  const size_t stride = ((size_t)kmax * rec + 255) & ~(size_t)255;
+  size_t stride = ((size_t)kmax * rec + 255) & ~(size_t)255;
+  // several lines in one launch also keep the ray's raw samples (6 floats)
+  if (lines) stride += ((size_t)kmax * 24 + 255) & ~(size_t)255;
   return (size_t)std::max(sms, 1) * kFwdWarpsPerSm * stride;
 }
 
@@ -687,6 +716,7 @@ irt_status run_forward(const irt_job* jobs, int njobs, const PhysParams& P, cons
     L.stats = (opts->flags & IRT_FLAG_STATS) ? jobs[0].grid->ctl + 1 : nullptr;
     L.rscr = sc.p;
     L.rbytes = sc.bytes;
+    L.lines = nullptr;
     if (L.queue) {
       const cudaError_t ce = cudaMemsetAsync(L.queue, 0, sizeof(unsigned long long), s);
       if (ce != cudaSuccess) return cuda_fail(ce, "irt_forward_ppv: queue reset");
@@ -794,10 +824,70 @@ irt_status autotune(const irt_job* jobs, int njobs, const PhysParams& P, const P
 }  // namespace
 }  // namespace irt
 
+struct irt_ot_table {
+  irt::OTTableDev t;
+};
+
+namespace irt {
+namespace {
+
+// The launch constants of the optically thin level balance: line q of the
+// grid (float pairs for the float kernels, cgs doubles for the double ones).
+void bind_ot(const OTTableDev& t, int q, PhysParams* P, PhysF* PF) {
+  const long long nodes = (long long)t.n[0] * t.n[1] * t.n[2];
+  P->ot_tab = t.tab64 + (size_t)q * nodes * 2;
+  PF->ot_tab = t.tab32 + (size_t)q * t.n[0] * t.n[1] * (t.n[2] - 1);
+  for (int a = 0; a < 3; ++a) {
+    P->ot_n[a] = PF->ot_n[a] = t.n[a];
+    P->ot_lo[a] = t.lo[a];
+    P->ot_s[a] = (t.n[a] - 1) / (t.hi[a] - t.lo[a]);
+    PF->ot_lo[a] = (float)P->ot_lo[a];
+    PF->ot_s[a] = (float)P->ot_s[a];
+  }
+  P->ot_jk = t.jk[q];
+  P->ot_ak = t.ak[q];
+}
+
+irt_status forward_entry(const irt_job* jobs, int njobs, const irt_line* line,
+                         const irt_dust* dust, const irt_opts* opts, void* cuda_stream,
+                         const irt_ot_table* ot, int ot_line);
+
+}  // namespace
+}  // namespace irt
+
 extern "C" irt_status irt_forward_ppv(const irt_job* jobs, int njobs, const irt_line* line,
                                       const irt_dust* dust, const irt_opts* opts,
                                       void* cuda_stream) {
   g_err.clear();
+  return forward_entry(jobs, njobs, line, dust, opts, cuda_stream, nullptr, 0);
+}
+
+extern "C" irt_status irt_forward_ppv_ot(const irt_job* jobs, int njobs,
+                                         const irt_ot_table* table, int line_index,
+                                         const irt_line* line, const irt_dust* dust,
+                                         const irt_opts* opts, void* cuda_stream) {
+  g_err.clear();
+  if (!table) return fail(IRT_EINVAL, "irt_forward_ppv_ot: NULL table");
+  if (line_index < 0 || line_index >= table->t.nlines)
+    return fail(IRT_EINVAL, "irt_forward_ppv_ot: line index %d outside the table's %d lines",
+                line_index, table->t.nlines);
+  if (!line) return fail(IRT_EINVAL, "irt_forward_ppv_ot: NULL line");
+  const double nu_t = table->t.nu[line_index];
+  if (!(std::fabs(line->nu_ul_hz - nu_t) <= 1e-12 * nu_t))
+    return fail(IRT_EINVAL, "irt_forward_ppv_ot: line frequency %.12g Hz differs from the "
+                            "table line's %.12g Hz", line->nu_ul_hz, nu_t);
+  if (opts && (opts->flags & IRT_FLAG_SAVE_CHECKPOINTS))
+    return fail(IRT_EUNSUPPORTED, "irt_forward_ppv_ot: no checkpoints (the adjoint takes LTE "
+                                  "populations only)");
+  return forward_entry(jobs, njobs, line, dust, opts, cuda_stream, table, line_index);
+}
+
+namespace irt {
+namespace {
+
+irt_status forward_entry(const irt_job* jobs, int njobs, const irt_line* line,
+                         const irt_dust* dust, const irt_opts* opts, void* cuda_stream,
+                         const irt_ot_table* ot, int ot_line) {
   if (!jobs || njobs < 1) return fail(IRT_EINVAL, "irt_forward_ppv: no jobs");
   irt_status st = check_line(line, dust, opts);
   if (st) return st;
@@ -806,17 +896,19 @@ extern "C" irt_status irt_forward_ppv(const irt_job* jobs, int njobs, const irt_
     if (st) return st;
   }
   if (opts->flags & IRT_FLAG_SAVE_CHECKPOINTS) {
-    if (njobs != 1 || jobs[0].view.trilinear != 0 || opts->integration != IRT_SMOOTH ||
+    if (njobs != 1 || jobs[0].view.trilinear == 1 || opts->integration != IRT_SMOOTH ||
         opts->precision != IRT_PREC_F32)
       return fail(IRT_EUNSUPPORTED, "irt_forward_ppv: IRT_FLAG_SAVE_CHECKPOINTS needs one "
-                                    "z-view job, smooth integration, float precision");
+                                    "z- or radial-view job, smooth integration, float precision");
   }
   cudaStream_t s = (cudaStream_t)cuda_stream;
   if (opts->mode != IRT_MODE_THICK) {
     if (opts->flags & IRT_FLAG_SAVE_CHECKPOINTS)
       return fail(IRT_EUNSUPPORTED, "irt_forward_ppv: checkpoints belong to the thick mode");
-    const PhysParams P = fold_constants(line, dust, opts);
-    return run_thin(jobs, njobs, P, to_float(P), opts, s);
+    PhysParams P = fold_constants(line, dust, opts);
+    PhysF PF = to_float(P);
+    if (ot) bind_ot(ot->t, ot_line, &P, &PF);
+    return run_thin(jobs, njobs, P, PF, opts, s);
   }
   // T_B output of the thick mode: rendered in T_RJ, then converted in place
   // by a separate pass (which needs the [T], [C] and [B] cubes)
@@ -829,8 +921,9 @@ extern "C" irt_status irt_forward_ppv(const irt_job* jobs, int njobs, const irt_
                                 "every job");
     o.units = IRT_UNITS_TRJ;
   }
-  const PhysParams P = fold_constants(line, dust, &o);
-  const PhysF PF = to_float(P);
+  PhysParams P = fold_constants(line, dust, &o);
+  PhysF PF = to_float(P);
+  if (ot) bind_ot(ot->t, ot_line, &P, &PF);
   Tuned tp;
   if (o.precision != IRT_PREC_F64) {
     const unsigned long long sig = job_signature(jobs, njobs, &o);
@@ -853,6 +946,319 @@ extern "C" irt_status irt_forward_ppv(const irt_job* jobs, int njobs, const irt_
     ++g_launches;
     if (e) return cuda_fail(e, "irt_forward_ppv: T_B conversion");
   }
+  return IRT_OK;
+}
+
+}  // namespace
+}  // namespace irt
+
+// ---------------------------------------------------------------------------
+// Several lines of one job in one launch (Sec. 4.1: one or several spectral
+// lines, each with its own dust opacity, Sec. 3.2)
+// ---------------------------------------------------------------------------
+extern "C" irt_status irt_forward_ppv_lines(const irt_job* job, int nlines,
+                                            const irt_line* lines, const irt_dust* dusts,
+                                            const irt_cubes* outs, const irt_ot_table* table,
+                                            const int* table_lines, const irt_opts* opts,
+                                            void* cuda_stream) {
+  g_err.clear();
+  if (!job || !lines || !dusts || !outs || !opts)
+    return fail(IRT_EINVAL, "irt_forward_ppv_lines: NULL argument");
+  if (nlines < 1) return fail(IRT_EINVAL, "irt_forward_ppv_lines: no lines");
+  if (nlines > kMaxLinesPerRender)
+    return fail(IRT_EUNSUPPORTED, "irt_forward_ppv_lines: %d lines (at most %d)", nlines,
+                kMaxLinesPerRender);
+  irt_status st = IRT_OK;
+  for (int q = 0; q < nlines; ++q) {
+    st = check_line(&lines[q], &dusts[q], opts);
+    if (st) return st;
+    irt_job jq = *job;
+    jq.out = outs[q];
+    st = check_job(jq, opts->precision);
+    if (st) return st;
+  }
+  if (opts->mode != IRT_MODE_THICK)
+    return fail(IRT_EUNSUPPORTED, "irt_forward_ppv_lines: optically thick mode only");
+  if (opts->precision != IRT_PREC_F32)
+    return fail(IRT_EUNSUPPORTED, "irt_forward_ppv_lines: float precision only");
+  if (job->grid->store == ST_F64)
+    return fail(IRT_EUNSUPPORTED, "irt_forward_ppv_lines: float or 16-bit field storage only");
+  if (opts->flags & IRT_FLAG_SAVE_CHECKPOINTS)
+    return fail(IRT_EUNSUPPORTED, "irt_forward_ppv_lines: no checkpoints");
+  if (table) {
+    if (!table_lines) return fail(IRT_EINVAL, "irt_forward_ppv_lines: NULL table line indices");
+    for (int q = 0; q < nlines; ++q) {
+      const int li = table_lines[q];
+      if (li < 0 || li >= table->t.nlines)
+        return fail(IRT_EINVAL, "irt_forward_ppv_lines: table line %d outside the table's %d",
+                    li, table->t.nlines);
+      const double nu_t = table->t.nu[li];
+      if (!(std::fabs(lines[q].nu_ul_hz - nu_t) <= 1e-12 * nu_t))
+        return fail(IRT_EINVAL, "irt_forward_ppv_lines: line %d frequency %.12g Hz differs from "
+                                "the table line's %.12g Hz", q, lines[q].nu_ul_hz, nu_t);
+    }
+  }
+  const bool tb = opts->units == IRT_UNITS_TB;
+  if (tb)
+    for (int q = 0; q < nlines; ++q)
+      if (!outs[q].T || !outs[q].C || !outs[q].B)
+        return fail(IRT_EINVAL, "irt_forward_ppv_lines: IRT_UNITS_TB needs the T, C and B cubes "
+                                "of every line");
+  irt_opts o = *opts;
+  if (tb) o.units = IRT_UNITS_TRJ;
+  LineSet ls;
+  std::memset(&ls, 0, sizeof ls);
+  ls.n = nlines;
+  PhysParams P0;
+  std::vector<PhysParams> Ps(nlines);
+  for (int q = 0; q < nlines; ++q) {
+    Ps[q] = fold_constants(&lines[q], &dusts[q], &o);
+    PhysF pf = to_float(Ps[q]);
+    if (table) bind_ot(table->t, table_lines[q], &Ps[q], &pf);
+    ls.pf[q] = pf;
+    ls.out[q][0] = outs[q].T; ls.out[q][1] = outs[q].C; ls.out[q][2] = outs[q].D;
+    ls.out[q][3] = outs[q].L; ls.out[q][4] = outs[q].B;
+  }
+  P0 = Ps[0];
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  irt_job jb = *job;
+  jb.out = outs[0];
+  Tuned tp;
+  forced_plan(&tp);
+  Plan p = plan_job(jb, IRT_PREC_F32, tp.ni > 0 ? tp.ni : 0);
+  p.tw = tp.tw;
+  p.th = tp.th;
+  JobTable tab;
+  std::memset(&tab, 0, sizeof tab);
+  tab.j[0] = make_jobdev(jb, p);
+  tab.j[0].item_begin = 0;
+  StreamScratch& ss = stream_scratch(s);
+  st = grow(&ss.fwd, &ss.fwd_bytes, fwd_scratch_need({p}, IRT_PREC_F32, true), s,
+            "irt_forward_ppv_lines");
+  if (st) return st;
+  FwdLaunch L;
+  L.total = tab.j[0].nitems;
+  L.queue = nullptr;
+  L.grid_blocks = 0;
+  L.kmax = p.kmax;
+  L.fwmax = 32 * p.ni;
+  L.cwmax = p.cw;
+  L.flags = o.flags;
+  L.stats = (o.flags & IRT_FLAG_STATS) ? jb.grid->ctl + 1 : nullptr;
+  L.rscr = ss.fwd;
+  L.rbytes = ss.fwd_bytes;
+  L.lines = &ls;
+  const int store = jb.grid->store;
+  int e;
+  if (o.integration == IRT_SMOOTH)
+    e = dispatch_fwd_ml_smooth(store, p.ni, tab, 1, P0, ls.pf[0], L, s);
+  else if (o.integration == IRT_FORMAL)
+    e = dispatch_fwd_ml_formal(store, p.ni, tab, 1, P0, ls.pf[0], L, s);
+  else
+    e = dispatch_fwd_ml_kahan(store, p.ni, tab, 1, P0, ls.pf[0], L, s);
+  ++g_launches;
+  if (e) return cuda_fail(e, "irt_forward_ppv_lines: forward kernel");
+  if (!tb) return IRT_OK;
+  for (int q = 0; q < nlines; ++q) {
+    e = launch_tb_convert(0, outs[q].T, outs[q].C, outs[q].B, outs[q].L, outs[q].D,
+                          (long long)jb.view.npx * jb.view.npy, jb.vaxis.nchan,
+                          jb.vaxis.v_first_edge_kms, jb.vaxis.dv_kms, Ps[q].T0, Ps[q].inv_c_kms,
+                          s);
+    ++g_launches;
+    if (e) return cuda_fail(e, "irt_forward_ppv_lines: T_B conversion");
+  }
+  return IRT_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Optically thin level-balance grids (Sec. 4.2) and the H2 abundance field
+// ---------------------------------------------------------------------------
+extern "C" irt_status irt_create_ot_table(const irt_level_model* m, const irt_ot_axes* ax,
+                                          const int* lines, int nlines, void* cuda_stream,
+                                          irt_ot_table** out) {
+  g_err.clear();
+  if (!m || !ax || !lines || !out) return fail(IRT_EINVAL, "irt_create_ot_table: NULL argument");
+  *out = nullptr;
+  if (m->nlev < 2) return fail(IRT_EINVAL, "irt_create_ot_table: %d levels (at least 2)", m->nlev);
+  if (m->nlev > kOTMaxLevels)
+    return fail(IRT_EUNSUPPORTED, "irt_create_ot_table: %d levels (at most %d)", m->nlev,
+                kOTMaxLevels);
+  if (nlines < 1) return fail(IRT_EINVAL, "irt_create_ot_table: no lines");
+  if (nlines > kOTMaxLines)
+    return fail(IRT_EUNSUPPORTED, "irt_create_ot_table: %d lines (at most %d)", nlines,
+                kOTMaxLines);
+  if (m->nrad < 1 || m->npartner < 0 || m->ntemp < 1 || m->ncoll < 0)
+    return fail(IRT_EINVAL, "irt_create_ot_table: transition or temperature counts");
+  if (m->npartner > 5)
+    return fail(IRT_EUNSUPPORTED, "irt_create_ot_table: %d partners (at most 5)", m->npartner);
+  if (!m->energy_k || !m->g || !m->rad_up || !m->rad_lo || !m->a_ul_s || !m->nu_hz ||
+      (m->npartner > 0 && m->ncoll > 0 &&
+       (!m->partner || !m->coll_temp_k || !m->coll_up || !m->coll_lo || !m->k_ul_cm3_s)))
+    return fail(IRT_EINVAL, "irt_create_ot_table: NULL model array");
+  const int n = m->nlev;
+  for (int i = 0; i < n; ++i)
+    if (!std::isfinite(m->energy_k[i]) || !finite_pos(m->g[i]))
+      return fail(IRT_EINVAL, "irt_create_ot_table: level %d energy or weight", i);
+  for (int r = 0; r < m->nrad; ++r) {
+    const int u = m->rad_up[r], l = m->rad_lo[r];
+    if (u < 0 || u >= n || l < 0 || l >= n || u <= l)
+      return fail(IRT_EINVAL, "irt_create_ot_table: radiative transition %d (%d -> %d)", r, u, l);
+    if (!finite_pos(m->a_ul_s[r]) || !finite_pos(m->nu_hz[r]))
+      return fail(IRT_EINVAL, "irt_create_ot_table: radiative transition %d: A or frequency", r);
+  }
+  const int np = m->npartner, nt = m->ntemp, nc = m->ncoll;
+  for (int p = 0; p < np && nc > 0; ++p) {
+    if (m->partner[p] < IRT_PARTNER_H2 || m->partner[p] > IRT_PARTNER_HE)
+      return fail(IRT_EINVAL, "irt_create_ot_table: partner %d kind %d", p, m->partner[p]);
+    for (int t = 0; t < nt; ++t) {
+      const double T = m->coll_temp_k[p * nt + t];
+      if (!finite_pos(T) || (t > 0 && !(T > m->coll_temp_k[p * nt + t - 1])))
+        return fail(IRT_EINVAL, "irt_create_ot_table: partner %d temperatures must be positive "
+                                "and ascending", p);
+    }
+    for (int c = 0; c < nc; ++c) {
+      const int u = m->coll_up[p * nc + c], l = m->coll_lo[p * nc + c];
+      if (u < 0 || u >= n || l < 0 || l >= n || u <= l)
+        return fail(IRT_EINVAL, "irt_create_ot_table: partner %d transition %d (%d -> %d)", p, c,
+                    u, l);
+      for (int t = 0; t < nt; ++t)
+        if (!finite_nonneg(m->k_ul_cm3_s[((size_t)p * nc + c) * nt + t]))
+          return fail(IRT_EINVAL, "irt_create_ot_table: negative or non-finite rate");
+    }
+  }
+  if (!finite_nonneg(m->t_rad_k) || !finite_nonneg(m->ortho_para) || !finite_nonneg(m->x_he))
+    return fail(IRT_EINVAL, "irt_create_ot_table: t_rad_k, ortho_para and x_he must be >= 0");
+  const int na[3] = {ax->n_n, ax->n_chi, ax->n_t};
+  const double lo[3] = {ax->log10_nh_min, ax->chi_min, ax->log10_t_min};
+  const double hi[3] = {ax->log10_nh_max, ax->chi_max, ax->log10_t_max};
+  for (int a = 0; a < 3; ++a)
+    if (na[a] < 2 || !std::isfinite(lo[a]) || !std::isfinite(hi[a]) || !(hi[a] > lo[a]))
+      return fail(IRT_EINVAL, "irt_create_ot_table: axis %d needs >= 2 nodes and hi > lo", a);
+  if (lo[1] < 0.0 || hi[1] > 0.5)
+    return fail(IRT_EINVAL, "irt_create_ot_table: chi axis outside [0, 0.5]");
+  for (int q = 0; q < nlines; ++q)
+    if (lines[q] < 0 || lines[q] >= m->nrad)
+      return fail(IRT_EINVAL, "irt_create_ot_table: line %d names transition %d of %d", q,
+                  lines[q], m->nrad);
+  const long long nodes = (long long)na[0] * na[1] * na[2];
+  if (nodes > (1ll << 26))
+    return fail(IRT_EUNSUPPORTED, "irt_create_ot_table: %lld nodes (at most 2^26)", nodes);
+
+  // the model in one device buffer: doubles first, then ints
+  std::vector<double> dv;
+  auto put_d = [&](const double* p, size_t cnt) {
+    const size_t off = dv.size();
+    dv.insert(dv.end(), p, p + cnt);
+    return off;
+  };
+  const size_t o_e = put_d(m->energy_k, n), o_g = put_d(m->g, n);
+  const size_t o_a = put_d(m->a_ul_s, m->nrad), o_nu = put_d(m->nu_hz, m->nrad);
+  const bool coll = np > 0 && nc > 0;
+  const size_t o_ct = coll ? put_d(m->coll_temp_k, (size_t)np * nt) : 0;
+  const size_t o_k = coll ? put_d(m->k_ul_cm3_s, (size_t)np * nc * nt) : 0;
+  std::vector<int> iv;
+  auto put_i = [&](const int* p, size_t cnt) {
+    const size_t off = iv.size();
+    iv.insert(iv.end(), p, p + cnt);
+    return off;
+  };
+  const size_t o_ru = put_i(m->rad_up, m->nrad), o_rl = put_i(m->rad_lo, m->nrad);
+  const size_t o_p = coll ? put_i(m->partner, np) : 0;
+  const size_t o_cu = coll ? put_i(m->coll_up, (size_t)np * nc) : 0;
+  const size_t o_cl = coll ? put_i(m->coll_lo, (size_t)np * nc) : 0;
+  const size_t o_ln = put_i(lines, nlines);
+  const size_t dbytes = dv.size() * sizeof(double), ibytes = iv.size() * sizeof(int);
+  const size_t tab64_bytes = (size_t)nlines * nodes * 2 * sizeof(double);
+  const size_t tab32_bytes = (size_t)nlines * na[0] * na[1] * (na[2] - 1) * sizeof(float4);
+  irt_ot_table* t = new irt_ot_table();
+  std::memset(&t->t, 0, sizeof t->t);
+  unsigned char* mbuf = nullptr;
+  if (dev_malloc((void**)&mbuf, dbytes + ibytes) != cudaSuccess ||
+      dev_malloc((void**)&t->t.tab64, tab64_bytes) != cudaSuccess ||
+      dev_malloc((void**)&t->t.tab32, tab32_bytes) != cudaSuccess) {
+    cudaGetLastError();
+    if (mbuf) cudaFree(mbuf);
+    if (t->t.tab64) cudaFree(t->t.tab64);
+    delete t;
+    return fail(IRT_ENOMEM, "irt_create_ot_table: cannot allocate %zu bytes",
+                dbytes + ibytes + tab64_bytes + tab32_bytes);
+  }
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  cudaError_t ce = cudaMemcpyAsync(mbuf, dv.data(), dbytes, cudaMemcpyHostToDevice, s);
+  if (ce == cudaSuccess)
+    ce = cudaMemcpyAsync(mbuf + dbytes, iv.data(), ibytes, cudaMemcpyHostToDevice, s);
+  OTBuildArgs A;
+  std::memset(&A, 0, sizeof A);
+  const double* dd = reinterpret_cast<const double*>(mbuf);
+  const int* di = reinterpret_cast<const int*>(mbuf + dbytes);
+  A.nlev = n; A.nrad = m->nrad; A.npartner = coll ? np : 0; A.ntemp = nt; A.ncoll = coll ? nc : 0;
+  A.nlines = nlines;
+  A.energy = dd + o_e; A.g = dd + o_g; A.a = dd + o_a; A.nu = dd + o_nu;
+  A.ctemp = dd + o_ct; A.k = dd + o_k;
+  A.rad_up = di + o_ru; A.rad_lo = di + o_rl; A.partner = di + o_p;
+  A.cup = di + o_cu; A.clo = di + o_cl; A.lines = di + o_ln;
+  A.t_rad = m->t_rad_k; A.opr = m->ortho_para; A.x_he = m->x_he;
+  t->t.nlines = nlines;
+  for (int a = 0; a < 3; ++a) {
+    A.n[a] = t->t.n[a] = na[a];
+    A.lo[a] = t->t.lo[a] = lo[a];
+    A.hi[a] = t->t.hi[a] = hi[a];
+  }
+  for (int q = 0; q < nlines; ++q) {
+    // cgs per molecule -> per-step K units: c^2 / (2 k nu^2) for intensities
+    // and the profile peak per Hz times b, c / (nu sqrt(pi))
+    const double nu = m->nu_hz[lines[q]];
+    const double per_hz = kCkms / nu / std::sqrt(kPi);
+    t->t.nu[q] = nu;
+    A.jk[q] = t->t.jk[q] = kC * kC / (2.0 * kK * nu * nu) * per_hz;
+    A.ak[q] = t->t.ak[q] = per_hz;
+  }
+  cudaGetDevice(&t->t.device);
+  int e = ce == cudaSuccess ? launch_ot_build(A, t->t.tab64, t->t.tab32, s) : (int)ce;
+  ++g_launches;
+  // the staging vectors must outlive the copies; the model buffer the build
+  if (e == 0) e = (int)cudaStreamSynchronize(s);
+  cudaFree(mbuf);
+  if (e) {
+    cudaFree(t->t.tab64);
+    cudaFree(t->t.tab32);
+    delete t;
+    return cuda_fail(e, "irt_create_ot_table: level-balance kernel");
+  }
+  *out = t;
+  return IRT_OK;
+}
+
+extern "C" irt_status irt_ot_table_values(const irt_ot_table* t, double* out) {
+  g_err.clear();
+  if (!t || !out) return fail(IRT_EINVAL, "irt_ot_table_values: NULL argument");
+  const size_t bytes =
+      (size_t)t->t.nlines * t->t.n[0] * t->t.n[1] * t->t.n[2] * 2 * sizeof(double);
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) e = cudaMemcpy(out, t->t.tab64, bytes, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(e, "irt_ot_table_values");
+  return IRT_OK;
+}
+
+extern "C" irt_status irt_destroy_ot_table(irt_ot_table* t) {
+  g_err.clear();
+  if (!t) return IRT_OK;
+  cudaFree(t->t.tab64);
+  cudaFree(t->t.tab32);
+  delete t;
+  return IRT_OK;
+}
+
+extern "C" irt_status irt_grid_set_h2_fraction(irt_grid* g, const void* chi, int dtype,
+                                               void* cuda_stream) {
+  g_err.clear();
+  if (!g || !chi) return fail(IRT_EINVAL, "irt_grid_set_h2_fraction: NULL argument");
+  if (dtype < IRT_F32 || dtype > IRT_F64)
+    return fail(IRT_EINVAL, "irt_grid_set_h2_fraction: unknown dtype %d", dtype);
+  const long long ncell = (long long)g->nx * g->ny * g->nz;
+  const int e = launch_set_chi(g->store, chi, dtype, g->cells, ncell, cuda_stream);
+  ++g_launches;
+  if (e) return cuda_fail(e, "irt_grid_set_h2_fraction");
   return IRT_OK;
 }
 
@@ -999,7 +1405,8 @@ extern "C" irt_status irt_adjoint_ppv(const irt_job* job, const irt_line* line,
     return fail(IRT_EUNSUPPORTED, "irt_adjoint_ppv: float precision only");
   if (opts->integration != IRT_SMOOTH)
     return fail(IRT_EUNSUPPORTED, "irt_adjoint_ppv: smooth integration only");
-  if (jb.view.trilinear != 0) return fail(IRT_EUNSUPPORTED, "irt_adjoint_ppv: z view only");
+  if (jb.view.trilinear == 1)
+    return fail(IRT_EUNSUPPORTED, "irt_adjoint_ppv: z or radial view only");
   if (jb.vaxis.subsample_f < 1) return fail(IRT_EUNSUPPORTED, "irt_adjoint_ppv: needs f >= 1");
   irt_grid* g = jb.grid;
   if (g->store == ST_F64)
@@ -1295,6 +1702,7 @@ extern "C" irt_status irt_forward_ppv_static(const irt_grid_desc* desc, const ir
   L.stats = nullptr;
   L.rscr = recs;
   L.rbytes = kStaticRecBytes;
+  L.lines = nullptr;
   e = dispatch(opts->precision, opts->integration, store, p.ni, tab, 1, P, to_float(P), L, s);
   ++g_launches;
   if (e) return cuda_fail(e, "irt_forward_ppv_static: forward kernel");

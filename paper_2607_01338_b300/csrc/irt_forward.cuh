@@ -86,6 +86,11 @@ __device__ __forceinline__ void load_cell(const void* cells, long long idx, int 
   }
 }
 
+// Cell z of sample k on the cell-exact views: k on the z view; nz - 1 - k on
+// the radial view of an observer-centred [r][b][l] tensor (the ray runs from
+// the far end of the radial axis to the observer at r = 0).
+__device__ __forceinline__ int zcell(const JobDev& J, int k) { return J.zrev ? J.nz - 1 - k : k; }
+
 // ---------------------------------------------------------------------------
 // ray geometry (double precision: the sample count must be exact)
 // ---------------------------------------------------------------------------
@@ -180,7 +185,8 @@ template <int ST>
 __device__ __forceinline__ void sample_raw(const JobDev& J, const RayGeom& g, int px, int py,
                                            int k, double v[5]) {
   if (J.zview) {
-    load_cell<double, ST>(J.cells, ((long long)k * J.ny + py) * J.nx + px, J.bf16_mask, J.scale,
+    load_cell<double, ST>(J.cells, ((long long)zcell(J, k) * J.ny + py) * J.nx + px, J.bf16_mask,
+                          J.scale,
                           v);
     return;
   }
@@ -222,7 +228,8 @@ template <int ST>
 __device__ __forceinline__ void sample_raw(const JobDev& J, const RayPos& rp, int px, int py,
                                            int k, float v[5]) {
   if (J.zview) {
-    load_cell<float, ST>(J.cells, ((long long)k * J.ny + py) * J.nx + px, J.bf16_mask, J.scale,
+    load_cell<float, ST>(J.cells, ((long long)zcell(J, k) * J.ny + py) * J.nx + px, J.bf16_mask,
+                         J.scale,
                          v);
     return;
   }
@@ -235,6 +242,83 @@ __device__ __forceinline__ void sample_raw(const JobDev& J, const RayPos& rp, in
     w[a] = (float)(unsigned)(p & 0xFFFFFFFFll) * 2.3283064365386963e-10f;   // 2^-32
   }
   trilinear<float, ST>(J, i0, w, v);
+}
+
+// H2 abundance of sample k (the cells' spare slot; optically thin level
+// balance only): the cell value on the z view, the trilinear blend of the
+// eight cells (already loaded for the other fields) on oblique views.
+template <typename R, int ST>
+__device__ __forceinline__ R cell_chi(const void* cells, long long idx) {
+  if constexpr (ST == ST_F32) return (R)__ldg(reinterpret_cast<const float*>(cells) + 8 * idx + 5);
+  else if constexpr (ST == ST_H16)
+    return (R)__half2float(__ushort_as_half(
+        __ldg(reinterpret_cast<const unsigned short*>(cells) + 8 * idx + 5)));
+  else return (R)__ldg(reinterpret_cast<const double*>(cells) + 8 * idx + 5);
+}
+
+template <typename R, int ST>
+__device__ __forceinline__ R chi_trilinear(const JobDev& J, const int i0[3], const R w[3]) {
+  const int n[3] = {J.nx, J.ny, J.nz};
+  int lo[3], hi[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    lo[a] = min(max(i0[a], 0), n[a] - 1);
+    hi[a] = min(max(i0[a] + 1, 0), n[a] - 1);
+  }
+  R acc = (R)0;
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    const int ix = (c & 1) ? hi[0] : lo[0];
+    const int iy = (c & 2) ? hi[1] : lo[1];
+    const int iz = (c & 4) ? hi[2] : lo[2];
+    const R ww = ((c & 1) ? w[0] : (R)1 - w[0]) * ((c & 2) ? w[1] : (R)1 - w[1]) *
+                 ((c & 4) ? w[2] : (R)1 - w[2]);
+    acc += ww * cell_chi<R, ST>(J.cells, ((long long)iz * J.ny + iy) * J.nx + ix);
+  }
+  return acc;
+}
+
+// Only the optically thin level-balance kernel instances call it.
+template <int ST>
+__device__ __forceinline__ float sample_chi_pos(const JobDev& J, long long b0, long long b1,
+                                             long long b2, long long s0, long long s1,
+                                             long long s2, int px, int py, int k) {
+  if (J.zview)
+    return cell_chi<float, ST>(J.cells, ((long long)zcell(J, k) * J.ny + py) * J.nx + px);
+  const long long base[3] = {b0, b1, b2}, step[3] = {s0, s1, s2};
+  int i0[3];
+  float w[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const long long p = base[a] + (long long)k * step[a];
+    i0[a] = (int)(p >> 32);
+    w[a] = (float)(unsigned)(p & 0xFFFFFFFFll) * 2.3283064365386963e-10f;
+  }
+  return chi_trilinear<float, ST>(J, i0, w);
+}
+
+template <int ST>
+__device__ __forceinline__ float sample_chi(const JobDev& J, const RayPos& rp, int px, int py,
+                                            int k) {
+  return sample_chi_pos<ST>(J, rp.base[0], rp.base[1], rp.base[2], rp.step[0], rp.step[1],
+                            rp.step[2], px, py, k);
+}
+
+template <int ST>
+__device__ __forceinline__ double sample_chi(const JobDev& J, const RayGeom& g, int px, int py,
+                                             int k) {
+  if (J.zview)
+    return cell_chi<double, ST>(J.cells, ((long long)zcell(J, k) * J.ny + py) * J.nx + px);
+  const double t = g.t0 + (k + 0.5) * g.h;
+  int i0[3];
+  double w[3];
+  for (int a = 0; a < 3; ++a) {
+    const double s = (g.o[a] + t * g.d[a]) * J.inv_dx - 0.5;
+    const double fl = floor(s);
+    w[a] = s - fl;
+    i0[a] = (int)fl;
+  }
+  return chi_trilinear<double, ST>(J, i0, w);
 }
 
 // ---------------------------------------------------------------------------
@@ -271,14 +355,87 @@ __device__ inline double partition(const PhysParams& P, double T) {
   return z;
 }
 
+// Optically thin level balance (Sec. 4.2, 4.3): trilinear interpolation of
+// the line's coefficient grid in (log10 n_H, chi, log10 T), n_H = n_H2 / chi,
+// the cell index clamped to the grid so that outside it the edge cell
+// continues linearly.  Returns (j, alpha) per tracer molecule in per-step K
+// units (to be multiplied by N h / b).
+__device__ __forceinline__ float2 ot_lookup(const PhysF& P, float n, float chi, float T) {
+  const float x[3] = {log10f(n / chi), chi, log10f(T)};
+  int i[3];
+  float w[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const float u = (x[a] - P.ot_lo[a]) * P.ot_s[a];
+    const int iu = min(max((int)floorf(u), 0), P.ot_n[a] - 2);
+    i[a] = iu;
+    w[a] = u - (float)iu;
+  }
+  const int n2p = P.ot_n[2] - 1;
+  const float4* p = P.ot_tab + ((long long)i[0] * P.ot_n[1] + i[1]) * n2p + i[2];
+  const float4 c00 = __ldg(p), c01 = __ldg(p + n2p);
+  const float4 c10 = __ldg(p + (long long)P.ot_n[1] * n2p);
+  const float4 c11 = __ldg(p + (long long)P.ot_n[1] * n2p + n2p);
+  // along T within each of the four (n, chi) corners, then chi, then n
+  const float w2 = w[2], v2 = 1.0f - w2;
+  const float j00 = v2 * c00.x + w2 * c00.z, a00 = v2 * c00.y + w2 * c00.w;
+  const float j01 = v2 * c01.x + w2 * c01.z, a01 = v2 * c01.y + w2 * c01.w;
+  const float j10 = v2 * c10.x + w2 * c10.z, a10 = v2 * c10.y + w2 * c10.w;
+  const float j11 = v2 * c11.x + w2 * c11.z, a11 = v2 * c11.y + w2 * c11.w;
+  const float w1 = w[1], v1 = 1.0f - w1;
+  const float j0 = v1 * j00 + w1 * j01, a0 = v1 * a00 + w1 * a01;
+  const float j1 = v1 * j10 + w1 * j11, a1 = v1 * a10 + w1 * a11;
+  const float w0 = w[0], v0 = 1.0f - w0;
+  return make_float2(v0 * j0 + w0 * j1, v0 * a0 + w0 * a1);
+}
+
+__device__ inline double2 ot_lookup(const PhysParams& P, double n, double chi, double T) {
+  const double x[3] = {log10(n / chi), chi, log10(T)};
+  int i[3];
+  double w[3];
+  for (int a = 0; a < 3; ++a) {
+    const double u = (x[a] - P.ot_lo[a]) * P.ot_s[a];
+    const int iu = min(max((int)floor(u), 0), P.ot_n[a] - 2);
+    i[a] = iu;
+    w[a] = u - (double)iu;
+  }
+  double acc0 = 0.0, acc1 = 0.0;
+  for (int c = 0; c < 8; ++c) {
+    const int a0 = i[0] + (c & 1), a1 = i[1] + ((c >> 1) & 1), a2 = i[2] + ((c >> 2) & 1);
+    const double wc = ((c & 1) ? w[0] : 1.0 - w[0]) * ((c & 2) ? w[1] : 1.0 - w[1]) *
+                      ((c & 4) ? w[2] : 1.0 - w[2]);
+    const long long idx = (((long long)a0 * P.ot_n[1] + a1) * P.ot_n[2] + a2) * 2;
+    acc0 += wc * __ldg(P.ot_tab + idx);
+    acc1 += wc * __ldg(P.ot_tab + idx + 1);
+  }
+  return make_double2(acc0 * P.ot_jk, acc1 * P.ot_ak);
+}
+
 // Frequency-independent per-step line coefficients at the profile peak (K
-// units / optical depth) and the Doppler parameter b [km/s].
-__device__ __forceinline__ void line_coeffs(const PhysF& P, float n, float T, float x, float h,
-                                            float* jl, float* al, float* b) {
+// units / optical depth) and the Doppler parameter b [km/s]: LTE populations,
+// or the optically thin level-balance grid when the launch has one (chi =
+// the sample's H2 abundance per H nucleus).
+// OTC = false compiles the LTE path alone (kernel instances that never take
+// a grid).
+template <bool OTC = true>
+__device__ __forceinline__ void line_coeffs(const PhysF& P, float n, float T, float x, float chi,
+                                            float h, float* jl, float* al, float* b) {
   *b = sqrtf(P.c_th * T + P.two_sig2);
   if (!(T > 0.0f) || T > P.t_inf) {
     *jl = 0.0f;
     *al = 0.0f;
+    return;
+  }
+  if (OTC && P.ot_tab) {
+    if (!(n > 0.0f) || !(chi > 0.0f) || !(x > 0.0f)) {
+      *jl = 0.0f;
+      *al = 0.0f;
+      return;
+    }
+    const float2 c = ot_lookup(P, n, chi, T);
+    const float s = (x * n) * h / *b;
+    *jl = s * c.x;
+    *al = s * c.y;
     return;
   }
   const float Z = partition(P, T);
@@ -287,12 +444,26 @@ __device__ __forceinline__ void line_coeffs(const PhysF& P, float n, float T, fl
   *al = P.ca * c * expf(-P.e_l / T) * (-expm1f(-P.T0 / T));
 }
 
+template <bool OTC = true>
 __device__ __forceinline__ void line_coeffs(const PhysParams& P, double n, double T, double x,
-                                            double h, double* jl, double* al, double* b) {
+                                            double chi, double h, double* jl, double* al,
+                                            double* b) {
   *b = sqrt(P.c_th * T + P.two_sig2);
   if (!(T > 0.0) || T > P.t_inf) {
     *jl = 0.0;
     *al = 0.0;
+    return;
+  }
+  if (OTC && P.ot_tab) {
+    if (!(n > 0.0) || !(chi > 0.0) || !(x > 0.0)) {
+      *jl = 0.0;
+      *al = 0.0;
+      return;
+    }
+    const double2 c = ot_lookup(P, n, chi, T);
+    const double s = (x * n) * h / *b;
+    *jl = s * c.x;
+    *al = s * c.y;
     return;
   }
   const double Z = partition(P, T);

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <algorithm>
+#include <cstring>
 #include <type_traits>
 
 #include "irt_forward.cuh"
@@ -12,13 +13,13 @@ namespace dev {
 // ---------------------------------------------------------------------------
 // sample pass: record of one sample; returns h alpha_D of the sample
 // ---------------------------------------------------------------------------
-template <int MODE>
-__device__ __forceinline__ float make_record(const PhysF& P, const float raw[5], float h,
+template <int MODE, bool OTC = true>
+__device__ __forceinline__ float make_record(const PhysF& P, const float raw[6], float h,
                                              const VGrid& G, int nfw,
                                              typename RecOf<float, MODE>::type* out) {
   const float n = raw[0], T = raw[1], Td = raw[2], v = raw[3], x = raw[4];
   float jl, al, b;
-  line_coeffs(P, n, T, x, h, &jl, &al, &b);
+  line_coeffs<OTC>(P, n, T, x, raw[5], h, &jl, &al, &b);
   const float ad = P.cad * n * h;
   float bk0, bk1;
   dust_source_lin(P, Td, &bk0, &bk1);
@@ -60,12 +61,12 @@ __device__ __forceinline__ float make_record(const PhysF& P, const float raw[5],
   return ad;
 }
 
-template <int MODE>
-__device__ __forceinline__ double make_record(const PhysParams& P, const double raw[5], double h,
+template <int MODE, bool OTC = true>
+__device__ __forceinline__ double make_record(const PhysParams& P, const double raw[6], double h,
                                               int nfw, RecD* out) {
   const double n = raw[0], T = raw[1], Td = raw[2], v = raw[3], x = raw[4];
   double jl, al, b;
-  line_coeffs(P, n, T, x, h, &jl, &al, &b);
+  line_coeffs<OTC>(P, n, T, x, raw[5], h, &jl, &al, &b);
   RecD r;
   r.jl = jl;
   r.al = al;
@@ -904,11 +905,14 @@ template <> struct PSel<false> {
 // ---------------------------------------------------------------------------
 // one work item: ray (px, py) of job J, every channel
 // ---------------------------------------------------------------------------
-template <typename R, int NI, int ST, int MODE, bool CK>
+// ML: one of several lines of the ray (line q); the first line samples the
+// fields and keeps the raw samples in rawbuf, the others read them back.
+template <typename R, int NI, int ST, int MODE, bool CK, bool OT, bool ML = false>
 __device__ void render_ray(const JobDev& J, const PhysParams& PD, const PhysF& PF, int px,
                            int py, unsigned char* wsm, int fw_off, int cw_off, int kb_off,
                            typename RecOf<R, MODE>::type* grec, int lane, unsigned flags,
-                           unsigned long long* stats) {
+                           unsigned long long* stats, void* const* outp = nullptr,
+                           float* rawbuf = nullptr, int q = 0) {
   using F = Fwd<R, NI, MODE>;
   using Rec = typename F::Rec;
   using Gen = RecStream<Rec>;
@@ -946,15 +950,29 @@ __device__ void render_ray(const JobDev& J, const PhysParams& PD, const PhysF& P
   for (int k0 = 0; k0 < K; k0 += 32) {
     const int k = k0 + lane;
     if (k < K) {
-      R raw[5];
+      R raw[6];
       Rec r;
       R ad;
       if constexpr (kDouble) {
         sample_raw<ST>(J, geo, px, py, k, raw);
-        ad = make_record<MODE>(PD, raw, h, nfw, &r);
+        raw[5] = OT ? sample_chi<ST>(J, geo, px, py, k) : 0.5;
+        ad = make_record<MODE, OT>(PD, raw, h, nfw, &r);
+      } else if constexpr (ML) {
+        float* rb = rawbuf + 6 * k;
+        if (q == 0) {
+          sample_raw<ST>(J, rp, px, py, k, raw);
+          raw[5] = PF.ot_tab ? sample_chi<ST>(J, rp, px, py, k) : 0.5f;
+#pragma unroll
+          for (int i = 0; i < 6; ++i) rb[i] = raw[i];
+        } else {
+#pragma unroll
+          for (int i = 0; i < 6; ++i) raw[i] = rb[i];
+        }
+        ad = make_record<MODE, true>(PF, raw, h, G, nfw, &r);
       } else {
         sample_raw<ST>(J, rp, px, py, k, raw);
-        ad = make_record<MODE>(PF, raw, h, G, nfw, &r);
+        raw[5] = OT ? sample_chi<ST>(J, rp, px, py, k) : 0.5f;
+        ad = make_record<MODE, OT>(PF, raw, h, G, nfw, &r);
       }
       grec[k] = r;
       const int lo = win_lo(r.win), hi = win_hi(r.win);
@@ -1000,7 +1018,7 @@ __device__ void render_ray(const JobDev& J, const PhysParams& PD, const PhysF& P
   // the continuum at the channel centre
   const long long plane = (long long)J.npx * J.npy;
   const long long pix = (long long)py * J.npx + px;
-  R* const* out = reinterpret_cast<R* const*>(J.out);
+  R* const* out = reinterpret_cast<R* const*>(ML ? outp : J.out);
   auto emit = [&](int c, R ibar, R ic_or_nan, bool have_ic, R X0, R X1, R X2) {
     const R uc = (R)J.v0 + ((R)c + (R)0.5) * (R)J.dv;
     const R ib = planck_k(P, (R)P.t_bg, uc);
@@ -1143,12 +1161,12 @@ __device__ void render_ray(const JobDev& J, const PhysParams& PD, const PhysF& P
 
 // CK: the job saves smooth-transfer checkpoints (a separate instance, so that
 // renders without them run no checkpoint code)
-template <typename R, int NI, int ST, int MODE, bool CK>
+template <typename R, int NI, int ST, int MODE, bool CK, bool OT, bool ML>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32, (sizeof(R) == 4 && NI <= 17) ? 4 : 1)
 fwd_kernel(const __grid_constant__ JobTable tab, int njobs, const PhysParams PD, const PhysF PF,
            long long total_items, unsigned long long* queue, int per_warp, int fw_off, int cw_off,
            int kb_off, unsigned flags, unsigned long long* stats, unsigned char* rscr,
-           long long rstride) {
+           long long rstride, long long raw_off, const __grid_constant__ LineSet LS) {
   using Rec = typename RecOf<R, MODE>::type;
   extern __shared__ __align__(16) unsigned char smem[];
   const int lane = threadIdx.x & 31;
@@ -1179,9 +1197,26 @@ fwd_kernel(const __grid_constant__ JobTable tab, int njobs, const PhysParams PD,
     const int within = (int)(ray - tile * tsz);
     const int px = (int)(tile % J.ntx) * J.tw + within % J.tw;
     const int py = (int)(tile / J.ntx) * J.th + within / J.tw;
-    if constexpr (ST == ST_F64 || sizeof(R) == 4) {
+    if constexpr (ML) {
+      // every line of the ray in turn; the line's constants go to a
+      // per-warp slot in shared memory (the line index is not a constant)
+      __shared__ PhysF spf[kWarpsPerBlock];
+      if (px < J.npx && py < J.npy) {
+        float* rawbuf = reinterpret_cast<float*>(rscr + gw * rstride + raw_off);
+        for (int q = 0; q < LS.n; ++q) {
+          const int* src = reinterpret_cast<const int*>(&LS.pf[q]);
+          int* dst = reinterpret_cast<int*>(&spf[warp]);
+          for (int i = lane; i < (int)(sizeof(PhysF) / sizeof(int)); i += 32) dst[i] = src[i];
+          __syncwarp();
+          render_ray<R, NI, ST, MODE, false, false, true>(J, PD, spf[warp], px, py, wsm, fw_off,
+                                                          cw_off, kb_off, grec, lane, flags,
+                                                          stats, LS.out[q], rawbuf, q);
+          __syncwarp();
+        }
+      }
+    } else if constexpr (ST == ST_F64 || sizeof(R) == 4) {
       if (px < J.npx && py < J.npy)
-        render_ray<R, NI, ST, MODE, CK>(J, PD, PF, px, py, wsm, fw_off, cw_off, kb_off, grec,
+        render_ray<R, NI, ST, MODE, CK, OT>(J, PD, PF, px, py, wsm, fw_off, cw_off, kb_off, grec,
                                         lane, flags, stats);
     }
     if (queue) {
@@ -1200,7 +1235,10 @@ fwd_kernel(const __grid_constant__ JobTable tab, int njobs, const PhysParams PD,
 // is the resident maximum, capped by the record scratch: each warp needs kmax
 // records.  L.queue (zero at launch) selects the dynamic schedule, nullptr the
 // round-robin one.
-template <typename R, int NI, int ST, int MODE, bool CK = false>
+// CK: the job keeps smooth-transfer checkpoints; OT: line coefficients from an
+// optically thin level-balance grid (separate instances, so that the LTE
+// renders' register allocation carries neither).
+template <typename R, int NI, int ST, int MODE, bool CK = false, bool OT = false, bool ML = false>
 int launch_fwd_inst(const JobTable& tab, int njobs, const PhysParams& P, const PhysF& PF,
                     const FwdLaunch& L, cudaStream_t stream) {
   using Rec = typename dev::RecOf<R, MODE>::type;
@@ -1214,8 +1252,16 @@ int launch_fwd_inst(const JobTable& tab, int njobs, const PhysParams& P, const P
   const int kb_bytes = (sizeof(R) == 4 && MODE == M_FORMAL_KAHAN) ? 2 * 32 * NI * 4 : 0;
   const int per_warp = (kb_off + kb_bytes + 15) & ~15;
   const size_t smem = (size_t)per_warp * kWarpsPerBlock;
-  const long long rstride = ((long long)L.kmax * (long long)sizeof(Rec) + 255) & ~255ll;
-  auto kern = dev::fwd_kernel<R, NI, ST, MODE, CK>;
+  // per warp: the records of the longest ray, and with several lines the
+  // raw field samples of the ray (6 floats a sample) after them
+  const long long rec_area = ((long long)L.kmax * (long long)sizeof(Rec) + 255) & ~255ll;
+  const long long raw_area = ML ? (((long long)L.kmax * 24 + 255) & ~255ll) : 0;
+  const long long rstride = rec_area + raw_area;
+  if (ML && !L.lines) return (int)cudaErrorInvalidValue;
+  LineSet ls;
+  if (ML) ls = *L.lines;
+  else std::memset(&ls, 0, sizeof ls);
+  auto kern = dev::fwd_kernel<R, NI, ST, MODE, CK, OT, ML>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return (int)e;
@@ -1232,7 +1278,7 @@ int launch_fwd_inst(const JobTable& tab, int njobs, const PhysParams& P, const P
   if (blocks < 1) return (int)cudaErrorInvalidValue;   // scratch below one block
   kern<<<(unsigned)blocks, kWarpsPerBlock * 32, smem, stream>>>(
       tab, njobs, P, PF, L.total, L.queue, per_warp, fw_off, cw_off, kb_off, L.flags, L.stats,
-      L.rscr, rstride);
+      L.rscr, rstride, rec_area, ls);
   return (int)cudaGetLastError();
 }
 

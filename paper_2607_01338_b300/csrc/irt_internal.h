@@ -2,6 +2,7 @@
 #pragma once
 
 #include <stdint.h>
+#include <cuda_runtime.h>
 
 #include "../../include/irt.h"
 
@@ -13,6 +14,9 @@ enum Store { ST_F32 = 0, ST_H16 = 1, ST_F64 = 2 };
 // Integration variants (values of irt_integration).
 enum Mode { M_FORMAL = 0, M_SMOOTH = 1, M_FORMAL_KAHAN = 2 };
 
+// pad[0] holds the H2 abundance per H nucleus (fp16 in 16-bit cells), read
+// only by the optically thin level balance; 0.5 (fully molecular) unless set
+// by irt_grid_set_h2_fraction.
 struct alignas(32) CellF32 { float v[5]; float pad[3]; };
 struct alignas(16) CellH16 { uint16_t v[5]; uint16_t pad[3]; };
 struct alignas(64) CellF64 { double v[5]; double pad[3]; };
@@ -38,6 +42,16 @@ struct PhysParams {
   double out_scale;   // K units -> output units at nu_ul: 1 (T_RJ) or 2 k nu^2 / c^2
   int units;          // irt_units
   int integration;    // irt_integration
+  // optically thin level balance (irt_forward_ppv_ot): the line's coefficient
+  // grid [n0][n1][n2] of (j, alpha) per tracer molecule [cgs], or nullptr for
+  // LTE; axes log10 n_H, chi, log10 T from lo[a] with ot_s[a] nodes per unit;
+  // ot_jk, ot_ak turn the cgs values into the per-step K-unit coefficients
+  // (times N h / b)
+  const double* ot_tab;
+  int ot_n[3];
+  int ot_pad;
+  double ot_lo[3], ot_s[3];
+  double ot_jk, ot_ak;
 };
 
 // The same constants rounded to float for the float kernels (no FP64 work
@@ -45,7 +59,62 @@ struct PhysParams {
 struct PhysF {
   float T0, e_u, e_l, theta_rot, cj, ca, c_th, two_sig2, t_inf, cad, inv_c_kms, t_bg, out_scale;
   int units;
+  // optically thin level balance: the line's grid as float4 pairs along the
+  // temperature axis, (j, alpha) at nodes i2 and i2 + 1, [n0][n1][n2 - 1],
+  // already in per-step K units (times N h / b); nullptr for LTE
+  const float4* ot_tab;
+  int ot_n[3];
+  float ot_lo[3], ot_s[3];
 };
+
+// Optically thin level-balance grid (irt_create_ot_table): per line, the
+// frequency-integrated coefficients per tracer molecule on the (log10 n_H,
+// chi, log10 T) nodes, in double (cgs) and as the float kernels read them.
+struct OTTableDev {
+  int n[3];
+  double lo[3], hi[3];
+  int nlines;
+  double nu[8];            // line frequencies [Hz]
+  double jk[8], ak[8];     // cgs -> per-step K units (times N h / b)
+  double* tab64;           // [nlines][n0][n1][n2][2]
+  float4* tab32;           // [nlines][n0][n1][n2 - 1]
+  int device;
+};
+// Several lines rendered in one launch (irt_forward_ppv_lines): per line its
+// constants and its five output cubes; the rays' field samples are taken once
+// and reused by every line.
+constexpr int kMaxLinesPerRender = 4;
+struct LineSet {
+  int n;
+  int pad;
+  PhysF pf[kMaxLinesPerRender];
+  void* out[kMaxLinesPerRender][5];
+};
+
+constexpr int kOTMaxLines = 8;
+constexpr int kOTMaxLevels = 64;
+
+// The level model in device memory (one buffer) and the grid of one build.
+struct OTBuildArgs {
+  int nlev, nrad, npartner, ntemp, ncoll, nlines;
+  const double* energy;   // [nlev] E_i / k [K]
+  const double* g;        // [nlev]
+  const double* a;        // [nrad] Einstein A [1/s]
+  const double* nu;       // [nrad] [Hz]
+  const double* ctemp;    // [npartner][ntemp] [K]
+  const double* k;        // [npartner][ncoll][ntemp] de-excitation [cm^3/s]
+  const int* rad_up;
+  const int* rad_lo;
+  const int* partner;     // irt_partner kinds
+  const int* cup;         // [npartner][ncoll]
+  const int* clo;
+  const int* lines;       // [nlines] radiative transition indices
+  double t_rad, opr, x_he;
+  int n[3];
+  double lo[3], hi[3];
+  double jk[kOTMaxLines], ak[kOTMaxLines];   // cgs -> per-step K units
+};
+int launch_ot_build(const OTBuildArgs& args, double* tab64, float4* tab32, cudaStream_t stream);
 
 // One render job as the kernels see it.
 struct JobDev {
@@ -56,7 +125,8 @@ struct JobDev {
   int pad1;
   int nx, ny, nz;
   double dx;             // cell size [cm]
-  int zview;             // 1 = z view (cell exact)
+  int zview;             // 1 = cell-exact view along the z axis (z or radial)
+  int zrev;              // radial view: sample k is the cell z = nz - 1 - k
   double theta, phi;     // view angles [rad]
   // oblique view basis (set up on the host from theta, phi): ray direction d,
   // pixel axes et, ep, 1/d per axis (infinite where d = 0), 1/dx
@@ -129,6 +199,7 @@ struct FwdLaunch {
   unsigned long long* stats;   // 6 work counters or nullptr
   unsigned char* rscr;         // per-warp sample records (global memory)
   size_t rbytes;               // size of rscr; bounds the resident warps
+  const LineSet* lines;        // several lines in one launch, or nullptr
 };
 
 // Shared memory per warp the thin-mode kernel may use (records and masks).
@@ -138,6 +209,9 @@ size_t thin_smem_per_warp(int precision, int transfer, int kmax, int nchan_max,
 
 int launch_pack(int store, const void* const* src, const int* dtypes, const double* scale,
                 void* cells, long long ncell, void* stream);
+// H2 abundance into the spare slot of every cell (default 0.5 from the pack)
+int launch_set_chi(int store, const void* chi, int dtype, void* cells, long long ncell,
+                   void* stream);
 
 
 }  // namespace irt

@@ -142,10 +142,14 @@ thin_kernel(const __grid_constant__ JobTable tab, int njobs, const PhysParams P,
     // reaches go to blo_k .. bhi_k
     auto record = [&](int k, int& blo_k, int& bhi_k) {
       R raw[5];
-      if constexpr (kD)
+      R chi = (R)0.5;   // H2 abundance (optically thin level balance only)
+      if constexpr (kD) {
         sample_raw<ST>(J, g, px, py, k, raw);
-      else
+        if (P.ot_tab) chi = sample_chi<ST>(J, g, px, py, k);
+      } else {
         sample_raw<ST>(J, rp, px, py, k, raw);
+        if (PF.ot_tab) chi = sample_chi<ST>(J, rp, px, py, k);
+      }
       R jl, al, b, ad;
       Rec e;
       if constexpr (TRANSFER == IRT_MODE_DENSITY_TRACING) {
@@ -163,12 +167,12 @@ thin_kernel(const __grid_constant__ JobTable tab, int njobs, const PhysParams P,
         e.aw = (R)0;
       } else {
         if constexpr (kD) {
-          line_coeffs(P, raw[0], raw[1], raw[4], h, &jl, &al, &b);
+          line_coeffs(P, raw[0], raw[1], raw[4], chi, h, &jl, &al, &b);
           ad = (R)P.cad * raw[0] * h;
           e.d0 = ad;
           e.d1 = raw[2];
         } else {
-          line_coeffs(PF, raw[0], raw[1], raw[4], h, &jl, &al, &b);
+          line_coeffs(PF, raw[0], raw[1], raw[4], chi, h, &jl, &al, &b);
           ad = PF.cad * raw[0] * h;
           R bk0, bk1;
           dust_source_lin(PF, raw[2], &bk0, &bk1);

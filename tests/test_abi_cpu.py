@@ -48,7 +48,7 @@ def test_build_targets_sm_103a_only():
 
 
 STRUCTS = ["irt_grid_desc", "irt_fields", "irt_line", "irt_dust", "irt_view", "irt_vaxis",
-           "irt_opts", "irt_cubes", "irt_job"]
+           "irt_opts", "irt_cubes", "irt_job", "irt_level_model", "irt_ot_axes"]
 
 
 def test_ctypes_layout_matches_c(B, tmp_path):
@@ -243,3 +243,64 @@ def _has_gpu():
         return torch.cuda.is_available()
     except Exception:
         return False
+
+
+def test_ot_table_arguments_validate_before_any_cuda_call(B):
+    """irt_create_ot_table refuses bad level models and axes with IRT_EINVAL
+    or IRT_EUNSUPPORTED before any device work; irt_forward_ppv_ot refuses a
+    NULL table."""
+    import numpy as np
+    from synth.levels import rotor_model
+    L = B.lib
+    m = rotor_model(nlev=6)
+    keep = {k: np.ascontiguousarray(np.asarray(m[k], dtype=np.float64)) for k in
+            ("energy_k", "g", "a_ul_s", "nu_hz", "coll_temp_k", "k_ul_cm3_s")}
+    keepi = {k: np.ascontiguousarray(np.asarray(m[k], dtype=np.int32)) for k in
+             ("rad_up", "rad_lo", "partner", "coll_up", "coll_lo")}
+    dp = lambda a: a.ctypes.data_as(B._DP)  # noqa: E731
+    ip = lambda a: a.ctypes.data_as(B._IP)  # noqa: E731
+
+    def model(**kw):
+        args = dict(nlev=m["nlev"], nrad=len(keepi["rad_up"]), npartner=len(keepi["partner"]),
+                    ntemp=keep["coll_temp_k"].shape[-1], ncoll=keepi["coll_up"].shape[-1],
+                    t_rad=2.725)
+        args.update(kw)
+        return B.irt_level_model(args["nlev"], dp(keep["energy_k"]), dp(keep["g"]), args["nrad"],
+                                 ip(keepi["rad_up"]), ip(keepi["rad_lo"]), dp(keep["a_ul_s"]),
+                                 dp(keep["nu_hz"]), args["npartner"], ip(keepi["partner"]),
+                                 args["ntemp"], dp(keep["coll_temp_k"]), args["ncoll"],
+                                 ip(keepi["coll_up"]), ip(keepi["coll_lo"]),
+                                 dp(keep["k_ul_cm3_s"]), args["t_rad"], 3.0, 0.1)
+
+    ax = B.irt_ot_axes(8, 4, 6, 1.0, 7.0, 0.05, 0.5, 0.7, 2.5)
+    lines = (ctypes.c_int * 1)(1)
+    out = ctypes.c_void_p()
+    cases = [(model(nlev=1), ax, lines, 1, B.IRT_EINVAL),
+             (model(nlev=65), ax, lines, 1, B.IRT_EUNSUPPORTED),
+             (model(), ax, (ctypes.c_int * 1)(9), 1, B.IRT_EINVAL),
+             (model(), ax, lines, 0, B.IRT_EINVAL),
+             (model(), ax, (ctypes.c_int * 9)(*[1] * 9), 9, B.IRT_EUNSUPPORTED),
+             (model(t_rad=-1.0), ax, lines, 1, B.IRT_EINVAL),
+             (model(), B.irt_ot_axes(1, 4, 6, 1.0, 7.0, 0.05, 0.5, 0.7, 2.5), lines, 1,
+              B.IRT_EINVAL),
+             (model(), B.irt_ot_axes(8, 4, 6, 1.0, 7.0, 0.05, 0.7, 0.7, 2.5), lines, 1,
+              B.IRT_EINVAL),
+             (model(), B.irt_ot_axes(8, 4, 6, 7.0, 1.0, 0.05, 0.5, 0.7, 2.5), lines, 1,
+              B.IRT_EINVAL)]
+    for mm, aa, ll, nl, code in cases:
+        assert L.irt_create_ot_table(ctypes.byref(mm), ctypes.byref(aa), ll, nl, None,
+                                     ctypes.byref(out)) == code, L.irt_last_error()
+    bad_idx = np.array([[1, 0, 7]], np.int32)   # a collisional level index out of range
+    mm = model()
+    mm.coll_up = bad_idx.ctypes.data_as(B._IP)
+    mm.ncoll = 3
+    assert L.irt_create_ot_table(ctypes.byref(mm), ctypes.byref(ax), lines, 1, None,
+                                 ctypes.byref(out)) == B.IRT_EINVAL
+    line = _line(B)
+    dust = B.irt_dust(0.01, 2.8)
+    job = B.irt_job(None, B.irt_view(0, 0, 4, 4, 1.0, 0), B.irt_vaxis(4, -2.0, 1.0, 1),
+                    B.irt_cubes(1, None, None, None, None))
+    opts = B.irt_opts(0, 1, 0, 2.725, 0, 0)
+    assert L.irt_forward_ppv_ot(ctypes.byref(job), 1, None, 0, ctypes.byref(line),
+                                ctypes.byref(dust), ctypes.byref(opts), None) == B.IRT_EINVAL
+    assert L.irt_grid_set_h2_fraction(None, None, 0, None) == B.IRT_EINVAL

@@ -149,3 +149,21 @@ def test_central_ray_chord_length():
         chord = n * dx / np.abs(d).max()
         assert len(smp) * h == pytest.approx(chord, rel=1e-13)
         assert len(smp) == math.ceil(chord / dx - 1e-9)
+
+
+def test_radial_view_reads_the_column_from_the_far_end():
+    """The radial view of an [r][b][l] tensor (view.trilinear = 2) samples the
+    column (l, b) = (x, y) from r = nz - 1 down to r = 0 (the observer), one
+    sample per cell at step dx; it equals the z view of the r-reversed
+    tensor."""
+    n, dx = 5, 2.0
+    rng = np.random.default_rng(3)
+    fields = tuple(rng.uniform(1.0, 2.0, (n + 2, n, n + 1)) for _ in range(5))
+    view = View(0.0, 0.0, n + 1, n, dx, 2)
+    smp, h = oracle.ray_samples(fields, dx, view, 3, 1)
+    assert h == dx and len(smp) == n + 2
+    for q in range(5):
+        np.testing.assert_array_equal(smp[:, q], fields[q][::-1, 1, 3])
+    flipped = tuple(np.ascontiguousarray(f[::-1]) for f in fields)
+    smp_z, _ = oracle.ray_samples(flipped, dx, View(0.0, 0.0, n + 1, n, dx, 0), 3, 1)
+    np.testing.assert_array_equal(smp, smp_z)
