@@ -56,6 +56,9 @@ OPS_ADJ_SAMPLE = (ADJ_FWD * 165 + 60, ADJ_FWD * 9 + 6)
 # the two Simpson sums 3).  The erf channel averages of the pairs the line
 # reaches are not counted, so the rate derived from these is a lower bound.
 OPS_THIN_PAIR = {"selectively_thin": 12, "thin": 5, "density_tracing": 2}
+#: kernel sources whose DRAM traffic the committed step profile records
+KERNEL_SOURCES = ("irt_adjoint.cu", "irt_forward.cuh", "irt_forward_impl.cuh",
+                  "irt_internal.h", "irt_fwd_f32_smooth.cu")
 
 
 def parse():
@@ -430,13 +433,15 @@ def gpu_arm(args):
     hbm_bytes = nx ** 3 * 32 + 5 * 4 * w.vaxis.nchan * vw.npx * vw.npy
     kname = ("adjoint: adj_kernel<9,F32> + deferred-ray pass adj_kernel<17,F32> (z view)"
              if is_adj else f"fwd_kernel<float,17,F32,smooth> ({['z', 'oblique'][dom]} view)")
-    # DRAM bytes per launch of the dominant kernel from one ncu capture of
-    # this workload (the committed step profile); other sizes have no capture
+    # DRAM bytes per launch of the dominant kernel from the committed ncu
+    # summary of this workload, only while the kernel sources it was captured
+    # from are unchanged; other sizes have no capture
     traffic = None
-    if nx == 256 and is_adj:
-        traffic = 1.365e9 + 1.581e9 + 66.56e3
-    elif nx == 256 and not is_adj:
-        traffic = (602.62e6 + 1.379e9) if dom == 0 else (1.73e9 + 1.149e9)
+    tp = traffic_from_profile() if nx == 256 else None
+    if tp:
+        key = "adjoint_dram_bytes_per_launch" if is_adj else \
+            ("z_view_dram_bytes_per_launch" if dom == 0 else "oblique_view_dram_bytes_per_launch")
+        traffic = tp.get(key)
     roofline = {"bound": "alu", "pipe": pipe, "achieved": ach, "peak": peak, "unit": "Top/s",
                 "frac": ach / peak, "traffic": traffic, "traffic_unit": "bytes per launch",
                 "kernel": kname,
@@ -559,6 +564,13 @@ def gpu_arm(args):
                "sample": sample + f"; adjoint: dual-number gradient of {na} seeded z-view rays",
                "forward_rate": r, "adjoint_rate": ra, "seconds": dt + dta}
 
+    accuracy = None
+    if rank == 0 and not args.no_cpu_baseline:
+        accuracy = accuracy_measure(w, deq, outs, grads, l_target)
+    extra = {}
+    if rank == 0 and not args.no_thin:
+        extra["ot"] = ot_measure(grid, w)
+        extra["lines"] = lines_measure(grid, w)
     reduce_ = beam = None
     if rank == 0 and not args.no_thin:
         reduce_ = reduce_measure(outs[0])
@@ -578,6 +590,10 @@ def gpu_arm(args):
     if not args.no_large and args.n == 256:
         torch.cuda.empty_cache()
         large = large_measure()
+    adj128 = None
+    if not args.no_large and rank == 0:
+        torch.cuda.empty_cache()
+        adj128 = adjoint128_measure()
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
@@ -591,8 +607,9 @@ def gpu_arm(args):
                                  f"{w.n ** 3 * 32 / 1e6:.0f} MB > 126 MB)",
                            "parallelism": f"replicas x{ws}", "per_view_ms": view_ms,
                            "adjoint_ms": adj_ms, "units_adjoint": units_adj},
-                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "batch": batch, "large": large,
-                "thin": thin, "latitude_mean": reduce_, "beam": beam,
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "accuracy": accuracy,
+                "batch": batch, "large": large, "adjoint_128cube": adj128,
+                "thin": thin, "latitude_mean": reduce_, "beam": beam, **extra,
                 "clocks": clk, "gpu_launches": launches}
         print(json.dumps(line), flush=True)
     if ws > 1:
@@ -732,6 +749,249 @@ def thin_measure(grid, w, deq, outs, units_view, pipe_peaks, cpu=True, reps=5):
             r["oracle_sample"] = f"{nr} seeded rays per view, all channels, full depth, " \
                                  f"{oracle.num_threads()} threads"
         res[tr] = r
+    return res
+
+
+def accuracy_measure(w, deq, outs, grads, l_target, seed=11):
+    """Error of every output of the timed step against the FP64 oracle on the
+    same stored inputs, measured in the run: the five cubes of both views on
+    an 8 x 8 pixel window at a seeded offset (all channels, rays at full
+    depth), and the three gradients on two z-view columns (the oracle's
+    dual-number gradient of the same loss).  Per output: the largest error
+    over its allowance (FP32 rule: 1e-5 relative or 1e-6 of the cube peak;
+    gradients: 1e-3 relative or 1e-7 of the largest) and the largest error
+    over the peak."""
+    import oracle
+    mode = oracle.SMOOTH
+    rng = np.random.default_rng(seed)
+    res = {}
+    for vi, (view, out) in enumerate(zip(w.views, outs)):
+        x0 = int(rng.integers(0, view.npx - 8))
+        y0 = int(rng.integers(0, view.npy - 8))
+        py, px = np.meshgrid(np.arange(y0, y0 + 8), np.arange(x0, x0 + 8), indexing="ij")
+        pix = np.stack([px.ravel(), py.ravel()], axis=1)
+        orc = oracle.render(deq.as_tuple(), w.cell_cm, w.line, w.dust, view, w.vaxis, pix,
+                            integration=mode)
+        peak = float(np.abs(orc["T"]).max())
+        comp = {}
+        for k in "TCDLB":
+            g = out[k][:, y0:y0 + 8, x0:x0 + 8].double().cpu().numpy()
+            g = g.reshape(g.shape[0], -1).T
+            err = np.abs(g - orc[k])
+            allow = np.maximum(1e-5 * np.abs(orc[k]), 1e-6 * peak)
+            comp[k] = {"worst_error_over_allowance": float((err / allow).max()),
+                       "max_error_over_peak": float(err.max() / peak)}
+        res[["z_view", "oblique_view"][vi]] = {"window": [x0, y0, 8, 8], "cubes": comp}
+    cols = np.stack([rng.integers(0, w.n, 2), rng.integers(0, w.n, 2)], axis=1)
+    tgt = l_target.double().cpu().numpy()
+    loss, on, ot, ov = oracle.loss_grad_zview(deq.as_tuple(), w.cell_cm, w.line, w.dust,
+                                              w.vaxis, tgt, pixels=cols)
+    gres = {}
+    for name, gg, oo in (("n_h2", grads[0], on), ("t_gas", grads[1], ot),
+                         ("v_los", grads[2], ov)):
+        gh = gg.double().cpu().numpy()
+        a = np.stack([gh[:, y, x] for x, y in cols])
+        b = np.stack([oo[:, y, x] for x, y in cols])
+        err = np.abs(a - b)
+        allow = 1e-3 * np.abs(b) + 1e-7 * np.abs(b).max()
+        gres[name] = {"worst_error_over_allowance": float((err / allow).max()),
+                      "max_error_over_max": float(err.max() / np.abs(b).max())}
+    res["adjoint_columns"] = {"columns": cols.tolist(), "gradients": gres}
+    res["rule"] = ("cubes: |gpu - oracle| <= max(1e-5 |oracle|, 1e-6 peak[T]); gradients: "
+                   "<= 1e-3 |oracle| + 1e-7 max|oracle|; values <= 1 pass")
+    return res
+
+
+def traffic_from_profile():
+    """DRAM bytes per launch of the step's kernels from the committed ncu
+    summary, valid only while the kernel sources it was captured from are
+    unchanged (their SHA-256 is recorded beside the numbers); else None."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "step_256cube_launches_and_dram.md")
+    try:
+        text = open(path).read()
+    except OSError:
+        return None
+    vals = {}
+    for line in text.splitlines():
+        line = line.strip().strip("`")
+        if ":" in line and line.split(":", 1)[0].strip() in (
+                "kernel_sources_sha256", "adjoint_dram_bytes_per_launch",
+                "z_view_dram_bytes_per_launch", "oblique_view_dram_bytes_per_launch"):
+            k, v = line.split(":", 1)
+            vals[k.strip()] = v.strip()
+    if "kernel_sources_sha256" not in vals:
+        return None
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2607_01338_b300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    if h.hexdigest() != vals["kernel_sources_sha256"]:
+        return None
+    try:
+        return {k: float(v) for k, v in vals.items() if k != "kernel_sources_sha256"}
+    except ValueError:
+        return None
+
+
+def adjoint128_measure(reps=5):
+    """The 128^3 / 128-channel / f = 2 adjoint workload (smooth): the z-view
+    forward keeping its checkpoints, the adjoint of a squared-error loss on
+    [L]; and the same grid's (30, 45) deg oblique view through the general
+    sweep.  Units: samples x channels of the adjoint's rays."""
+    import torch
+    import paper_2607_01338_b300 as irt
+    from paper_2607_01338_b300 import binding as B
+    from synth import make_fields, to_storage, workload
+    w = workload(3)
+    f32, _ = to_storage(make_fields(w.n, w.seed), np.float32)
+    t32, _ = to_storage(make_fields(w.n, w.seed + 7), np.float32)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    g = irt.Grid(*[torch.from_numpy(a).to(dev) for a in f32.as_tuple()], w.cell_cm)
+    tg = irt.Grid(*[torch.from_numpy(a).to(dev) for a in t32.as_tuple()], w.cell_cm)
+    view = w.views[0]
+    tgt = irt.forward(tg, view, w.vaxis, w.line, w.dust, components=("L",))["L"]
+    tg.close()
+    out = irt.alloc_cubes(view, w.vaxis)
+    grads = tuple(torch.empty((w.n,) * 3, device=dev) for _ in range(3))
+    from synth import View
+    obl = View(math.radians(30), math.radians(45), w.n, w.n, w.cell_cm, 1)
+    oout = irt.alloc_cubes(obl, w.vaxis)
+    B.irt_grid_stats(g.handle, reset=True)
+    irt.forward(g, obl, w.vaxis, w.line, w.dust, out=oout, flags=B.IRT_FLAG_STATS)
+    units_obl = B.irt_grid_stats(g.handle, reset=True)["samples"] * w.vaxis.nchan
+
+    def z_step():
+        irt.forward(g, view, w.vaxis, w.line, w.dust, out=out,
+                    flags=B.IRT_FLAG_SAVE_CHECKPOINTS)
+        cot = {"L": 2.0 * (out["L"] - tgt) / out["L"].numel()}
+        return cot
+
+    cot = z_step()
+    ocot = {"L": 2.0 * (oout["L"] - oout["L"].mean()) / oout["L"].numel()}
+    for _ in range(2):
+        irt.adjoint(g, view, w.vaxis, w.line, w.dust, cot, grads=grads)
+        irt.adjoint(g, obl, w.vaxis, w.line, w.dust, ocot, grads=grads)
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
+    ev[0].record()
+    for _ in range(reps):
+        z_step()
+    ev[1].record()
+    for _ in range(reps):
+        irt.adjoint(g, view, w.vaxis, w.line, w.dust, cot, grads=grads)
+    ev[2].record()
+    for _ in range(reps):
+        irt.adjoint(g, obl, w.vaxis, w.line, w.dust, ocot, grads=grads)
+    ev[3].record()
+    torch.cuda.synchronize()
+    t_f = ev[0].elapsed_time(ev[1]) / reps
+    t_a = ev[1].elapsed_time(ev[2]) / reps
+    t_o = ev[2].elapsed_time(ev[3]) / reps
+    units = w.n ** 3 * w.vaxis.nchan
+    g.close()
+    return {"workload": f"{w.name}: z view, smooth; forward keeping checkpoints, adjoint of "
+                        "mean(([L] - target)^2); and the (30, 45) deg oblique view's adjoint "
+                        "(general sweep, every velocity explicit)",
+            "forward_ms": t_f, "adjoint_ms": t_a, "forward_value": units / (t_f / 1e3),
+            "adjoint_value": units / (t_a / 1e3), "unit": UNIT,
+            "oblique_adjoint_ms": t_o, "oblique_adjoint_value": units_obl / (t_o / 1e3),
+            "accuracy": "gradients vs FP64 central differences on 200 cells and the oracle "
+                        "gradient (tests/test_gpu_adjoint.py, tests/test_gpu_adjoint_general.py)"}
+
+
+def ot_measure(grid, w, reps=5):
+    """The optically thin level balance (Sec. 4.2, 4.3): the paper's
+    128 x 64 x 64 grid built on the GPU for a 41-level rotor model (FP64
+    solves, timed with CUDA events on the stream), and the z- and oblique-view
+    renders of the step's grid with the 13CO 2-1 line's coefficients from that
+    grid, against the LTE renders of the same line (units of the step)."""
+    import torch
+    import paper_2607_01338_b300 as irt
+    from paper_2607_01338_b300 import binding as B
+    from synth.levels import OT_AXES, rotor_model
+    model = rotor_model(nlev=41, seed=2)
+    line = dict(w.line, nu_ul_hz=float(model["nu_hz"][1]))
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    irt.LevelTable(model, dict(OT_AXES, n_n=8, n_chi=4, n_t=8), [1]).close()   # warm-up
+    torch.cuda.synchronize()
+    e[0].record()
+    tab = irt.LevelTable(model, OT_AXES, [0, 1, 2])
+    e[1].record()
+    torch.cuda.synchronize()
+    build_ms = e[0].elapsed_time(e[1])
+    res = {"grid": [OT_AXES["n_n"], OT_AXES["n_chi"], OT_AXES["n_t"]], "levels": 41,
+           "lines": 3, "build_ms": build_ms,
+           "model": "synthetic rigid rotor (13CO B0, 0.11 D dipole, invented collision rates "
+                    "for p-H2, o-H2, H, He): no LAMDA file is available"}
+    for vi, view in enumerate(w.views):
+        out = irt.alloc_cubes(view, w.vaxis)
+        B.irt_grid_stats(grid.handle, reset=True)
+        irt.forward(grid, view, w.vaxis, line, w.dust, out=out, flags=B.IRT_FLAG_STATS)
+        units = B.irt_grid_stats(grid.handle, reset=True)["samples"] * w.vaxis.nchan
+        t = {}
+        for kind in ("lte", "ot"):
+            kw = dict(levels=tab, line_index=1) if kind == "ot" else {}
+            for _ in range(2):
+                irt.forward(grid, view, w.vaxis, line, w.dust, out=out, **kw)
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+            ev[0].record()
+            for _ in range(reps):
+                irt.forward(grid, view, w.vaxis, line, w.dust, out=out, **kw)
+            ev[1].record()
+            torch.cuda.synchronize()
+            t[kind] = ev[0].elapsed_time(ev[1]) / reps
+        res[["z_view", "oblique_view"][vi]] = {
+            "lte_ms": t["lte"], "ot_ms": t["ot"], "ot_value": units / (t["ot"] / 1e3),
+            "unit": UNIT}
+    res["accuracy"] = ("grid vs the oracle's grid to 1e-10 and renders vs the oracle with the "
+                       "same grid at the FP32 rule (tests/test_gpu_ot.py)")
+    tab.close()
+    return res
+
+
+def lines_measure(grid, w, reps=5):
+    """Three lines (13CO 1-0, 2-1, 3-2 of a rigid rotor, each with its own
+    dust opacity) rendered in one launch that samples each ray's fields once,
+    against three single-line launches, on both views of the step's grid."""
+    import torch
+    import paper_2607_01338_b300 as irt
+    from synth.levels import rotor_model
+    model = rotor_model(nlev=8)
+    b0 = float(model["nu_hz"][0]) / 2.0
+    lines = []
+    for r in (0, 1, 2):
+        u, l = int(model["rad_up"][r]), int(model["rad_lo"][r])
+        lines.append(dict(w.line, nu_ul_hz=float(model["nu_hz"][r]),
+                          a_ul_s=float(model["a_ul_s"][r]), e_u_k=float(model["energy_k"][u]),
+                          b0_hz=b0, g_u=float(model["g"][u]), g_l=float(model["g"][l])))
+    dusts = [dict(w.dust, kappa_cm2_per_g_gas=k) for k in (0.004, 0.01, 0.02)]
+    res = {"lines": "13CO 1-0, 2-1, 3-2 (rotor constants), kappa 0.004 / 0.01 / 0.02 cm^2/g"}
+    for vi, view in enumerate(w.views):
+        outs = [irt.alloc_cubes(view, w.vaxis) for _ in lines]
+        t = {}
+        for kind in ("one_launch", "three_launches"):
+            def run():
+                if kind == "one_launch":
+                    irt.forward_lines(grid, view, w.vaxis, lines, dusts, outs=outs)
+                else:
+                    for ln, du, o in zip(lines, dusts, outs):
+                        irt.forward(grid, view, w.vaxis, ln, du, out=o)
+            for _ in range(2):
+                run()
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+            ev[0].record()
+            for _ in range(reps):
+                run()
+            ev[1].record()
+            torch.cuda.synchronize()
+            t[kind] = ev[0].elapsed_time(ev[1]) / reps
+        res[["z_view", "oblique_view"][vi]] = {
+            "one_launch_ms": t["one_launch"], "three_launches_ms": t["three_launches"],
+            "speedup": t["three_launches"] / t["one_launch"]}
+        del outs
+    res["accuracy"] = ("each line equals its single-line render to 1e-6 of the peak and the "
+                       "oracle at the FP32 rule (tests/test_gpu_lines.py)")
     return res
 
 

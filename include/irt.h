@@ -116,7 +116,7 @@ typedef enum {
 #define IRT_FLAG_AUTOTUNE 4u           /* time the launch plans for this job mix
                                           (synchronous; not during stream capture)
                                           and cache the fastest */
-#define IRT_FLAG_SAVE_CHECKPOINTS 8u   /* one z-view job, smooth, float: also keep
+#define IRT_FLAG_SAVE_CHECKPOINTS 8u   /* one z- or radial-view job, smooth, float: keep
                                           the transfer state every 32 samples in
                                           the grid, for irt_adjoint_ppv of the
                                           same job, which then skips its own
@@ -215,6 +215,17 @@ irt_status irt_create_grid(const irt_grid_desc* desc, const irt_fields* fields,
                            void* cuda_stream, irt_grid** out);
 
 /*
+ * irt_update_grid - copy new field values into an existing grid (same size,
+ * cell, storage and 16-bit scales as at creation; IRT_EINVAL otherwise),
+ * asynchronously on cuda_stream, without any allocation: a caller rendering
+ * many snapshots of one shape (a training loop) keeps its grids.  The H2
+ * abundance returns to 0.5 and checkpoints kept by earlier renders no longer
+ * apply.  Launches using the grid on other streams must have finished.
+ */
+irt_status irt_update_grid(irt_grid* grid, const irt_grid_desc* desc, const irt_fields* fields,
+                           void* cuda_stream);
+
+/*
  * irt_forward_ppv - render njobs >= 1 jobs (Sec. 4.4-4.10).  A work item is
  * one ray with every channel.  njobs == 1 runs one persistent launch whose
  * warps take the rays round-robin; njobs > 1 runs one persistent launch per
@@ -228,7 +239,7 @@ irt_status irt_create_grid(const irt_grid_desc* desc, const irt_fields* fields,
  * pointers NULL.  IRT_EUNSUPPORTED for IRT_PREC_F64 on a grid that is not
  * stored as double, f > 64, or more than 32000 fine velocities (2 f nchan + 1).
  *
- * IRT_FLAG_SAVE_CHECKPOINTS (njobs == 1, z view, IRT_SMOOTH, float precision,
+ * IRT_FLAG_SAVE_CHECKPOINTS (njobs == 1, z or radial view, IRT_SMOOTH, float precision,
  * else IRT_EUNSUPPORTED) stores, in a buffer the grid owns (npx x npy x
  * ceil(nz / 32) x 2 x 10 x 32 floats, grown on demand), the transfer state of
  * every ray every 32 samples, with a signature of the job (velocity axis,
@@ -271,20 +282,26 @@ irt_status irt_tuned_plan(const irt_job* jobs, int njobs, const irt_opts* opts, 
 
 /*
  * irt_adjoint_ppv - gradients of a scalar loss with respect to n_H2, T_gas
- * and v_los of every cell for one z- or radial-view job (Sec. 4.8 run in
- * reverse), given
- * the cotangents dLoss/d[T], d[C], d[D], d[L], d[B] (float cubes
- * [nchan][npy][npx], NULL = zero).  grad_* are float [nz][ny][nx], written
- * completely (overwritten, not accumulated).  The forward transfer state is
- * recomputed from per-ray checkpoints every 32 samples held in device
- * scratch kept per (device, stream).  IRT_EINVAL as irt_forward_ppv plus NULL
- * gradients; IRT_EUNSUPPORTED for oblique views, IRT_PREC_F64, integrators
- * other than IRT_SMOOTH, f = 0, or channel counts needing more than one
- * window.  The cells of a ray whose render needs every channel explicit
- * (h alpha_D > 1/2 on some sample, or a line window wider than 64 fine
- * velocities) get NaN gradients; a ray of one sample gets zero.  The
- * rays run in two launches: 9 register blocks first, then the rays whose line
- * hull is wider, with the job's full width.
+ * and v_los of every cell for one job (Sec. 4 intro: the observation is
+ * differentiable end to end; Sec. 4.8 run in reverse), given the cotangents
+ * dLoss/d[T], d[C], d[D], d[L], d[B] (float cubes [nchan][npy][npx], NULL =
+ * zero).  grad_* are float [nz][ny][nx], written completely (overwritten, not
+ * accumulated; a cell no ray samples gets zero).  Any view, integrator
+ * (IRT_FORMAL_KAHAN is differentiated as the formal step it equals), f and
+ * channel count.  Two sweeps: z- and radial-view smooth jobs of one channel
+ * window run the fast sweep (line hull in registers, continuum basis; 9
+ * register blocks first, then the rays with wider hulls at the job's full
+ * width), which hands the rays it cannot take (h alpha_D > 1/2 on some
+ * sample, a line window wider than 64 fine velocities) to the general sweep;
+ * every other job runs the general sweep alone (every velocity explicit;
+ * oblique views add each sample's partials to its eight trilinear cells with
+ * atomics, so their sums may differ in the last bits between runs).  The
+ * forward state is recomputed from checkpoints every 32 samples held in
+ * device scratch kept per (device, stream).  IRT_EINVAL as irt_forward_ppv
+ * plus NULL gradients; IRT_EUNSUPPORTED for IRT_PREC_F64, double field
+ * storage, the thin modes, T_B units, or rays and channel counts whose
+ * per-warp shared memory (52 bytes a sample + 8 bytes a channel) exceeds
+ * 110 KiB.
  */
 irt_status irt_adjoint_ppv(const irt_job* job, const irt_line* line, const irt_dust* dust,
                            const irt_opts* opts, const irt_cubes* cotangent,

@@ -78,6 +78,13 @@ def lib():
                                                   ctypes.c_double, _dp, ctypes.c_int, _ip,
                                                   _dp, _dp, _dp])
             L.oracle_num_threads.restype = ctypes.c_int
+            L.oracle_loss_grad_cells.restype = ctypes.c_double
+            L.oracle_loss_grad_cells.argtypes = ([ctypes.POINTER(_dp), ctypes.c_int, ctypes.c_int,
+                                                  ctypes.c_int, ctypes.c_double, _dp, _dp, _dp,
+                                                  ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                                  ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                                  ctypes.c_double, _dp, ctypes.c_int, _ip,
+                                                  _dp, _dp, _dp])
             L.oracle_render_levels.restype = ctypes.c_int
             L.oracle_render_levels.argtypes = ([ctypes.POINTER(_dp), _dp, ctypes.c_int,
                                                 ctypes.c_int, ctypes.c_int, ctypes.c_double,
@@ -359,6 +366,29 @@ def loss_grad_zview(fields, cell_cm, line, dust, vaxis, target_L, pixels=None,
                                         vaxis.subsample_f, integration, units, t_bg,
                                         tgt.ctypes.data_as(_dp), pix.shape[0],
                                         pix.ctypes.data_as(_ip),
+                                        *[g.ctypes.data_as(_dp) for g in gs])
+    return loss, gs[0], gs[1], gs[2]
+
+
+def loss_grad_cells(fields, cell_cm, line, dust, view, vaxis, target_L, cells,
+                    integration=SMOOTH, units=TRJ, t_bg=2.725):
+    """Loss = mean over all voxels of ([L] - target)^2 and its gradient with
+    respect to n_H2, T_gas, v_los of the cells ``cells`` (int [n, 3] of
+    (x, y, z)), any view and integrator, by forward-mode dual numbers.
+    ``target_L`` is [nchan][npy][npx].  Returns (loss, g_n, g_t, g_v), each
+    gradient an array [n]."""
+    nz, ny, nx = np.asarray(fields[0]).shape
+    arrs, ptrs = _fields(fields)
+    kl, pl = _line(line)
+    kd, pd = _dust(dust)
+    kv, pv = _view(view)
+    tgt = np.ascontiguousarray(np.asarray(target_L, dtype=np.float64))
+    cl = np.ascontiguousarray(np.asarray(cells, dtype=np.int32).reshape(-1, 3))
+    gs = [np.zeros(cl.shape[0]) for _ in range(3)]
+    loss = lib().oracle_loss_grad_cells(ptrs, nx, ny, nz, cell_cm, pl, pd, pv, vaxis.nchan,
+                                        vaxis.v_first_edge_kms, vaxis.dv_kms, vaxis.subsample_f,
+                                        integration, units, t_bg, tgt.ctypes.data_as(_dp),
+                                        cl.shape[0], cl.ctypes.data_as(_ip),
                                         *[g.ctypes.data_as(_dp) for g in gs])
     return loss, gs[0], gs[1], gs[2]
 

@@ -854,6 +854,54 @@ void ray_samples(const Grid& g, const ViewP& v, int px, int py,
   }
 }
 
+// The cells each sample of a ray draws on and their weights (the sample
+// value of every field is the weighted sum of these cells' values): the one
+// cell of the z and radial views, the eight trilinear corners (index clamped,
+// so a corner may repeat) of the oblique view.  Same order and positions as
+// ray_samples.
+void ray_stencils(const Grid& g, const ViewP& v, int px, int py,
+                  std::vector<std::vector<std::pair<int64_t, double>>>* st) {
+  st->clear();
+  auto cell = [&](int x, int y, int z) { return ((int64_t)z * g.ny + y) * g.nx + x; };
+  if (v.trilinear == 0 || v.trilinear == 2) {
+    for (int k = 0; k < g.nz; ++k) {
+      const int z = (v.trilinear == 2) ? g.nz - 1 - k : k;
+      st->push_back({{cell(px, py, z), 1.0}});
+    }
+    return;
+  }
+  double o[3], d[3], t0, t1;
+  if (!ray_chord(g, v, px, py, o, d, &t0, &t1)) return;
+  const double chord = t1 - t0;
+  const int K = (int)std::ceil(chord / g.dx - 1e-9);
+  if (K <= 0) return;
+  const double h = chord / K;
+  const int n[3] = {g.nx, g.ny, g.nz};
+  for (int k = 0; k < K; ++k) {
+    const double t = t0 + (k + 0.5) * h;
+    const double r[3] = {o[0] + t * d[0], o[1] + t * d[1], o[2] + t * d[2]};
+    int i0[3], i1[3];
+    double w[3];
+    for (int a = 0; a < 3; ++a) {
+      const double sa = r[a] / g.dx - 0.5;
+      const double fl = std::floor(sa);
+      w[a] = sa - fl;
+      i0[a] = std::min(std::max((int)fl, 0), n[a] - 1);
+      i1[a] = std::min(std::max((int)fl + 1, 0), n[a] - 1);
+    }
+    std::vector<std::pair<int64_t, double>> cs;
+    for (int c = 0; c < 8; ++c) {
+      const int ix = (c & 1) ? i1[0] : i0[0];
+      const int iy = (c & 2) ? i1[1] : i0[1];
+      const int iz = (c & 4) ? i1[2] : i0[2];
+      const double wc = ((c & 1) ? w[0] : 1.0 - w[0]) * ((c & 2) ? w[1] : 1.0 - w[1]) *
+                        ((c & 4) ? w[2] : 1.0 - w[2]);
+      cs.push_back({cell(ix, iy, iz), wc});
+    }
+    st->push_back(cs);
+  }
+}
+
 Line line_from(const double* p) {
   Line l;
   l.nu_ul = p[0]; l.a_ul = p[1]; l.e_u = p[2]; l.b0 = p[3]; l.g_u = p[4]; l.g_l = p[5];
@@ -1163,5 +1211,109 @@ void oracle_ot_lookup(const void* t, int line, double n_h, double chi, double T,
 }
 
 void oracle_ot_table_free(void* t) { delete static_cast<OTTable*>(t); }
+
+// Gradient of Loss = mean over all voxels of ([L] - target)^2 with respect to
+// n_H2, T_gas and v_los of the listed cells (cells[3 i] = x, y, z), for any
+// view (z, oblique, radial) and integrator, by forward-mode dual numbers
+// through the whole definition: each sample's field values carry the
+// derivatives of the listed cells through the sample's stencil weights.
+// target is [nchan][npy][npx]; g_*[ncell].  Returns the loss.
+double oracle_loss_grad_cells(const double* const* fields, int nx, int ny, int nz,
+                              double cell_cm, const double* line, const double* dust,
+                              const double* view, int nchan, double v0, double dv, int f,
+                              int integration, int units, double t_bg, const double* target,
+                              int ncell, const int* cells, double* g_n, double* g_t,
+                              double* g_v) {
+  constexpr int CELLS = 8;
+  constexpr int ND = 3 * CELLS;
+  typedef Dual<ND> D;
+  Grid g;
+  for (int q = 0; q < 5; ++q) g.f[q] = fields[q];
+  g.nx = nx; g.ny = ny; g.nz = nz; g.dx = cell_cm;
+  const ViewP v{view[0], view[1], (int)view[2], (int)view[3], view[4], (int)view[5]};
+  const Line ln = line_from(line);
+  const DustP du = dust_from(dust);
+  const VAxis va = vaxis_from(nchan, v0, dv, f);
+  const int npix = v.npx * v.npy;
+  const double nvox = (double)nchan * npix;
+  double loss = 0.0;
+  for (int i = 0; i < ncell; ++i) g_n[i] = g_t[i] = g_v[i] = 0.0;
+  for (int c0 = 0; c0 < ncell; c0 += CELLS) {
+    const int nc = std::min(CELLS, ncell - c0);
+    std::vector<int64_t> seed(nc);
+    for (int c = 0; c < nc; ++c)
+      seed[c] = ((int64_t)cells[3 * (c0 + c) + 2] * ny + cells[3 * (c0 + c) + 1]) * nx +
+                cells[3 * (c0 + c)];
+    std::vector<double> acc(ND, 0.0);
+    double lsum = 0.0;
+#pragma omp parallel
+    {
+      std::vector<double> acc_t(ND, 0.0);
+      double l_t = 0.0;
+#pragma omp for schedule(dynamic, 4)
+      for (int p = 0; p < npix; ++p) {
+        const int px = p % v.npx, py = p / v.npx;
+        std::vector<Sample<double>> smp;
+        double h = 0.0;
+        ray_samples(g, v, px, py, &smp, &h);
+        std::vector<std::vector<std::pair<int64_t, double>>> stn;
+        ray_stencils(g, v, px, py, &stn);
+        const int K = (int)smp.size();
+        std::vector<Sample<D>> sd(K);
+        bool touched = false;
+        for (int k = 0; k < K; ++k) {
+          sd[k].n_h2 = D(smp[k].n_h2);
+          sd[k].t_gas = D(smp[k].t_gas);
+          sd[k].t_dust = D(smp[k].t_dust);
+          sd[k].v_los = D(smp[k].v_los);
+          sd[k].x_tr = D(smp[k].x_tr);
+          for (const auto& cw : stn[k])
+            for (int c = 0; c < nc; ++c)
+              if (cw.first == seed[c]) {
+                sd[k].n_h2.d[3 * c + 0] += cw.second;
+                sd[k].t_gas.d[3 * c + 1] += cw.second;
+                sd[k].v_los.d[3 * c + 2] += cw.second;
+                touched = true;
+              }
+        }
+        std::vector<D> T(nchan), C(nchan), Dd(nchan), L(nchan), B(nchan);
+        if (!touched) {
+          if (c0 == 0) {
+            std::vector<double> Tq(nchan), Cq(nchan), Dq(nchan), Lq(nchan), Bq(nchan);
+            ray_outputs(ln, du, va, integration, units, t_bg, smp, h, Tq.data(), Cq.data(),
+                        Dq.data(), Lq.data(), Bq.data());
+            for (int ch = 0; ch < nchan; ++ch) {
+              const double r = Lq[ch] - target[((int64_t)ch * v.npy + py) * v.npx + px];
+              l_t += r * r / nvox;
+            }
+          }
+          continue;
+        }
+        ray_outputs(ln, du, va, integration, units, t_bg, sd, h, T.data(), C.data(), Dd.data(),
+                    L.data(), B.data());
+        D l(0.0);
+        for (int ch = 0; ch < nchan; ++ch) {
+          const D r = L[ch] - target[((int64_t)ch * v.npy + py) * v.npx + px];
+          l = l + r * r;
+        }
+        l = l / nvox;
+        if (c0 == 0) l_t += l.v;
+        for (int i = 0; i < ND; ++i) acc_t[i] += l.d[i];
+      }
+#pragma omp critical
+      {
+        for (int i = 0; i < ND; ++i) acc[i] += acc_t[i];
+        lsum += l_t;
+      }
+    }
+    if (c0 == 0) loss = lsum;
+    for (int c = 0; c < nc; ++c) {
+      g_n[c0 + c] = acc[3 * c + 0];
+      g_t[c0 + c] = acc[3 * c + 1];
+      g_v[c0 + c] = acc[3 * c + 2];
+    }
+  }
+  return loss;
+}
 
 }  // extern "C"

@@ -44,16 +44,30 @@ class Grid:
                 raise ValueError(f"unsupported field dtype {t.dtype}")
         ts = [t.contiguous() for t in ts]
         nz, ny, nx = shape
-        sc = [1.0] * 5 if scales is None else [float(x) for x in scales]
-        desc = B.irt_grid_desc(nx, ny, nz, float(cell_cm),
-                               (B.ctypes.c_int * 5)(*[_DTYPE[t.dtype] for t in ts]),
-                               (B.ctypes.c_double * 5)(*sc))
-        fields = B.irt_fields(*[t.data_ptr() for t in ts])
+        self.scales = [1.0] * 5 if scales is None else [float(x) for x in scales]
+        desc, fields = self._desc(ts, float(cell_cm))
         self.handle = B.irt_create_grid(desc, fields, _stream_ptr(stream))
         self._keep = ts   # the pack kernel reads them on the stream
         self.shape = (nz, ny, nx)
         self.cell_cm = float(cell_cm)
         self.dtypes = tuple(t.dtype for t in ts)
+
+    def _desc(self, ts, cell_cm):
+        nz, ny, nx = ts[0].shape
+        desc = B.irt_grid_desc(nx, ny, nz, cell_cm,
+                               (B.ctypes.c_int * 5)(*[_DTYPE[t.dtype] for t in ts]),
+                               (B.ctypes.c_double * 5)(*self.scales))
+        return desc, B.irt_fields(*[t.data_ptr() for t in ts])
+
+    def update(self, n_h2, t_gas, t_dust, v_los, x_tracer, stream=None):
+        """New field values of the same shape and dtypes (``irt_update_grid``:
+        no allocation, asynchronous on the stream)."""
+        ts = [t.contiguous() for t in (n_h2, t_gas, t_dust, v_los, x_tracer)]
+        if tuple(ts[0].shape) != self.shape or tuple(t.dtype for t in ts) != self.dtypes:
+            raise ValueError("update needs the grid's shape and dtypes")
+        desc, fields = self._desc(ts, self.cell_cm)
+        B.irt_update_grid(self.handle, desc, fields, _stream_ptr(stream))
+        self._keep = ts
 
     def set_h2_fraction(self, chi: torch.Tensor, stream=None):
         """H2 abundance per H nucleus of every cell ([nz, ny, nx] CUDA tensor),
@@ -332,18 +346,45 @@ class RenderConfig:
     t_bg: float = 2.725
 
 
+# Grids of the autograd function, reused across calls: keyed by (device,
+# stream, shape, cell size); a grid goes back to the pool when its backward
+# has been enqueued (launches on one stream run in order, so the next
+# forward's field update waits for that adjoint without a host sync).
+_GRID_POOL = {}
+
+
+def _pooled_grid(fields, cell_cm):
+    key = (fields[0].device, torch.cuda.current_stream().cuda_stream, tuple(fields[0].shape),
+           float(cell_cm))
+    free = _GRID_POOL.get(key)
+    if free:
+        g = free.pop()
+        g.update(*fields)
+    else:
+        g = Grid(*fields, cell_cm)
+    g._pool_key = key
+    return g
+
+
+def _release_grid(g):
+    _GRID_POOL.setdefault(g._pool_key, []).append(g)
+
+
 class RenderPPV(torch.autograd.Function):
-    """Differentiable z-view render: (n_H2, T_gas, v_los, T_dust, x) -> the
-    five cubes; gradients flow to n_H2, T_gas and v_los through the
-    hand-written adjoint kernel."""
+    """Differentiable render: (n_H2, T_gas, v_los, T_dust, x) -> the five
+    cubes of any view; gradients flow to n_H2, T_gas and v_los through the
+    hand-written adjoint kernels.  The library grid comes from a per-stream
+    pool and returns to it after backward (no device synchronisation)."""
 
     @staticmethod
     def forward(ctx, n_h2, t_gas, v_los, t_dust, x_tracer, cfg: RenderConfig):
-        grid = Grid(n_h2.detach().float(), t_gas.detach().float(), t_dust.detach().float(),
-                    v_los.detach().float(), x_tracer.detach().float(), cfg.cell_cm)
-        # the z-view smooth render keeps its transfer checkpoints in the grid,
-        # so that backward skips re-integrating the forward
-        save = (cfg.integration == "smooth" and int(cfg.view.trilinear) == 0)
+        grid = _pooled_grid([n_h2.detach().float(), t_gas.detach().float(),
+                             t_dust.detach().float(), v_los.detach().float(),
+                             x_tracer.detach().float()], cfg.cell_cm)
+        # the z- and radial-view smooth renders keep their transfer
+        # checkpoints in the grid, so that backward skips re-integrating the
+        # forward
+        save = (cfg.integration == "smooth" and int(cfg.view.trilinear) != 1)
         cubes = forward(grid, cfg.view, cfg.vaxis, cfg.line, cfg.dust,
                         integration=cfg.integration, units=cfg.units, t_bg=cfg.t_bg,
                         flags=B.IRT_FLAG_SAVE_CHECKPOINTS if save else 0)
@@ -357,7 +398,8 @@ class RenderPPV(torch.autograd.Function):
         cot = dict(T=gT, C=gC, D=gD, L=gL, B=gB)
         gn, gt, gv = adjoint(ctx.grid, cfg.view, cfg.vaxis, cfg.line, cfg.dust, cot,
                              integration=cfg.integration, units=cfg.units, t_bg=cfg.t_bg)
-        ctx.grid.close()
+        _release_grid(ctx.grid)
+        ctx.grid = None
         return gn, gt, gv, None, None, None
 
 

@@ -37,7 +37,7 @@ EXPORTED = ("irt_create_grid", "irt_forward_ppv", "irt_adjoint_ppv", "irt_destro
             "irt_last_error", "irt_launch_count", "irt_measure_pipe_peaks", "irt_mean_axis1",
             "irt_beam_convolve", "irt_create_ot_table", "irt_ot_table_values",
             "irt_destroy_ot_table", "irt_grid_set_h2_fraction", "irt_forward_ppv_ot",
-            "irt_forward_ppv_lines")
+            "irt_forward_ppv_lines", "irt_update_grid")
 IRT_PARTNER_H2, IRT_PARTNER_PH2, IRT_PARTNER_OH2, IRT_PARTNER_H, IRT_PARTNER_HE = range(5)
 
 
@@ -173,6 +173,9 @@ def _load():
     L.irt_grid_set_h2_fraction.restype = ctypes.c_int
     L.irt_grid_set_h2_fraction.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
                                            ctypes.c_void_p]
+    L.irt_update_grid.restype = ctypes.c_int
+    L.irt_update_grid.argtypes = [ctypes.c_void_p, P(irt_grid_desc), P(irt_fields),
+                                  ctypes.c_void_p]
     L.irt_forward_ppv_lines.restype = ctypes.c_int
     L.irt_forward_ppv_lines.argtypes = [P(irt_job), ctypes.c_int, P(irt_line), P(irt_dust),
                                         P(irt_cubes), ctypes.c_void_p, _IP, P(irt_opts),
@@ -329,3 +332,8 @@ def irt_forward_ppv_lines(job: irt_job, lines, dusts, outs, table, table_lines,
     _check(lib.irt_forward_ppv_lines(ctypes.byref(job), n, la, da, oa,
                                      ctypes.c_void_p(table) if table else None, ta,
                                      ctypes.byref(opts), ctypes.c_void_p(stream)))
+
+
+def irt_update_grid(handle: int, desc: irt_grid_desc, fields: irt_fields, stream: int) -> None:
+    _check(lib.irt_update_grid(ctypes.c_void_p(handle), ctypes.byref(desc), ctypes.byref(fields),
+                               ctypes.c_void_p(stream)))

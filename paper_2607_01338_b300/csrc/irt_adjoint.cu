@@ -748,14 +748,19 @@ adj_kernel(const __grid_constant__ JobTable tab, const PhysF PF, const AdjArgs A
     __syncwarp();
 
     if (!ok) {
-      // K <= 1: the output is the background, no gradient; otherwise the ray
-      // is outside what this kernel integrates (NaN marks it)
-      const float val = (K <= 1) ? 0.0f : __int_as_float(0x7fc00000);
-      for (int k = lane; k < K; k += 32) {
-        const long long idx = ((long long)zcell(J, k) * J.ny + py) * J.nx + px;
-        A.grad[0][idx] = val;
-        A.grad[1][idx] = val;
-        A.grad[2][idx] = val;
+      if (K <= 1) {
+        // the output is the background: no gradient
+        for (int k = lane; k < K; k += 32) {
+          const long long idx = ((long long)zcell(J, k) * J.ny + py) * J.nx + px;
+          A.grad[0][idx] = 0.0f;
+          A.grad[1][idx] = 0.0f;
+          A.grad[2][idx] = 0.0f;
+        }
+      } else if (lane == 0) {
+        // every channel explicit (the ReLU may clamp the continuum, or a line
+        // window is wider than two slots): the general sweep takes the ray
+        const unsigned i = atomicAdd(A.dense, 1u);
+        A.dense[1 + i] = (unsigned)item;
       }
       __syncwarp();
       continue;
@@ -768,6 +773,378 @@ adj_kernel(const __grid_constant__ JobTable tab, const PhysF PF, const AdjArgs A
     else
       adj_dispatch<2, NI, ST>(std::integer_sequence<int, IRT_ADJ_BUCKETS2>{}, nb, RA, rec, chainf,
                               K, hb, lane, G, nfw, lamf, lx, pbuf, scr, px, py);
+    __syncwarp();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// General reverse sweep: every velocity explicit.  It differentiates what
+// the forward render computes for any ray the fast sweep above does not take:
+// oblique views (the sample partials scattered to the eight trilinear corners
+// with atomics), the formal and Kahan-compensated formal integrators (both
+// reversed as the exponential step of Sec. 4.8), f = 0, channel counts of
+// several windows, smooth rays with h alpha_D > 1/2 on some sample (the ReLU
+// may clamp the continuum) and line windows wider than 64 fine velocities.
+// One warp per ray; the lanes take 32 frequencies at a time, each running
+// its own forward recurrence with a checkpoint every 32 samples and the
+// reverse sweep segment by segment (the segment's pre-ReLU values, or the
+// formal step's incoming intensities, recomputed from the checkpoint); the
+// per-sample partials of the 32 frequencies are reduced across the warp and
+// summed over the batches in shared memory; the chain rule runs once per
+// sample at the end.  Frequencies: the fine velocities of [T] (cotangent by
+// the Simpson weights) and the channel centres of [C] (dust only).
+// ---------------------------------------------------------------------------
+constexpr int kDWarps = 2;
+constexpr int kDSeg = 32;
+
+// per-sample quantities of the dense sweep: the per-step line coefficients at
+// the profile peak (h-scaled, K units), the line centre as the nearest fine
+// index gv and the residual vr = u(gv) - v_los (so that u - v_los keeps its
+// precision on long velocity axes), 1 / b^2 (0 without a line), h alpha_D
+// and the linear dust source B(u) = bk0 + bk1 u
+struct RecA {
+  float jl, al, vr, ib2, ad, bk0, bk1;
+  int gv;
+};
+
+struct DenseArgs {
+  const float* cot[5];      // cotangent cubes T, C, D, L, B (NULL = 0)
+  float* grad[3];           // n_H2, T_gas, v_los
+  float* scratch;           // per-warp checkpoints and segment values
+  long long scratch_per_warp;   // floats
+  const unsigned* list;     // [0] = count, then ray indices; nullptr = every ray
+  int smooth;               // 1: TR + BDF2 with ReLU; 0: exponential (formal) step
+  int direct;               // 1: a cell belongs to one ray (plain stores); 0: atomics
+};
+
+__device__ __forceinline__ float warp_sum_f(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// line profile factor at fine velocity index g (the forward's window cut:
+// exp(-30))
+__device__ __forceinline__ float dense_profile(const RecA& r, const VGrid& G, int g, float* du) {
+  *du = vel_offset(G, g, r.gv, r.vr);
+  const float x2 = (*du) * (*du) * r.ib2;
+  return (r.ib2 > 0.0f && x2 <= 30.0f) ? ex2_approx(-kLog2e * x2) : 0.0f;
+}
+
+// (1 - e^-tau) / tau and its derivative (series below tau = 1e-3)
+__device__ __forceinline__ void expg(float tau, float* E, float* g, float* gp) {
+  *E = expf(-tau);
+  if (tau < 1e-3f) {
+    *g = 1.0f + tau * (-0.5f + tau * (1.0f / 6.0f - tau * (1.0f / 24.0f)));
+    *gp = -0.5f + tau * (1.0f / 3.0f - tau * (1.0f / 8.0f));
+  } else {
+    const float em = -expm1f(-tau);   // 1 - e^-tau
+    *g = em / tau;
+    *gp = (tau * (*E) - em) / (tau * tau);
+  }
+}
+
+// accumulate the partials (h alpha_D, 2h j_L, 2h alpha_L, v, b) of one
+// sample from the cotangents of its step's source term t and coefficient d
+// (smooth: t = 2 jl e + 2 ad B(u), d = 3 + 2 al e + 2 ad; formal: t = jl e +
+// ad B(u), d = tau = al e + ad)
+__device__ __forceinline__ void dense_partials(const RecA& r, float u, float e, float du,
+                                               float dt, float dd, bool smooth, float* p) {
+  const float Bu = fmaf(r.bk1, u, r.bk0);
+  const float c = smooth ? 2.0f : 1.0f;
+  p[0] = fmaf(c, dd, fmaf(c * Bu, dt, p[0]));
+  // d/d(2h j_L) and d/d(2h alpha_L): the records' jl, al are h-scaled
+  const float s = smooth ? 1.0f : 0.5f;
+  p[1] = fmaf(s * e, dt, p[1]);
+  p[2] = fmaf(s * e, dd, p[2]);
+  const float de = c * fmaf(r.jl, dt, r.al * dd);
+  const float t = 2.0f * du * r.ib2 * de * e;
+  p[3] += t;
+  p[4] = fmaf(t * du, sqrtf(r.ib2), p[4]);
+}
+
+template <int ST>
+__global__ void __launch_bounds__(kDWarps * 32)
+adj_dense_kernel(const __grid_constant__ JobTable tab, const PhysF PF, const DenseArgs A,
+                 long long total_items, unsigned long long* queue, int per_warp, int kmax) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  unsigned char* wsm = smem + (size_t)warp * per_warp;
+  const JobDev& J = tab.j[0];
+  const int nch = J.nchan;
+  const int f = J.f;
+  const int nfw = (f >= 1) ? 2 * f * nch + 1 : nch;
+  RecA* rec = reinterpret_cast<RecA*>(wsm);
+  float* P = reinterpret_cast<float*>(wsm + (size_t)kmax * sizeof(RecA));   // [K][5]
+  float* lamT = P + (size_t)kmax * 5;
+  float* lamC = lamT + nch;
+  const long long gw = (long long)blockIdx.x * kDWarps + warp;
+  float* scr = A.scratch + gw * A.scratch_per_warp;
+  const int nseg_max = (kmax + kDSeg - 1) / kDSeg;
+  float* ckp = scr;                                  // [nseg][2][32]
+  float* seg = scr + (long long)nseg_max * 2 * 32;   // [kDSeg][32]
+  const long long n_items = A.list ? (long long)A.list[0] : total_items;
+  const bool smooth = A.smooth != 0;
+  for (;;) {
+    unsigned long long t = 0;
+    if (lane == 0) t = atomicAdd(queue, 1ull);
+    const long long slot = (long long)__shfl_sync(0xffffffffu, t, 0);
+    if (slot >= n_items) break;
+    const long long item = A.list ? (long long)A.list[1 + slot] : slot;
+    const int px = (int)(item % J.npx), py = (int)(item / J.npx);
+    const RayGeom geo = ray_geom(J, px, py);
+    const int K = geo.K;
+    if (K <= 0) continue;   // a ray missing the box has no gradient
+    const float h = (float)geo.h;
+    RayPos rp;
+    if (!J.zview) rp = ray_pos(J, geo);
+    VGrid G;
+    G.ufw_hi = (float)J.ufirst;
+    G.ufw_lo = (float)(J.ufirst - (double)G.ufw_hi);
+    G.dvf_hi = (float)J.dvf;
+    G.dvf_lo = (float)(J.dvf - (double)G.dvf_hi);
+    // ---- per-sample quantities
+    for (int k = lane; k < K; k += 32) {
+      float raw[6];
+      sample_raw<ST>(J, rp, px, py, k, raw);
+      float jl, al, b, bk0, bk1;
+      line_coeffs<false>(PF, raw[0], raw[1], raw[4], 0.5f, h, &jl, &al, &b);
+      dust_source_lin(PF, raw[2], &bk0, &bk1);
+      RecA r;
+      r.jl = jl;
+      r.al = al;
+      centre_offset(G, raw[3], &r.gv, &r.vr);
+      r.ib2 = (jl != 0.0f || al != 0.0f) ? 1.0f / (b * b) : 0.0f;
+      r.ad = PF.cad * raw[0] * h;
+      r.bk0 = bk0;
+      r.bk1 = bk1;
+      rec[k] = r;
+#pragma unroll
+      for (int q = 0; q < 5; ++q) P[k * 5 + q] = 0.0f;
+    }
+    // ---- channel cotangents of [T] (through the Simpson weights) and [C]
+    const long long plane = (long long)J.npx * J.npy;
+    const long long pix = (long long)py * J.npx + px;
+    for (int c = lane; c < nch; c += 32) {
+      const long long o = (long long)c * plane + pix;
+      const float gT = A.cot[0] ? A.cot[0][o] : 0.0f;
+      const float gC = A.cot[1] ? A.cot[1][o] : 0.0f;
+      const float gD = A.cot[2] ? A.cot[2][o] : 0.0f;
+      const float gL = A.cot[3] ? A.cot[3][o] : 0.0f;
+      const float uc = (float)J.v0 + ((float)c + 0.5f) * (float)J.dv;
+      float s = PF.out_scale;
+      if (PF.units == IRT_UNITS_TRJ) {
+        const float y = 1.0f - uc * PF.inv_c_kms;
+        s = s / (y * y);
+      }
+      lamT[c] = s * (gT + gL);
+      lamC[c] = s * (gC - gL + gD);
+    }
+    __syncwarp();
+    const int nseg = (K + kDSeg - 1) / kDSeg;
+    const int nfreq = nfw + nch;
+    for (int b0 = 0; b0 < nfreq; b0 += 32) {
+      const int phi = b0 + lane;
+      const bool kindT = phi < nfw;
+      float u, lend = 0.0f;
+      int gphi = phi;   // fine index of the frequency (line profile offsets)
+      if (kindT) {
+        u = fmaf((float)phi, G.dvf_hi, G.ufw_hi);
+        lend = (f >= 1) ? fine_cotangent(phi, f, nch, lamT) : lamT[phi];
+      } else {
+        const int c = min(phi - nfw, nch - 1);
+        u = (float)J.v0 + ((float)c + 0.5f) * (float)J.dv;
+        gphi = (f >= 1) ? 2 * f * c + f : c;
+        if (phi < nfreq) lend = lamC[c];
+      }
+      if (__all_sync(0xffffffffu, lend == 0.0f)) continue;
+      const float I0 = planck_k(PF, PF.t_bg, u);
+      // coefficients of sample n at this lane's frequency
+      auto coeff = [&](int n, float* tt, float* dd, float* e, float* du) {
+        const RecA r = rec[n];
+        *e = kindT ? dense_profile(r, G, gphi, du) : 0.0f;
+        if (!kindT) *du = 0.0f;
+        const float Bu = fmaf(r.bk1, u, r.bk0);
+        if (smooth) {
+          *tt = 2.0f * fmaf(r.jl, *e, r.ad * Bu);
+          *dd = 3.0f + 2.0f * fmaf(r.al, *e, r.ad);
+        } else {
+          *tt = fmaf(r.jl, *e, r.ad * Bu);
+          *dd = fmaf(r.al, *e, r.ad);
+        }
+      };
+      // ---- forward with checkpoints at samples 32 s (s >= 1)
+      if (smooth) {
+        if (K >= 2) {
+          float t0, d0, t1, d1, e, du;
+          coeff(0, &t0, &d0, &e, &du);
+          coeff(1, &t1, &d1, &e, &du);
+          float a = I0, b = fmaxf((t0 + t1 + (7.0f - d0) * I0) / (1.0f + d1), 0.0f);
+          for (int n = 2; n < K; ++n) {
+            if ((n & (kDSeg - 1)) == 0) {
+              ckp[(n / kDSeg) * 64 + lane] = a;
+              ckp[(n / kDSeg) * 64 + 32 + lane] = b;
+            }
+            float tn, dn;
+            coeff(n, &tn, &dn, &e, &du);
+            const float c = fmaxf((tn + 4.0f * b - a) / dn, 0.0f);
+            a = b;
+            b = c;
+          }
+        }
+      } else {
+        float I = I0;
+        for (int n = 0; n < K; ++n) {
+          if ((n & (kDSeg - 1)) == 0 && n > 0) ckp[(n / kDSeg) * 64 + lane] = I;
+          float tn, dn, e, du, E, g, gp;
+          coeff(n, &tn, &dn, &e, &du);
+          expg(dn, &E, &g, &gp);
+          I = fmaf(I, E, tn * g);
+        }
+      }
+      // ---- reverse sweep, segment by segment
+      float ln = lend, lm = 0.0f;   // smooth: lambda_n and the pending part of lambda_{n-1}
+      for (int s = nseg - 1; s >= 0; --s) {
+        const int lo = s * kDSeg, hi = min(lo + kDSeg, K);
+        // recompute the segment: smooth stores pre_n, formal the intensity
+        // entering step n
+        if (smooth) {
+          float a, b;
+          int n0;
+          if (s == 0) {
+            if (K < 2) break;
+            float t0, d0, t1, d1, e, du;
+            coeff(0, &t0, &d0, &e, &du);
+            coeff(1, &t1, &d1, &e, &du);
+            const float pre1 = (t0 + t1 + (7.0f - d0) * I0) / (1.0f + d1);
+            seg[1 * 32 + lane] = pre1;
+            a = I0;
+            b = fmaxf(pre1, 0.0f);
+            n0 = 2;
+          } else {
+            a = ckp[s * 64 + lane];
+            b = ckp[s * 64 + 32 + lane];
+            n0 = lo;
+          }
+          for (int n = n0; n < hi; ++n) {
+            float tn, dn, e, du;
+            coeff(n, &tn, &dn, &e, &du);
+            const float pre = (tn + 4.0f * b - a) / dn;
+            seg[(n - lo) * 32 + lane] = pre;
+            a = b;
+            b = fmaxf(pre, 0.0f);
+          }
+        } else {
+          float I = (s == 0) ? I0 : ckp[s * 64 + lane];
+          for (int n = lo; n < hi; ++n) {
+            seg[(n - lo) * 32 + lane] = I;
+            float tn, dn, e, du, E, g, gp;
+            coeff(n, &tn, &dn, &e, &du);
+            expg(dn, &E, &g, &gp);
+            I = fmaf(I, E, tn * g);
+          }
+        }
+        for (int n = hi - 1; n >= lo; --n) {
+          float p[5] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+          float p0[5] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+          bool has0 = false;
+          if (smooth) {
+            if (n == 0) break;
+            const float pre = seg[(n - lo) * 32 + lane];
+            const float mu = (pre >= 0.0f) ? ln : 0.0f;
+            float tn, dn, e, du;
+            coeff(n, &tn, &dn, &e, &du);
+            if (n >= 2) {
+              const float q = mu / dn;
+              dense_partials(rec[n], u, e, du, q, -q * pre, true, p);
+              ln = fmaf(4.0f, q, lm);
+              lm = -q;
+            } else {
+              // trapezoidal step: pre_1 = (t_0 + t_1 + (7 - d_0) I_0) / (1 + d_1)
+              const float q = mu / (1.0f + dn);
+              dense_partials(rec[1], u, e, du, q, -q * pre, true, p);
+              float t0, d0, e0, du0;
+              coeff(0, &t0, &d0, &e0, &du0);
+              dense_partials(rec[0], u, e0, du0, q, -q * I0, true, p0);
+              has0 = true;
+            }
+          } else {
+            const float Iin = seg[(n - lo) * 32 + lane];
+            float tn, dn, e, du, E, g, gp;
+            coeff(n, &tn, &dn, &e, &du);
+            expg(dn, &E, &g, &gp);
+            const float dt = ln * g;
+            const float dd = ln * fmaf(-Iin, E, tn * gp);
+            dense_partials(rec[n], u, e, du, dt, dd, false, p);
+            ln *= E;
+          }
+#pragma unroll
+          for (int q = 0; q < 5; ++q) {
+            const float v = warp_sum_f(p[q]);
+            if (lane == 0) P[n * 5 + q] += v;
+          }
+          if (has0) {
+#pragma unroll
+            for (int q = 0; q < 5; ++q) {
+              const float v = warp_sum_f(p0[q]);
+              if (lane == 0) P[q] += v;
+            }
+          }
+        }
+      }
+      __syncwarp();
+    }
+    __syncwarp();
+    // ---- chain rule and the gradients of the cells
+    for (int k = lane; k < K; k += 32) {
+      float raw[6];
+      sample_raw<ST>(J, rp, px, py, k, raw);
+      float gn, gt, gv;
+      chain(PF, raw, h, P + k * 5, &gn, &gt, &gv);
+      if (J.zview) {
+        const long long idx = ((long long)zcell(J, k) * J.ny + py) * J.nx + px;
+        if (A.direct) {
+          A.grad[0][idx] = gn;
+          A.grad[1][idx] = gt;
+          A.grad[2][idx] = gv;
+        } else {
+          atomicAdd(A.grad[0] + idx, gn);
+          atomicAdd(A.grad[1] + idx, gt);
+          atomicAdd(A.grad[2] + idx, gv);
+        }
+        continue;
+      }
+      // oblique: the sample is the trilinear blend of eight cells (indices
+      // clamped to the grid), so each takes its weight of the sample's partials
+      int i0[3];
+      float w[3];
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        const long long pp = rp.base[a] + (long long)k * rp.step[a];
+        i0[a] = (int)(pp >> 32);
+        w[a] = (float)(unsigned)(pp & 0xFFFFFFFFll) * 2.3283064365386963e-10f;
+      }
+      const int nn[3] = {J.nx, J.ny, J.nz};
+      int lo3[3], hi3[3];
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        lo3[a] = min(max(i0[a], 0), nn[a] - 1);
+        hi3[a] = min(max(i0[a] + 1, 0), nn[a] - 1);
+      }
+#pragma unroll
+      for (int c = 0; c < 8; ++c) {
+        const int ix = (c & 1) ? hi3[0] : lo3[0];
+        const int iy = (c & 2) ? hi3[1] : lo3[1];
+        const int iz = (c & 4) ? hi3[2] : lo3[2];
+        const float ww = ((c & 1) ? w[0] : 1.0f - w[0]) * ((c & 2) ? w[1] : 1.0f - w[1]) *
+                         ((c & 4) ? w[2] : 1.0f - w[2]);
+        const long long idx = ((long long)iz * J.ny + iy) * J.nx + ix;
+        atomicAdd(A.grad[0] + idx, ww * gn);
+        atomicAdd(A.grad[1] + idx, ww * gt);
+        atomicAdd(A.grad[2] + idx, ww * gv);
+      }
+    }
     __syncwarp();
   }
 }
@@ -804,6 +1181,57 @@ int launch_adjoint(int store, int ni, const JobTable& tab, const PhysF& PF, cons
   IRT_LAUNCH(9, ST_F32) IRT_LAUNCH(17, ST_F32) IRT_LAUNCH(33, ST_F32)
   IRT_LAUNCH(9, ST_H16) IRT_LAUNCH(17, ST_H16) IRT_LAUNCH(33, ST_H16)
 #undef IRT_LAUNCH
+  return (int)cudaErrorInvalidValue;
+}
+
+// Host launcher of the general reverse sweep: per-warp shared memory for
+// the records of the longest ray, their partials and the channel
+// cotangents; per-warp scratch for the checkpoints and one segment.
+size_t adjoint_dense_smem_per_warp(int kmax, int nchan) {
+  return (((size_t)kmax * (sizeof(dev::RecA) + 5 * sizeof(float)) + 8 * (size_t)nchan) + 15) &
+         ~(size_t)15;
+}
+long long adjoint_dense_scratch_per_warp(int kmax) {
+  const long long nseg = (kmax + dev::kDSeg - 1) / dev::kDSeg;
+  return nseg * 2 * 32 + (long long)dev::kDSeg * 32;
+}
+
+int launch_adjoint_dense(int store, const JobTable& tab, const PhysF& PF, float* const grad[3],
+                         const float* const cot[5], float* scratch, long long scratch_per_warp,
+                         const unsigned* list, int smooth, int direct, long long total_items,
+                         unsigned long long* queue, int kmax, int nchan, int* blocks_out,
+                         cudaStream_t stream) {
+  const size_t per_warp = adjoint_dense_smem_per_warp(kmax, nchan);
+  const size_t smem = per_warp * dev::kDWarps;
+  dev::DenseArgs A;
+  for (int q = 0; q < 5; ++q) A.cot[q] = cot[q];
+  for (int q = 0; q < 3; ++q) A.grad[q] = grad[q];
+  A.scratch = scratch;
+  A.scratch_per_warp = scratch_per_warp;
+  A.list = list;
+  A.smooth = smooth;
+  A.direct = direct;
+#define IRT_DENSE(ST_)                                                                        \
+  if (store == ST_) {                                                                         \
+    auto kern = dev::adj_dense_kernel<ST_>;                                                   \
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,   \
+                                         (int)smem);                                          \
+    if (e != cudaSuccess) return (int)e;                                                      \
+    int per_sm = 0, dev = 0, sms = 0;                                                         \
+    cudaGetDevice(&dev);                                                                      \
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);                        \
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, dev::kDWarps * 32, smem);    \
+    const int blocks = std::max(per_sm, 1) * sms;                                             \
+    if (blocks_out) {                                                                         \
+      *blocks_out = blocks;                                                                   \
+      return 0;                                                                               \
+    }                                                                                         \
+    kern<<<blocks, dev::kDWarps * 32, smem, stream>>>(tab, PF, A, total_items, queue,         \
+                                                      (int)per_warp, kmax);                   \
+    return (int)cudaGetLastError();                                                           \
+  }
+  IRT_DENSE(ST_F32) IRT_DENSE(ST_H16)
+#undef IRT_DENSE
   return (int)cudaErrorInvalidValue;
 }
 

@@ -43,6 +43,13 @@ int launch_adjoint(int store, int ni, const JobTable& tab, const PhysF& PF, cons
                    long long total_items, unsigned long long* queue, int blocks, int kmax,
                    int nfw, int nchan, cudaStream_t stream, int* per_warp_smem);
 int adjoint_blocks_per_sm(int store, int ni, size_t smem);
+size_t adjoint_dense_smem_per_warp(int kmax, int nchan);
+long long adjoint_dense_scratch_per_warp(int kmax);
+int launch_adjoint_dense(int store, const JobTable& tab, const PhysF& PF, float* const grad[3],
+                         const float* const cot[5], float* scratch, long long scratch_per_warp,
+                         const unsigned* list, int smooth, int direct, long long total_items,
+                         unsigned long long* queue, int kmax, int nchan, int* blocks_out,
+                         cudaStream_t stream);
 int dispatch_fwd_f64(int mode, int store, int ni, const JobTable& jobs, int njobs,
                      const PhysParams& P, const PhysF& PF, const FwdLaunch& L, cudaStream_t s);
 int dispatch_fwd_ml_smooth(int store, int ni, const JobTable& jobs, int njobs,
@@ -211,6 +218,43 @@ irt_status irt_create_grid(const irt_grid_desc* desc, const irt_fields* fields,
     return cuda_fail(e, "irt_create_grid: pack kernel");
   }
   *out = g;
+  return IRT_OK;
+}
+
+irt_status irt_update_grid(irt_grid* g, const irt_grid_desc* desc, const irt_fields* fields,
+                           void* cuda_stream) {
+  g_err.clear();
+  if (!g || !desc || !fields) return fail(IRT_EINVAL, "irt_update_grid: NULL argument");
+  if (desc->nx != g->nx || desc->ny != g->ny || desc->nz != g->nz || desc->cell_cm != g->dx)
+    return fail(IRT_EINVAL, "irt_update_grid: size or cell differs from the grid's");
+  const void* src[5] = {fields->n_h2_cm3, fields->t_gas_k, fields->t_dust_k, fields->v_los_kms,
+                        fields->x_tracer};
+  int dt[5];
+  bool any64 = false, all16 = true;
+  int bf_mask = 0;
+  double scale[5];
+  for (int q = 0; q < 5; ++q) {
+    if (!src[q]) return fail(IRT_EINVAL, "irt_update_grid: field %d is NULL", q);
+    dt[q] = (int)desc->dtype[q];
+    if (dt[q] < IRT_F32 || dt[q] > IRT_F64)
+      return fail(IRT_EINVAL, "irt_update_grid: field %d has unknown dtype %d", q, dt[q]);
+    if (dt[q] == IRT_F64) any64 = true;
+    if (dt[q] != IRT_F16 && dt[q] != IRT_BF16) all16 = false;
+    if (dt[q] == IRT_BF16) bf_mask |= 1 << q;
+    scale[q] = desc->scale[q] == 0.0 ? 1.0 : desc->scale[q];
+    if (!std::isfinite(scale[q]) || scale[q] <= 0.0)
+      return fail(IRT_EINVAL, "irt_update_grid: scale[%d] must be finite and > 0", q);
+  }
+  const int store = any64 ? ST_F64 : (all16 ? ST_H16 : ST_F32);
+  if (store != g->store || (store == ST_H16 && (bf_mask != g->bf16_mask ||
+                                                 std::memcmp(scale, g->scale, sizeof scale))))
+    return fail(IRT_EINVAL, "irt_update_grid: field storage differs from the grid's");
+  // new field values: checkpoints of earlier renders no longer apply
+  g->ck_sig = 0;
+  const long long ncell = (long long)g->nx * g->ny * g->nz;
+  const int e = launch_pack(store, src, dt, scale, g->cells, ncell, cuda_stream);
+  ++g_launches;
+  if (e) return cuda_fail(e, "irt_update_grid: pack kernel");
   return IRT_OK;
 }
 
@@ -1403,93 +1447,135 @@ extern "C" irt_status irt_adjoint_ppv(const irt_job* job, const irt_line* line,
   if (st) return st;
   if (opts->precision != IRT_PREC_F32)
     return fail(IRT_EUNSUPPORTED, "irt_adjoint_ppv: float precision only");
-  if (opts->integration != IRT_SMOOTH)
-    return fail(IRT_EUNSUPPORTED, "irt_adjoint_ppv: smooth integration only");
-  if (jb.view.trilinear == 1)
-    return fail(IRT_EUNSUPPORTED, "irt_adjoint_ppv: z or radial view only");
-  if (jb.vaxis.subsample_f < 1) return fail(IRT_EUNSUPPORTED, "irt_adjoint_ppv: needs f >= 1");
   irt_grid* g = jb.grid;
   if (g->store == ST_F64)
     return fail(IRT_EUNSUPPORTED, "irt_adjoint_ppv: float or 16-bit field storage only");
   const Plan p = plan_job(jb, IRT_PREC_F32, 0);
-  if (p.nwin != 1)
-    return fail(IRT_EUNSUPPORTED,
-                "irt_adjoint_ppv: %d channels at f = %d need %d channel windows (one supported)",
-                jb.vaxis.nchan, jb.vaxis.subsample_f, p.nwin);
   const PhysParams P = fold_constants(line, dust, opts);
   const PhysF PF = to_float(P);
   cudaStream_t s = (cudaStream_t)cuda_stream;
-
-  // shared memory per warp and persistent grid size
-  int per_warp = 0;
+  const int nch = jb.vaxis.nchan;
+  // the general sweep's shared memory (records, partials, channel cotangents)
+  const size_t dense_smem = adjoint_dense_smem_per_warp(p.kmax, nch);
+  if (dense_smem > 110 * 1024)
+    return fail(IRT_EUNSUPPORTED, "irt_adjoint_ppv: rays of %d samples with %d channels need "
+                                  "%zu bytes of shared memory per warp (at most 112640)",
+                p.kmax, nch, dense_smem);
+  // the fast sweep (hull blocks in registers, continuum basis) takes z- and
+  // radial-view smooth jobs of one channel window; every other job, and the
+  // rays of a fast job that it cannot take, go to the general sweep
+  const bool fast = jb.view.trilinear != 1 && opts->integration == IRT_SMOOTH &&
+                    jb.vaxis.subsample_f >= 1 && p.nwin == 1;
   JobTable tab;
   std::memset(&tab, 0, sizeof tab);
   tab.j[0] = make_jobdev(jb, p);
-  AdjArgs A;
-  std::memset(&A, 0, sizeof A);
+  const float* cot[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
   if (cotangent) {
-    A.cot[0] = (const float*)cotangent->T;
-    A.cot[1] = (const float*)cotangent->C;
-    A.cot[2] = (const float*)cotangent->D;
-    A.cot[3] = (const float*)cotangent->L;
-    A.cot[4] = (const float*)cotangent->B;
+    cot[0] = (const float*)cotangent->T;
+    cot[1] = (const float*)cotangent->C;
+    cot[2] = (const float*)cotangent->D;
+    cot[3] = (const float*)cotangent->L;
+    cot[4] = (const float*)cotangent->B;
   }
-  A.grad[0] = grad_n_h2;
-  A.grad[1] = grad_t_gas;
-  A.grad[2] = grad_v_los;
-  // pass 0 runs with 9 register blocks (128 registers, 16 warps per SM) and
-  // defers the rays with wider hulls to pass 1 with the job's full width
-  const int ni0 = 9;
-  const int ni1 = p.ni > ni0 ? p.ni : 0;
-  int e = launch_adjoint(g->store, ni0, tab, PF, A, 0, nullptr, 0, p.kmax, p.nfw,
-                         jb.vaxis.nchan, s, &per_warp);
-  if (e) return cuda_fail(e, "irt_adjoint_ppv: kernel attributes");
-  const size_t smem = (size_t)per_warp * kAdjWarps;
+  float* grads[3] = {grad_n_h2, grad_t_gas, grad_v_los};
+  const long long total = (long long)jb.view.npx * jb.view.npy;
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const int blocks0 = std::max(1, adjoint_blocks_per_sm(g->store, ni0, smem)) * sms;
-  const int blocks1 = ni1 ? std::max(1, adjoint_blocks_per_sm(g->store, ni1, smem)) * sms : 0;
+
+  // scratch of this stream: the fast sweep's per-warp buffers, the general
+  // sweep's, and the lists (deferred wide rays, general rays, the general
+  // sweep's queue counter)
+  int blocks_d = 0;
+  int e = launch_adjoint_dense(g->store, tab, PF, grads, cot, nullptr, 0, nullptr, 1, 1, 0,
+                               nullptr, p.kmax, nch, &blocks_d, s);
+  if (e) return cuda_fail(e, "irt_adjoint_ppv: general sweep attributes");
+  const long long dense_floats = (adjoint_dense_scratch_per_warp(p.kmax) + 63) & ~63ll;
+  size_t need = (size_t)blocks_d * 2 * (size_t)dense_floats * sizeof(float);
+  int per_warp = 0, blocks0 = 0, blocks1 = 0, ni1 = 0;
+  const int ni0 = 9;
+  long long per_warp_floats = 0;
   const int nseg = (p.kmax + kAdjSeg - 1) / kAdjSeg;
-  // checkpoints, one stored sub-segment, the per-sample chain-rule factors
-  const int nb_alloc = std::max(ni0, ni1) + 1;
-  long long per_warp_floats =
-      (long long)(2 * nseg + kAdjSub) * nb_alloc * 32 + (long long)kAdjChain * p.kmax;
-  per_warp_floats = (per_warp_floats + 63) & ~63ll;
-  const size_t need =
-      (size_t)std::max(blocks0, blocks1) * kAdjWarps * (size_t)per_warp_floats * sizeof(float);
-  const long long total = (long long)jb.view.npx * jb.view.npy;
-  const size_t defer_need = (size_t)(total + 1) * sizeof(unsigned);
+  AdjArgs A;
+  std::memset(&A, 0, sizeof A);
+  if (fast) {
+    for (int q = 0; q < 5; ++q) A.cot[q] = cot[q];
+    for (int q = 0; q < 3; ++q) A.grad[q] = grads[q];
+    // pass 0 runs with 9 register blocks (128 registers, 16 warps per SM) and
+    // defers the rays with wider hulls to pass 1 with the job's full width
+    ni1 = p.ni > ni0 ? p.ni : 0;
+    e = launch_adjoint(g->store, ni0, tab, PF, A, 0, nullptr, 0, p.kmax, p.nfw, nch, s,
+                       &per_warp);
+    if (e) return cuda_fail(e, "irt_adjoint_ppv: kernel attributes");
+    const size_t smem = (size_t)per_warp * kAdjWarps;
+    blocks0 = std::max(1, adjoint_blocks_per_sm(g->store, ni0, smem)) * sms;
+    blocks1 = ni1 ? std::max(1, adjoint_blocks_per_sm(g->store, ni1, smem)) * sms : 0;
+    // checkpoints, one stored sub-segment, the per-sample chain-rule factors
+    const int nb_alloc = std::max(ni0, ni1) + 1;
+    per_warp_floats =
+        (long long)(2 * nseg + kAdjSub) * nb_alloc * 32 + (long long)kAdjChain * p.kmax;
+    per_warp_floats = (per_warp_floats + 63) & ~63ll;
+    need = std::max(need, (size_t)std::max(blocks0, blocks1) * kAdjWarps *
+                              (size_t)per_warp_floats * sizeof(float));
+  }
+  // lists: [0] deferred count, deferred rays; [total + 1] general count,
+  // general rays; then the general sweep's queue counter (8-byte aligned)
+  const size_t list_words = 2 * (size_t)(total + 1);
+  const size_t queue_off = ((list_words * sizeof(unsigned)) + 7) & ~(size_t)7;
+  const size_t defer_need = queue_off + sizeof(unsigned long long);
   StreamScratch& ss = stream_scratch(s);
   irt_status gs = grow(&ss.adj, &ss.adj_bytes, need, s, "irt_adjoint_ppv");
   if (!gs) gs = grow(&ss.defer, &ss.defer_bytes, defer_need, s, "irt_adjoint_ppv");
   if (gs) return gs;
-  A.scratch = reinterpret_cast<float*>(ss.adj);
-  A.scratch_per_warp = per_warp_floats;
-  A.defer = reinterpret_cast<unsigned*>(ss.defer);
-  A.defer_max_nb = ni1;
-  if (g->ck && g->ck_sig == checkpoint_signature(jb, P)) {
-    A.ck_saved = g->ck;
-    A.ck_nb = kCkRows;
-    A.ck_ray = (long long)nseg * 2 * kCkRows * 32;
-  }
-  // control words: [0] pass-0 queue, [7] pass-1 queue; defer[0] = 0
-  cudaError_t ce = cudaMemsetAsync(g->ctl, 0, sizeof(unsigned long long), s);
-  if (ce == cudaSuccess) ce = cudaMemsetAsync(g->ctl + 7, 0, sizeof(unsigned long long), s);
-  if (ce == cudaSuccess) ce = cudaMemsetAsync(A.defer, 0, sizeof(unsigned), s);
+  unsigned* defer = reinterpret_cast<unsigned*>(ss.defer);
+  unsigned* dense_list = defer + (total + 1);
+  unsigned long long* dense_queue = reinterpret_cast<unsigned long long*>(ss.defer + queue_off);
+  cudaError_t ce = cudaMemsetAsync(dense_queue, 0, sizeof(unsigned long long), s);
+  if (ce == cudaSuccess) ce = cudaMemsetAsync(dense_list, 0, sizeof(unsigned), s);
   if (ce != cudaSuccess) return cuda_fail(ce, "irt_adjoint_ppv: queue reset");
-  A.pass = 0;
-  e = launch_adjoint(g->store, ni0, tab, PF, A, total, g->ctl, blocks0, p.kmax, p.nfw,
-                     jb.vaxis.nchan, s, nullptr);
-  ++g_launches;
-  if (e) return cuda_fail(e, "irt_adjoint_ppv: adjoint kernel");
-  if (ni1) {
-    A.pass = 1;
-    e = launch_adjoint(g->store, ni1, tab, PF, A, total, g->ctl + 7, blocks1, p.kmax, p.nfw,
-                       jb.vaxis.nchan, s, nullptr);
+  if (fast) {
+    A.scratch = reinterpret_cast<float*>(ss.adj);
+    A.scratch_per_warp = per_warp_floats;
+    A.defer = defer;
+    A.dense = dense_list;
+    A.defer_max_nb = ni1;
+    if (g->ck && g->ck_sig == checkpoint_signature(jb, P)) {
+      A.ck_saved = g->ck;
+      A.ck_nb = kCkRows;
+      A.ck_ray = (long long)nseg * 2 * kCkRows * 32;
+    }
+    // control words: [0] pass-0 queue, [7] pass-1 queue; defer[0] = 0
+    ce = cudaMemsetAsync(g->ctl, 0, sizeof(unsigned long long), s);
+    if (ce == cudaSuccess) ce = cudaMemsetAsync(g->ctl + 7, 0, sizeof(unsigned long long), s);
+    if (ce == cudaSuccess) ce = cudaMemsetAsync(A.defer, 0, sizeof(unsigned), s);
+    if (ce != cudaSuccess) return cuda_fail(ce, "irt_adjoint_ppv: queue reset");
+    A.pass = 0;
+    e = launch_adjoint(g->store, ni0, tab, PF, A, total, g->ctl, blocks0, p.kmax, p.nfw, nch, s,
+                       nullptr);
     ++g_launches;
+    if (e) return cuda_fail(e, "irt_adjoint_ppv: adjoint kernel");
+    if (ni1) {
+      A.pass = 1;
+      e = launch_adjoint(g->store, ni1, tab, PF, A, total, g->ctl + 7, blocks1, p.kmax, p.nfw,
+                         nch, s, nullptr);
+      ++g_launches;
+      if (e) return cuda_fail(e, "irt_adjoint_ppv: adjoint kernel");
+    }
+  } else if (jb.view.trilinear == 1) {
+    // oblique views: every ray adds into the cells of its samples' stencils
+    const size_t cb = (size_t)g->nx * g->ny * g->nz * sizeof(float);
+    for (int q = 0; q < 3 && ce == cudaSuccess; ++q) ce = cudaMemsetAsync(grads[q], 0, cb, s);
+    if (ce != cudaSuccess) return cuda_fail(ce, "irt_adjoint_ppv: clear gradients");
   }
-  if (e) return cuda_fail(e, "irt_adjoint_ppv: adjoint kernel");
+  // the general sweep: the fast job's leftover rays (a list filled on the
+  // device), or every ray of the job
+  e = launch_adjoint_dense(g->store, tab, PF, grads, cot, reinterpret_cast<float*>(ss.adj),
+                           dense_floats, fast ? dense_list : nullptr,
+                           opts->integration == IRT_SMOOTH ? 1 : 0,
+                           jb.view.trilinear != 1 ? 1 : 0, total, dense_queue, p.kmax, nch,
+                           nullptr, s);
+  ++g_launches;
+  if (e) return cuda_fail(e, "irt_adjoint_ppv: general sweep");
   return IRT_OK;
 }
 

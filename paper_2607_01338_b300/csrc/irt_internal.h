@@ -177,6 +177,7 @@ struct AdjArgs {
   int pass;                     // 0: every ray, wide hulls deferred; 1: the deferred rays
   int defer_max_nb;             // widest hull bucket the second pass handles (0: none)
   unsigned* defer;              // [0] = count, then deferred ray indices
+  unsigned* dense;              // [0] = count, then the rays the general sweep takes
 };
 
 // Job table passed to the kernels by value (__grid_constant__ parameter).

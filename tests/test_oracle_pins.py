@@ -506,3 +506,72 @@ def test_dual_gradient_matches_central_differences(mode):
             fields[q][z, y, x] = v0
             fd = (vals[0] - vals[1]) / (2 * eps) / target.size
             assert g[z, y, x] == pytest.approx(fd, rel=1e-5, abs=1e-9 * abs(g).max())
+
+
+# ----------------------------------------------------------------------------
+# gradients of any view: dual numbers through the stencils of the samples
+# ----------------------------------------------------------------------------
+def _grad_problem(n=7, seed=21, nch=14):
+    fs = make_fields(n, seed)
+    fields = fs.as_tuple()
+    tgt_f = make_fields(n, seed + 7).as_tuple()
+    dx = 3.0856775814913673e17
+    va = VelocityAxis(nch, -42.0, 6.0, 1)
+    return fields, tgt_f, dx, va
+
+
+def _loss(fields, dx, view, va, target, integration):
+    cube = oracle.render_cube(fields, dx, LINE, DUST, view, va, integration=integration)["L"]
+    return float(np.mean((cube - target) ** 2))
+
+
+@pytest.mark.parametrize("integration", [oracle.SMOOTH, oracle.FORMAL])
+def test_gradient_of_any_view_equals_central_differences(integration):
+    """Oblique (30, 45) deg and radial views: the dual-number gradient at
+    seeded cells equals FP64 central differences of the primal loss (every
+    pixel re-rendered), to the difference's own accuracy."""
+    fields, tgt_f, dx, va = _grad_problem()
+    n = fields[0].shape[0]
+    rng = np.random.default_rng(5)
+    cells = np.stack([rng.integers(1, n - 1, 6), rng.integers(1, n - 1, 6),
+                      rng.integers(1, n - 1, 6)], axis=1)
+    for view in (View(math.radians(30), math.radians(45), 9, 8, 0.9 * dx, 1),
+                 View(0.0, 0.0, n, n, dx, 2)):
+        target = oracle.render_cube(tgt_f, dx, LINE, DUST, view, va,
+                                    integration=integration)["L"]
+        loss, gn, gt, gv = oracle.loss_grad_cells(fields, dx, LINE, DUST, view, va, target,
+                                                  cells, integration=integration)
+        assert loss == pytest.approx(_loss(fields, dx, view, va, target, integration),
+                                     rel=1e-12)
+        work = [a.copy() for a in fields]
+        for q, g in ((0, gn), (1, gt), (3, gv)):
+            for i, (x, y, z) in enumerate(cells):
+                v0 = work[q][z, y, x]
+                eps = 1e-5 * max(abs(v0), 1.0)
+                work[q][z, y, x] = v0 + eps
+                lp = _loss(work, dx, view, va, target, integration)
+                work[q][z, y, x] = v0 - eps
+                lm = _loss(work, dx, view, va, target, integration)
+                work[q][z, y, x] = v0
+                fd = (lp - lm) / (2 * eps)
+                # central-difference error: truncation eps^2 f'''/6 and the
+                # rounding of two loss evaluations (~1e-15 loss / eps)
+                tol = 1e-6 * abs(fd) + 1e-14 * loss / eps + 1e-9 * np.abs(g).max()
+                assert abs(g[i] - fd) <= tol, (view.trilinear, q, i, g[i], fd)
+
+
+def test_gradient_of_cells_equals_the_column_gradient_on_the_z_view():
+    """On the z view the stencil-seeded gradient reduces to the column
+    gradient of the (separately pinned) z-view dual-number oracle."""
+    fields, tgt_f, dx, va = _grad_problem()
+    n = fields[0].shape[0]
+    view = View(0.0, 0.0, n, n, dx, 0)
+    target = oracle.render_cube(tgt_f, dx, LINE, DUST, view, va)["L"]
+    loss, gn, gt, gv = oracle.loss_grad_zview(fields, dx, LINE, DUST, va, target)
+    cells = np.array([[1, 2, 3], [4, 0, 6], [6, 6, 0], [3, 3, 3]])
+    loss2, cn, ct, cv = oracle.loss_grad_cells(fields, dx, LINE, DUST, view, va, target, cells)
+    assert loss2 == pytest.approx(loss, rel=1e-13)
+    for i, (x, y, z) in enumerate(cells):
+        assert cn[i] == pytest.approx(gn[z, y, x], rel=1e-11)
+        assert ct[i] == pytest.approx(gt[z, y, x], rel=1e-11)
+        assert cv[i] == pytest.approx(gv[z, y, x], rel=1e-11, abs=1e-30)
