@@ -1170,6 +1170,25 @@ extern "C" irt_status irt_create_ot_table(const irt_level_model* m, const irt_ot
           return fail(IRT_EINVAL, "irt_create_ot_table: negative or non-finite rate");
     }
   }
+  {
+    // each level pair once per partner and once among the radiative
+    // transitions (the build kernel adds each transition's rates in place)
+    std::vector<unsigned char> seen((size_t)n * n);
+    for (int p = 0; p < np && nc > 0; ++p) {
+      std::fill(seen.begin(), seen.end(), 0);
+      for (int c = 0; c < nc; ++c) {
+        unsigned char& f = seen[(size_t)m->coll_up[p * nc + c] * n + m->coll_lo[p * nc + c]];
+        if (f) return fail(IRT_EINVAL, "irt_create_ot_table: partner %d lists a level pair twice", p);
+        f = 1;
+      }
+    }
+    std::fill(seen.begin(), seen.end(), 0);
+    for (int r = 0; r < m->nrad; ++r) {
+      unsigned char& f = seen[(size_t)m->rad_up[r] * n + m->rad_lo[r]];
+      if (f) return fail(IRT_EINVAL, "irt_create_ot_table: a radiative level pair is listed twice");
+      f = 1;
+    }
+  }
   if (!finite_nonneg(m->t_rad_k) || !finite_nonneg(m->ortho_para) || !finite_nonneg(m->x_he))
     return fail(IRT_EINVAL, "irt_create_ot_table: t_rad_k, ortho_para and x_he must be >= 0");
   const int na[3] = {ax->n_n, ax->n_chi, ax->n_t};

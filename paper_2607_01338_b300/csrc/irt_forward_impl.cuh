@@ -958,12 +958,15 @@ __device__ void render_ray(const JobDev& J, const PhysParams& PD, const PhysF& P
         raw[5] = OT ? sample_chi<ST>(J, geo, px, py, k) : 0.5;
         ad = make_record<MODE, OT>(PD, raw, h, nfw, &r);
       } else if constexpr (ML) {
+        // the z view's sample is one cell load: cheaper than the cache
         float* rb = rawbuf + 6 * k;
-        if (q == 0) {
+        if (q == 0 || J.zview) {
           sample_raw<ST>(J, rp, px, py, k, raw);
           raw[5] = PF.ot_tab ? sample_chi<ST>(J, rp, px, py, k) : 0.5f;
+          if (!J.zview) {
 #pragma unroll
-          for (int i = 0; i < 6; ++i) rb[i] = raw[i];
+            for (int i = 0; i < 6; ++i) rb[i] = raw[i];
+          }
         } else {
 #pragma unroll
           for (int i = 0; i < 6; ++i) raw[i] = rb[i];
@@ -1198,17 +1201,12 @@ fwd_kernel(const __grid_constant__ JobTable tab, int njobs, const PhysParams PD,
     const int px = (int)(tile % J.ntx) * J.tw + within % J.tw;
     const int py = (int)(tile / J.ntx) * J.th + within / J.tw;
     if constexpr (ML) {
-      // every line of the ray in turn; the line's constants go to a
-      // per-warp slot in shared memory (the line index is not a constant)
-      __shared__ PhysF spf[kWarpsPerBlock];
+      // every line of the ray in turn, its constants read in place from the
+      // kernel's parameter space (a __grid_constant__ parameter)
       if (px < J.npx && py < J.npy) {
         float* rawbuf = reinterpret_cast<float*>(rscr + gw * rstride + raw_off);
         for (int q = 0; q < LS.n; ++q) {
-          const int* src = reinterpret_cast<const int*>(&LS.pf[q]);
-          int* dst = reinterpret_cast<int*>(&spf[warp]);
-          for (int i = lane; i < (int)(sizeof(PhysF) / sizeof(int)); i += 32) dst[i] = src[i];
-          __syncwarp();
-          render_ray<R, NI, ST, MODE, false, false, true>(J, PD, spf[warp], px, py, wsm, fw_off,
+          render_ray<R, NI, ST, MODE, false, false, true>(J, PD, LS.pf[q], px, py, wsm, fw_off,
                                                           cw_off, kb_off, grec, lane, flags,
                                                           stats, LS.out[q], rawbuf, q);
           __syncwarp();

@@ -14,11 +14,14 @@
 // j = (h nu / 4 pi) A f_u and alpha = (h nu / 4 pi)(f_l B_lu - f_u B_ul).
 //
 // One warp per node, the augmented matrix of the node in shared memory (FP64,
-// at most 64 levels): lane l assembles the rows i = l (mod 32) from every
-// transition that touches them (no atomics, the same sums in the same order
-// on every run), then Gaussian elimination with partial pivoting (pivot by a
-// warp reduction, rows eliminated by lanes) and back substitution (sums by
-// warp reduction).  FP64 because the grid is built once at start-up and the
+// at most 64 levels): the lanes take the transitions of one partner at a time
+// and add each one's two off-diagonal inflows (a partner lists a level pair
+// once, so no two lanes write one element: no atomics, the same sums in the
+// same order on every run), the diagonal is minus the column sum (the total
+// outflow), then Gaussian elimination with partial pivoting (pivot by a warp
+// reduction, rows eliminated by lanes) and back substitution (sums by warp
+// reduction).  The detailed-balance factor is the ratio of per-level
+// Boltzmann factors (one exponential per level, not per transition).  FP64 because the grid is built once at start-up and the
 // level systems span many orders of magnitude in their rates; the render
 // reads the float copy.
 #include <cuda_runtime.h>
@@ -66,6 +69,9 @@ __device__ double planck_cgs(double nu, double T) {
   return 2.0 * kHP * nu * nu * nu / (kCL * kCL) / expm1(kHP * nu / (kKB * T));
 }
 
+// doubles of shared memory one warp of the build needs
+__host__ __device__ inline int ot_warp_doubles(int n) { return n * (n + 1) + 2 * n + 8 + 8 + 4; }
+
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -78,7 +84,14 @@ ot_build_kernel(OTBuildArgs M, double* tab64, float4* tab32, long long nodes) {
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
   const int n = M.nlev, ld = n + 1;
-  double* A = sm + (size_t)warp * n * ld;   // augmented matrix, row major
+  // per warp: the augmented matrix (row major), the level factors, the
+  // partners' rate brackets
+  double* A = sm + (size_t)warp * ot_warp_doubles(n);
+  double* xs = A + n * ld;
+  double* rx = xs + n;
+  double* pw = rx + n;
+  double* pn = pw + 8;
+  int* pbr = reinterpret_cast<int*>(pn + 8);
   const long long n12 = (long long)M.n[1] * M.n[2];
   for (long long node = (long long)blockIdx.x * kBuildWarps + warp; node < nodes;
        node += (long long)gridDim.x * kBuildWarps) {
@@ -89,42 +102,69 @@ ot_build_kernel(OTBuildArgs M, double* tab64, float4* tab32, long long nodes) {
     const double chi = M.lo[1] + (M.hi[1] - M.lo[1]) * i1 / (M.n[1] - 1);
     const double T = pow(10.0, M.lo[2] + (M.hi[2] - M.lo[2]) * i2 / (M.n[2] - 1));
     for (int e = lane; e < n * ld; e += 32) A[e] = 0.0;
-    __syncwarp();
-    // rows of this lane: a rate i -> j adds to the inflow A[j][i] and the
-    // outflow A[i][i]
-    for (int p = 0; p < M.npartner; ++p) {
-      const double np = partner_density(M, M.partner[p], n_h, chi);
-      for (int c = 0; c < M.ncoll; ++c) {
-        const int u = M.cup[p * M.ncoll + c], l = M.clo[p * M.ncoll + c];
-        if ((u & 31) != lane && (l & 31) != lane) continue;
-        const double cul = rate_coefficient(M, p, c, T) * np;
-        const double clu = cul * (M.g[u] / M.g[l]) * exp(-(M.energy[u] - M.energy[l]) / T);
-        if ((l & 31) == lane) {
-          A[l * ld + u] += cul;   // u -> l into l
-          A[l * ld + l] -= clu;   // l -> u out of l
-        }
-        if ((u & 31) == lane) {
-          A[u * ld + l] += clu;
-          A[u * ld + u] -= cul;
+    // per level: x_i = exp(-(E_i - E_0) / T) and 1 / x_i (detailed balance
+    // as a ratio, one exponential per level instead of per transition);
+    // per partner: its density and the bracket of T in its rate table
+    for (int i = lane; i < n; i += 32) {
+      const double x = exp(-(M.energy[i] - M.energy[0]) / T);
+      xs[i] = x;
+      rx[i] = (x > 1e-250) ? 1.0 / x : 0.0;
+    }
+    for (int p = lane; p < M.npartner; p += 32) {
+      const double* tt = M.ctemp + (long long)p * M.ntemp;
+      int it = 0;
+      double w = 0.0;
+      if (M.ntemp > 1 && T > tt[0]) {
+        if (T >= tt[M.ntemp - 1]) {
+          it = M.ntemp - 2;
+          w = 1.0;
+        } else {
+          while (T > tt[it + 1]) ++it;
+          w = (T - tt[it]) / (tt[it + 1] - tt[it]);
         }
       }
+      pbr[p] = it;
+      pw[p] = w;
+      pn[p] = partner_density(M, M.partner[p], n_h, chi);
     }
-    for (int r = 0; r < M.nrad; ++r) {
+    __syncwarp();
+    // off-diagonal inflows: A[l][u] += rate u -> l, A[u][l] += rate l -> u.
+    // Lanes take the transitions of one partner at a time; a partner lists
+    // each level pair once (checked on the host), so no two lanes write the
+    // same element and every run sums in the same order.
+    for (int p = 0; p < M.npartner; ++p) {
+      const int it = pbr[p];
+      const double w = pw[p], np = pn[p];
+      for (int c = lane; c < M.ncoll; c += 32) {
+        const int u = M.cup[p * M.ncoll + c], l = M.clo[p * M.ncoll + c];
+        const double* kk = M.k + ((long long)p * M.ncoll + c) * M.ntemp;
+        const double K = (M.ntemp > 1) ? kk[it] + w * (kk[it + 1] - kk[it]) : kk[0];
+        const double cul = K * np;
+        // detailed balance (Sec. 3.6): K_lu = K_ul (g_u / g_l) exp(-(E_u - E_l) / kT)
+        const double db = (rx[l] != 0.0) ? xs[u] * rx[l]
+                                          : exp(-(M.energy[u] - M.energy[l]) / T);
+        A[l * ld + u] += cul;
+        A[u * ld + l] += cul * (M.g[u] / M.g[l]) * db;
+      }
+      __syncwarp();
+    }
+    for (int r = lane; r < M.nrad; r += 32) {
       const int u = M.rad_up[r], l = M.rad_lo[r];
-      if ((u & 31) != lane && (l & 31) != lane) continue;
       const double nu = M.nu[r];
       const double b_ul = kCL * kCL * M.a[r] / (2.0 * kHP * nu * nu * nu);
       const double b_lu = (M.g[u] / M.g[l]) * b_ul;
       const double J = planck_cgs(nu, M.t_rad);
-      const double down = M.a[r] + b_ul * J, up = b_lu * J;
-      if ((l & 31) == lane) {
-        A[l * ld + u] += down;
-        A[l * ld + l] -= up;
-      }
-      if ((u & 31) == lane) {
-        A[u * ld + l] += up;
-        A[u * ld + u] -= down;
-      }
+      A[l * ld + u] += M.a[r] + b_ul * J;
+      A[u * ld + l] += b_lu * J;
+    }
+    __syncwarp();
+    // diagonal: minus the total outflow of level i, the sum of the inflows
+    // it feeds (column i)
+    for (int c = lane; c < n; c += 32) {
+      double out = 0.0;
+      for (int r = 0; r < n; ++r)
+        if (r != c) out += A[r * ld + c];
+      A[c * ld + c] = -out;
     }
     __syncwarp();
     // conservation row and right-hand side e_0
@@ -211,7 +251,7 @@ ot_build_kernel(OTBuildArgs M, double* tab64, float4* tab32, long long nodes) {
 
 int launch_ot_build(const OTBuildArgs& M, double* tab64, float4* tab32, cudaStream_t stream) {
   const long long nodes = (long long)M.n[0] * M.n[1] * M.n[2];
-  const size_t smem = (size_t)kBuildWarps * M.nlev * (M.nlev + 1) * sizeof(double);
+  const size_t smem = (size_t)kBuildWarps * ot_warp_doubles(M.nlev) * sizeof(double);
   cudaError_t e = cudaFuncSetAttribute(ot_build_kernel,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return (int)e;

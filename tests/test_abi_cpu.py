@@ -304,3 +304,30 @@ def test_ot_table_arguments_validate_before_any_cuda_call(B):
     assert L.irt_forward_ppv_ot(ctypes.byref(job), 1, None, 0, ctypes.byref(line),
                                 ctypes.byref(dust), ctypes.byref(opts), None) == B.IRT_EINVAL
     assert L.irt_grid_set_h2_fraction(None, None, 0, None) == B.IRT_EINVAL
+
+
+def test_ot_table_refuses_a_level_pair_listed_twice(B):
+    """The grid build adds each transition's rates in place, so a partner (or
+    the radiative list) naming one level pair twice is refused."""
+    import numpy as np
+    from synth.levels import rotor_model
+    m = rotor_model(nlev=5, partners=(0,))
+    m["coll_up"] = np.array([[1, 1, 2]], np.int32)
+    m["coll_lo"] = np.array([[0, 0, 1]], np.int32)
+    m["k_ul_cm3_s"] = m["k_ul_cm3_s"][:, :3]
+    keep = {k: np.ascontiguousarray(np.asarray(m[k], dtype=np.float64)) for k in
+            ("energy_k", "g", "a_ul_s", "nu_hz", "coll_temp_k", "k_ul_cm3_s")}
+    keepi = {k: np.ascontiguousarray(np.asarray(m[k], dtype=np.int32)) for k in
+             ("rad_up", "rad_lo", "partner", "coll_up", "coll_lo")}
+    dp = lambda a: a.ctypes.data_as(B._DP)  # noqa: E731
+    ip = lambda a: a.ctypes.data_as(B._IP)  # noqa: E731
+    mm = B.irt_level_model(5, dp(keep["energy_k"]), dp(keep["g"]), 4, ip(keepi["rad_up"]),
+                           ip(keepi["rad_lo"]), dp(keep["a_ul_s"]), dp(keep["nu_hz"]), 1,
+                           ip(keepi["partner"]), keep["coll_temp_k"].shape[-1],
+                           dp(keep["coll_temp_k"]), 3, ip(keepi["coll_up"]), ip(keepi["coll_lo"]),
+                           dp(keep["k_ul_cm3_s"]), 2.725, 3.0, 0.1)
+    ax = B.irt_ot_axes(4, 3, 4, 1.0, 6.0, 0.1, 0.5, 1.0, 2.5)
+    out = ctypes.c_void_p()
+    assert B.lib.irt_create_ot_table(ctypes.byref(mm), ctypes.byref(ax), (ctypes.c_int * 1)(1), 1,
+                                     None, ctypes.byref(out)) == B.IRT_EINVAL
+    assert b"twice" in B.lib.irt_last_error()
