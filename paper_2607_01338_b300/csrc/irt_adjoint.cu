@@ -590,11 +590,12 @@ __device__ __forceinline__ void adj_dispatch(std::integer_sequence<int, B...>, i
    ...);
 }
 
-// Pass 0 (A.pass == 0) takes every ray of the image from the queue and
-// defers the rays whose hull is wider than NI blocks to the list A.defer
+// A pass takes the rays of A.in_list (every ray of the image if nullptr)
+// from the queue and defers the rays whose hull is wider than NI blocks to
+// the list A.defer (if set)
 // ([0] = count, then ray indices); pass 1 takes the rays of that list.
 template <int NI, int ST>
-__global__ void __launch_bounds__(kAdjWarps * 32, (NI <= 9) ? 6 : 1)
+__global__ void __launch_bounds__(kAdjWarps * 32, (NI <= 4) ? 8 : ((NI <= 9) ? 6 : 1))
 adj_kernel(const __grid_constant__ JobTable tab, const PhysF PF, const AdjArgs A,
            long long total_items, unsigned long long* queue, int per_warp, int fw_off,
            int cw_off, int pb_off, int ra_off) {
@@ -631,13 +632,13 @@ adj_kernel(const __grid_constant__ JobTable tab, const PhysF PF, const AdjArgs A
   }
   __syncwarp();
 
-  const long long n_items = (A.pass == 0) ? total_items : (long long)A.defer[0];
+  const long long n_items = A.in_list ? (long long)A.in_list[0] : total_items;
   for (;;) {
     unsigned long long t = 0;
     if (lane == 0) t = atomicAdd(queue, 1ull);
     const long long slot = (long long)__shfl_sync(0xffffffffu, t, 0);
     if (slot >= n_items) break;
-    const long long item = (A.pass == 0) ? slot : (long long)A.defer[1 + slot];
+    const long long item = A.in_list ? (long long)A.in_list[1 + slot] : slot;
     const int px = (int)(item % J.npx), py = (int)(item / J.npx);
     const int cwn = J.nchan;      // one window
     const int f = J.f;
@@ -711,7 +712,7 @@ adj_kernel(const __grid_constant__ JobTable tab, const PhysF PF, const AdjArgs A
     int nb = adj_bucket(none ? 1 : hhi - hlo + 1, ns);
     const int hb = none ? 0 : min(hlo, max(nblk - nb, 0));
     const bool fits = (ns <= 2) && admax <= 0.5f && K >= 2;
-    if (A.pass == 0 && fits && nb > NI && nb <= A.defer_max_nb) {
+    if (A.defer && fits && nb > NI && nb <= A.defer_max_nb) {
       // wider hull: the second pass (more register blocks) takes this ray
       if (lane == 0) {
         const unsigned i = atomicAdd(A.defer, 1u);
@@ -1178,8 +1179,8 @@ int launch_adjoint(int store, int ni, const JobTable& tab, const PhysF& PF, cons
                                                    per_warp, fw_off, cw_off, pb_off, ra_off); \
     return (int)cudaGetLastError();                                                           \
   }
-  IRT_LAUNCH(9, ST_F32) IRT_LAUNCH(17, ST_F32) IRT_LAUNCH(33, ST_F32)
-  IRT_LAUNCH(9, ST_H16) IRT_LAUNCH(17, ST_H16) IRT_LAUNCH(33, ST_H16)
+  IRT_LAUNCH(4, ST_F32) IRT_LAUNCH(9, ST_F32) IRT_LAUNCH(17, ST_F32) IRT_LAUNCH(33, ST_F32)
+  IRT_LAUNCH(4, ST_H16) IRT_LAUNCH(9, ST_H16) IRT_LAUNCH(17, ST_H16) IRT_LAUNCH(33, ST_H16)
 #undef IRT_LAUNCH
   return (int)cudaErrorInvalidValue;
 }
@@ -1246,8 +1247,8 @@ int adjoint_blocks_per_sm(int store, int ni, size_t smem) {
                                                   kAdjWarps * 32, smem);                      \
     return per_sm;                                                                            \
   }
-  IRT_OCC(9, ST_F32) IRT_OCC(17, ST_F32) IRT_OCC(33, ST_F32)
-  IRT_OCC(9, ST_H16) IRT_OCC(17, ST_H16) IRT_OCC(33, ST_H16)
+  IRT_OCC(4, ST_F32) IRT_OCC(9, ST_F32) IRT_OCC(17, ST_F32) IRT_OCC(33, ST_F32)
+  IRT_OCC(4, ST_H16) IRT_OCC(9, ST_H16) IRT_OCC(17, ST_H16) IRT_OCC(33, ST_H16)
 #undef IRT_OCC
   return 0;
 }

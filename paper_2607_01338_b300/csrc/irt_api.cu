@@ -1511,8 +1511,14 @@ extern "C" irt_status irt_adjoint_ppv(const irt_job* job, const irt_line* line,
   if (e) return cuda_fail(e, "irt_adjoint_ppv: general sweep attributes");
   const long long dense_floats = (adjoint_dense_scratch_per_warp(p.kmax) + 63) & ~63ll;
   size_t need = (size_t)blocks_d * 2 * (size_t)dense_floats * sizeof(float);
-  int per_warp = 0, blocks0 = 0, blocks1 = 0, ni1 = 0;
-  const int ni0 = 9;
+  // fast sweep passes: hull buckets up to 4 register blocks first (128
+  // registers, the most resident warps), then up to 9, then the job's full
+  // width; each pass defers the wider rays to the next through a device list
+  int per_warp = 0;
+  std::vector<int> nis;
+  for (int ni : {4, 9, p.ni})
+    if (fast && (nis.empty() || ni > nis.back())) nis.push_back(ni);
+  std::vector<int> blocks(nis.size(), 0);
   long long per_warp_floats = 0;
   const int nseg = (p.kmax + kAdjSeg - 1) / kAdjSeg;
   AdjArgs A;
@@ -1520,63 +1526,57 @@ extern "C" irt_status irt_adjoint_ppv(const irt_job* job, const irt_line* line,
   if (fast) {
     for (int q = 0; q < 5; ++q) A.cot[q] = cot[q];
     for (int q = 0; q < 3; ++q) A.grad[q] = grads[q];
-    // pass 0 runs with 9 register blocks (128 registers, 16 warps per SM) and
-    // defers the rays with wider hulls to pass 1 with the job's full width
-    ni1 = p.ni > ni0 ? p.ni : 0;
-    e = launch_adjoint(g->store, ni0, tab, PF, A, 0, nullptr, 0, p.kmax, p.nfw, nch, s,
+    e = launch_adjoint(g->store, nis[0], tab, PF, A, 0, nullptr, 0, p.kmax, p.nfw, nch, s,
                        &per_warp);
     if (e) return cuda_fail(e, "irt_adjoint_ppv: kernel attributes");
     const size_t smem = (size_t)per_warp * kAdjWarps;
-    blocks0 = std::max(1, adjoint_blocks_per_sm(g->store, ni0, smem)) * sms;
-    blocks1 = ni1 ? std::max(1, adjoint_blocks_per_sm(g->store, ni1, smem)) * sms : 0;
+    int bmax = 0;
+    for (size_t i = 0; i < nis.size(); ++i) {
+      blocks[i] = std::max(1, adjoint_blocks_per_sm(g->store, nis[i], smem)) * sms;
+      bmax = std::max(bmax, blocks[i]);
+    }
     // checkpoints, one stored sub-segment, the per-sample chain-rule factors
-    const int nb_alloc = std::max(ni0, ni1) + 1;
+    const int nb_alloc = nis.back() + 1;
     per_warp_floats =
         (long long)(2 * nseg + kAdjSub) * nb_alloc * 32 + (long long)kAdjChain * p.kmax;
     per_warp_floats = (per_warp_floats + 63) & ~63ll;
-    need = std::max(need, (size_t)std::max(blocks0, blocks1) * kAdjWarps *
-                              (size_t)per_warp_floats * sizeof(float));
+    need = std::max(need, (size_t)bmax * kAdjWarps * (size_t)per_warp_floats * sizeof(float));
   }
-  // lists: [0] deferred count, deferred rays; [total + 1] general count,
-  // general rays; then the general sweep's queue counter (8-byte aligned)
-  const size_t list_words = 2 * (size_t)(total + 1);
+  // lists: [0] the general sweep's rays, then one per later fast pass, each
+  // [count, indices...] of total + 1 words; then the queue counters of the
+  // general sweep and of every fast pass (8-byte aligned)
+  const size_t lists = 1 + (nis.empty() ? 0 : nis.size() - 1);
+  const size_t list_words = lists * (size_t)(total + 1);
   const size_t queue_off = ((list_words * sizeof(unsigned)) + 7) & ~(size_t)7;
-  const size_t defer_need = queue_off + sizeof(unsigned long long);
+  const size_t defer_need = queue_off + (1 + nis.size()) * sizeof(unsigned long long);
   StreamScratch& ss = stream_scratch(s);
   irt_status gs = grow(&ss.adj, &ss.adj_bytes, need, s, "irt_adjoint_ppv");
   if (!gs) gs = grow(&ss.defer, &ss.defer_bytes, defer_need, s, "irt_adjoint_ppv");
   if (gs) return gs;
-  unsigned* defer = reinterpret_cast<unsigned*>(ss.defer);
-  unsigned* dense_list = defer + (total + 1);
-  unsigned long long* dense_queue = reinterpret_cast<unsigned long long*>(ss.defer + queue_off);
-  cudaError_t ce = cudaMemsetAsync(dense_queue, 0, sizeof(unsigned long long), s);
-  if (ce == cudaSuccess) ce = cudaMemsetAsync(dense_list, 0, sizeof(unsigned), s);
+  unsigned* dense_list = reinterpret_cast<unsigned*>(ss.defer);
+  unsigned long long* queues = reinterpret_cast<unsigned long long*>(ss.defer + queue_off);
+  // counts of every list and every queue counter start at zero
+  cudaError_t ce = cudaMemsetAsync(queues, 0, (1 + nis.size()) * sizeof(unsigned long long), s);
+  for (size_t l = 0; l < lists && ce == cudaSuccess; ++l)
+    ce = cudaMemsetAsync(dense_list + l * (size_t)(total + 1), 0, sizeof(unsigned), s);
   if (ce != cudaSuccess) return cuda_fail(ce, "irt_adjoint_ppv: queue reset");
+  unsigned long long* dense_queue = queues;
   if (fast) {
     A.scratch = reinterpret_cast<float*>(ss.adj);
     A.scratch_per_warp = per_warp_floats;
-    A.defer = defer;
     A.dense = dense_list;
-    A.defer_max_nb = ni1;
     if (g->ck && g->ck_sig == checkpoint_signature(jb, P)) {
       A.ck_saved = g->ck;
       A.ck_nb = kCkRows;
       A.ck_ray = (long long)nseg * 2 * kCkRows * 32;
     }
-    // control words: [0] pass-0 queue, [7] pass-1 queue; defer[0] = 0
-    ce = cudaMemsetAsync(g->ctl, 0, sizeof(unsigned long long), s);
-    if (ce == cudaSuccess) ce = cudaMemsetAsync(g->ctl + 7, 0, sizeof(unsigned long long), s);
-    if (ce == cudaSuccess) ce = cudaMemsetAsync(A.defer, 0, sizeof(unsigned), s);
-    if (ce != cudaSuccess) return cuda_fail(ce, "irt_adjoint_ppv: queue reset");
-    A.pass = 0;
-    e = launch_adjoint(g->store, ni0, tab, PF, A, total, g->ctl, blocks0, p.kmax, p.nfw, nch, s,
-                       nullptr);
-    ++g_launches;
-    if (e) return cuda_fail(e, "irt_adjoint_ppv: adjoint kernel");
-    if (ni1) {
-      A.pass = 1;
-      e = launch_adjoint(g->store, ni1, tab, PF, A, total, g->ctl + 7, blocks1, p.kmax, p.nfw,
-                         nch, s, nullptr);
+    for (size_t i = 0; i < nis.size(); ++i) {
+      A.in_list = i == 0 ? nullptr : dense_list + i * (size_t)(total + 1);
+      const bool last = i + 1 == nis.size();
+      A.defer = last ? nullptr : dense_list + (i + 1) * (size_t)(total + 1);
+      A.defer_max_nb = last ? 0 : nis.back();
+      e = launch_adjoint(g->store, nis[i], tab, PF, A, total, queues + 1 + i, blocks[i], p.kmax,
+                         p.nfw, nch, s, nullptr);
       ++g_launches;
       if (e) return cuda_fail(e, "irt_adjoint_ppv: adjoint kernel");
     }

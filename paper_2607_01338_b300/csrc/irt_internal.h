@@ -174,9 +174,9 @@ struct AdjArgs {
   const float* ck_saved;        // checkpoints saved by the forward render, or nullptr
   int ck_nb;                    // their rows (hull blocks < ck_nb)
   long long ck_ray;             // floats per ray
-  int pass;                     // 0: every ray, wide hulls deferred; 1: the deferred rays
-  int defer_max_nb;             // widest hull bucket the second pass handles (0: none)
-  unsigned* defer;              // [0] = count, then deferred ray indices
+  const unsigned* in_list;      // rays of this pass: [0] = count, then indices (nullptr: all)
+  int defer_max_nb;             // widest hull bucket a later pass handles (0: none)
+  unsigned* defer;              // rays with wider hulls for the next pass, or nullptr
   unsigned* dense;              // [0] = count, then the rays the general sweep takes
 };
 
