@@ -431,7 +431,8 @@ def gpu_arm(args):
     nx = w.n
     vw = w.views[0 if is_adj else dom]
     hbm_bytes = nx ** 3 * 32 + 5 * 4 * w.vaxis.nchan * vw.npx * vw.npy
-    kname = ("adjoint: adj_kernel<9,F32> + deferred-ray pass adj_kernel<17,F32> (z view)"
+    kname = ("adjoint (z view): adj_kernel<4,F32>, then the wider hulls in adj_kernel<9,F32> "
+             "and adj_kernel<17,F32>, then adj_dense_kernel for explicit-channel rays"
              if is_adj else f"fwd_kernel<float,17,F32,smooth> ({['z', 'oblique'][dom]} view)")
     # DRAM bytes per launch of the dominant kernel from the committed ncu
     # summary of this workload, only while the kernel sources it was captured

@@ -203,6 +203,9 @@ struct Adj {
                                                        const float* qs, const float* ds, int lane,
                                                        const VGrid& G, float* part) {
     const float ib2 = -r.nib2 * 0.69314718055994531f;   // 1 / b^2
+    float ib;   // 1 / b = (1 / b^2) b
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(ib) : "f"(ib2));
+    ib *= ib2;
 #pragma unroll
     for (int q = 0; q < NS; ++q) {
       // qs = ds = 0 for an empty slot: its terms vanish
@@ -214,7 +217,7 @@ struct Adj {
       // de/dv = e 2 (u - v) / b^2 ; de/db = e 2 (u - v)^2 / b^3
       const float t = 2.0f * dv * ib2 * de;
       part[3] += t;
-      part[4] = fmaf(t * dv, sqrtf(ib2), part[4]);
+      part[4] = fmaf(t * dv, ib, part[4]);
     }
   }
 
