@@ -897,12 +897,11 @@ adj_dense_kernel(const __grid_constant__ JobTable tab, const PhysF PF, const Den
     if (slot >= n_items) break;
     const long long item = A.list ? (long long)A.list[1 + slot] : slot;
     const int px = (int)(item % J.npx), py = (int)(item / J.npx);
-    const RayGeom geo = ray_geom(J, px, py);
-    const int K = geo.K;
+    const RaySet rs = ray_setup(J, px, py);
+    const int K = rs.K;
     if (K <= 0) continue;   // a ray missing the box has no gradient
-    const float h = (float)geo.h;
-    RayPos rp;
-    if (!J.zview) rp = ray_pos(J, geo);
+    const float h = rs.h;
+    const RayPos rp = rs.rp;
     VGrid G;
     G.ufw_hi = (float)J.ufirst;
     G.ufw_lo = (float)(J.ufirst - (double)G.ufw_hi);

@@ -451,13 +451,11 @@ JobDev make_jobdev(const irt_job& jb, const Plan& p) {
   d.dx = g->dx;
   d.zview = jb.view.trilinear == 0 || jb.view.trilinear == 2;
   d.zrev = jb.view.trilinear == 2;
-  d.theta = jb.view.theta_rad;
-  d.phi = jb.view.phi_rad;
   {
     // orthographic view basis: direction d = (st cp, st sp, ct), pixel axes
     // e_theta = (ct cp, ct sp, -st), e_phi = (-sp, cp, 0)
-    const double st = std::sin(d.theta), ct = std::cos(d.theta);
-    const double sp = std::sin(d.phi), cp = std::cos(d.phi);
+    const double st = std::sin(jb.view.theta_rad), ct = std::cos(jb.view.theta_rad);
+    const double sp = std::sin(jb.view.phi_rad), cp = std::cos(jb.view.phi_rad);
     const double dd[3] = {st * cp, st * sp, ct};
     const double et[3] = {ct * cp, ct * sp, -st};
     const double ep[3] = {-sp, cp, 0.0};
@@ -468,6 +466,25 @@ JobDev make_jobdev(const irt_job& jb, const Plan& p) {
       d.inv_d[a] = dd[a] != 0.0 ? 1.0 / dd[a] : HUGE_VAL;
     }
     d.inv_dx = 1.0 / g->dx;
+    // float-float form in cell units: o = (n/2 + (px - cx) P e_theta + (py -
+    // cy) P e_phi), P = pixel / dx, cx = (npx - 1)/2
+    auto split = [](double x, float out[2]) {
+      out[0] = (float)x;
+      out[1] = (float)(x - (double)out[0]);
+    };
+    const double P = jb.view.pixel_cm / g->dx;
+    const double cx = 0.5 * (jb.view.npx - 1), cy = 0.5 * (jb.view.npy - 1);
+    const int n[3] = {g->nx, g->ny, g->nz};
+    for (int a = 0; a < 3; ++a) {
+      split(0.5 * n[a] - cx * P * et[a] - cy * P * ep[a], d.fo0[a]);
+      split(P * et[a], d.fox[a]);
+      split(P * ep[a], d.foy[a]);
+      // an axis with |d| < 1e-30 counts as parallel (1/d would not fit a float)
+      const bool par = std::fabs(dd[a]) < 1e-30;
+      split(par ? 0.0 : dd[a], d.fd[a]);
+      split(par ? 0.0 : 1.0 / dd[a], d.finv_d[a]);
+    }
+    split(g->dx, d.fdx);
   }
   d.npx = jb.view.npx;
   d.npy = jb.view.npy;

@@ -223,6 +223,126 @@ __device__ __forceinline__ RayPos ray_pos(const JobDev& J, const RayGeom& g) {
   return c;
 }
 
+// ---------------------------------------------------------------------------
+// Ray set-up of the float kernels, without double arithmetic.  The chord, the
+// sample count K = ceil(chord / dx - 1e-9), the step and the 32.32 sample
+// positions are evaluated in float-float arithmetic: a value is the
+// unevaluated sum hi + lo of two floats (about 48 significant bits), built
+// from the error-free sum of two floats (Knuth's two-sum) and the error-free
+// product (the fma residual).  Its rounding, about 1e-11 cells on a
+// 1000-cell chord, is far below the 1e-9 slack of the sample count, so K is
+// the double-precision value except on chords within ~1e-11 of that slack.
+// The double kernels keep ray_geom / ray_pos above.
+// ---------------------------------------------------------------------------
+struct FF {
+  float hi, lo;
+};
+
+__device__ __forceinline__ FF ff_load(const float v[2]) { return FF{v[0], v[1]}; }
+__device__ __forceinline__ FF ff_two_sum(float a, float b) {
+  const float s = a + b;
+  const float bb = s - a;
+  return FF{s, (a - (s - bb)) + (b - bb)};
+}
+__device__ __forceinline__ FF ff_add(FF x, FF y) {
+  const FF s = ff_two_sum(x.hi, y.hi);
+  return ff_two_sum(s.hi, s.lo + (x.lo + y.lo));
+}
+__device__ __forceinline__ FF ff_neg(FF x) { return FF{-x.hi, -x.lo}; }
+__device__ __forceinline__ FF ff_mul(FF x, FF y) {
+  const float p = x.hi * y.hi;
+  const float e = fmaf(x.hi, y.hi, -p);
+  return ff_two_sum(p, fmaf(x.hi, y.lo, fmaf(x.lo, y.hi, e)));
+}
+// x b for a float b
+__device__ __forceinline__ FF ff_mul_f(FF x, float b) {
+  const float p = x.hi * b;
+  return ff_two_sum(p, fmaf(x.lo, b, fmaf(x.hi, b, -p)));
+}
+__device__ __forceinline__ bool ff_lt(FF a, FF b) {
+  return a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo);
+}
+// x / k for an integer 0 < k < 2^24: quotient, exact remainder, correction
+__device__ __forceinline__ FF ff_div_i(FF x, int k) {
+  const float kf = (float)k;
+  const float q1 = __fdiv_rn(x.hi, kf);
+  const FF r = ff_add(x, ff_neg(ff_mul_f(FF{q1, 0.0f}, kf)));
+  return ff_two_sum(q1, __fdiv_rn(r.hi, kf));
+}
+// smallest integer >= x (|x| < 2^23; a normalised pair cannot straddle an
+// integer unless hi is that integer)
+__device__ __forceinline__ int ff_ceil(FF x) {
+  const float c = ceilf(x.hi);
+  return (int)c + ((c == x.hi && x.lo > 0.0f) ? 1 : 0);
+}
+// x 2^32 rounded to a 64-bit integer (|x| < 2^30)
+__device__ __forceinline__ long long ff_fix32(FF x) {
+  return __float2ll_rn(x.hi * 4294967296.0f) + __float2ll_rn(x.lo * 4294967296.0f);
+}
+
+struct RaySet {
+  int K;       // samples (0: the ray misses the box)
+  float h;     // step [cm]
+  RayPos rp;   // oblique views: sample positions
+};
+
+// The chord of pixel (px, py) through the box [0, n]^3 (cell units): the
+// latest entry and the earliest exit over the three slabs; an axis with
+// d = 0 is a miss when the origin lies outside its slab.
+__device__ inline RaySet ray_setup(const JobDev& J, int px, int py) {
+  RaySet r;
+  r.K = 0;
+  r.h = 0.0f;
+  if (J.zview) {
+    r.K = J.nz;
+    r.h = J.fdx[0];
+    return r;
+  }
+  const float fx = (float)px, fy = (float)py;
+  const int n[3] = {J.nx, J.ny, J.nz};
+  FF o[3];
+  FF lo{-INFINITY, 0.0f}, hi{INFINITY, 0.0f};
+  bool miss = false;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    o[a] = ff_add(ff_load(J.fo0[a]),
+                  ff_add(ff_mul_f(ff_load(J.fox[a]), fx), ff_mul_f(ff_load(J.foy[a]), fy)));
+    const FF na{(float)n[a], 0.0f};
+    if (J.fd[a][0] == 0.0f) {
+      if (ff_lt(o[a], FF{0.0f, 0.0f}) || ff_lt(na, o[a])) miss = true;
+      continue;
+    }
+    const FF inv = ff_load(J.finv_d[a]);
+    FF t0 = ff_mul(ff_neg(o[a]), inv);
+    FF t1 = ff_mul(ff_add(na, ff_neg(o[a])), inv);
+    if (ff_lt(t1, t0)) {
+      const FF t = t0;
+      t0 = t1;
+      t1 = t;
+    }
+    if (ff_lt(lo, t0)) lo = t0;
+    if (ff_lt(t1, hi)) hi = t1;
+  }
+  if (miss || !ff_lt(lo, hi)) return r;
+  const FF chord = ff_add(hi, ff_neg(lo));
+  // 1e-9 as a float-float pair
+  const int K = ff_ceil(ff_add(chord, FF{-9.999999717180685e-10f, -2.8281930491731106e-17f}));
+  if (K <= 0) return r;
+  const FF h = ff_div_i(chord, K);
+  r.K = K;
+  r.h = ff_mul(h, ff_load(J.fdx)).hi;
+  // sample k at t_in + (k + 1/2) h; trilinear coordinates are shifted by
+  // half a cell (cell centres at integers)
+  const FF tm = ff_add(lo, FF{0.5f * h.hi, 0.5f * h.lo});
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const FF d = ff_load(J.fd[a]);
+    r.rp.base[a] = ff_fix32(ff_add(ff_add(o[a], ff_mul(tm, d)), FF{-0.5f, 0.0f}));
+    r.rp.step[a] = ff_fix32(ff_mul(h, d));
+  }
+  return r;
+}
+
 // float kernels: sample k of the ray
 template <int ST>
 __device__ __forceinline__ void sample_raw(const JobDev& J, const RayPos& rp, int px, int py,

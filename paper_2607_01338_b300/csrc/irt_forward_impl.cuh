@@ -937,12 +937,21 @@ __device__ void render_ray(const JobDev& J, const PhysParams& PD, const PhysF& P
   // ---- sample pass: lane l evaluates samples l, l + 32, ... into this warp's
   // record slot; the hull of the line windows, the widest window and the
   // largest dust step depth come along
-  const RayGeom geo = ray_geom(J, px, py);
-  const int K = geo.K;
-  const R h = (R)geo.h;
+  // ray set-up: double arithmetic on the double kernels, float-float on the
+  // float kernels
+  RayGeom geo;
   RayPos rp;
-  if constexpr (!kDouble) {
-    if (!J.zview && K > 0) rp = ray_pos(J, geo);
+  int K;
+  R h;
+  if constexpr (kDouble) {
+    geo = ray_geom(J, px, py);
+    K = geo.K;
+    h = (R)geo.h;
+  } else {
+    const RaySet rs = ray_setup(J, px, py);
+    K = rs.K;
+    h = rs.h;
+    rp = rs.rp;
   }
   int hlo = 1 << 20, hhi = -1, wmax = 0;
   R admax = (R)0;

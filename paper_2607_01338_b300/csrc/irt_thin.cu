@@ -114,8 +114,22 @@ thin_kernel(const __grid_constant__ JobTable tab, int njobs, const PhysParams P,
     const JobDev& J = tab.j[jj];
     const long long r = item - J.item_begin;
     const int px = (int)(r % J.npx), py = (int)(r / J.npx);
-    const RayGeom g = ray_geom(J, px, py);
-    const int K = g.K;
+    // ray set-up: double arithmetic on the double kernels, float-float on the
+    // float kernels
+    RayGeom g;
+    RayPos rp;
+    int K;
+    R h;
+    if constexpr (kD) {
+      g = ray_geom(J, px, py);
+      K = g.K;
+      h = (R)g.h;
+    } else {
+      const RaySet rs = ray_setup(J, px, py);
+      K = rs.K;
+      h = rs.h;
+      rp = rs.rp;
+    }
     const long long plane = (long long)J.npx * J.npy;
     const long long pix = (long long)py * J.npx + px;
     R* out[5];
@@ -129,10 +143,7 @@ thin_kernel(const __grid_constant__ JobTable tab, int njobs, const PhysParams P,
       continue;
     }
     // ---- records
-    const R h = (R)g.h;
     const R sq = (R)0.88622692545275801365 / (R)J.dv;   // sqrt(pi) / (2 dv)
-    RayPos rp;
-    if constexpr (!kD) rp = ray_pos(J, g);
     int hlo = 1 << 30, hhi = -1;   // channels any sample's line reaches
     const R v0r = (R)J.v0, inv_dv = (R)(1.0 / J.dv);
     R admax = (R)0;
