@@ -288,14 +288,15 @@ irt_status irt_tuned_plan(const irt_job* jobs, int njobs, const irt_opts* opts, 
  * zero).  grad_* are float [nz][ny][nx], written completely (overwritten, not
  * accumulated; a cell no ray samples gets zero).  Any view, integrator
  * (IRT_FORMAL_KAHAN is differentiated as the formal step it equals), f and
- * channel count.  Two sweeps: z- and radial-view smooth jobs of one channel
- * window run the fast sweep (line hull in registers, continuum basis; 9
- * register blocks first, then the rays with wider hulls at the job's full
- * width), which hands the rays it cannot take (h alpha_D > 1/2 on some
- * sample, a line window wider than 64 fine velocities) to the general sweep;
- * every other job runs the general sweep alone (every velocity explicit;
- * oblique views add each sample's partials to its eight trilinear cells with
- * atomics, so their sums may differ in the last bits between runs).  The
+ * channel count.  Two sweeps: smooth jobs of one channel window, on any
+ * view, run the fast sweep (line hull in registers, continuum basis; 4
+ * register blocks first, then the rays with wider hulls at 9 blocks, then at
+ * the job's full width), which hands the rays it cannot take (h alpha_D >
+ * 1/2 on some sample, a line window wider than 64 fine velocities) to the
+ * general sweep; every other job runs the general sweep alone (every
+ * velocity explicit).  Oblique views add each sample's gradients to its
+ * eight trilinear cells with atomics, so their sums may differ in the last
+ * bits between runs.  The
  * forward state is recomputed from checkpoints every 32 samples held in
  * device scratch kept per (device, stream).  IRT_EINVAL as irt_forward_ppv
  * plus NULL gradients; IRT_EUNSUPPORTED for IRT_PREC_F64, double field

@@ -373,6 +373,47 @@ __device__ __forceinline__ float fine_cotangent(int g, int f, int cwn, const flo
   return acc / (float)(6 * f);
 }
 
+// Oblique views: a sample is the trilinear blend of eight cells (indices
+// clamped to the grid), so each cell takes its weight of the sample's
+// gradients (atomics: neighbouring rays share cells).
+__device__ __forceinline__ void scatter_trilinear(int nx, int ny, int nz, const long long* base,
+                                                  const long long* step, int k, float gn,
+                                                  float gt, float gv, float* const* grad) {
+  int i0[3];
+  float w[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const long long pp = base[a] + (long long)k * step[a];
+    i0[a] = (int)(pp >> 32);
+    w[a] = (float)(unsigned)(pp & 0xFFFFFFFFll) * 2.3283064365386963e-10f;
+  }
+  const int nn[3] = {nx, ny, nz};
+  int lo3[3], hi3[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    lo3[a] = min(max(i0[a], 0), nn[a] - 1);
+    hi3[a] = min(max(i0[a] + 1, 0), nn[a] - 1);
+  }
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    const int ix = (c & 1) ? hi3[0] : lo3[0];
+    const int iy = (c & 2) ? hi3[1] : lo3[1];
+    const int iz = (c & 4) ? hi3[2] : lo3[2];
+    const float ww = ((c & 1) ? w[0] : 1.0f - w[0]) * ((c & 2) ? w[1] : 1.0f - w[1]) *
+                     ((c & 4) ? w[2] : 1.0f - w[2]);
+    const long long idx = ((long long)iz * ny + iy) * nx + ix;
+    atomicAdd(grad[0] + idx, ww * gn);
+    atomicAdd(grad[1] + idx, ww * gt);
+    atomicAdd(grad[2] + idx, ww * gv);
+  }
+}
+
+// The ray set-up as a call of its own: its float-float temporaries then take
+// no registers of the sweep kernel around it.
+__device__ __noinline__ RaySet ray_setup_call(const JobDev& J, int px, int py) {
+  return ray_setup(J, px, py);
+}
+
 // Launch constants the reverse sweep reads, kept in shared memory: the sweep
 // is a separate (non-inlined) function per hull bucket, and a reference to
 // the kernel's parameters would make the compiler copy them to the stack,
@@ -384,12 +425,14 @@ struct AdjRayArgs {
   int ck_nb;               // rows of a saved checkpoint
   int npx, nx, ny;         // image width, grid extent in x and y
   int nz, zrev;            // grid extent in z; radial view: sample n is cell nz - 1 - n
-  float cad_h;             // cad * cell size: d(h alpha_D) / d n_H2
+  int zview;               // 1: sample n is one cell of the ray's column; 0: oblique view
+  RayPos rp;               // oblique: the ray's 32.32 sample positions
+  float cad_h;             // cad * the ray's step h: d(h alpha_D) / d n_H2
   float T0, inv_c_kms, t_bg;   // background Planck function (K units)
 };
 
 // Reverse sweep of one ray with NA explicit hull blocks and NS line slots.
-template <int NA, int NS, int ST>
+template <int NA, int NS, int ST, bool OBL>
 __device__ __noinline__ void adj_ray(const AdjRayArgs* __restrict__ Ap, const RecS32* rec,
                                      const float* chainf, int K, int hb, int lane, const VGrid G,
                                      int nfw, const float* lamf, float lx, float* pbuf, float* scr,
@@ -479,7 +522,10 @@ __device__ __noinline__ void adj_ray(const AdjRayArgs* __restrict__ Ap, const Re
       // reverse steps of the sub-segment, flushing the partials of every
       // kFlush samples (lane l reduces sample bot + l and writes its gradients)
       for (int top = sub_hi; top > sub_lo;) {
-        const int bot = max(sub_lo, top - kFlush);
+        // samples 0 and 1 share a group (the trapezoidal start reverses
+        // both): a group never ends at sample 1
+        int bot = max(sub_lo, top - kFlush);
+        if (bot == 1) bot = 2;
         const int nlo = max(bot, 2);
         for (int n = top - 1; n >= nlo; --n) {
           float pc[NB];
@@ -528,11 +574,15 @@ __device__ __noinline__ void adj_ray(const AdjRayArgs* __restrict__ Ap, const Re
           const float gvv = g5[3 * kPStride], gb = g5[4 * kPStride];
           const float gn = fmaf(gjl, cf[0], fmaf(gal, cf[1], gad * A.cad_h));
           const float gt = fmaf(gjl, cf[2], fmaf(gal, cf[3], gb * cf[4]));
-          const int zc = A.zrev ? A.nz - 1 - n : n;
-          const long long idx = ((long long)zc * A.ny + py) * A.nx + px;
-          A.grad[0][idx] = gn;
-          A.grad[1][idx] = gt;
-          A.grad[2][idx] = gvv;
+          if constexpr (!OBL) {
+            const int zc = A.zrev ? A.nz - 1 - n : n;
+            const long long idx = ((long long)zc * A.ny + py) * A.nx + px;
+            A.grad[0][idx] = gn;
+            A.grad[1][idx] = gt;
+            A.grad[2][idx] = gvv;
+          } else {
+            scatter_trilinear(A.nx, A.ny, A.nz, A.rp.base, A.rp.step, n, gn, gt, gvv, A.grad);
+          }
         }
         __syncwarp();
         top = bot;
@@ -566,20 +616,20 @@ __device__ __forceinline__ int adj_bucket(int na, int ns) {
   return 33;
 }
 
-template <int NA, int NS, int NI, int ST>
+template <int NA, int NS, int NI, int ST, bool OBL>
 __device__ __forceinline__ bool adj_run_bucket(const AdjRayArgs* A, const RecS32* rec,
                                                const float* chainf, int K, int hb, int lane,
                                                const VGrid& G, int nfw, const float* lamf,
                                                float lx, float* pbuf, float* scr, int px,
                                                int py) {
   if constexpr (NA <= NI) {
-    adj_ray<NA, NS, ST>(A, rec, chainf, K, hb, lane, G, nfw, lamf, lx, pbuf, scr, px, py);
+    adj_ray<NA, NS, ST, OBL>(A, rec, chainf, K, hb, lane, G, nfw, lamf, lx, pbuf, scr, px, py);
     return true;
   }
   return false;
 }
 
-template <int NS, int NI, int ST, int... B>
+template <int NS, int NI, int ST, bool OBL, int... B>
 __device__ __forceinline__ void adj_dispatch(std::integer_sequence<int, B...>, int nb,
                                              const AdjRayArgs* A, const RecS32* rec,
                                              const float* chainf, int K, int hb, int lane,
@@ -587,7 +637,7 @@ __device__ __forceinline__ void adj_dispatch(std::integer_sequence<int, B...>, i
                                              float lx, float* pbuf, float* scr, int px,
                                              int py) {
   bool done = false;
-  ((done = done || (nb == B && adj_run_bucket<B, NS, NI, ST>(A, rec, chainf, K, hb, lane, G,
+  ((done = done || (nb == B && adj_run_bucket<B, NS, NI, ST, OBL>(A, rec, chainf, K, hb, lane, G,
                                                              nfw, lamf, lx, pbuf, scr, px,
                                                              py))),
    ...);
@@ -597,7 +647,7 @@ __device__ __forceinline__ void adj_dispatch(std::integer_sequence<int, B...>, i
 // from the queue and defers the rays whose hull is wider than NI blocks to
 // the list A.defer (if set)
 // ([0] = count, then ray indices); pass 1 takes the rays of that list.
-template <int NI, int ST>
+template <int NI, int ST, bool OBL>
 __global__ void __launch_bounds__(kAdjWarps * 32, (NI <= 4) ? 8 : ((NI <= 9) ? 6 : 1))
 adj_kernel(const __grid_constant__ JobTable tab, const PhysF PF, const AdjArgs A,
            long long total_items, unsigned long long* queue, int per_warp, int fw_off,
@@ -628,7 +678,8 @@ adj_kernel(const __grid_constant__ JobTable tab, const PhysF PF, const AdjArgs A
     RA->ny = J.ny;
     RA->nz = J.nz;
     RA->zrev = J.zrev;
-    RA->cad_h = PF.cad * (float)J.dx;
+    RA->zview = J.zview;
+    RA->cad_h = PF.cad * (float)J.dx;   // cell-exact views (oblique rays: per ray below)
     RA->T0 = PF.T0;
     RA->inv_c_kms = PF.inv_c_kms;
     RA->t_bg = PF.t_bg;
@@ -647,8 +698,25 @@ adj_kernel(const __grid_constant__ JobTable tab, const PhysF PF, const AdjArgs A
     const int f = J.f;
     const int nfw = 2 * f * cwn + 1;
     const int nblk = (nfw + 31) >> 5;
-    const int K = J.nz;
-    const float h = (float)J.dx;
+    int K;
+    float h;
+    RayPos rp_cell;   // unused on the cell-exact views
+    if constexpr (OBL) {
+      const RaySet rs = ray_setup_call(J, px, py);
+      K = rs.K;
+      h = rs.h;
+      if (K <= 0) continue;   // a ray that misses the box has no gradient
+      // the ray's sample positions and step go to the warp's shared slot (the
+      // records pass and the reverse sweep read them there)
+      if (lane == 0) {
+        RA->rp = rs.rp;
+        RA->cad_h = PF.cad * h;   // d(h alpha_D) / d n_H2 with the ray's step
+      }
+      __syncwarp();
+    } else {
+      K = J.nz;
+      h = (float)J.dx;
+    }
     VGrid G;
     G.ufw_hi = (float)J.ufirst;
     G.ufw_lo = (float)(J.ufirst - (double)G.ufw_hi);
@@ -656,7 +724,7 @@ adj_kernel(const __grid_constant__ JobTable tab, const PhysF PF, const AdjArgs A
     G.dvf_lo = (float)(J.dvf - (double)G.dvf_hi);
 
     // ---- records
-    RayPos rp;
+    const RayPos& rp = OBL ? RA->rp : rp_cell;
     int hlo = 1 << 20, hhi = -1, wmax = 0;
     float admax = 0.0f;
     for (int k0 = 0; k0 < K; k0 += 32) {
@@ -753,8 +821,9 @@ adj_kernel(const __grid_constant__ JobTable tab, const PhysF PF, const AdjArgs A
 
     if (!ok) {
       if (K <= 1) {
-        // the output is the background: no gradient
-        for (int k = lane; k < K; k += 32) {
+        // the output is the background: no gradient (an oblique ray adds
+        // nothing to the cleared gradients)
+        for (int k = lane; !OBL && k < K; k += 32) {
           const long long idx = ((long long)zcell(J, k) * J.ny + py) * J.nx + px;
           A.grad[0][idx] = 0.0f;
           A.grad[1][idx] = 0.0f;
@@ -772,10 +841,10 @@ adj_kernel(const __grid_constant__ JobTable tab, const PhysF PF, const AdjArgs A
     const float lx = (lane == 0) ? lx0 : ((lane == 1) ? lx1 : ((lane == 2) ? lx2 : 0.0f));
 
     if (ns == 1)
-      adj_dispatch<1, NI, ST>(std::integer_sequence<int, IRT_ADJ_BUCKETS1>{}, nb, RA, rec, chainf,
+      adj_dispatch<1, NI, ST, OBL>(std::integer_sequence<int, IRT_ADJ_BUCKETS1>{}, nb, RA, rec, chainf,
                               K, hb, lane, G, nfw, lamf, lx, pbuf, scr, px, py);
     else
-      adj_dispatch<2, NI, ST>(std::integer_sequence<int, IRT_ADJ_BUCKETS2>{}, nb, RA, rec, chainf,
+      adj_dispatch<2, NI, ST, OBL>(std::integer_sequence<int, IRT_ADJ_BUCKETS2>{}, nb, RA, rec, chainf,
                               K, hb, lane, G, nfw, lamf, lx, pbuf, scr, px, py);
     __syncwarp();
   }
@@ -1118,35 +1187,7 @@ adj_dense_kernel(const __grid_constant__ JobTable tab, const PhysF PF, const Den
         }
         continue;
       }
-      // oblique: the sample is the trilinear blend of eight cells (indices
-      // clamped to the grid), so each takes its weight of the sample's partials
-      int i0[3];
-      float w[3];
-#pragma unroll
-      for (int a = 0; a < 3; ++a) {
-        const long long pp = rp.base[a] + (long long)k * rp.step[a];
-        i0[a] = (int)(pp >> 32);
-        w[a] = (float)(unsigned)(pp & 0xFFFFFFFFll) * 2.3283064365386963e-10f;
-      }
-      const int nn[3] = {J.nx, J.ny, J.nz};
-      int lo3[3], hi3[3];
-#pragma unroll
-      for (int a = 0; a < 3; ++a) {
-        lo3[a] = min(max(i0[a], 0), nn[a] - 1);
-        hi3[a] = min(max(i0[a] + 1, 0), nn[a] - 1);
-      }
-#pragma unroll
-      for (int c = 0; c < 8; ++c) {
-        const int ix = (c & 1) ? hi3[0] : lo3[0];
-        const int iy = (c & 2) ? hi3[1] : lo3[1];
-        const int iz = (c & 4) ? hi3[2] : lo3[2];
-        const float ww = ((c & 1) ? w[0] : 1.0f - w[0]) * ((c & 2) ? w[1] : 1.0f - w[1]) *
-                         ((c & 4) ? w[2] : 1.0f - w[2]);
-        const long long idx = ((long long)iz * J.ny + iy) * J.nx + ix;
-        atomicAdd(A.grad[0] + idx, ww * gn);
-        atomicAdd(A.grad[1] + idx, ww * gt);
-        atomicAdd(A.grad[2] + idx, ww * gv);
-      }
+      scatter_trilinear(J.nx, J.ny, J.nz, rp.base, rp.step, k, gn, gt, gv, A.grad);
     }
     __syncwarp();
   }
@@ -1155,7 +1196,8 @@ adj_dense_kernel(const __grid_constant__ JobTable tab, const PhysF PF, const Den
 }  // namespace dev
 
 // Host launcher: smooth integration, float arithmetic, one window.
-int launch_adjoint(int store, int ni, const JobTable& tab, const PhysF& PF, const AdjArgs& A,
+int launch_adjoint(int store, int ni, bool obl, const JobTable& tab, const PhysF& PF,
+                   const AdjArgs& A,
                    long long total_items, unsigned long long* queue, int blocks, int kmax,
                    int nfw, int nchan, cudaStream_t stream, int* per_warp_smem) {
   const int rec_bytes = (int)sizeof(dev::RecS32) * kmax;
@@ -1172,7 +1214,7 @@ int launch_adjoint(int store, int ni, const JobTable& tab, const PhysF& PF, cons
   const size_t smem = (size_t)per_warp * kAdjWarps;
 #define IRT_LAUNCH(NI_, ST_)                                                                  \
   if (ni == NI_ && store == ST_) {                                                            \
-    auto kern = dev::adj_kernel<NI_, ST_>;                                                    \
+    auto kern = obl ? dev::adj_kernel<NI_, ST_, true> : dev::adj_kernel<NI_, ST_, false>;      \
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,   \
                                          (int)smem);                                          \
     if (e != cudaSuccess) return (int)e;                                                      \
@@ -1239,14 +1281,13 @@ int launch_adjoint_dense(int store, const JobTable& tab, const PhysF& PF, float*
 }
 
 // Blocks per SM the adjoint kernel reaches with the given shared memory.
-int adjoint_blocks_per_sm(int store, int ni, size_t smem) {
+int adjoint_blocks_per_sm(int store, int ni, bool obl, size_t smem) {
   int per_sm = 0;
 #define IRT_OCC(NI_, ST_)                                                                     \
   if (ni == NI_ && store == ST_) {                                                            \
-    cudaFuncSetAttribute(dev::adj_kernel<NI_, ST_>,                                           \
-                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);             \
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dev::adj_kernel<NI_, ST_>,         \
-                                                  kAdjWarps * 32, smem);                      \
+    auto kern = obl ? dev::adj_kernel<NI_, ST_, true> : dev::adj_kernel<NI_, ST_, false>;      \
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);       \
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kAdjWarps * 32, smem);       \
     return per_sm;                                                                            \
   }
   IRT_OCC(4, ST_F32) IRT_OCC(9, ST_F32) IRT_OCC(17, ST_F32) IRT_OCC(33, ST_F32)

@@ -39,10 +39,10 @@ int launch_tb_convert(int precision, void* T, void* C, void* B, void* L, void* D
 int launch_thin(int precision, int store, int integ, int transfer, const JobTable& tab,
                 int njobs, const PhysParams& P, const PhysF& PF, long long total, int kmax,
                 int nchan_max, unsigned long long* stats, cudaStream_t stream);
-int launch_adjoint(int store, int ni, const JobTable& tab, const PhysF& PF, const AdjArgs& A,
-                   long long total_items, unsigned long long* queue, int blocks, int kmax,
+int launch_adjoint(int store, int ni, bool obl, const JobTable& tab, const PhysF& PF,
+                   const AdjArgs& A, long long total_items, unsigned long long* queue, int blocks, int kmax,
                    int nfw, int nchan, cudaStream_t stream, int* per_warp_smem);
-int adjoint_blocks_per_sm(int store, int ni, size_t smem);
+int adjoint_blocks_per_sm(int store, int ni, bool obl, size_t smem);
 size_t adjoint_dense_smem_per_warp(int kmax, int nchan);
 long long adjoint_dense_scratch_per_warp(int kmax);
 int launch_adjoint_dense(int store, const JobTable& tab, const PhysF& PF, float* const grad[3],
@@ -1497,11 +1497,13 @@ extern "C" irt_status irt_adjoint_ppv(const irt_job* job, const irt_line* line,
     return fail(IRT_EUNSUPPORTED, "irt_adjoint_ppv: rays of %d samples with %d channels need "
                                   "%zu bytes of shared memory per warp (at most 112640)",
                 p.kmax, nch, dense_smem);
-  // the fast sweep (hull blocks in registers, continuum basis) takes z- and
-  // radial-view smooth jobs of one channel window; every other job, and the
-  // rays of a fast job that it cannot take, go to the general sweep
-  const bool fast = jb.view.trilinear != 1 && opts->integration == IRT_SMOOTH &&
-                    jb.vaxis.subsample_f >= 1 && p.nwin == 1;
+  // the fast sweep (hull blocks in registers, continuum basis) takes smooth
+  // jobs of one channel window on any view; every other job, and the rays of
+  // a fast job that it cannot take, go to the general sweep
+  const bool fast = opts->integration == IRT_SMOOTH && jb.vaxis.subsample_f >= 1 && p.nwin == 1;
+  // oblique rays run their own kernel instances (ray set-up, trilinear
+  // scatter of the gradients), so the cell-exact instances carry neither
+  const bool obl = jb.view.trilinear == 1;
   JobTable tab;
   std::memset(&tab, 0, sizeof tab);
   tab.j[0] = make_jobdev(jb, p);
@@ -1543,13 +1545,13 @@ extern "C" irt_status irt_adjoint_ppv(const irt_job* job, const irt_line* line,
   if (fast) {
     for (int q = 0; q < 5; ++q) A.cot[q] = cot[q];
     for (int q = 0; q < 3; ++q) A.grad[q] = grads[q];
-    e = launch_adjoint(g->store, nis[0], tab, PF, A, 0, nullptr, 0, p.kmax, p.nfw, nch, s,
+    e = launch_adjoint(g->store, nis[0], obl, tab, PF, A, 0, nullptr, 0, p.kmax, p.nfw, nch, s,
                        &per_warp);
     if (e) return cuda_fail(e, "irt_adjoint_ppv: kernel attributes");
     const size_t smem = (size_t)per_warp * kAdjWarps;
     int bmax = 0;
     for (size_t i = 0; i < nis.size(); ++i) {
-      blocks[i] = std::max(1, adjoint_blocks_per_sm(g->store, nis[i], smem)) * sms;
+      blocks[i] = std::max(1, adjoint_blocks_per_sm(g->store, nis[i], obl, smem)) * sms;
       bmax = std::max(bmax, blocks[i]);
     }
     // checkpoints, one stored sub-segment, the per-sample chain-rule factors
@@ -1578,6 +1580,12 @@ extern "C" irt_status irt_adjoint_ppv(const irt_job* job, const irt_line* line,
     ce = cudaMemsetAsync(dense_list + l * (size_t)(total + 1), 0, sizeof(unsigned), s);
   if (ce != cudaSuccess) return cuda_fail(ce, "irt_adjoint_ppv: queue reset");
   unsigned long long* dense_queue = queues;
+  if (jb.view.trilinear == 1) {
+    // oblique views: every ray adds into the cells of its samples' stencils
+    const size_t cb = (size_t)g->nx * g->ny * g->nz * sizeof(float);
+    for (int q = 0; q < 3 && ce == cudaSuccess; ++q) ce = cudaMemsetAsync(grads[q], 0, cb, s);
+    if (ce != cudaSuccess) return cuda_fail(ce, "irt_adjoint_ppv: clear gradients");
+  }
   if (fast) {
     A.scratch = reinterpret_cast<float*>(ss.adj);
     A.scratch_per_warp = per_warp_floats;
@@ -1592,16 +1600,11 @@ extern "C" irt_status irt_adjoint_ppv(const irt_job* job, const irt_line* line,
       const bool last = i + 1 == nis.size();
       A.defer = last ? nullptr : dense_list + (i + 1) * (size_t)(total + 1);
       A.defer_max_nb = last ? 0 : nis.back();
-      e = launch_adjoint(g->store, nis[i], tab, PF, A, total, queues + 1 + i, blocks[i], p.kmax,
+      e = launch_adjoint(g->store, nis[i], obl, tab, PF, A, total, queues + 1 + i, blocks[i], p.kmax,
                          p.nfw, nch, s, nullptr);
       ++g_launches;
       if (e) return cuda_fail(e, "irt_adjoint_ppv: adjoint kernel");
     }
-  } else if (jb.view.trilinear == 1) {
-    // oblique views: every ray adds into the cells of its samples' stencils
-    const size_t cb = (size_t)g->nx * g->ny * g->nz * sizeof(float);
-    for (int q = 0; q < 3 && ce == cudaSuccess; ++q) ce = cudaMemsetAsync(grads[q], 0, cb, s);
-    if (ce != cudaSuccess) return cuda_fail(ce, "irt_adjoint_ppv: clear gradients");
   }
   // the general sweep: the fast job's leftover rays (a list filled on the
   // device), or every ray of the job

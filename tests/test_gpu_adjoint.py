@@ -110,6 +110,29 @@ def test_adjoint_matches_oracle_gradient_16cube(save):
     assert all(v <= 1.0 for v in r.values()), r
 
 
+@pytest.mark.parametrize("nz", [9, 17, 25, 33])
+def test_adjoint_columns_of_every_flush_split(nz):
+    """Columns whose first 32-sample segment is not a multiple of the partial
+    flush: the trapezoidal start reverses samples 0 and 1 together, so no
+    flush group may end at sample 1 (nz = 9, 17, 25 put a group boundary
+    there with eight-sample groups)."""
+    w = workload(3, n=48)
+    fs = make_fields(48, w.seed)
+    tfs = make_fields(48, w.seed + 7)
+    sl = (slice(0, nz), slice(0, 6), slice(0, 7))
+    fs = FieldSet(*[np.ascontiguousarray(a[sl]) for a in fs.as_tuple()])
+    tfs = FieldSet(*[np.ascontiguousarray(a[sl]) for a in tfs.as_tuple()])
+    f32, deq = to_storage(fs, np.float32)
+    t32, tdeq = to_storage(tfs, np.float32)
+    view = View(0.0, 0.0, 7, 6, w.cell_cm, 0)
+    va = w.vaxis
+    target = oracle.render_cube(tdeq.as_tuple(), w.cell_cm, LINE, DUST, view, va)["L"]
+    loss, (gn, gt, gv) = _gpu_loss_grads(f32, w.cell_cm, view, va, target)
+    oloss, on, ot, ov = oracle.loss_grad_zview(deq.as_tuple(), w.cell_cm, LINE, DUST, va, target)
+    r = {k: _cmp(a, b, nz) for k, a, b in (("n", gn, on), ("T", gt, ot), ("v", gv, ov))}
+    assert all(v <= 1.0 for v in r.values()), r
+
+
 def test_saved_checkpoints_serve_only_the_same_job():
     """Checkpoints written by one render are used by the adjoint of the same
     job (results within float rounding of the self-contained adjoint) and

@@ -1,7 +1,9 @@
-"""The general reverse sweep (every velocity explicit): oblique views, the
-formal and Kahan-compensated formal integrators, f = 0, several channel
-windows, and the smooth z-view rays the fast sweep hands over (dust optically
-thick per step, line windows wider than two slots).  Gradients of
+"""The adjoint beyond the z-view fast sweep: oblique views (the fast sweep
+for smooth integration, the general sweep otherwise), and the general reverse
+sweep (every velocity explicit) for the formal and Kahan-compensated formal
+integrators, f = 0, several channel windows, and the smooth z-view rays the
+fast sweep hands over (dust optically thick per step, line windows wider
+than two slots).  Gradients of
 Loss = mean(([L] - target)^2) against the FP64 oracle's dual-number
 gradients, 1e-3 relative per cell with an absolute floor at the float32
 rounding of the K-step recurrences (K 2^-24 of the largest gradient)."""
@@ -77,6 +79,33 @@ def test_oblique_view_gradient(integration):
     assert all(v <= 1.0 for v in r.values()), r
     # the gradient reaches cells of many rays: the stencils overlap
     assert np.count_nonzero(gn) > n * n
+
+
+def test_oblique_fast_sweep_all_passes():
+    """Smooth oblique rays go through the fast sweep (4, 9 and full-width
+    register passes by hull width, records and positions per ray); f = 2 and a
+    13-block fine axis give hulls of every width."""
+    n = 24
+    fs = make_fields(n, 81)
+    f32, deq = to_storage(fs, np.float32)
+    tf32, tdeq = to_storage(make_fields(n, 88), np.float32)
+    dx = 0.1 * PC
+    view = View(math.radians(70), math.radians(200), 30, 28, 0.8 * dx, 1)
+    va = VelocityAxis(96, -72.0, 1.5, 2)
+    target = oracle.render_cube(tdeq.as_tuple(), dx, LINE, DUST, view, va,
+                                integration=oracle.SMOOTH)["L"]
+    gn, gt, gv = _gpu(f32, dx, view, va, target, "smooth")
+    rng = np.random.default_rng(17)
+    cells = np.stack([rng.integers(0, n, 40), rng.integers(0, n, 40), rng.integers(0, n, 40)],
+                     axis=1)
+    loss, on, ot, ov = oracle.loss_grad_cells(deq.as_tuple(), dx, LINE, DUST, view, va, target,
+                                              cells, integration=oracle.SMOOTH)
+    got = {k: np.array([a[z, y, x] for x, y, z in cells]) for k, a in (("n", gn), ("T", gt),
+                                                                        ("v", gv))}
+    K = 2 * n
+    r = {"n": _cmp(got["n"], on, K), "T": _cmp(got["T"], ot, K), "v": _cmp(got["v"], ov, K)}
+    assert all(v <= 1.0 for v in r.values()), r
+    assert np.count_nonzero(on) > 20
 
 
 @pytest.mark.parametrize("integration,f,nch,dv", [("formal", 2, 40, 3.0),
