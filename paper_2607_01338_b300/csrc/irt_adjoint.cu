@@ -408,12 +408,6 @@ __device__ __forceinline__ void scatter_trilinear(int nx, int ny, int nz, const 
   }
 }
 
-// The ray set-up as a call of its own: its float-float temporaries then take
-// no registers of the sweep kernel around it.
-__device__ __noinline__ RaySet ray_setup_call(const JobDev& J, int px, int py) {
-  return ray_setup(J, px, py);
-}
-
 // Launch constants the reverse sweep reads, kept in shared memory: the sweep
 // is a separate (non-inlined) function per hull bucket, and a reference to
 // the kernel's parameters would make the compiler copy them to the stack,
@@ -679,7 +673,7 @@ adj_kernel(const __grid_constant__ JobTable tab, const PhysF PF, const AdjArgs A
     RA->nz = J.nz;
     RA->zrev = J.zrev;
     RA->zview = J.zview;
-    RA->cad_h = PF.cad * (float)J.dx;   // cell-exact views (oblique rays: per ray below)
+    RA->cad_h = PF.cad * J.fdx[0];   // cell-exact views (oblique rays: per ray below)
     RA->T0 = PF.T0;
     RA->inv_c_kms = PF.inv_c_kms;
     RA->t_bg = PF.t_bg;
@@ -715,13 +709,13 @@ adj_kernel(const __grid_constant__ JobTable tab, const PhysF PF, const AdjArgs A
       __syncwarp();
     } else {
       K = J.nz;
-      h = (float)J.dx;
+      h = J.fdx[0];
     }
     VGrid G;
-    G.ufw_hi = (float)J.ufirst;
-    G.ufw_lo = (float)(J.ufirst - (double)G.ufw_hi);
-    G.dvf_hi = (float)J.dvf;
-    G.dvf_lo = (float)(J.dvf - (double)G.dvf_hi);
+    G.ufw_hi = J.fufirst[0];
+    G.ufw_lo = J.fufirst[1];
+    G.dvf_hi = J.fdvf[0];
+    G.dvf_lo = J.fdvf[1];
 
     // ---- records
     const RayPos& rp = OBL ? RA->rp : rp_cell;
@@ -766,7 +760,7 @@ adj_kernel(const __grid_constant__ JobTable tab, const PhysF PF, const AdjArgs A
       const float gC = A.cot[1] ? A.cot[1][o] : 0.0f;
       const float gD = A.cot[2] ? A.cot[2][o] : 0.0f;
       const float gL = A.cot[3] ? A.cot[3][o] : 0.0f;
-      const float uc = (float)J.v0 + ((float)c + 0.5f) * (float)J.dv;
+      const float uc = J.fv0[0] + ((float)c + 0.5f) * J.fdv[0];
       float s = PF.out_scale;
       if (PF.units == IRT_UNITS_TRJ) {
         const float y = 1.0f - uc * PF.inv_c_kms;
@@ -966,16 +960,16 @@ adj_dense_kernel(const __grid_constant__ JobTable tab, const PhysF PF, const Den
     if (slot >= n_items) break;
     const long long item = A.list ? (long long)A.list[1 + slot] : slot;
     const int px = (int)(item % J.npx), py = (int)(item / J.npx);
-    const RaySet rs = ray_setup(J, px, py);
+    const RaySet rs = ray_setup_call(J, px, py);
     const int K = rs.K;
     if (K <= 0) continue;   // a ray missing the box has no gradient
     const float h = rs.h;
     const RayPos rp = rs.rp;
     VGrid G;
-    G.ufw_hi = (float)J.ufirst;
-    G.ufw_lo = (float)(J.ufirst - (double)G.ufw_hi);
-    G.dvf_hi = (float)J.dvf;
-    G.dvf_lo = (float)(J.dvf - (double)G.dvf_hi);
+    G.ufw_hi = J.fufirst[0];
+    G.ufw_lo = J.fufirst[1];
+    G.dvf_hi = J.fdvf[0];
+    G.dvf_lo = J.fdvf[1];
     // ---- per-sample quantities
     for (int k = lane; k < K; k += 32) {
       float raw[6];
@@ -1004,7 +998,7 @@ adj_dense_kernel(const __grid_constant__ JobTable tab, const PhysF PF, const Den
       const float gC = A.cot[1] ? A.cot[1][o] : 0.0f;
       const float gD = A.cot[2] ? A.cot[2][o] : 0.0f;
       const float gL = A.cot[3] ? A.cot[3][o] : 0.0f;
-      const float uc = (float)J.v0 + ((float)c + 0.5f) * (float)J.dv;
+      const float uc = J.fv0[0] + ((float)c + 0.5f) * J.fdv[0];
       float s = PF.out_scale;
       if (PF.units == IRT_UNITS_TRJ) {
         const float y = 1.0f - uc * PF.inv_c_kms;
@@ -1026,7 +1020,7 @@ adj_dense_kernel(const __grid_constant__ JobTable tab, const PhysF PF, const Den
         lend = (f >= 1) ? fine_cotangent(phi, f, nch, lamT) : lamT[phi];
       } else {
         const int c = min(phi - nfw, nch - 1);
-        u = (float)J.v0 + ((float)c + 0.5f) * (float)J.dv;
+        u = J.fv0[0] + ((float)c + 0.5f) * J.fdv[0];
         gphi = (f >= 1) ? 2 * f * c + f : c;
         if (phi < nfreq) lend = lamC[c];
       }

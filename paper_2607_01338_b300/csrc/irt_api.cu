@@ -437,6 +437,13 @@ Plan plan_job(const irt_job& jb, int precision, int force_ni) {
   return p;
 }
 
+// x as a float-float pair {hi, lo}: hi = x rounded to float, lo = the
+// rest rounded to float
+static void split_ff(double x, float out[2]) {
+  out[0] = (float)x;
+  out[1] = (float)(x - (double)out[0]);
+}
+
 JobDev make_jobdev(const irt_job& jb, const Plan& p) {
   JobDev d;
   std::memset(&d, 0, sizeof d);
@@ -459,36 +466,24 @@ JobDev make_jobdev(const irt_job& jb, const Plan& p) {
     const double dd[3] = {st * cp, st * sp, ct};
     const double et[3] = {ct * cp, ct * sp, -st};
     const double ep[3] = {-sp, cp, 0.0};
-    for (int a = 0; a < 3; ++a) {
-      d.d[a] = dd[a];
-      d.et[a] = et[a];
-      d.ep[a] = ep[a];
-      d.inv_d[a] = dd[a] != 0.0 ? 1.0 / dd[a] : HUGE_VAL;
-    }
-    d.inv_dx = 1.0 / g->dx;
     // float-float form in cell units: o = (n/2 + (px - cx) P e_theta + (py -
     // cy) P e_phi), P = pixel / dx, cx = (npx - 1)/2
-    auto split = [](double x, float out[2]) {
-      out[0] = (float)x;
-      out[1] = (float)(x - (double)out[0]);
-    };
     const double P = jb.view.pixel_cm / g->dx;
     const double cx = 0.5 * (jb.view.npx - 1), cy = 0.5 * (jb.view.npy - 1);
     const int n[3] = {g->nx, g->ny, g->nz};
     for (int a = 0; a < 3; ++a) {
-      split(0.5 * n[a] - cx * P * et[a] - cy * P * ep[a], d.fo0[a]);
-      split(P * et[a], d.fox[a]);
-      split(P * ep[a], d.foy[a]);
+      split_ff(0.5 * n[a] - cx * P * et[a] - cy * P * ep[a], d.fo0[a]);
+      split_ff(P * et[a], d.fox[a]);
+      split_ff(P * ep[a], d.foy[a]);
       // an axis with |d| < 1e-30 counts as parallel (1/d would not fit a float)
       const bool par = std::fabs(dd[a]) < 1e-30;
-      split(par ? 0.0 : dd[a], d.fd[a]);
-      split(par ? 0.0 : 1.0 / dd[a], d.finv_d[a]);
+      split_ff(par ? 0.0 : dd[a], d.fd[a]);
+      split_ff(par ? 0.0 : 1.0 / dd[a], d.finv_d[a]);
     }
-    split(g->dx, d.fdx);
+    split_ff(g->dx, d.fdx);
   }
   d.npx = jb.view.npx;
   d.npy = jb.view.npy;
-  d.pixel = jb.view.pixel_cm;
   d.nchan = jb.vaxis.nchan;
   d.f = jb.vaxis.subsample_f;
   d.v0 = jb.vaxis.v_first_edge_kms;
@@ -500,6 +495,11 @@ JobDev make_jobdev(const irt_job& jb, const Plan& p) {
     d.ufirst = d.v0 + 0.5 * d.dv;
     d.dvf = d.dv;
   }
+  split_ff(d.v0, d.fv0);
+  split_ff(d.dv, d.fdv);
+  split_ff(d.ufirst, d.fufirst);
+  split_ff(d.dvf, d.fdvf);
+  d.finv_dv = (float)(1.0 / d.dv);
   d.cw = p.cw;
   d.nwin = p.nwin;
   d.kmax = p.kmax;

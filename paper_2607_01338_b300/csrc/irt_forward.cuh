@@ -92,14 +92,19 @@ __device__ __forceinline__ void load_cell(const void* cells, long long idx, int 
 __device__ __forceinline__ int zcell(const JobDev& J, int k) { return J.zrev ? J.nz - 1 - k : k; }
 
 // ---------------------------------------------------------------------------
-// ray geometry (double precision: the sample count must be exact)
+// ray geometry of the double kernels: the view's float-float coefficients
+// (cell units) evaluated in double; the sample count K = ceil(chord - 1e-9)
+// must be exact, and is the one the float kernels' set-up below reaches
 // ---------------------------------------------------------------------------
 struct RayGeom {
   int K;
-  double h;
-  double o[3], d[3];
-  double t0;
+  double h;        // step [cm]
+  double hc;       // step [cells]
+  double o[3], d[3];   // origin [cells], direction
+  double t0;       // entry [cells]
 };
+
+__device__ __forceinline__ double ff_wide(const float v[2]) { return (double)v[0] + (double)v[1]; }
 
 __device__ inline RayGeom ray_geom(const JobDev& J, int px, int py) {
   RayGeom g;
@@ -107,39 +112,53 @@ __device__ inline RayGeom ray_geom(const JobDev& J, int px, int py) {
   if (J.zview) {
     g.K = J.nz;
     g.h = J.dx;
+    g.hc = 1.0;
     g.o[0] = g.o[1] = g.o[2] = 0.0;
     g.d[0] = g.d[1] = 0.0;
     g.d[2] = 1.0;
     return g;
   }
-  const double L[3] = {J.nx * J.dx, J.ny * J.dx, J.nz * J.dx};
-  const double a = (px - 0.5 * (J.npx - 1)) * J.pixel;
-  const double b = (py - 0.5 * (J.npy - 1)) * J.pixel;
+  const double L[3] = {(double)J.nx, (double)J.ny, (double)J.nz};
   double lo = -CUDART_INF, hi = CUDART_INF;
   bool miss = false;
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
-    g.d[i] = J.d[i];
-    g.o[i] = 0.5 * L[i] + a * J.et[i] + b * J.ep[i];
-    if (J.d[i] == 0.0) {
+    g.d[i] = ff_wide(J.fd[i]);
+    g.o[i] = ff_wide(J.fo0[i]) + px * ff_wide(J.fox[i]) + py * ff_wide(J.foy[i]);
+    if (J.fd[i][0] == 0.0f) {
       if (g.o[i] < 0.0 || g.o[i] > L[i]) miss = true;
       continue;
     }
-    double t0 = (0.0 - g.o[i]) * J.inv_d[i], t1 = (L[i] - g.o[i]) * J.inv_d[i];
+    const double inv = ff_wide(J.finv_d[i]);
+    double t0 = (0.0 - g.o[i]) * inv, t1 = (L[i] - g.o[i]) * inv;
     if (t0 > t1) { const double t = t0; t0 = t1; t1 = t; }
     lo = fmax(lo, t0);
     hi = fmin(hi, t1);
   }
-  if (miss || !(hi > lo)) {
+  g.K = 0;
+  g.h = g.hc = 0.0;
+  if (miss || !(hi > lo)) return g;
+  const double chord = hi - lo;
+  g.K = (int)ceil(chord - 1e-9);
+  if (g.K <= 0) {
     g.K = 0;
-    g.h = 0.0;
     return g;
   }
-  const double chord = hi - lo;
-  g.K = (int)ceil(chord * J.inv_dx - 1e-9);
-  g.h = (g.K > 0) ? chord / g.K : 0.0;
+  g.hc = chord / g.K;
+  g.h = g.hc * J.dx;
   g.t0 = lo;
   return g;
+}
+
+// fractional cell coordinates (cell centres at integers) of sample k
+__device__ __forceinline__ void sample_cell(const RayGeom& g, int k, int i0[3], double w[3]) {
+  const double t = g.t0 + (k + 0.5) * g.hc;
+  for (int a = 0; a < 3; ++a) {
+    const double s = g.o[a] + t * g.d[a] - 0.5;
+    const double fl = floor(s);
+    w[a] = s - fl;
+    i0[a] = (int)fl;
+  }
 }
 
 // Trilinear blend of the eight cells around fractional cell coordinates
@@ -190,38 +209,19 @@ __device__ __forceinline__ void sample_raw(const JobDev& J, const RayGeom& g, in
                           v);
     return;
   }
-  const double t = g.t0 + (k + 0.5) * g.h;
   int i0[3];
   double w[3];
-  for (int a = 0; a < 3; ++a) {
-    const double s = (g.o[a] + t * g.d[a]) * J.inv_dx - 0.5;
-    const double fl = floor(s);
-    w[a] = s - fl;
-    i0[a] = (int)fl;
-  }
+  sample_cell(g, k, i0, w);
   trilinear<double, ST>(J, i0, w, v);
 }
 
-// Oblique sample positions in 32.32 fixed point (cell units, cell centres at
-// integers): sample k sits at base + k step.  Base and step are rounded from
-// double once per ray; the position of sample k is then exact to
-// k * 2^-33 cells (1e-7 cells after 900 samples).
+// Oblique sample positions of the float kernels in 32.32 fixed point (cell
+// units, cell centres at integers): sample k sits at base + k step.  Base and
+// step are rounded once per ray (ray_setup below); the position of sample k
+// is then exact to k * 2^-33 cells (1e-7 cells after 900 samples).
 struct RayPos {
   long long base[3], step[3];
 };
-
-__device__ __forceinline__ RayPos ray_pos(const JobDev& J, const RayGeom& g) {
-  RayPos c;
-  const double t = g.t0 + 0.5 * g.h;
-  const double sc = 4294967296.0;   // 2^32
-#pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    const double s = (g.o[a] + t * g.d[a]) * J.inv_dx - 0.5;
-    c.base[a] = __double2ll_rn(s * sc);
-    c.step[a] = __double2ll_rn(g.h * g.d[a] * J.inv_dx * sc);
-  }
-  return c;
-}
 
 // ---------------------------------------------------------------------------
 // Ray set-up of the float kernels, without double arithmetic.  The chord, the
@@ -232,7 +232,7 @@ __device__ __forceinline__ RayPos ray_pos(const JobDev& J, const RayGeom& g) {
 // product (the fma residual).  Its rounding, about 1e-11 cells on a
 // 1000-cell chord, is far below the 1e-9 slack of the sample count, so K is
 // the double-precision value except on chords within ~1e-11 of that slack.
-// The double kernels keep ray_geom / ray_pos above.
+// The double kernels keep ray_geom above.
 // ---------------------------------------------------------------------------
 struct FF {
   float hi, lo;
@@ -289,6 +289,13 @@ struct RaySet {
 // The chord of pixel (px, py) through the box [0, n]^3 (cell units): the
 // latest entry and the earliest exit over the three slabs; an axis with
 // d = 0 is a miss when the origin lies outside its slab.
+__device__ __forceinline__ FF ff_shfl(FF x, int src) {
+  return FF{__shfl_sync(0xffffffffu, x.hi, src), __shfl_sync(0xffffffffu, x.lo, src)};
+}
+
+// Called by the 32 lanes of a warp together (one ray per warp): lane a < 3
+// evaluates axis a, the entry / exit and the positions are exchanged with
+// shuffles, so the warp issues the per-axis work once instead of three times.
 __device__ inline RaySet ray_setup(const JobDev& J, int px, int py) {
   RaySet r;
   r.K = 0;
@@ -298,31 +305,35 @@ __device__ inline RaySet ray_setup(const JobDev& J, int px, int py) {
     r.h = J.fdx[0];
     return r;
   }
-  const float fx = (float)px, fy = (float)py;
-  const int n[3] = {J.nx, J.ny, J.nz};
-  FF o[3];
-  FF lo{-INFINITY, 0.0f}, hi{INFINITY, 0.0f};
+  const int lane = threadIdx.x & 31;
+  const int a = min(lane, 2);   // this lane's axis (lanes 3..31 repeat axis 2)
+  const int na_i = (a == 0) ? J.nx : ((a == 1) ? J.ny : J.nz);
+  const FF o = ff_add(ff_load(J.fo0[a]), ff_add(ff_mul_f(ff_load(J.fox[a]), (float)px),
+                                                ff_mul_f(ff_load(J.foy[a]), (float)py)));
+  const FF na{(float)na_i, 0.0f};
+  FF t0{-INFINITY, 0.0f}, t1{INFINITY, 0.0f};
   bool miss = false;
-#pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    o[a] = ff_add(ff_load(J.fo0[a]),
-                  ff_add(ff_mul_f(ff_load(J.fox[a]), fx), ff_mul_f(ff_load(J.foy[a]), fy)));
-    const FF na{(float)n[a], 0.0f};
-    if (J.fd[a][0] == 0.0f) {
-      if (ff_lt(o[a], FF{0.0f, 0.0f}) || ff_lt(na, o[a])) miss = true;
-      continue;
-    }
+  if (J.fd[a][0] == 0.0f) {
+    miss = ff_lt(o, FF{0.0f, 0.0f}) || ff_lt(na, o);
+  } else {
     const FF inv = ff_load(J.finv_d[a]);
-    FF t0 = ff_mul(ff_neg(o[a]), inv);
-    FF t1 = ff_mul(ff_add(na, ff_neg(o[a])), inv);
+    t0 = ff_mul(ff_neg(o), inv);
+    t1 = ff_mul(ff_add(na, ff_neg(o)), inv);
     if (ff_lt(t1, t0)) {
       const FF t = t0;
       t0 = t1;
       t1 = t;
     }
-    if (ff_lt(lo, t0)) lo = t0;
-    if (ff_lt(t1, hi)) hi = t1;
   }
+  // latest entry and earliest exit over the three axes (lanes 0, 1, 2)
+  FF lo = ff_shfl(t0, 0), hi = ff_shfl(t1, 0);
+#pragma unroll
+  for (int b = 1; b < 3; ++b) {
+    const FF e = ff_shfl(t0, b), x = ff_shfl(t1, b);
+    if (ff_lt(lo, e)) lo = e;
+    if (ff_lt(x, hi)) hi = x;
+  }
+  miss = __any_sync(0xffffffffu, miss && lane < 3);
   if (miss || !ff_lt(lo, hi)) return r;
   const FF chord = ff_add(hi, ff_neg(lo));
   // 1e-9 as a float-float pair
@@ -334,13 +345,22 @@ __device__ inline RaySet ray_setup(const JobDev& J, int px, int py) {
   // sample k at t_in + (k + 1/2) h; trilinear coordinates are shifted by
   // half a cell (cell centres at integers)
   const FF tm = ff_add(lo, FF{0.5f * h.hi, 0.5f * h.lo});
+  const FF d = ff_load(J.fd[a]);
+  const long long base = ff_fix32(ff_add(ff_add(o, ff_mul(tm, d)), FF{-0.5f, 0.0f}));
+  const long long step = ff_fix32(ff_mul(h, d));
 #pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    const FF d = ff_load(J.fd[a]);
-    r.rp.base[a] = ff_fix32(ff_add(ff_add(o[a], ff_mul(tm, d)), FF{-0.5f, 0.0f}));
-    r.rp.step[a] = ff_fix32(ff_mul(h, d));
+  for (int b = 0; b < 3; ++b) {
+    r.rp.base[b] = __shfl_sync(0xffffffffu, base, b);
+    r.rp.step[b] = __shfl_sync(0xffffffffu, step, b);
   }
   return r;
+}
+
+// The ray set-up as a call of its own (once per ray): its float-float
+// temporaries take no registers of the kernel around it, and its code stays
+// out of the kernel's hot instruction stream.
+static __device__ __noinline__ RaySet ray_setup_call(const JobDev& J, int px, int py) {
+  return ray_setup(J, px, py);
 }
 
 // float kernels: sample k of the ray
@@ -429,15 +449,9 @@ __device__ __forceinline__ double sample_chi(const JobDev& J, const RayGeom& g, 
                                              int k) {
   if (J.zview)
     return cell_chi<double, ST>(J.cells, ((long long)zcell(J, k) * J.ny + py) * J.nx + px);
-  const double t = g.t0 + (k + 0.5) * g.h;
   int i0[3];
   double w[3];
-  for (int a = 0; a < 3; ++a) {
-    const double s = (g.o[a] + t * g.d[a]) * J.inv_dx - 0.5;
-    const double fl = floor(s);
-    w[a] = s - fl;
-    i0[a] = (int)fl;
-  }
+  sample_cell(g, k, i0, w);
   return chi_trilinear<double, ST>(J, i0, w);
 }
 

@@ -929,10 +929,14 @@ __device__ void render_ray(const JobDev& J, const PhysParams& PD, const PhysF& P
   const int nfw = (f >= 1) ? 2 * f * nch + 1 : nch;
   const int nblk = (nfw + 31) >> 5;
   VGrid G;
-  G.ufw_hi = (float)J.ufirst;
-  G.ufw_lo = (float)(J.ufirst - (double)G.ufw_hi);
-  G.dvf_hi = (float)J.dvf;
-  G.dvf_lo = (float)(J.dvf - (double)G.dvf_hi);
+  G.ufw_hi = J.fufirst[0];
+  G.ufw_lo = J.fufirst[1];
+  G.dvf_hi = J.fdvf[0];
+  G.dvf_lo = J.fdvf[1];
+  // channel edges: double on the double kernels, the host's float roundings
+  // on the float kernels
+  const R v0r = kDouble ? (R)J.v0 : (R)J.fv0[0];
+  const R dvr = kDouble ? (R)J.dv : (R)J.fdv[0];
 
   // ---- sample pass: lane l evaluates samples l, l + 32, ... into this warp's
   // record slot; the hull of the line windows, the widest window and the
@@ -948,7 +952,7 @@ __device__ void render_ray(const JobDev& J, const PhysParams& PD, const PhysF& P
     K = geo.K;
     h = (R)geo.h;
   } else {
-    const RaySet rs = ray_setup(J, px, py);
+    const RaySet rs = ray_setup_call(J, px, py);
     K = rs.K;
     h = rs.h;
     rp = rs.rp;
@@ -1032,7 +1036,7 @@ __device__ void render_ray(const JobDev& J, const PhysParams& PD, const PhysF& P
   const long long pix = (long long)py * J.npx + px;
   R* const* out = reinterpret_cast<R* const*>(ML ? outp : J.out);
   auto emit = [&](int c, R ibar, R ic_or_nan, bool have_ic, R X0, R X1, R X2) {
-    const R uc = (R)J.v0 + ((R)c + (R)0.5) * (R)J.dv;
+    const R uc = v0r + ((R)c + (R)0.5) * dvr;
     const R ib = planck_k(P, (R)P.t_bg, uc);
     const R ic = have_ic ? ic_or_nan : X0 * ib + X1 + X2 * uc;
     R s = (R)P.out_scale;
@@ -1149,7 +1153,7 @@ __device__ void render_ray(const JobDev& J, const PhysParams& PD, const PhysF& P
 #pragma unroll
       for (int i = 0; i < NI; ++i) {
         const int c = min(lane + 32 * i, cwn - 1);
-        uc[i] = (R)J.v0 + ((R)(c0 + c) + (R)0.5) * (R)J.dv;
+        uc[i] = v0r + ((R)(c0 + c) + (R)0.5) * dvr;
         s0[i] = (i < cblk) ? planck_k(P, (R)P.t_bg, uc[i]) : (R)0;
         s1[i] = (R)0;
         s2[i] = (R)0;

@@ -127,18 +127,20 @@ struct JobDev {
   double dx;             // cell size [cm]
   int zview;             // 1 = cell-exact view along the z axis (z or radial)
   int zrev;              // radial view: sample k is the cell z = nz - 1 - k
-  // oblique view basis (set up on the host from the view angles): ray
-  // direction d, pixel axes et, ep, 1/d per axis (infinite where d = 0), 1/dx
-  double d[3], et[3], ep[3], inv_d[3], inv_dx;
-  // the same view in cell units as float-float pairs {hi, lo} (value = hi +
-  // lo) for the float kernels' ray set-up: ray origin o(px, py) = fo0 + px fox
-  // + py foy, direction fd, 1/d (0 on an axis with d = 0), cell size [cm]
+  // the orthographic view (set up on the host from the view angles) in cell
+  // units as float-float pairs {hi, lo} (value = hi + lo): ray origin
+  // o(px, py) = fo0 + px fox + py foy, direction fd, 1/d (0 on an axis with
+  // d = 0), cell size [cm]; the float kernels evaluate them in float-float
+  // arithmetic, the double kernels in double
   float fo0[3][2], fox[3][2], foy[3][2], fd[3][2], finv_d[3][2], fdx[2];
   int npx, npy;
-  double pixel;          // pixel pitch [cm]
   int nchan, f;
   double v0, dv;         // channel lower edge of channel 0, width [km/s]
   double ufirst, dvf;    // first fine velocity and fine step [km/s]
+  // the same as float-float pairs, and 1/dv rounded to float, for the float
+  // kernels (no double arithmetic per ray)
+  float fv0[2], fdv[2], fufirst[2], fdvf[2];
+  float finv_dv;
   int cw, nwin;          // channels per window, windows per ray
   int tw, th;            // rays are handed out in tiles of tw x th pixels
   int ntx;               // tiles per image row

@@ -125,7 +125,7 @@ thin_kernel(const __grid_constant__ JobTable tab, int njobs, const PhysParams P,
       K = g.K;
       h = (R)g.h;
     } else {
-      const RaySet rs = ray_setup(J, px, py);
+      const RaySet rs = ray_setup_call(J, px, py);
       K = rs.K;
       h = rs.h;
       rp = rs.rp;
@@ -143,9 +143,13 @@ thin_kernel(const __grid_constant__ JobTable tab, int njobs, const PhysParams P,
       continue;
     }
     // ---- records
-    const R sq = (R)0.88622692545275801365 / (R)J.dv;   // sqrt(pi) / (2 dv)
+    // channel width and edges: double on the double kernels, the host's
+    // float roundings on the float kernels
+    const R dvr = kD ? (R)J.dv : (R)J.fdv[0];
+    const R sq = (R)0.88622692545275801365 / dvr;   // sqrt(pi) / (2 dv)
     int hlo = 1 << 30, hhi = -1;   // channels any sample's line reaches
-    const R v0r = (R)J.v0, inv_dv = (R)(1.0 / J.dv);
+    const R v0r = kD ? (R)J.v0 : (R)J.fv0[0];
+    const R inv_dv = kD ? (R)(1.0 / J.dv) : (R)J.finv_dv;
     R admax = (R)0;
     const int nblk = (J.nchan + 30) / 31;
     const int nchunk = (K + 31) / 32;
@@ -174,7 +178,7 @@ thin_kernel(const __grid_constant__ JobTable tab, int njobs, const PhysParams P,
         ad = (R)0;
         e.d0 = (R)0;
         e.d1 = (R)0;
-        e.jw = jl * ((R)0.5 / (R)J.dv);   // times erf(x_hi) - erf(x_lo): x n h mass / dv
+        e.jw = jl * ((R)0.5 / dvr);   // times erf(x_hi) - erf(x_lo): x n h mass / dv
         e.aw = (R)0;
       } else {
         if constexpr (kD) {
@@ -287,8 +291,8 @@ thin_kernel(const __grid_constant__ JobTable tab, int njobs, const PhysParams P,
       atomicAdd(&stats[1], (unsigned long long)K);
     }
     // ---- channels, 31 per pass (lane 31 carries the last upper edge)
-    const float v0h = (float)J.v0, v0l = (float)(J.v0 - (double)v0h);
-    const float dvh = (float)J.dv, dvl = (float)(J.dv - (double)dvh);
+    const float v0h = J.fv0[0], v0l = J.fv0[1];
+    const float dvh = J.fdv[0], dvl = J.fdv[1];
     for (int c0 = 0; c0 < J.nchan; c0 += 31) {
       const int c = c0 + lane;
       const int cend = min(c0 + 31, J.nchan);
