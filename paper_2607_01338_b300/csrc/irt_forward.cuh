@@ -356,9 +356,10 @@ __device__ inline RaySet ray_setup(const JobDev& J, int px, int py) {
   return r;
 }
 
-// The ray set-up as a call of its own (once per ray): its float-float
-// temporaries take no registers of the kernel around it, and its code stays
-// out of the kernel's hot instruction stream.
+// The ray set-up as a call of its own (once per ray), for the adjoint
+// kernels: its float-float temporaries then take no registers of the sweep
+// around it.  The forward kernels inline it (a call there makes the
+// 128-register kernels save live registers to the stack around it).
 static __device__ __noinline__ RaySet ray_setup_call(const JobDev& J, int px, int py) {
   return ray_setup(J, px, py);
 }

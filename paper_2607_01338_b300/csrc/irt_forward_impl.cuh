@@ -952,7 +952,7 @@ __device__ void render_ray(const JobDev& J, const PhysParams& PD, const PhysF& P
     K = geo.K;
     h = (R)geo.h;
   } else {
-    const RaySet rs = ray_setup_call(J, px, py);
+    const RaySet rs = ray_setup(J, px, py);
     K = rs.K;
     h = rs.h;
     rp = rs.rp;

@@ -125,7 +125,7 @@ thin_kernel(const __grid_constant__ JobTable tab, int njobs, const PhysParams P,
       K = g.K;
       h = (R)g.h;
     } else {
-      const RaySet rs = ray_setup_call(J, px, py);
+      const RaySet rs = ray_setup(J, px, py);
       K = rs.K;
       h = rs.h;
       rp = rs.rp;
