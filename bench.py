@@ -838,8 +838,9 @@ def traffic_from_profile():
 def adjoint128_measure(reps=5):
     """The 128^3 / 128-channel / f = 2 adjoint workload (smooth): the z-view
     forward keeping its checkpoints, the adjoint of a squared-error loss on
-    [L]; and the same grid's (30, 45) deg oblique view through the general
-    sweep.  Units: samples x channels of the adjoint's rays."""
+    [L]; and the same grid's (30, 45) deg oblique view's adjoint (its own
+    forward sweep, gradients scattered to the trilinear cells).  Units:
+    samples x channels of the adjoint's rays."""
     import torch
     import paper_2607_01338_b300 as irt
     from paper_2607_01338_b300 import binding as B
@@ -893,7 +894,7 @@ def adjoint128_measure(reps=5):
     g.close()
     return {"workload": f"{w.name}: z view, smooth; forward keeping checkpoints, adjoint of "
                         "mean(([L] - target)^2); and the (30, 45) deg oblique view's adjoint "
-                        "(general sweep, every velocity explicit)",
+                        "(fast sweep, gradients scattered to the trilinear cells)",
             "forward_ms": t_f, "adjoint_ms": t_a, "forward_value": units / (t_f / 1e3),
             "adjoint_value": units / (t_a / 1e3), "unit": UNIT,
             "oblique_adjoint_ms": t_o, "oblique_adjoint_value": units_obl / (t_o / 1e3),
