@@ -108,6 +108,48 @@ def test_oblique_fast_sweep_all_passes():
     assert np.count_nonzero(on) > 20
 
 
+def test_oblique_fast_sweep_16bit_fields():
+    """The 16-bit storage instance of the oblique fast sweep: BF16 fields with
+    an FP16 velocity and per-field scales (the batch workload's storage),
+    against the oracle gradient on the dequantised values."""
+    import paper_2607_01338_b300 as irt
+    n = 16
+    scales = [1.0e4, 1.0, 1.0, 1.0, 1.0e-6]
+    fs = make_fields(n, 91)
+    h16, deq = to_storage(fs, ["bf16", "bf16", "bf16", np.float16, "bf16"], scales=scales)
+    tfs = make_fields(n, 98)
+    _, tdeq = to_storage(tfs, np.float32)
+    dx = 0.1 * PC
+    view = View(math.radians(40), math.radians(130), 18, 17, 0.9 * dx, 1)
+    va = VelocityAxis(64, -64.0, 2.0, 1)
+    target = oracle.render_cube(tdeq.as_tuple(), dx, LINE, DUST, view, va,
+                                integration=oracle.SMOOTH)["L"]
+    ts = []
+    for a in h16.as_tuple():
+        if a.dtype == np.uint16:
+            ts.append(torch.from_numpy(a.view(np.int16).copy()).view(torch.bfloat16).cuda())
+        else:
+            ts.append(torch.from_numpy(np.ascontiguousarray(a)).cuda())
+    g = irt.Grid(*ts, dx, scales=scales)
+    L = irt.forward(g, view, va, LINE, DUST, integration="smooth")["L"]
+    tgt = torch.from_numpy(target.astype(np.float32)).cuda()
+    grads = irt.adjoint(g, view, va, LINE, DUST, {"L": 2.0 * (L - tgt) / L.numel()},
+                        integration="smooth")
+    torch.cuda.synchronize()
+    gn, gt, gv = [x.double().cpu().numpy() for x in grads]
+    g.close()
+    rng = np.random.default_rng(27)
+    cells = np.stack([rng.integers(0, n, 40), rng.integers(0, n, 40), rng.integers(0, n, 40)],
+                     axis=1)
+    loss, on, ot, ov = oracle.loss_grad_cells(deq.as_tuple(), dx, LINE, DUST, view, va, target,
+                                              cells, integration=oracle.SMOOTH)
+    got = {k: np.array([a[z, y, x] for x, y, z in cells]) for k, a in (("n", gn), ("T", gt),
+                                                                        ("v", gv))}
+    K = 2 * n
+    r = {"n": _cmp(got["n"], on, K), "T": _cmp(got["T"], ot, K), "v": _cmp(got["v"], ov, K)}
+    assert all(v <= 1.0 for v in r.values()), r
+
+
 @pytest.mark.parametrize("integration,f,nch,dv", [("formal", 2, 40, 3.0),
                                                   ("formal_kahan", 1, 40, 3.0),
                                                   ("smooth", 0, 48, 3.0),
