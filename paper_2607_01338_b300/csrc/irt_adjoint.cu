@@ -158,12 +158,12 @@ struct Adj {
     const float xpre = pre[NA];
     const Slots<NS> sl = slots_smooth<NS>(r, hb, lane, G);
     const float rd0 = rcp_approx(r.d0);
-    float rl[NS], qs[NS], ds[NS];
+    float rl[NS], qs[NS], ds[NS], pl[NS];
 #pragma unroll
     for (int q = 0; q < NS; ++q) {
       rl[q] = rcp_approx(sl.b[q]);
       qs[q] = 0.0f;
-      ds[q] = 0.0f;
+      pl[q] = 0.0f;
     }
     const float b0x2 = rec_bk0x2(r), b1x2 = rec_bk1x2(r);
     float gad = 0.0f;
@@ -175,17 +175,19 @@ struct Adj {
       const float p = pre[j];
       const float mu = (p >= 0.0f) ? lam_n[j] : 0.0f;
       const float q = mu * rr;
-      const float dd = -q * p;                    // d loss / d (3 + 2h alpha)
-      gad = fmaf(q, fmaf(b1x2, u[j], b0x2), fmaf(2.0f, dd, gad));
+      // q (2 B(u)) + 2 d loss / d (3 + 2h alpha), the latter -q p
+      gad = fmaf(q, fmaf(-2.0f, p, fmaf(b1x2, u[j], b0x2)), gad);
 #pragma unroll
       for (int s = 0; s < NS; ++s) {
         const bool ps = sl.j[s] == j;
         qs[s] = ps ? q : qs[s];
-        ds[s] = ps ? dd : ds[s];
+        pl[s] = ps ? p : pl[s];
       }
       lam_n[j] = fmaf(4.0f, q, lam_m[j]);
       lam_m[j] = -q;
     }
+#pragma unroll
+    for (int s = 0; s < NS; ++s) ds[s] = -qs[s] * pl[s];   // d loss / d (3 + 2h alpha)
     // basis recurrences (lanes 0..2): linear, sources m1 jd0 + m2 jd1
     {
       const float q = xl_n * rd0;
