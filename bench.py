@@ -519,14 +519,19 @@ def gpu_arm(args):
                 resid = outs2[b][0]["L"] - dev_tgt[b]
                 inputs_free[b] = ev()
                 inputs_free[b].record(ms)
-                host_loss.copy_(torch.mean(resid * resid), non_blocking=True)
+                loss_d = torch.mean(resid * resid)
                 irt.adjoint(g, w.views[0], w.vaxis, w.line, w.dust,
                             {"L": 2.0 * resid / resid.numel()}, integration=args.integration,
                             grads=grads2[b])
                 done = ev()
                 done.record(ms)
+                # every read-back goes through the copy stream: a device-to-host
+                # copy queued on the compute stream would wait behind the
+                # cube copies in the copy engine and hold the adjoint back
+                loss_d.record_stream(down)
                 with torch.cuda.stream(down):
                     down.wait_event(done)
+                    host_loss.copy_(loss_d, non_blocking=True)
                     for hg, dg in zip(host_grads, grads2[b]):
                         hg.copy_(dg, non_blocking=True)
                     results_free[b] = ev()
