@@ -35,6 +35,46 @@ ANGLES = [(30.0, 45.0), (70.0, 200.0), (90.0, 0.0), (90.0, 45.0), (45.0, 90.0),
           (0.01, 10.0), (135.0, 300.0), (180.0, 0.0)]
 
 
+def _count(theta, phi, shape, npx, npy, pitch):
+    """(GPU stats, oracle total, oracle rays that hit) for one view."""
+    import paper_2607_01338_b300 as irt
+    from paper_2607_01338_b300 import binding as B
+    nz, ny, nx = shape
+    dx = 0.1 * PC
+    fs = make_fields(64, seed=3)
+    # a non-cubic box cut from the cube
+    sub = [np.ascontiguousarray(a[:nz, :ny, :nx]) for a in fs.as_tuple()]
+    f32 = [a.astype(np.float32) for a in sub]
+    deq = [a.astype(np.float64) for a in f32]
+    view = View(math.radians(theta), math.radians(phi), npx, npy, pitch * dx, 1)
+    va = VelocityAxis(4, -4.0, 2.0, 1)
+    g = irt.Grid(*[torch.from_numpy(a).cuda() for a in f32], dx)
+    B.irt_grid_stats(g.handle, reset=True)
+    irt.forward(g, view, va, LINE_13CO_21, DUST, components=("L",), flags=B.IRT_FLAG_STATS)
+    torch.cuda.synchronize()
+    st = B.irt_grid_stats(g.handle, reset=True)
+    g.close()
+    total = hit = 0
+    for py in range(npy):
+        for px in range(npx):
+            smp, _ = oracle.ray_samples(deq, dx, view, px, py)
+            total += len(smp)
+            hit += len(smp) > 0
+    return st, total, hit
+
+
+@pytest.mark.parametrize("theta,phi,shape,npx,npy,pitch", [
+    (60.0, 10.0, (13, 90, 5), 120, 96, 0.35),     # thin slab, fine pixels
+    (90.0, 90.0, (20, 8, 32), 40, 30, 1.7),       # d = (~0, 1, ~6e-17), coarse pixels
+    (1.0e-4, 33.0, (24, 20, 22), 30, 28, 1.0),    # nearly the z axis: chords within 2e-11 cells of nz
+])
+def test_sample_count_on_slabs_and_near_axis_views(theta, phi, shape, npx, npy, pitch):
+    st, total, hit = _count(theta, phi, shape, npx, npy, pitch)
+    assert hit > 0
+    assert st["items"] == npx * npy
+    assert st["samples"] == total, (st["samples"], total)
+
+
 @pytest.mark.parametrize("theta,phi", ANGLES)
 def test_oblique_sample_count_matches_oracle(theta, phi):
     import paper_2607_01338_b300 as irt
