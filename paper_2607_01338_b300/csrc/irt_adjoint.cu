@@ -597,7 +597,7 @@ __device__ __forceinline__ int J0kmax(const JobTable& t) { return t.j[0].kmax; }
 #ifndef IRT_ADJ_BUCKETS2
 #define IRT_ADJ_BUCKETS2 4, 8, 12, 17, 24, 33
 #endif
-__device__ __forceinline__ int adj_bucket(int na, int ns) {
+__host__ __device__ __forceinline__ constexpr int adj_bucket(int na, int ns) {
   constexpr int b1[] = {IRT_ADJ_BUCKETS1};
   constexpr int b2[] = {IRT_ADJ_BUCKETS2};
   if (ns == 1) {
@@ -611,6 +611,18 @@ __device__ __forceinline__ int adj_bucket(int na, int ns) {
     if (na <= b2[i]) return b2[i];
   return 33;
 }
+
+// The adjoint restarts each segment from the forward render's checkpoints,
+// whose rows are the render's hull blocks: both must pick the same bucket
+// (and so the same first block) for every hull width, or the rows would
+// belong to other velocities.
+constexpr bool buckets_agree() {
+  for (int ns = 1; ns <= 2; ++ns)
+    for (int na = 1; na <= 33; ++na)
+      if (adj_bucket(na, ns) != fast_bucket(na, ns)) return false;
+  return true;
+}
+static_assert(buckets_agree(), "adjoint and forward hull buckets differ");
 
 template <int NA, int NS, int NI, int ST, bool OBL>
 __device__ __forceinline__ bool adj_run_bucket(const AdjRayArgs* A, const RecS32* rec,

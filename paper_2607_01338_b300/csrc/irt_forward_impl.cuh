@@ -837,7 +837,7 @@ struct FastKahan {
 
 // Block-count buckets of the fast path (a hull of na blocks runs in the
 // smallest bucket >= na).
-__device__ __forceinline__ int fast_bucket(int na, int ns) {
+__host__ __device__ __forceinline__ constexpr int fast_bucket(int na, int ns) {
   if (ns == 1) {
     if (na <= 8) return (na + 1) & ~1;   // 2, 4, 6, 8
     if (na <= 10) return 10;
